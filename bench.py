@@ -1,0 +1,361 @@
+"""Benchmark: forward + gradient samples/s of the fused path on one GB300.
+
+Workload (default): hardware-efficient ansatz, 12 qubits, 20 layers of
+[RZ, RY, RZ on every qubit + CZ chain], RY(x) encoding, batch 256, MSE loss
+of <Z_0> against labels in {-1, +1}; one step = forward expectations + loss +
+adjoint gradients reduced per parameter (qf_train_step), inputs resident in
+HBM. Synthetic seeded inputs (theta ~ U[0, 2pi), x ~ U[0, pi]^12).
+
+Printed JSON line (rank 0): value = samples/s of the whole job, plus the
+unfused one-kernel-per-gate comparator on the same GPU, the roofline of the
+dominant kernel (fused adjoint pass), an end-to-end number through the
+host-buffer C-ABI call, the oracle's CPU throughput, and sampled SM clocks.
+
+``--impl reference`` times the float64 CPU oracle instead (the reference
+arm): each step is the oracle's training step on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_02804_gb300 import workloads  # noqa: E402
+
+WORKLOAD = "hea12"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-gate", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic_flops(n, d, B):
+    """Method arithmetic per step in FP32 flops (a fused multiply-add = 2):
+    forward: one fused complex 2x2 per qubit and layer = 16 real FMA per pair
+    of amplitudes; adjoint: per rotation, un-apply psi (8 FMA per pair),
+    Im<lambda|P|psi> (4 FMA per pair), un-apply lambda (8 FMA per pair)."""
+    pairs = B * (1 << (n - 1))
+    fwd = n * d * pairs * 16 * 2
+    bwd = 3 * n * d * pairs * 20 * 2
+    return fwd, bwd
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, max_seconds=20.0):
+    """The float64 oracle's training step (forward, MSE/sum loss, adjoint
+    gradient) on the host cores, over a bounded sample of the workload."""
+    from oracle import oracle as orc
+    orc.build()
+    theta, x, y = workloads.make_inputs(w)
+    c = orc.hea(w.n, w.d)
+    threads = orc.max_threads()
+    # size the sample: time one sample first
+    t0 = time.perf_counter()
+    _oracle_step(orc, c, w, theta, x[:1], None if y is None else y[:1], threads)
+    one = time.perf_counter() - t0
+    per_thread = max(1, int(max_seconds / max(one, 1e-6)))
+    B = int(min(w.B, max(threads, per_thread * threads // 4)))
+    t0 = time.perf_counter()
+    _oracle_step(orc, c, w, theta, x[:B], None if y is None else y[:B], threads)
+    dt = time.perf_counter() - t0
+    return {"value": B / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
+            "sample": f"{B} of the {w.B} samples of one {w.name} training step (n={w.n}, d={w.d}), "
+                      f"float64, OpenMP over samples"}
+
+
+def _oracle_step(orc, c, w, theta, x, y, threads):
+    th = theta.astype(np.float64)
+    xx = x.astype(np.float64)
+    if w.loss == "mse":
+        E = orc.expectation(c, th, xx, w.obs, threads=threads)
+        dLdE = orc.mse_dLdE(E, y) * len(E) / w.B
+    else:
+        dLdE = np.ones(len(xx))
+    return orc.gradient(c, th, xx, w.obs, dLdE=dLdE, threads=threads)
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    orc.build()
+    theta, x, y = workloads.make_inputs(w)
+    c = orc.hea(w.n, w.d)
+    threads = orc.max_threads()
+    t0 = time.perf_counter()
+    _oracle_step(orc, c, w, theta, x[:1], None if y is None else y[:1], threads)
+    one = time.perf_counter() - t0
+    # each step: a bounded sample sized so that the whole run stays within minutes
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    Bs = int(max(1, min(w.B, threads * max(1, int(budget / max(one, 1e-6))))))
+    for _ in range(args.warmup):
+        _oracle_step(orc, c, w, theta, x[:Bs], None if y is None else y[:Bs], threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_step(orc, c, w, theta, x[:Bs], None if y is None else y[:Bs], threads)
+    dt = time.perf_counter() - t0
+    value = Bs * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "fwd+grad samples/s", "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} batch={w.B} loss={w.loss} obs=Z0",
+                   "sample_per_step": Bs},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{Bs} samples of the {w.name} batch per step"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    w = workloads.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2603_02804_gb300 import build as qbuild
+    if rank == 0:
+        qbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2603_02804_gb300 import qfuse
+    from paper_2603_02804_gb300.torch_api import Simulator
+
+    peaks, peak_src = load_peaks()
+    theta_np, x_np, y_np = workloads.make_inputs(w)
+    # weak scaling: every rank processes its own batch of w.B samples
+    if rank > 0:
+        x_np = workloads.draw_x(w.B, w.n, w.seeds[1] + 1000 * rank)
+    dev = torch.device("cuda", local)
+    theta = torch.from_numpy(theta_np).to(dev)
+    x = torch.from_numpy(x_np).to(dev)
+    y = torch.from_numpy(y_np).to(dev) if y_np is not None else None
+    ckpt = w.ckpt_layers or 0
+    sim = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(s):
+        loss, E, g = s.train_step(theta, x, y, loss=w.loss)
+        if world > 1:
+            dist.all_reduce(g)  # data-parallel gradient sum over ranks
+        return g
+
+    def timed(s, K):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        launches = 0
+        for k in range(K):
+            flush.fill_(k & 255)  # evict the state from L2 between timed steps
+            starts[k].record(stream)
+            step(s)
+            ends[k].record(stream)
+            launches += s.launches()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), launches
+
+    for _ in range(args.warmup):
+        step(sim)
+    torch.cuda.synchronize()
+    qfuse.qf_profile(sim.handle, True)
+    qfuse.qf_profile_read(sim.handle)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        total_ms, launches = timed(sim, args.steps)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    prof = qfuse.qf_profile_read(sim.handle)
+    qfuse.qf_profile(sim.handle, False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = w.B * world * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel: the fused adjoint pass kernel
+    fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, w.B)
+    info = sim.info()
+    bwd_launch_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
+    fwd_launch_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
+    bwd_per_launch = bwd_fl / info["n_passes"]
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    achieved = bwd_per_launch / (bwd_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "pass_kernel<true> (fused adjoint)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz",
+                "fwd_kernel": {"achieved": (fwd_fl / info["n_passes"]) / (fwd_launch_ms / 1e3) / 1e12,
+                               "ms": fwd_launch_ms},
+                "bwd_kernel_ms": bwd_launch_ms}
+    state_bytes = w.B * (1 << w.n) * 8
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    hbm = {"algorithmic_bytes_per_step": 4 * state_bytes,
+           "achieved_gbs": 4 * state_bytes / (ms_per_step / 1e3) / 1e9,
+           "peak_gbs": hbm_gbs, "peak_source": peak_src,
+           "frac": 4 * state_bytes / (ms_per_step / 1e3) / 1e9 / hbm_gbs,
+           "note": "state of this workload fits in L2; the path is ALU-bound, see roofline"}
+
+    # ---- unfused per-gate comparator on the same GPU
+    per_gate = None
+    if not args.no_per_gate:
+        pg = Simulator(w.n, w.d, w.B, path="per_gate", ckpt_layers=ckpt, obs=w.obs)
+        for _ in range(args.warmup):
+            step(pg)
+        torch.cuda.synchronize()
+        pg_ms, pg_launches = timed(pg, args.steps)
+        per_gate = {"value": w.B * world * args.steps / (pg_ms / 1e3), "unit": "samples/s",
+                    "ms_per_step": pg_ms / args.steps, "gpu_launches_per_step": pg_launches // args.steps}
+        del pg
+
+    # ---- end to end through the host-buffer call (pinned host memory)
+    th_h = torch.from_numpy(theta_np).pin_memory()
+    x_h = torch.from_numpy(x_np).pin_memory()
+    y_h = torch.from_numpy(y_np).pin_memory() if y_np is not None else None
+    for _ in range(2):
+        sim.train_step_host(th_h, x_h, y_h, loss=w.loss)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        loss_h, E_h, g_h = sim.train_step_host(th_h, x_h, y_h, loss=w.loss)
+    e_dt = time.perf_counter() - e0
+    h2d = theta_np.nbytes + x_np.nbytes + (y_np.nbytes if y_np is not None else 0)
+    d2h = 8 + 8 * w.B + 8 * w.n_params
+    e2e = {"value": w.B * world * args.steps / e_dt, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": "fwd+grad samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded): theta~U[0,2pi), x~U[0,pi]^n, y~{-1,+1}",
+            "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} [RZ,RY,RZ + CZ chain], RY(x) encoding, "
+                                   f"batch={w.B}/GPU, loss={w.loss}, obs=Z0",
+                       "path": "fused", "tile_bits": info["tile_bits"], "passes": info["n_passes"],
+                       "ckpt_layers": info["ckpt_layers"], "parallelism": f"dp{world}",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "per_gate": per_gate,
+            "speedup_vs_per_gate": (value / per_gate["value"]) if per_gate else None,
+            "roofline": roofline,
+            "hbm": hbm,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "peaks": {"source": peak_src, "hbm_gbs": hbm_gbs},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

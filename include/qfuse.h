@@ -1,0 +1,230 @@
+/*
+ * qfuse: batched state-vector simulation of parametrised quantum circuits
+ * with fused forward and fused adjoint-method backward passes, for NVIDIA
+ * GB300 (sm_103a).
+ *
+ * Method: Kawase, "Fast and memory-efficient classical simulation of quantum
+ * machine learning via forward and backward gate fusion" (arXiv 2603.02804).
+ *   - state and gate application: Sec. 3.1 (qubit i is bit i of the index)
+ *   - forward gate fusion: Sec. 3.2
+ *   - fused backward with in-register recompute: Sec. 3.3, Eqs. 2-3
+ *   - adjoint seed lambda_M = 2 (dL/dE) O psi_M: Eq. 4 with the chain rule
+ *   - gradient checkpointing of the state: Sec. 3.4, Eqs. 5-8
+ *   - matrix-free Pauli expectation and fused CZ: Appendix B
+ *
+ * Conventions for every entry point:
+ *   - Return value is a qf_status; QF_OK on success. No C++ exception
+ *     crosses this boundary. qf_last_error() returns a thread-local message
+ *     describing the most recent failure of the calling thread.
+ *   - Pointers named *_d are device pointers, *_h host pointers. The library
+ *     never frees or takes ownership of caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All device work of a call is enqueued on it; calls return
+ *     without synchronising unless documented otherwise.
+ *   - A circuit handle serves one stream at a time. Concurrent calls on the
+ *     same handle from several threads are not supported.
+ *   - A CUDA error raised by an earlier asynchronous launch surfaces as
+ *     QF_ERR_CUDA on a later call.
+ */
+#ifndef QFUSE_H
+#define QFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qf_status;
+#define QF_OK 0
+#define QF_ERR_INVALID_ARG 1  /* a pointer, size or enum is out of range   */
+#define QF_ERR_UNSUPPORTED 2  /* valid request this build does not handle  */
+#define QF_ERR_WORKSPACE 3    /* workspace too small or plan missing       */
+#define QF_ERR_OOM 4          /* a plan-time device allocation failed      */
+#define QF_ERR_CUDA 5         /* a CUDA runtime call or launch failed      */
+#define QF_ERR_TIMEOUT 6      /* a bounded device-side wait gave up        */
+
+/* Gate kinds. Rotations are u(t) = cos(t/2) I - i sin(t/2) P, P in {X,Y,Z}
+ * (Sec. 3.3, gradient step); CZ negates amplitudes whose control and target
+ * bits are both 1 (Sec. 3.1). */
+#define QF_GATE_RX 0
+#define QF_GATE_RY 1
+#define QF_GATE_RZ 2
+#define QF_GATE_CZ 3
+
+/* Entangler of the hardware-efficient ansatz. */
+#define QF_ENT_CHAIN 0 /* CZ(0,1), CZ(1,2), ..., CZ(n-2,n-1)            */
+#define QF_ENT_RING 1  /* the chain plus CZ(n-1, 0)                       */
+
+/* Execution paths. */
+#define QF_PATH_FUSED 0    /* fused forward / fused adjoint (Secs. 3.2-3.3) */
+#define QF_PATH_PER_GATE 1 /* one kernel per gate; the unfused comparator   */
+
+/* Losses understood by qf_loss / qf_train_step. */
+#define QF_LOSS_SUM 0 /* L = sum_b E_b (the paper's L = E, Sec. 2.1)       */
+#define QF_LOSS_MSE 1 /* L = mean_b (E_b - y_b)^2                          */
+
+typedef struct qf_circuit qf_circuit;
+
+/* One gate of a user circuit. q1 is the target of a CZ (-1 otherwise);
+ * param indexes theta (-1 for constant gates). */
+typedef struct {
+  int32_t kind;
+  int32_t q0;
+  int32_t q1;
+  int32_t param;
+} qf_gate;
+
+/* Pauli-string observable O = i^{#Y} X^{x_mask} Z^{z_mask}: bit q of x_mask
+ * (z_mask) set means an X (Z) factor on qubit q; both bits set is a Y
+ * (Y = iXZ, Appendix B.2). */
+typedef struct {
+  uint64_t x_mask;
+  uint64_t z_mask;
+} qf_pauli;
+
+/* Planning options; zero-initialise and set what you need. */
+typedef struct {
+  int32_t path;        /* QF_PATH_FUSED (default) or QF_PATH_PER_GATE           */
+  int32_t tile_bits;   /* fused: qubits per tile, 4..12; 0 = min(n, 12). Circuits
+                          wider than the tile need >= 5 (4 is raised to 5)      */
+  int32_t ckpt_layers; /* checkpoint interval c in ansatz layers (per-gate: same);
+                          0 = 10 layers; a value >= depth keeps only psi_M       */
+  int32_t host_only;   /* 1 = build the plan on the host only (no device tables;
+                          forward/backward then fail with QF_ERR_WORKSPACE)      */
+  int32_t reserved[12];
+} qf_plan_opts;
+
+/* Summary of a plan (host-side numbers). */
+typedef struct {
+  int32_t n_qubits;        /* as created                                       */
+  int32_t n_eff;           /* simulated qubits (>= 4: smaller circuits padded)  */
+  int32_t n_params;
+  int32_t n_slots;         /* gradient slots = parametrised gates               */
+  int32_t path;
+  int32_t tile_bits;       /* K */
+  int32_t n_passes;        /* forward passes (= backward passes)                */
+  int32_t n_steps;         /* register steps over all forward passes            */
+  int32_t n_fused_ops;     /* fused 2x2 ops of the forward program              */
+  int32_t n_ckpt;          /* checkpoint slots incl. the final state            */
+  int32_t ckpt_layers;
+  int32_t launches_fwd;    /* kernels launched by qf_forward                    */
+  int32_t launches_bwd;    /* kernels launched by qf_backward                   */
+  int64_t batch;           /* batch the workspace was sized for                 */
+  int64_t workspace_bytes;
+  int64_t state_bytes;     /* one batched state buffer                          */
+} qf_plan_info_t;
+
+/* Create the hardware-efficient ansatz of the paper's benchmarks with the
+ * gate set of this build: every layer applies RZ, RY, RZ to every qubit and
+ * then the entangler (Sec. 4.2 and the ansatz figure; RZ,RY,RZ + CZ chain per
+ * layer). The data encoding RY(x_q)|0> on every qubit precedes layer 0.
+ * Parameter index of rotation g in {0: first RZ, 1: RY, 2: second RZ} on
+ * qubit q of layer l is l*3n + 3q + g, so theta has 3*n*n_layers entries.
+ * n_qubits in 1..30, n_layers >= 0. *out receives a new handle (free with
+ * qf_circuit_destroy). */
+qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler,
+                        qf_circuit** out);
+
+/* Create a circuit from a gate list applied in order after the RY(x)
+ * encoding (Sec. 2.1: U = U_M ... U_1). Supported kinds: QF_GATE_RX/RY/RZ
+ * (param in 0..n_params-1; several gates may share a parameter, their
+ * gradients add) and QF_GATE_CZ (param -1). The gate array is copied. */
+qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_gates,
+                            int32_t n_params, qf_circuit** out);
+
+/* Destroy a handle and the device tables its plan owns. NULL is accepted. */
+qf_status qf_circuit_destroy(qf_circuit* c);
+
+/* Plan the circuit for batches of up to `batch` samples (Secs. 3.2-3.4):
+ * fuse gates into passes over shared-memory tiles, place checkpoints of the
+ * state every opts->ckpt_layers layers, size the workspace, and (unless
+ * host_only) upload the plan's device tables. This is the only call that
+ * allocates device memory; it may be called again to re-plan.
+ * *workspace_bytes receives the size of the caller-allocated workspace that
+ * forward/backward/train_step need (256-byte aligned base required). */
+qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch,
+                  size_t* workspace_bytes);
+
+/* Fill *info with the current plan's summary. */
+qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
+
+/* Export the forward (direction 0) or backward (1) program for inspection:
+ * writes up to cap int32 words to buf (may be NULL) and the full length to
+ * *len. Layout: [n_passes, then per pass: 11 header words (op_begin, op_end,
+ * psi_src, psi_dst, lam_src, lam_dst, flags, K, n_groups, outer_mask,
+ * xm_local), 16 gmap words, 16 group words], then [n_ops, 2 words per op],
+ * then [n_fused, per fused op: count, then count (kind, param) pairs].
+ * Host only. */
+qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf,
+                         int64_t cap, int64_t* len);
+
+/* Forward expectations E_b = <psi_M|O|psi_M> (Eq. 1) for b < batch.
+ * theta_d: float32 [n_params]; x_d: float32 [batch][n_qubits] encoding
+ * angles; E_d: float64 [batch] (written). The final state and the
+ * checkpoints stay in the workspace for a following qf_backward with the
+ * same theta, x, batch and observable. batch <= the planned batch. */
+qf_status qf_forward(qf_circuit* c, const float* theta_d, const float* x_d, int64_t batch,
+                     qf_pauli obs, double* E_d, void* ws_d, size_t ws_bytes, void* stream);
+
+/* Adjoint gradients (Eqs. 2-4) after qf_forward on the same workspace:
+ * lambda_M = 2 dLdE_b O psi_M, then gates are un-applied in reverse with
+ * dL/dtheta_j = Re<lambda_j| dU_j/dtheta_j |psi_{j-1}> reduced per parameter
+ * in float64. dLdE_d: float64 [batch]. grad_d: float64 [n_params] (sum over
+ * samples) or [batch][n_params] when per_sample != 0; overwritten. */
+qf_status qf_backward(qf_circuit* c, const float* theta_d, const float* x_d, int64_t batch,
+                      qf_pauli obs, const double* dLdE_d, double* grad_d, int32_t per_sample,
+                      void* ws_d, size_t ws_bytes, void* stream);
+
+/* Loss and dL/dE_b from E (float64 [batch]) and labels y (float32 [batch];
+ * ignored for QF_LOSS_SUM, may be NULL then). loss_d: float64 [1];
+ * dLdE_d: float64 [batch]. Deterministic single-block reduction. */
+qf_status qf_loss(int32_t kind, const double* E_d, const float* y_d, int64_t batch,
+                  double* loss_d, double* dLdE_d, void* stream);
+
+/* One training step on device buffers: qf_forward, qf_loss, qf_backward.
+ * grad_d: float64 [n_params] = dL/dtheta of the whole batch. */
+qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d,
+                        const float* y_d, int64_t batch, int32_t loss_kind, qf_pauli obs,
+                        double* loss_d, double* E_d, double* grad_d, void* ws_d,
+                        size_t ws_bytes, void* stream);
+
+/* The same step from HOST buffers: copies theta_h, x_h (and y_h) into the
+ * workspace's staging area, runs qf_train_step, copies loss, E (may be NULL)
+ * and grad back, and synchronises `stream` before returning. Pinned host
+ * memory gives asynchronous copies; pageable memory works but is slower. */
+qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x_h,
+                             const float* y_h, int64_t batch, int32_t loss_kind, qf_pauli obs,
+                             double* loss_h, double* E_h, double* grad_h, void* ws_d,
+                             size_t ws_bytes, void* stream);
+
+/* Kernels launched by the most recent qf_forward + qf_backward (+ qf_loss
+ * inside qf_train_step) on this handle; for launch accounting. */
+qf_status qf_launch_count(const qf_circuit* c, int64_t* launches);
+
+/* Start (on != 0) or stop timing the pass kernels of the following
+ * qf_forward / qf_backward calls on this handle: a CUDA event pair is
+ * recorded on the call's stream around the forward passes and around the
+ * backward passes (up to 4096 pairs are kept between reads). Starting
+ * creates the events (no device memory). */
+qf_status qf_profile(qf_circuit* c, int32_t on);
+
+/* Sum of the recorded forward / backward pass-kernel time in milliseconds
+ * and the number of pass-kernel launches they cover, since the last read.
+ * Waits for the recorded events; resets the counters. Any output may be
+ * NULL. */
+qf_status qf_profile_read(qf_circuit* c, double* fwd_ms, int64_t* fwd_launches, double* bwd_ms,
+                          int64_t* bwd_launches);
+
+/* Thread-local description of the last error ("" if none). */
+const char* qf_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t qf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFUSE_H */

@@ -1,0 +1,754 @@
+// C-ABI of the library (declared in include/qfuse.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <exception>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "planner.h"
+#include "qfuse.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+qf_status fail(qf_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t theta = 0, x = 0, y = 0, E = 0, dLdE = 0, grad = 0, loss = 0;  // staging
+  size_t mats = 0, cs = 0, enc = 0;
+  size_t work = 0, lam = 0, slots = 0;
+  size_t epart = 0, gpart = 0;
+  size_t total = 0;
+  int64_t state_elems = 0;  // batch * 2^n_eff
+  int64_t rows = 0;         // partial rows per sample (tiles or chunks)
+};
+
+}  // namespace
+
+struct qf_circuit {
+  qf::Circuit circ;
+  bool planned = false;
+  bool host_only = false;
+  int path = QF_PATH_FUSED;
+  int ckpt_layers = 10;
+  int64_t batch = 0;
+  qf::FusedPlan fp;
+  qf::PerGatePlan gp;
+  Layout L;
+  void* d_tables = nullptr;
+  const uint2* d_fwd_ops = nullptr;
+  const uint2* d_bwd_ops = nullptr;
+  const int32_t* d_fuse_off = nullptr;
+  const qf::FuseGate* d_fuse_gates = nullptr;
+  const int32_t* d_slot_param = nullptr;
+  const int32_t* d_param_off = nullptr;
+  const int32_t* d_param_slots = nullptr;
+  int64_t launches = 0;
+  int64_t call_launches = 0;
+  // pass-kernel timing (qf_profile)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;          // 2 per record
+  std::vector<int> ev_dir;              // 0 fwd, 1 bwd
+  std::vector<int64_t> ev_launches;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr size_t kMaxProfilePairs = 4096;
+
+void destroy_events(qf_circuit* c) {
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  c->ev_dir.clear();
+  c->ev_launches.clear();
+  c->ev_used = 0;
+}
+
+// Record the start of a timed range; returns the pair index or -1.
+int prof_begin(qf_circuit* c, cudaStream_t st) {
+  if (!c->profile || c->ev_used >= kMaxProfilePairs) return -1;
+  const size_t k = c->ev_used++;
+  cudaEventRecord(c->ev[2 * k], st);
+  return (int)k;
+}
+
+void prof_end(qf_circuit* c, int k, int dir, int64_t launches, cudaStream_t st) {
+  if (k < 0) return;
+  cudaEventRecord(c->ev[2 * k + 1], st);
+  c->ev_dir[k] = dir;
+  c->ev_launches[k] = launches;
+}
+
+void free_tables(qf_circuit* c) {
+  if (c->d_tables) cudaFree(c->d_tables);
+  c->d_tables = nullptr;
+  c->d_fwd_ops = c->d_bwd_ops = nullptr;
+  c->d_fuse_off = c->d_slot_param = c->d_param_off = c->d_param_slots = nullptr;
+  c->d_fuse_gates = nullptr;
+}
+
+int n_eff_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_eff : c->gp.n_eff; }
+int n_slots_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_slots : c->gp.n_slots; }
+
+Layout make_layout(const qf_circuit* c, int64_t B) {
+  Layout L;
+  const int n_eff = n_eff_of(c);
+  const int64_t dim = 1ll << n_eff;
+  const int P = c->circ.n_params;
+  const int S = n_slots_of(c);
+  L.state_elems = B * dim;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += al(bytes);
+    return at;
+  };
+  L.theta = take((size_t)P * 4);
+  L.x = take((size_t)B * c->circ.n * 4);
+  L.y = take((size_t)B * 4);
+  L.E = take((size_t)B * 8);
+  L.dLdE = take((size_t)B * 8);
+  L.grad = take((size_t)P * 8);
+  L.loss = take(8);
+  L.cs = take((size_t)S * 8);
+  L.enc = take((size_t)B * n_eff * 8);
+  L.work = take((size_t)L.state_elems * 8);
+  L.lam = take((size_t)L.state_elems * 8);
+  if (c->path == QF_PATH_FUSED) {
+    const int n_fused = (int)c->fp.fuse_off.size() - 1;
+    L.mats = take((size_t)std::max(n_fused, 0) * 32);
+    L.slots = take((size_t)c->fp.n_ckpt * L.state_elems * 8);
+    L.rows = 1ll << (c->fp.n_eff - c->fp.K);
+  } else {
+    L.slots = take((size_t)c->gp.ckpt_after.size() * L.state_elems * 8);
+    L.rows = qf::pg_chunks(n_eff);
+  }
+  L.epart = take((size_t)B * L.rows * 8);
+  L.gpart = take((size_t)B * L.rows * S * 8);
+  L.total = o;
+  return L;
+}
+
+template <class T>
+size_t push_table(std::vector<char>& blob, const std::vector<T>& v) {
+  size_t at = al(blob.size());
+  blob.resize(at + al(std::max<size_t>(v.size() * sizeof(T), 1)));
+  if (!v.empty()) memcpy(blob.data() + at, v.data(), v.size() * sizeof(T));
+  return at;
+}
+
+qf_status upload(qf_circuit* c) {
+  std::vector<char> blob;
+  size_t o_fwd = 0, o_bwd = 0, o_foff = 0, o_fg = 0, o_sp, o_po, o_ps;
+  if (c->path == QF_PATH_FUSED) {
+    o_fwd = push_table(blob, c->fp.fwd_ops);
+    o_bwd = push_table(blob, c->fp.bwd_ops);
+    o_foff = push_table(blob, c->fp.fuse_off);
+    o_fg = push_table(blob, c->fp.fuse_gates);
+    o_sp = push_table(blob, c->fp.slot_param);
+    o_po = push_table(blob, c->fp.param_off);
+    o_ps = push_table(blob, c->fp.param_slots);
+  } else {
+    o_sp = push_table(blob, c->gp.slot_param);
+    o_po = push_table(blob, c->gp.param_off);
+    o_ps = push_table(blob, c->gp.param_slots);
+  }
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, blob.size());
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QF_ERR_OOM, std::string("cudaMalloc of plan tables failed: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return fail(QF_ERR_CUDA, std::string("plan upload failed: ") + cudaGetErrorString(e));
+  }
+  char* b = static_cast<char*>(d);
+  c->d_tables = d;
+  if (c->path == QF_PATH_FUSED) {
+    c->d_fwd_ops = reinterpret_cast<const uint2*>(b + o_fwd);
+    c->d_bwd_ops = reinterpret_cast<const uint2*>(b + o_bwd);
+    c->d_fuse_off = reinterpret_cast<const int32_t*>(b + o_foff);
+    c->d_fuse_gates = reinterpret_cast<const qf::FuseGate*>(b + o_fg);
+  }
+  c->d_slot_param = reinterpret_cast<const int32_t*>(b + o_sp);
+  c->d_param_off = reinterpret_cast<const int32_t*>(b + o_po);
+  c->d_param_slots = reinterpret_cast<const int32_t*>(b + o_ps);
+  return QF_OK;
+}
+
+struct Obs {
+  uint32_t x = 0, z = 0, y = 0;
+};
+
+qf_status check_obs(const qf_circuit* c, qf_pauli obs, Obs* o) {
+  const uint64_t valid = (c->circ.n >= 64) ? ~0ull : ((1ull << c->circ.n) - 1);
+  if ((obs.x_mask | obs.z_mask) & ~valid)
+    return fail(QF_ERR_INVALID_ARG, "observable acts on a qubit outside the circuit");
+  o->x = (uint32_t)obs.x_mask;
+  o->z = (uint32_t)obs.z_mask;
+  o->y = (uint32_t)__builtin_popcountll(obs.x_mask & obs.z_mask) & 3u;
+  return QF_OK;
+}
+
+qf_status check_call(const qf_circuit* c, int64_t batch, void* ws, size_t ws_bytes) {
+  if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
+  if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan (call qf_plan)");
+  if (c->host_only || !c->d_tables) return fail(QF_ERR_WORKSPACE, "plan was built host-only");
+  if (batch < 0 || batch > c->batch) return fail(QF_ERR_INVALID_ARG, "batch exceeds the planned batch");
+  if (!ws) return fail(QF_ERR_INVALID_ARG, "null workspace");
+  if (((uintptr_t)ws & 255) != 0) return fail(QF_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < c->L.total) return fail(QF_ERR_WORKSPACE, "workspace smaller than qf_plan reported");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QF_ERR_CUDA, std::string("pending CUDA error: ") + cudaGetErrorString(e));
+  return QF_OK;
+}
+
+#define QF_CU(call)                                                                   \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) return fail(QF_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+// x-mask in the tile coordinates of a pass; false when a bit is outside it.
+bool local_xmask(const qf::PassDesc& pd, uint32_t xm, uint32_t* out) {
+  uint32_t r = 0;
+  for (int q = 0; q < 32; ++q) {
+    if (!((xm >> q) & 1u)) continue;
+    int lb = -1;
+    for (int j = 0; j < pd.K; ++j)
+      if (pd.gmap[j] == q) lb = j;
+    if (lb < 0) return false;
+    r |= 1u << lb;
+  }
+  *out = r;
+  return true;
+}
+
+qf_status fused_forward(qf_circuit* c, const float* theta, const float* x, int64_t B, const Obs& o,
+                        double* E, void* ws, cudaStream_t st) {
+  const qf::FusedPlan& P = c->fp;
+  const Layout& L = c->L;
+  qf::PrepArgs pa{};
+  pa.theta = theta;
+  pa.n_fused = (int32_t)P.fuse_off.size() - 1;
+  pa.fuse_off = c->d_fuse_off;
+  pa.fuse_gates = c->d_fuse_gates;
+  pa.mats = at<float4>(ws, L.mats);
+  pa.n_slots = P.n_slots;
+  pa.slot_param = c->d_slot_param;
+  pa.cs = at<float2>(ws, L.cs);
+  pa.x = x;
+  pa.B = B;
+  pa.n = c->circ.n;
+  pa.n_eff = P.n_eff;
+  pa.enc = at<float2>(ws, L.enc);
+  QF_CU(qf::launch_prep(pa, st));
+  c->call_launches++;
+  qf::PassArgs a{};
+  a.n_eff = P.n_eff;
+  a.tps_log2 = P.n_eff - P.K;
+  a.B = B;
+  a.ops = c->d_fwd_ops;
+  a.mats = pa.mats;
+  a.cs = pa.cs;
+  a.enc = pa.enc;
+  a.work = at<float2>(ws, L.work);
+  a.lam = at<float2>(ws, L.lam);
+  a.slots = at<float2>(ws, L.slots);
+  a.slot_stride = L.state_elems;
+  a.z_mask = o.z;
+  a.y_count = o.y;
+  a.e_part = at<double>(ws, L.epart);
+  a.g_part = at<double>(ws, L.gpart);
+  a.n_slots = P.n_slots;
+  const int prof = prof_begin(c, st);
+  for (size_t pi = 0; pi < P.fwd.size(); ++pi) {
+    a.pd = P.fwd[pi];
+    a.pd.xm_local = 0;
+    if ((a.pd.flags & qf::PF_EXPECT) && !local_xmask(a.pd, o.x, &a.pd.xm_local))
+      return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+    QF_CU(qf::launch_pass(false, a, st));
+    c->call_launches++;
+  }
+  prof_end(c, prof, 0, (int64_t)P.fwd.size(), st);
+  QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+  c->call_launches++;
+  return QF_OK;
+}
+
+qf_status fused_backward(qf_circuit* c, const float* theta, int64_t B, const Obs& o, const double* dLdE,
+                         double* grad, int per_sample, void* ws, cudaStream_t st) {
+  const qf::FusedPlan& P = c->fp;
+  const Layout& L = c->L;
+  qf::PrepArgs pa{};
+  pa.theta = theta;
+  pa.n_fused = 0;
+  pa.n_slots = P.n_slots;
+  pa.slot_param = c->d_slot_param;
+  pa.cs = at<float2>(ws, L.cs);
+  pa.B = 0;
+  pa.n = c->circ.n;
+  pa.n_eff = P.n_eff;
+  QF_CU(qf::launch_prep(pa, st));
+  c->call_launches++;
+  qf::PassArgs a{};
+  a.n_eff = P.n_eff;
+  a.tps_log2 = P.n_eff - P.K;
+  a.B = B;
+  a.ops = c->d_bwd_ops;
+  a.cs = pa.cs;
+  a.work = at<float2>(ws, L.work);
+  a.lam = at<float2>(ws, L.lam);
+  a.slots = at<float2>(ws, L.slots);
+  a.slot_stride = L.state_elems;
+  a.z_mask = o.z;
+  a.y_count = o.y;
+  a.dLdE = dLdE;
+  a.e_part = at<double>(ws, L.epart);
+  a.g_part = at<double>(ws, L.gpart);
+  a.n_slots = P.n_slots;
+  const int prof = prof_begin(c, st);
+  for (size_t pi = 0; pi < P.bwd.size(); ++pi) {
+    a.pd = P.bwd[pi];
+    a.pd.xm_local = 0;
+    if (a.pd.lam_src == qf::LAM_SEED && !local_xmask(a.pd, o.x, &a.pd.xm_local))
+      return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+    QF_CU(qf::launch_pass(true, a, st));
+    c->call_launches++;
+  }
+  prof_end(c, prof, 1, (int64_t)P.bwd.size(), st);
+  qf::GradReduceArgs g{};
+  g.g_part = a.g_part;
+  g.B = B;
+  g.tps = L.rows;
+  g.slot_stride = P.n_slots;
+  g.slot_step = 1;
+  g.n_params = c->circ.n_params;
+  g.param_off = c->d_param_off;
+  g.param_slots = c->d_param_slots;
+  g.per_sample = per_sample;
+  g.grad = grad;
+  QF_CU(qf::launch_g_reduce(g, st));
+  c->call_launches++;
+  return QF_OK;
+}
+
+qf_status pg_forward(qf_circuit* c, const float* theta, const float* x, int64_t B, const Obs& o, double* E,
+                     void* ws, cudaStream_t st) {
+  const qf::PerGatePlan& P = c->gp;
+  const Layout& L = c->L;
+  qf::PrepArgs pa{};
+  pa.theta = theta;
+  pa.n_slots = P.n_slots;
+  pa.slot_param = c->d_slot_param;
+  pa.cs = at<float2>(ws, L.cs);
+  pa.x = x;
+  pa.B = B;
+  pa.n = c->circ.n;
+  pa.n_eff = P.n_eff;
+  pa.enc = at<float2>(ws, L.enc);
+  QF_CU(qf::launch_prep(pa, st));
+  c->call_launches++;
+  qf::PerGateArgs a{P.n_eff, B, at<float2>(ws, L.work), at<float2>(ws, L.lam), (int32_t)L.rows};
+  if (B == 0) return QF_OK;
+  QF_CU(qf::pg_encode(a, pa.enc, st));
+  c->call_launches++;
+  size_t k = 0;
+  int slot = 0;
+  for (int g = 0; g < (int)c->circ.gates.size(); ++g) {
+    const qf::Gate& gt = c->circ.gates[g];
+    if (gt.kind == qf::G_CZ) {
+      QF_CU(qf::pg_cz(a, gt.q0, gt.q1, false, st));
+    } else {
+      QF_CU(qf::pg_rot(a, gt.kind, gt.q0, pa.cs, slot++, st));
+    }
+    c->call_launches++;
+    if (k < P.ckpt_after.size() && P.ckpt_after[k] == g) {
+      QF_CU(qf::pg_copy(a.psi, at<float2>(ws, L.slots) + (int64_t)k * L.state_elems, L.state_elems, st));
+      c->call_launches++;
+      ++k;
+    }
+  }
+  QF_CU(qf::pg_expect(a, o.x, o.z, o.y, at<double>(ws, L.epart), st));
+  QF_CU(qf::launch_e_reduce(at<double>(ws, L.epart), B, (int)L.rows, E, st));
+  c->call_launches += 2;
+  return QF_OK;
+}
+
+qf_status pg_backward(qf_circuit* c, const float* theta, int64_t B, const Obs& o, const double* dLdE,
+                      double* grad, int per_sample, void* ws, cudaStream_t st) {
+  const qf::PerGatePlan& P = c->gp;
+  const Layout& L = c->L;
+  qf::PrepArgs pa{};
+  pa.theta = theta;
+  pa.n_slots = P.n_slots;
+  pa.slot_param = c->d_slot_param;
+  pa.cs = at<float2>(ws, L.cs);
+  pa.n = c->circ.n;
+  pa.n_eff = P.n_eff;
+  QF_CU(qf::launch_prep(pa, st));
+  c->call_launches++;
+  qf::PerGateArgs a{P.n_eff, B, at<float2>(ws, L.work), at<float2>(ws, L.lam), (int32_t)L.rows};
+  double* gpart = at<double>(ws, L.gpart);
+  if (B > 0) {
+    QF_CU(qf::pg_seed(a, o.x, o.z, o.y, dLdE, st));
+    c->call_launches++;
+    int k = (int)P.ckpt_after.size() - 1;
+    int slot = P.n_slots - 1;
+    for (int g = (int)c->circ.gates.size() - 1; g >= 0; --g) {
+      if (k >= 0 && P.ckpt_after[k] == g) {
+        // re-anchor psi to the stored state after gate g
+        QF_CU(qf::pg_copy(at<float2>(ws, L.slots) + (int64_t)k * L.state_elems, a.psi, L.state_elems, st));
+        c->call_launches++;
+        --k;
+      }
+      const qf::Gate& gt = c->circ.gates[g];
+      if (gt.kind == qf::G_CZ) {
+        QF_CU(qf::pg_cz(a, gt.q0, gt.q1, true, st));
+      } else {
+        QF_CU(qf::pg_rot_bwd(a, gt.kind, gt.q0, pa.cs, slot, gpart + (int64_t)slot * B * L.rows, st));
+        --slot;
+      }
+      c->call_launches++;
+    }
+  }
+  qf::GradReduceArgs g{};
+  g.g_part = gpart;
+  g.B = B;
+  g.tps = L.rows;
+  g.slot_stride = 1;
+  g.slot_step = B * L.rows;
+  g.n_params = c->circ.n_params;
+  g.param_off = c->d_param_off;
+  g.param_slots = c->d_param_slots;
+  g.per_sample = per_sample;
+  g.grad = grad;
+  QF_CU(qf::launch_g_reduce(g, st));
+  c->call_launches++;
+  return QF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qf_last_error(void) { return g_err.c_str(); }
+
+int32_t qf_version(void) { return 100; }
+
+qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler, qf_circuit** out) {
+  if (!out) return fail(QF_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  try {
+    qf_circuit* c = new qf_circuit();
+    try {
+      qf::build_hea(c->circ, n_qubits, n_layers, entangler);
+    } catch (...) {
+      delete c;
+      throw;
+    }
+    *out = c;
+    return QF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(QF_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(QF_ERR_INVALID_ARG, e.what());
+  }
+}
+
+qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_gates, int32_t n_params,
+                            qf_circuit** out) {
+  if (!out) return fail(QF_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(QF_ERR_INVALID_ARG, "bad gate array");
+  try {
+    qf_circuit* c = new qf_circuit();
+    c->circ.n = n_qubits;
+    c->circ.n_params = n_params;
+    for (int i = 0; i < n_gates; ++i) {
+      qf::Gate g{gates[i].kind, gates[i].q0, gates[i].q1, gates[i].param};
+      if (g.kind == qf::G_CZ) g.param = -1;
+      else g.q1 = -1;
+      c->circ.gates.push_back(g);
+    }
+    try {
+      qf::validate_circuit(c->circ);
+    } catch (...) {
+      delete c;
+      throw;
+    }
+    *out = c;
+    return QF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(QF_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(QF_ERR_INVALID_ARG, e.what());
+  }
+}
+
+qf_status qf_circuit_destroy(qf_circuit* c) {
+  if (!c) return QF_OK;
+  destroy_events(c);
+  free_tables(c);
+  delete c;
+  return QF_OK;
+}
+
+qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t* workspace_bytes) {
+  if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
+  if (batch < 0) return fail(QF_ERR_INVALID_ARG, "negative batch");
+  qf_plan_opts o{};
+  if (opts) o = *opts;
+  if (o.path != QF_PATH_FUSED && o.path != QF_PATH_PER_GATE) return fail(QF_ERR_INVALID_ARG, "unknown path");
+  if (o.tile_bits != 0 && (o.tile_bits < 4 || o.tile_bits > 12))
+    return fail(QF_ERR_INVALID_ARG, "tile_bits must be 0 or in 4..12");
+  if (o.ckpt_layers < 0) return fail(QF_ERR_INVALID_ARG, "negative checkpoint interval");
+  try {
+    free_tables(c);
+    c->planned = false;
+    c->path = o.path;
+    c->ckpt_layers = o.ckpt_layers > 0 ? o.ckpt_layers : 10;
+    c->host_only = o.host_only != 0;
+    c->batch = batch;
+    qf::PlanRequest req;
+    req.tile_bits = o.tile_bits;
+    req.ckpt_layers = c->ckpt_layers;
+    if (c->path == QF_PATH_FUSED) {
+      c->fp = qf::plan_fused(c->circ, req);
+      c->gp = qf::PerGatePlan();
+    } else {
+      c->gp = qf::plan_per_gate(c->circ, req);
+      c->fp = qf::FusedPlan();
+    }
+    c->L = make_layout(c, batch);
+  } catch (const std::bad_alloc&) {
+    return fail(QF_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(QF_ERR_INVALID_ARG, e.what());
+  }
+  if (!c->host_only) {
+    qf_status s = upload(c);
+    if (s != QF_OK) return s;
+  }
+  c->planned = true;
+  if (workspace_bytes) *workspace_bytes = c->L.total;
+  return QF_OK;
+}
+
+qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
+  if (!c || !info) return fail(QF_ERR_INVALID_ARG, "null argument");
+  if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan");
+  memset(info, 0, sizeof(*info));
+  info->n_qubits = c->circ.n;
+  info->n_params = c->circ.n_params;
+  info->path = c->path;
+  info->ckpt_layers = c->ckpt_layers;
+  info->batch = c->batch;
+  info->workspace_bytes = (int64_t)c->L.total;
+  info->state_bytes = c->L.state_elems * 8;
+  if (c->path == QF_PATH_FUSED) {
+    info->n_eff = c->fp.n_eff;
+    info->n_slots = c->fp.n_slots;
+    info->tile_bits = c->fp.K;
+    info->n_passes = (int32_t)c->fp.fwd.size();
+    info->n_steps = c->fp.n_steps;
+    info->n_fused_ops = (int32_t)c->fp.fuse_off.size() - 1;
+    info->n_ckpt = c->fp.n_ckpt;
+    info->launches_fwd = info->n_passes + 2;
+    info->launches_bwd = info->n_passes + 2;
+  } else {
+    info->n_eff = c->gp.n_eff;
+    info->n_slots = c->gp.n_slots;
+    info->n_passes = (int32_t)c->circ.gates.size();
+    info->n_ckpt = c->gp.n_ckpt;
+    const int M = (int)c->circ.gates.size(), k = (int)c->gp.ckpt_after.size();
+    info->launches_fwd = M + k + 4;
+    info->launches_bwd = M + k + 3;
+  }
+  return QF_OK;
+}
+
+qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, int64_t cap, int64_t* len) {
+  if (!c || !len) return fail(QF_ERR_INVALID_ARG, "null argument");
+  if (!c->planned || c->path != QF_PATH_FUSED) return fail(QF_ERR_WORKSPACE, "no fused plan");
+  if (direction != 0 && direction != 1) return fail(QF_ERR_INVALID_ARG, "direction must be 0 or 1");
+  const qf::FusedPlan& P = c->fp;
+  const auto& passes = direction == 0 ? P.fwd : P.bwd;
+  const auto& ops = direction == 0 ? P.fwd_ops : P.bwd_ops;
+  std::vector<int32_t> w;
+  w.push_back((int32_t)passes.size());
+  for (const qf::PassDesc& pd : passes) {
+    const int32_t hdr[11] = {pd.op_begin, pd.op_end, pd.psi_src, pd.psi_dst, pd.lam_src, pd.lam_dst,
+                             pd.flags, pd.K, pd.n_groups, (int32_t)pd.outer_mask, (int32_t)pd.xm_local};
+    w.insert(w.end(), hdr, hdr + 11);
+    for (int j = 0; j < 16; ++j) w.push_back(pd.gmap[j]);
+    for (int g = 0; g < 4; ++g)
+      for (int r = 0; r < 4; ++r) w.push_back(pd.groups[g][r]);
+  }
+  w.push_back((int32_t)(ops.size() / 2));
+  for (uint32_t v : ops) w.push_back((int32_t)v);
+  const int nf = (int)P.fuse_off.size() - 1;
+  w.push_back(nf);
+  for (int m = 0; m < nf; ++m) {
+    w.push_back(P.fuse_off[m + 1] - P.fuse_off[m]);
+    for (int j = P.fuse_off[m]; j < P.fuse_off[m + 1]; ++j) {
+      w.push_back(P.fuse_gates[j].kind);
+      w.push_back(P.fuse_gates[j].param);
+    }
+  }
+  *len = (int64_t)w.size();
+  if (buf) memcpy(buf, w.data(), sizeof(int32_t) * (size_t)std::min<int64_t>(cap, (int64_t)w.size()));
+  return QF_OK;
+}
+
+qf_status qf_forward(qf_circuit* c, const float* theta_d, const float* x_d, int64_t batch, qf_pauli obs,
+                     double* E_d, void* ws_d, size_t ws_bytes, void* stream) {
+  qf_status s = check_call(c, batch, ws_d, ws_bytes);
+  if (s != QF_OK) return s;
+  if ((!theta_d && c->circ.n_params > 0) || (!x_d && batch > 0) || (!E_d && batch > 0))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  Obs o;
+  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+  c->call_launches = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = c->path == QF_PATH_FUSED ? fused_forward(c, theta_d, x_d, batch, o, E_d, ws_d, st)
+                               : pg_forward(c, theta_d, x_d, batch, o, E_d, ws_d, st);
+  c->launches = c->call_launches;
+  return s;
+}
+
+qf_status qf_backward(qf_circuit* c, const float* theta_d, const float* x_d, int64_t batch, qf_pauli obs,
+                      const double* dLdE_d, double* grad_d, int32_t per_sample, void* ws_d, size_t ws_bytes,
+                      void* stream) {
+  (void)x_d;
+  qf_status s = check_call(c, batch, ws_d, ws_bytes);
+  if (s != QF_OK) return s;
+  if ((!theta_d && c->circ.n_params > 0) || (!dLdE_d && batch > 0) || (!grad_d && c->circ.n_params > 0))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  Obs o;
+  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+  c->call_launches = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = c->path == QF_PATH_FUSED ? fused_backward(c, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st)
+                               : pg_backward(c, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st);
+  c->launches += c->call_launches;
+  return s;
+}
+
+qf_status qf_loss(int32_t kind, const double* E_d, const float* y_d, int64_t batch, double* loss_d,
+                  double* dLdE_d, void* stream) {
+  if (kind != QF_LOSS_SUM && kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
+  if (batch < 0 || (batch > 0 && (!E_d || !dLdE_d)) || !loss_d || (kind == QF_LOSS_MSE && batch > 0 && !y_d))
+    return fail(QF_ERR_INVALID_ARG, "bad loss arguments");
+  QF_CU(qf::launch_loss(kind, E_d, y_d, batch, loss_d, dLdE_d, static_cast<cudaStream_t>(stream)));
+  return QF_OK;
+}
+
+qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d, const float* y_d, int64_t batch,
+                        int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d, double* grad_d, void* ws_d,
+                        size_t ws_bytes, void* stream) {
+  qf_status s = qf_forward(c, theta_d, x_d, batch, obs, E_d, ws_d, ws_bytes, stream);
+  if (s != QF_OK) return s;
+  double* dLdE = at<double>(ws_d, c->L.dLdE);
+  s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+  if (s != QF_OK) return s;
+  const int64_t fwd_launches = c->launches;
+  s = qf_backward(c, theta_d, x_d, batch, obs, dLdE, grad_d, 0, ws_d, ws_bytes, stream);
+  c->launches = fwd_launches + 1 + c->call_launches;
+  return s;
+}
+
+qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x_h, const float* y_h,
+                             int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_h, double* E_h,
+                             double* grad_h, void* ws_d, size_t ws_bytes, void* stream) {
+  qf_status s = check_call(c, batch, ws_d, ws_bytes);
+  if (s != QF_OK) return s;
+  if ((!theta_h && c->circ.n_params > 0) || (!x_h && batch > 0) || !loss_h || (!grad_h && c->circ.n_params > 0) ||
+      (loss_kind == QF_LOSS_MSE && batch > 0 && !y_h))
+    return fail(QF_ERR_INVALID_ARG, "null host pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout& L = c->L;
+  float* th = at<float>(ws_d, L.theta);
+  float* xd = at<float>(ws_d, L.x);
+  float* yd = at<float>(ws_d, L.y);
+  const int P = c->circ.n_params;
+  if (P) QF_CU(cudaMemcpyAsync(th, theta_h, (size_t)P * 4, cudaMemcpyHostToDevice, st));
+  if (batch) QF_CU(cudaMemcpyAsync(xd, x_h, (size_t)batch * c->circ.n * 4, cudaMemcpyHostToDevice, st));
+  if (batch && loss_kind == QF_LOSS_MSE) QF_CU(cudaMemcpyAsync(yd, y_h, (size_t)batch * 4, cudaMemcpyHostToDevice, st));
+  s = qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, L.loss), at<double>(ws_d, L.E),
+                    at<double>(ws_d, L.grad), ws_d, ws_bytes, stream);
+  if (s != QF_OK) return s;
+  QF_CU(cudaMemcpyAsync(loss_h, at<double>(ws_d, L.loss), 8, cudaMemcpyDeviceToHost, st));
+  if (E_h && batch) QF_CU(cudaMemcpyAsync(E_h, at<double>(ws_d, L.E), (size_t)batch * 8, cudaMemcpyDeviceToHost, st));
+  if (P) QF_CU(cudaMemcpyAsync(grad_h, at<double>(ws_d, L.grad), (size_t)P * 8, cudaMemcpyDeviceToHost, st));
+  QF_CU(cudaStreamSynchronize(st));
+  return QF_OK;
+}
+
+qf_status qf_profile(qf_circuit* c, int32_t on) {
+  if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
+  if (on && c->ev.empty()) {
+    c->ev.resize(2 * kMaxProfilePairs);
+    for (auto& e : c->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) {
+        e = nullptr;
+        destroy_events(c);
+        return fail(QF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(r));
+      }
+    }
+    c->ev_dir.assign(kMaxProfilePairs, 0);
+    c->ev_launches.assign(kMaxProfilePairs, 0);
+  }
+  c->profile = on != 0;
+  c->ev_used = 0;
+  return QF_OK;
+}
+
+qf_status qf_profile_read(qf_circuit* c, double* fwd_ms, int64_t* fwd_launches, double* bwd_ms,
+                          int64_t* bwd_launches) {
+  if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
+  double ms[2] = {0, 0};
+  int64_t nl[2] = {0, 0};
+  for (size_t k = 0; k < c->ev_used; ++k) {
+    QF_CU(cudaEventSynchronize(c->ev[2 * k + 1]));
+    float t = 0.f;
+    QF_CU(cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]));
+    ms[c->ev_dir[k]] += t;
+    nl[c->ev_dir[k]] += c->ev_launches[k];
+  }
+  c->ev_used = 0;
+  if (fwd_ms) *fwd_ms = ms[0];
+  if (fwd_launches) *fwd_launches = nl[0];
+  if (bwd_ms) *bwd_ms = ms[1];
+  if (bwd_launches) *bwd_launches = nl[1];
+  return QF_OK;
+}
+
+qf_status qf_launch_count(const qf_circuit* c, int64_t* launches) {
+  if (!c || !launches) return fail(QF_ERR_INVALID_ARG, "null argument");
+  *launches = c->launches;
+  return QF_OK;
+}
+
+}  // extern "C"

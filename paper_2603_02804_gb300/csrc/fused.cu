@@ -1,0 +1,558 @@
+// Fused forward / adjoint pass kernels for sm_103a.
+//
+// One CTA (256 threads) owns 4096 amplitudes of shared memory per state:
+// one tile of K = 12 tile bits, or 2^(12-K) tiles of a smaller circuit. A
+// pass loads its tiles from HBM once (or generates psi_0 in place), runs the
+// pass's step program on them in shared memory and registers, and stores them
+// once: the forward and backward gate fusion of Secs. 3.2-3.3.
+//
+// Shared-memory layout: amplitude with local index i lives at i ^ ((i>>4)&15)
+// (XOR swizzle on 8-byte words). Register groups are local nibbles, so the 16
+// lanes of a half-warp always hit 16 distinct bank pairs.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace qf {
+
+namespace {
+
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 4) & 15u); }
+
+// Scatter the low bits of src into the set bits of mask (ascending).
+__device__ __forceinline__ uint32_t pdep32(uint32_t src, uint32_t mask) {
+  uint32_t r = 0;
+  for (uint32_t bb = 1; mask; bb <<= 1) {
+    const uint32_t low = mask & (0u - mask);
+    if (src & bb) r |= low;
+    mask ^= low;
+  }
+  return r;
+}
+
+__device__ __forceinline__ float flip(float v, uint32_t s) {
+  return __int_as_float(__float_as_int(v) ^ (int)(s << 31));
+}
+
+// Pair (i, i+1), i even, to/from the swizzled tile.
+__device__ __forceinline__ void st_pair(float2* sm, uint32_t i, float4 v) {
+  const uint32_t p = swz(i);
+  if (p & 1u) *reinterpret_cast<float4*>(sm + (p ^ 1u)) = make_float4(v.z, v.w, v.x, v.y);
+  else *reinterpret_cast<float4*>(sm + p) = v;
+}
+__device__ __forceinline__ float4 ld_pair(const float2* sm, uint32_t i) {
+  const uint32_t p = swz(i);
+  if (p & 1u) {
+    const float4 v = *reinterpret_cast<const float4*>(sm + (p ^ 1u));
+    return make_float4(v.z, v.w, v.x, v.y);
+  }
+  return *reinterpret_cast<const float4*>(sm + p);
+}
+
+// ---- forward: fused 2x2 on register bit R -----------------------------------
+template <int R>
+__device__ __forceinline__ void apply_u(float2 (&r)[16], const float4 m0, const float4 m1) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    const float2 x = r[j], y = r[j1];
+    r[j].x = m0.x * x.x - m0.y * x.y + m0.z * y.x - m0.w * y.y;
+    r[j].y = m0.x * x.y + m0.y * x.x + m0.z * y.y + m0.w * y.x;
+    r[j1].x = m1.x * x.x - m1.y * x.y + m1.z * y.x - m1.w * y.y;
+    r[j1].y = m1.x * x.y + m1.y * x.x + m1.z * y.y + m1.w * y.x;
+  }
+}
+
+// ---- backward: un-apply one rotation to psi and lambda on register bit R and
+// return sum over the thread's pairs of Im<lambda|P|psi> taken before the
+// un-apply. With du/dt = -(i/2) P u (Sec. 3.3), Re<lambda_j|du|psi_{j-1}> =
+// (1/2) Im<lambda_j|P|psi_j>; the 1/2 is applied in float64 at the flush.
+template <int R, int KIND>
+__device__ __forceinline__ float bwd_gate(float2 (&p)[16], float2 (&l)[16], const float c,
+                                          const float s) {
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    const float2 p0 = p[j], p1 = p[j1], l0 = l[j], l1 = l[j1];
+    if (KIND == G_RZ) {
+      acc += l0.x * p0.y - l0.y * p0.x - l1.x * p1.y + l1.y * p1.x;
+      // u^dagger = diag(c + i s, c - i s)
+      p[j] = make_float2(c * p0.x - s * p0.y, c * p0.y + s * p0.x);
+      p[j1] = make_float2(c * p1.x + s * p1.y, c * p1.y - s * p1.x);
+      l[j] = make_float2(c * l0.x - s * l0.y, c * l0.y + s * l0.x);
+      l[j1] = make_float2(c * l1.x + s * l1.y, c * l1.y - s * l1.x);
+    } else if (KIND == G_RY) {
+      acc += l1.x * p0.x + l1.y * p0.y - l0.x * p1.x - l0.y * p1.y;
+      // u^dagger = [[c, s], [-s, c]]
+      p[j] = make_float2(c * p0.x + s * p1.x, c * p0.y + s * p1.y);
+      p[j1] = make_float2(c * p1.x - s * p0.x, c * p1.y - s * p0.y);
+      l[j] = make_float2(c * l0.x + s * l1.x, c * l0.y + s * l1.y);
+      l[j1] = make_float2(c * l1.x - s * l0.x, c * l1.y - s * l0.y);
+    } else {  // RX
+      acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
+      // u^dagger = [[c, i s], [i s, c]]
+      p[j] = make_float2(c * p0.x - s * p1.y, c * p0.y + s * p1.x);
+      p[j1] = make_float2(c * p1.x - s * p0.y, c * p1.y + s * p0.x);
+      l[j] = make_float2(c * l0.x - s * l1.y, c * l0.y + s * l1.x);
+      l[j1] = make_float2(c * l1.x - s * l0.y, c * l1.y + s * l0.x);
+    }
+  }
+  return acc;
+}
+
+template <int KIND>
+__device__ __forceinline__ float bwd_dispatch_r(uint32_t r, float2 (&p)[16], float2 (&l)[16], float c,
+                                                float s) {
+  switch (r) {
+    case 0: return bwd_gate<0, KIND>(p, l, c, s);
+    case 1: return bwd_gate<1, KIND>(p, l, c, s);
+    case 2: return bwd_gate<2, KIND>(p, l, c, s);
+    default: return bwd_gate<3, KIND>(p, l, c, s);
+  }
+}
+
+__device__ __forceinline__ uint32_t reg_off(uint32_t j, const uint32_t (&o)[4]) {
+  return ((j & 1u) ? o[0] : 0u) ^ ((j & 2u) ? o[1] : 0u) ^ ((j & 4u) ? o[2] : 0u) ^
+         ((j & 8u) ? o[3] : 0u);
+}
+
+// phase i^k times v
+__device__ __forceinline__ float2 mul_ipow(float2 v, uint32_t k) {
+  switch (k & 3u) {
+    case 0: return v;
+    case 1: return make_float2(-v.y, v.x);
+    case 2: return make_float2(-v.x, -v.y);
+    default: return make_float2(v.y, -v.x);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <bool BWD>
+__global__ void __launch_bounds__(kThreads) pass_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ uint32_t s_lg[256];
+  __shared__ float s_red[2][kThreads / 32][kMaxStepSlots];
+  __shared__ int32_t s_slot[2][kMaxStepSlots];
+  __shared__ double s_dred[kThreads / 32];
+  __shared__ uint32_t s_gmap[16];
+  __shared__ uint32_t s_grp[4][4];
+
+  const PassDesc& pd = a.pd;
+  const int K = pd.K;
+  const int tl2 = K - kRegBits;            // log2 threads per tile
+  const int Tt = 1 << tl2;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int tile_in_cta = tid >> tl2;
+  const uint32_t tau = (uint32_t)(tid & (Tt - 1));
+  const int tiles_per_cta = kThreads >> tl2;
+  const int64_t total_tiles = (int64_t)a.B << a.tps_log2;
+  const int64_t tile = (int64_t)blockIdx.x * tiles_per_cta + tile_in_cta;
+  const bool active = tile < total_tiles;
+  const int64_t b = active ? (tile >> a.tps_log2) : 0;
+  const uint32_t t_in = active ? (uint32_t)(tile & ((1ll << a.tps_log2) - 1)) : 0u;
+  const uint32_t outer = pdep32(t_in, pd.outer_mask);
+  const int64_t dim = 1ll << a.n_eff;
+  const int64_t sbase = b * dim;  // sample offset inside one state buffer
+  float2* tp = smem + (tile_in_cta << K);
+  float2* tl = smem + kTileAmps + (tile_in_cta << K);
+  const int wpt = Tt >= 32 ? Tt / 32 : 1;  // warps per tile
+  const int lanes = Tt < 32 ? Tt : 32;
+
+  if (tid < 16) {
+    s_gmap[tid] = pd.gmap[tid];
+    s_grp[tid >> 2][tid & 3] = pd.groups[tid >> 2][tid & 3];
+  }
+  __syncthreads();
+  for (int h = tid; h < (1 << tl2); h += kThreads) {
+    uint32_t g = 0;
+    for (int j = 0; j < tl2; ++j)
+      if ((h >> j) & 1) g |= 1u << s_gmap[kRegBits + j];
+    s_lg[h] = g;
+  }
+  __syncthreads();
+
+  auto gidx = [&](uint32_t i) -> uint32_t { return outer | (i & 15u) | s_lg[i >> 4]; };
+  auto state_ptr = [&](int32_t code) -> float2* {
+    if (code >= 0) return a.slots + (int64_t)code * a.slot_stride + sbase;
+    return a.work + sbase;
+  };
+
+  // ---- bring psi (and lambda) in -------------------------------------------
+  const int32_t psrc = pd.psi_src;
+  if (psrc == SRC_GENERATE) {
+    // psi_0 = (x) RY(x_q)|0>: a_x = prod_q (bit q of x ? sin(x_q/2) : cos(x_q/2))
+    const float2* e = a.enc + b * a.n_eff;
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      const uint32_t g = gidx(i);
+      float pr = 1.f;
+      for (int q = 1; q < a.n_eff; ++q) {
+        const float2 f = __ldg(e + q);
+        pr *= ((g >> q) & 1u) ? f.y : f.x;
+      }
+      const float2 f0 = __ldg(e);
+      if (active) st_pair(tp, i, make_float4(pr * f0.x, 0.f, pr * f0.y, 0.f));
+    }
+  } else {
+    const float2* src = state_ptr(psrc);
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      if (active) st_pair(tp, i, *reinterpret_cast<const float4*>(src + gidx(i)));
+    }
+  }
+  if (BWD && pd.lam_src == LAM_BUF) {
+    const float2* src = a.lam + sbase;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      if (active) st_pair(tl, i, *reinterpret_cast<const float4*>(src + gidx(i)));
+    }
+  }
+  __syncthreads();
+  if (BWD && pd.lam_src == LAM_SEED) {
+    // lambda_M = 2 (dL/dE_b) O psi_M (Eq. 4); (O psi)_x = i^{#Y} (-1)^{|(x^xm)&zm|} psi_{x^xm}
+    const float scale = active ? (float)(2.0 * a.dLdE[b]) : 0.f;
+#pragma unroll 1
+    for (int it = 0; it < 16; ++it) {
+      const uint32_t i = (uint32_t)it * Tt + tau;  // single amplitudes here
+      const uint32_t ip = i ^ pd.xm_local;
+      const uint32_t gp = gidx(ip);
+      float2 v = tp[swz(ip)];
+      v = mul_ipow(v, a.y_count);
+      const uint32_t sg = __popc(gp & a.z_mask) & 1u;
+      tl[swz(i)] = make_float2(flip(v.x, sg) * scale, flip(v.y, sg) * scale);
+    }
+    __syncthreads();
+  }
+
+  // ---- step program ------------------------------------------------------------
+  int buf = 0;
+  int32_t pc = pd.op_begin;
+  const uint2* ops = a.ops;
+#pragma unroll 1
+  while (pc < pd.op_end) {
+    const uint2 op = __ldg(ops + pc++);
+    const uint32_t code = op.x & 15u;
+    if (code == OP_STEP) {
+      const int g = (op.x >> 4) & 3;
+      const int nops = (op.x >> 8) & 0xffff;
+      const int nk = (int)op.y;
+      const uint32_t lb0 = s_grp[g][0], lb1 = s_grp[g][1], lb2 = s_grp[g][2], lb3 = s_grp[g][3];
+      const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
+      const uint32_t base = pdep32(tau, ((1u << K) - 1u) & ~gm);
+      const uint32_t pb = swz(base);
+      const uint32_t so[4] = {swz(1u << lb0), swz(1u << lb1), swz(1u << lb2), swz(1u << lb3)};
+      const uint32_t gb = gidx(base);
+      const uint32_t go[4] = {1u << s_gmap[lb0], 1u << s_gmap[lb1], 1u << s_gmap[lb2],
+                              1u << s_gmap[lb3]};
+      float2 r[16];
+      float2 l[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        r[j] = tp[pb ^ reg_off(j, so)];
+        if (BWD) l[j] = tl[pb ^ reg_off(j, so)];
+      }
+#pragma unroll 1
+      for (int k = 0; k < nops; ++k) {
+        const uint2 o = __ldg(ops + pc++);
+        const uint32_t oc = o.x & 15u;
+        if (!BWD && oc == OP_U) {
+          const uint32_t m = o.x >> 8;
+          const float4 m0 = __ldg(a.mats + 2 * m), m1 = __ldg(a.mats + 2 * m + 1);
+          switch ((o.x >> 4) & 3u) {
+            case 0: apply_u<0>(r, m0, m1); break;
+            case 1: apply_u<1>(r, m0, m1); break;
+            case 2: apply_u<2>(r, m0, m1); break;
+            default: apply_u<3>(r, m0, m1); break;
+          }
+        } else if (BWD && oc == OP_G) {
+          const uint32_t rr = (o.x >> 4) & 3u, kind = (o.x >> 6) & 3u, ks = (o.x >> 8) & 0xffu;
+          const float2 csv = __ldg(a.cs + o.y);
+          float acc;
+          if (kind == G_RZ) acc = bwd_dispatch_r<G_RZ>(rr, r, l, csv.x, csv.y);
+          else if (kind == G_RY) acc = bwd_dispatch_r<G_RY>(rr, r, l, csv.x, csv.y);
+          else acc = bwd_dispatch_r<G_RX>(rr, r, l, csv.x, csv.y);
+          for (int off = 1; off < lanes; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+          if (Tt >= 32) {
+            if (lane == 0) s_red[buf][warp][ks] = acc;
+            if (tid == 0) s_slot[buf][ks] = (int32_t)o.y;
+          } else if (active && (lane & (Tt - 1)) == 0) {
+            a.g_part[tile * a.n_slots + o.y] = 0.5 * (double)acc;
+          }
+        } else if (oc == OP_CHAIN || oc == OP_CZ) {
+          const uint32_t links = o.y, c0 = o.y & 0xffu, c1 = (o.y >> 8) & 0xffu;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t x = gb | reg_off(j, go);
+            const uint32_t sg = oc == OP_CHAIN ? (__popc(x & (x >> 1) & links) & 1u)
+                                               : ((x >> c0) & (x >> c1) & 1u);
+            r[j].x = flip(r[j].x, sg);
+            r[j].y = flip(r[j].y, sg);
+            if (BWD) {
+              l[j].x = flip(l[j].x, sg);
+              l[j].y = flip(l[j].y, sg);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        tp[pb ^ reg_off(j, so)] = r[j];
+        if (BWD) tl[pb ^ reg_off(j, so)] = l[j];
+      }
+      __syncthreads();
+      if (BWD && Tt >= 32) {
+        for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
+          const int tc = e / nk, kk = e - tc * nk;
+          const int64_t t2 = (int64_t)blockIdx.x * tiles_per_cta + tc;
+          if (t2 < total_tiles) {
+            double sum = 0.0;
+            for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
+            a.g_part[t2 * a.n_slots + s_slot[buf][kk]] = 0.5 * sum;
+          }
+        }
+        buf ^= 1;
+      }
+    } else if (code == OP_CKPT || code == OP_ANCHOR) {
+      float2* sp = a.slots + (int64_t)op.y * a.slot_stride + sbase;
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+        if (!active) continue;
+        if (code == OP_CKPT) *reinterpret_cast<float4*>(sp + gidx(i)) = ld_pair(tp, i);
+        else st_pair(tp, i, *reinterpret_cast<const float4*>(sp + gidx(i)));
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- write back -----------------------------------------------------------
+  if (pd.psi_dst != BUF_NONE) {
+    float2* dst = state_ptr(pd.psi_dst);
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      if (active) *reinterpret_cast<float4*>(dst + gidx(i)) = ld_pair(tp, i);
+    }
+  }
+  if (BWD && pd.lam_dst == LAM_BUF) {
+    float2* dst = a.lam + sbase;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      if (active) *reinterpret_cast<float4*>(dst + gidx(i)) = ld_pair(tl, i);
+    }
+  }
+  if (!BWD && (pd.flags & PF_EXPECT)) {
+    // <psi|O|psi> partial of this tile (Eq. 1, matrix-free as in Appendix B.2)
+    float acc = 0.f;
+#pragma unroll 1
+    for (int it = 0; it < 16; ++it) {
+      const uint32_t i = (uint32_t)it * Tt + tau;
+      const uint32_t ip = i ^ pd.xm_local;
+      const float2 v = tp[swz(i)];
+      float2 w = mul_ipow(tp[swz(ip)], a.y_count);
+      const uint32_t sg = __popc(gidx(ip) & a.z_mask) & 1u;
+      acc += flip(v.x * w.x + v.y * w.y, sg);  // Re(conj(v) w) with the Z signs
+    }
+    double d = (double)acc;
+    for (int off = 1; off < lanes; off <<= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (Tt >= 32) {
+      if (lane == 0) s_dred[warp] = d;
+      __syncthreads();
+      if (tid < tiles_per_cta) {
+        const int64_t t2 = (int64_t)blockIdx.x * tiles_per_cta + tid;
+        if (t2 < total_tiles) {
+          double sum = 0.0;
+          for (int w = 0; w < wpt; ++w) sum += s_dred[tid * wpt + w];
+          a.e_part[t2] = sum;
+        }
+      }
+    } else if (active && (lane & (Tt - 1)) == 0) {
+      a.e_part[tile] = d;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gate tables from theta in float64, rounded once to float32:
+//   fused 2x2 products (forward), (cos, sin) of theta/2 per slot (backward),
+//   (cos, sin) of x/2 per sample and qubit (encoding).
+__global__ void prep_kernel(const PrepArgs a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n_fused) {
+    double u[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {1, 0}}};  // [row][col][re/im]
+    for (int j = a.fuse_off[i]; j < a.fuse_off[i + 1]; ++j) {
+      const FuseGate fg = a.fuse_gates[j];
+      double s, c;
+      sincos(0.5 * (double)a.theta[fg.param], &s, &c);
+      // g = c I - i s P
+      double g[2][2][2];
+      if (fg.kind == G_RX) {
+        g[0][0][0] = c; g[0][0][1] = 0; g[0][1][0] = 0; g[0][1][1] = -s;
+        g[1][0][0] = 0; g[1][0][1] = -s; g[1][1][0] = c; g[1][1][1] = 0;
+      } else if (fg.kind == G_RY) {
+        g[0][0][0] = c; g[0][0][1] = 0; g[0][1][0] = -s; g[0][1][1] = 0;
+        g[1][0][0] = s; g[1][0][1] = 0; g[1][1][0] = c; g[1][1][1] = 0;
+      } else {
+        g[0][0][0] = c; g[0][0][1] = -s; g[0][1][0] = 0; g[0][1][1] = 0;
+        g[1][0][0] = 0; g[1][0][1] = 0; g[1][1][0] = c; g[1][1][1] = s;
+      }
+      double t[2][2][2];
+      for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 2; ++k) {
+          double re = 0, im = 0;
+          for (int m = 0; m < 2; ++m) {
+            re += g[r][m][0] * u[m][k][0] - g[r][m][1] * u[m][k][1];
+            im += g[r][m][0] * u[m][k][1] + g[r][m][1] * u[m][k][0];
+          }
+          t[r][k][0] = re;
+          t[r][k][1] = im;
+        }
+      for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 2; ++k) {
+          u[r][k][0] = t[r][k][0];
+          u[r][k][1] = t[r][k][1];
+        }
+    }
+    a.mats[2 * i] = make_float4((float)u[0][0][0], (float)u[0][0][1], (float)u[0][1][0], (float)u[0][1][1]);
+    a.mats[2 * i + 1] = make_float4((float)u[1][0][0], (float)u[1][0][1], (float)u[1][1][0], (float)u[1][1][1]);
+    return;
+  }
+  i -= a.n_fused;
+  if (i < a.n_slots) {
+    double s, c;
+    sincos(0.5 * (double)a.theta[a.slot_param[i]], &s, &c);
+    a.cs[i] = make_float2((float)c, (float)s);
+    return;
+  }
+  i -= a.n_slots;
+  if (i < (int64_t)a.B * a.n_eff) {
+    const int64_t bb = i / a.n_eff;
+    const int q = (int)(i - bb * a.n_eff);
+    if (q < a.n) {
+      double s, c;
+      sincos(0.5 * (double)a.x[bb * a.n + q], &s, &c);
+      a.enc[i] = make_float2((float)c, (float)s);
+    } else {
+      a.enc[i] = make_float2(1.f, 0.f);  // padding qubit stays |0>
+    }
+  }
+}
+
+// E_b = sum over the tiles of sample b, in tile order (deterministic).
+__global__ void e_reduce_kernel(const double* e_part, int64_t B, int tps, double* E) {
+  const int64_t bb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bb >= B) return;
+  double s = 0.0;
+  for (int t = 0; t < tps; ++t) s += e_part[bb * tps + t];
+  E[bb] = s;
+}
+
+// grad[p] (or grad[b][p]) = sum over tiles, then over the slots of p, in a
+// fixed order.
+__global__ void g_reduce_kernel(const GradReduceArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a.per_sample) {
+    if (i >= (int64_t)a.B * a.n_params) return;
+    const int64_t bb = i / a.n_params;
+    const int p = (int)(i - bb * a.n_params);
+    double s = 0.0;
+    for (int k = a.param_off[p]; k < a.param_off[p + 1]; ++k) {
+      const int slot = a.param_slots[k];
+      for (int64_t t = 0; t < a.tps; ++t) s += a.g_part[(bb * a.tps + t) * a.slot_stride + slot * a.slot_step];
+    }
+    a.grad[i] = s;
+  } else {
+    if (i >= a.n_params) return;
+    double s = 0.0;
+    for (int k = a.param_off[i]; k < a.param_off[i + 1]; ++k) {
+      const int slot = a.param_slots[k];
+      for (int64_t t = 0; t < (int64_t)a.B * a.tps; ++t) s += a.g_part[t * a.slot_stride + slot * a.slot_step];
+    }
+    a.grad[i] = s;
+  }
+}
+
+// Loss and dL/dE in one block, fixed-order tree reduction.
+__global__ void loss_kernel(int kind, const double* E, const float* y, int64_t B, double* loss,
+                            double* dLdE) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+    if (kind == 1) {
+      const double d = E[i] - (double)y[i];
+      s += d * d;
+      dLdE[i] = 2.0 * d / (double)B;
+    } else {
+      s += E[i];
+      dLdE[i] = 1.0;
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[0] = kind == 1 ? red[0] / (double)B : red[0];
+}
+
+// ---- launchers ----------------------------------------------------------------
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
+  const int64_t total = (int64_t)a.n_fused + a.n_slots + (int64_t)a.B * a.n_eff;
+  if (total == 0) return cudaSuccess;
+  const int blk = 256;
+  prep_kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
+  const int tiles_per_cta = kThreads >> (a.pd.K - kRegBits);
+  const int64_t total_tiles = (int64_t)a.B << a.tps_log2;
+  const int64_t grid = (total_tiles + tiles_per_cta - 1) / tiles_per_cta;
+  if (grid == 0) return cudaSuccess;
+  const size_t smem = (size_t)(bwd ? 2 : 1) * kTileAmps * sizeof(float2);
+  if (bwd) {
+    static bool once = false;
+    if (!once) {
+      cudaError_t e = cudaFuncSetAttribute(pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      once = true;
+    }
+    pass_kernel<true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  } else {
+    pass_kernel<false><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  e_reduce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(e_part, B, tps, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st) {
+  const int64_t n = a.per_sample ? (int64_t)a.B * a.n_params : a.n_params;
+  if (n == 0) return cudaSuccess;
+  g_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
+                        cudaStream_t st) {
+  loss_kernel<<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE);
+  return cudaGetLastError();
+}
+
+}  // namespace qf

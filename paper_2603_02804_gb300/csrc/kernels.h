@@ -1,0 +1,86 @@
+// Launch interfaces of the CUDA kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qf_internal.h"
+
+namespace qf {
+
+struct PassArgs {
+  PassDesc pd;
+  int32_t n_eff;
+  int32_t tps_log2;       // log2(tiles per sample) = n_eff - K
+  int64_t B;              // samples in this call
+  const uint2* ops;       // program of this direction
+  const float4* mats;     // fused 2x2 matrices, 2 float4 each
+  const float2* cs;       // (cos, sin) of theta/2 per gradient slot
+  const float2* enc;      // (cos, sin) of x/2, [B][n_eff]
+  float2* work;           // working state [B][2^n_eff]
+  float2* lam;            // adjoint state [B][2^n_eff]
+  float2* slots;          // checkpoint states [n_ckpt][slot_stride]
+  int64_t slot_stride;    // elements between consecutive checkpoint slots
+  uint32_t z_mask;        // observable Z part (global bits)
+  uint32_t y_count;       // number of Y factors (phase i^y_count)
+  const double* dLdE;     // [B]
+  double* e_part;         // [B * tiles per sample]
+  double* g_part;         // [B * tiles per sample][n_slots]
+  int32_t n_slots;
+};
+
+struct PrepArgs {
+  const float* theta;
+  int32_t n_fused;
+  const int32_t* fuse_off;
+  const FuseGate* fuse_gates;
+  float4* mats;
+  int32_t n_slots;
+  const int32_t* slot_param;
+  float2* cs;
+  const float* x;
+  int64_t B;
+  int32_t n, n_eff;
+  float2* enc;
+};
+
+struct GradReduceArgs {
+  const double* g_part;
+  int64_t B;
+  int64_t tps;          // partial rows per sample
+  int64_t slot_stride;  // elements between consecutive partial rows
+  int64_t slot_step;    // elements between consecutive slots of one row
+  int32_t n_params;
+  const int32_t* param_off;
+  const int32_t* param_slots;
+  int32_t per_sample;
+  double* grad;
+};
+
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
+cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st);
+cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st);
+cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st);
+cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
+                        cudaStream_t st);
+
+// ---- per-gate comparator ------------------------------------------------------
+struct PerGateArgs {
+  int32_t n_eff;
+  int64_t B;
+  float2* psi;          // [B][2^n_eff]
+  float2* lam;
+  int32_t chunks;       // partial rows per sample
+};
+cudaError_t pg_encode(const PerGateArgs& a, const float2* enc, cudaStream_t st);
+cudaError_t pg_rot(const PerGateArgs& a, int kind, int q, const float2* cs, int slot, cudaStream_t st);
+cudaError_t pg_cz(const PerGateArgs& a, int c, int t, bool both, cudaStream_t st);
+cudaError_t pg_expect(const PerGateArgs& a, uint32_t x_mask, uint32_t z_mask, uint32_t y_count,
+                      double* e_part, cudaStream_t st);
+cudaError_t pg_seed(const PerGateArgs& a, uint32_t x_mask, uint32_t z_mask, uint32_t y_count,
+                    const double* dLdE, cudaStream_t st);
+cudaError_t pg_rot_bwd(const PerGateArgs& a, int kind, int q, const float2* cs, int slot, double* g_part,
+                       cudaStream_t st);
+cudaError_t pg_copy(const float2* src, float2* dst, int64_t n, cudaStream_t st);
+int32_t pg_chunks(int32_t n_eff);
+
+}  // namespace qf

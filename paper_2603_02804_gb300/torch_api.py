@@ -1,0 +1,163 @@
+"""PyTorch integration: a simulator object, a ``torch.autograd.Function`` and an
+``nn.Module`` for the hardware-efficient ansatz.
+
+PyTorch supplies device memory (the workspace is one uint8 tensor from the
+caching allocator) and the current CUDA stream; every step of the simulation
+runs in the library's kernels. Autograd integration follows Sec. 3.3's
+out-of-place discipline: the forward keeps its checkpoints in the simulator's
+workspace and the backward consumes them; if another forward ran on the same
+simulator in between, the backward recomputes its forward first.
+"""
+from __future__ import annotations
+
+import itertools
+
+import torch
+
+from . import qfuse
+
+_PATHS = {"fused": qfuse.QF_PATH_FUSED, "per_gate": qfuse.QF_PATH_PER_GATE}
+_ENT = {"chain": qfuse.QF_ENT_CHAIN, "ring": qfuse.QF_ENT_RING}
+_LOSS = {"sum": qfuse.QF_LOSS_SUM, "mse": qfuse.QF_LOSS_MSE}
+_ids = itertools.count(1)
+
+
+def _cuda_check():
+    if not torch.cuda.is_available():
+        raise RuntimeError("qfuse needs a CUDA device (GB300, sm_103a); there is no CPU fallback")
+
+
+class Simulator:
+    """A planned circuit with its workspace.
+
+    ``n``/``d`` build the hardware-efficient ansatz; ``gates`` (rows of
+    (kind, q0, q1, param)) with ``n_params`` builds a user circuit instead.
+    """
+
+    def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
+                 tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
+                 device=None):
+        _cuda_check()
+        self.device = torch.device(device or "cuda")
+        if gates is None:
+            self.handle = qfuse.qf_hea_create(n, d, _ENT[entangler])
+            self.n_params = 3 * n * d
+        else:
+            self.handle = qfuse.qf_circuit_create(n, gates, n_params)
+            self.n_params = n_params
+        self.n, self.d = n, d
+        self.path = path
+        self.obs = qfuse.pauli(obs, n) if not isinstance(obs, qfuse.qf_pauli) else obs
+        with torch.cuda.device(self.device):
+            self.ws_bytes = qfuse.qf_plan(self.handle, batch, _PATHS[path], tile_bits, ckpt_layers)
+            self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
+        self.batch = batch
+        self._fwd_id = 0
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                qfuse.qf_circuit_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def info(self) -> dict:
+        return qfuse.qf_plan_info(self.handle)
+
+    def launches(self) -> int:
+        return qfuse.qf_launch_count(self.handle)
+
+    def _stream(self):
+        return torch.cuda.current_stream(self.device)
+
+    def _check(self, theta, x):
+        if theta.dtype != torch.float32 or x.dtype != torch.float32:
+            raise TypeError("theta and x must be float32")
+        if not (theta.is_cuda and x.is_cuda and theta.is_contiguous() and x.is_contiguous()):
+            raise ValueError("theta and x must be contiguous CUDA tensors")
+        if theta.numel() != self.n_params or x.dim() != 2 or x.shape[1] != self.n or x.shape[0] > self.batch:
+            raise ValueError("shape mismatch with the planned circuit")
+
+    def forward(self, theta: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+        """E_b for every sample (float64 [B])."""
+        self._check(theta, x)
+        B = x.shape[0]
+        E = torch.empty(B, dtype=torch.float64, device=self.device)
+        qfuse.qf_forward(self.handle, theta, x, B, self.obs, E, self.ws, self.ws_bytes, self._stream())
+        self._fwd_id = next(_ids)
+        return E
+
+    def backward(self, theta, x, dLdE, per_sample: bool = False) -> torch.Tensor:
+        """Adjoint gradient after forward(theta, x): float64 [P] or [B, P]."""
+        self._check(theta, x)
+        B = x.shape[0]
+        dLdE = dLdE.to(device=self.device, dtype=torch.float64).contiguous()
+        shape = (B, self.n_params) if per_sample else (self.n_params,)
+        g = torch.empty(shape, dtype=torch.float64, device=self.device)
+        qfuse.qf_backward(self.handle, theta, x, B, self.obs, dLdE, g, per_sample, self.ws, self.ws_bytes,
+                          self._stream())
+        return g
+
+    def train_step(self, theta, x, y=None, loss: str = "sum"):
+        """Forward, loss and backward in one call: (loss [1], E [B], grad [P]) on the device."""
+        self._check(theta, x)
+        B = x.shape[0]
+        out_loss = torch.empty(1, dtype=torch.float64, device=self.device)
+        E = torch.empty(B, dtype=torch.float64, device=self.device)
+        g = torch.empty(self.n_params, dtype=torch.float64, device=self.device)
+        qfuse.qf_train_step(self.handle, theta, x, y, B, _LOSS[loss], self.obs, out_loss, E, g, self.ws,
+                            self.ws_bytes, self._stream())
+        self._fwd_id = next(_ids)
+        return out_loss, E, g
+
+    def train_step_host(self, theta_h, x_h, y_h=None, loss: str = "sum"):
+        """The same step from host (ideally pinned) tensors; returns host results."""
+        B = x_h.shape[0]
+        out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        E = torch.empty(B, dtype=torch.float64).pin_memory()
+        g = torch.empty(self.n_params, dtype=torch.float64).pin_memory()
+        qfuse.qf_train_step_host(self.handle, theta_h, x_h, y_h, B, _LOSS[loss], self.obs, out_loss, E, g,
+                                 self.ws, self.ws_bytes, self._stream())
+        self._fwd_id = next(_ids)
+        return out_loss, E, g
+
+
+class QFuseFn(torch.autograd.Function):
+    """E = QFuseFn.apply(theta, x, sim): fused forward; backward runs the fused
+    adjoint kernels with dL/dE from autograd (Eq. 4's chain-rule seed)."""
+
+    @staticmethod
+    def forward(ctx, theta, x, sim: Simulator):
+        theta_c = theta.detach().contiguous()
+        x_c = x.detach().contiguous()
+        E = sim.forward(theta_c, x_c)
+        ctx.sim = sim
+        ctx.fwd_id = sim._fwd_id
+        ctx.save_for_backward(theta_c, x_c)
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        theta, x = ctx.saved_tensors
+        sim: Simulator = ctx.sim
+        if sim._fwd_id != ctx.fwd_id:  # workspace was reused: recompute this forward
+            sim.forward(theta, x)
+        g = sim.backward(theta, x, gE)
+        return g.to(theta.dtype), None, None
+
+
+class HEA(torch.nn.Module):
+    """Hardware-efficient ansatz with RY(x) encoding, returning <O> per sample."""
+
+    def __init__(self, n: int, d: int, max_batch: int, *, obs="Z", entangler="chain", path="fused",
+                 ckpt_layers: int = 0, tile_bits: int = 0, device=None, init=None):
+        super().__init__()
+        self.sim = Simulator(n, d, max_batch, entangler=entangler, path=path, tile_bits=tile_bits,
+                             ckpt_layers=ckpt_layers, obs=obs, device=device)
+        theta = init if init is not None else torch.rand(3 * n * d) * (2 * torch.pi)
+        self.theta = torch.nn.Parameter(theta.to(device=self.sim.device, dtype=torch.float32))
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        return QFuseFn.apply(self.theta, x.to(device=self.sim.device, dtype=torch.float32), self.sim)

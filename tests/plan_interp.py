@@ -1,0 +1,173 @@
+"""CPU interpreter of the fused plan programs (GPU-path side, not the oracle).
+
+It executes the forward and backward programs exported by qf_plan_export with
+the same semantics as the pass kernels, but on whole complex128 state vectors,
+so the planner's fusion, ordering, checkpoint placement and reversal can be
+checked against the oracle without a GPU.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+OP_STEP, OP_U, OP_G, OP_CHAIN, OP_CZ, OP_CKPT, OP_ANCHOR = 1, 2, 3, 4, 5, 6, 7
+SRC_GENERATE, BUF_WORK, BUF_NONE = -1, -2, -3
+LAM_SEED, LAM_BUF = -1, -2
+RX, RY, RZ = 0, 1, 2
+
+
+def parse(words):
+    w = list(map(int, words))
+    i = 0
+    n_pass = w[i]; i += 1
+    passes = []
+    for _ in range(n_pass):
+        hdr = w[i:i + 11]; i += 11
+        gmap = w[i:i + 16]; i += 16
+        groups = [w[i + 4 * g:i + 4 * g + 4] for g in range(4)]; i += 16
+        keys = ["op_begin", "op_end", "psi_src", "psi_dst", "lam_src", "lam_dst", "flags", "K", "n_groups",
+                "outer_mask", "xm_local"]
+        d = dict(zip(keys, hdr))
+        d["gmap"] = gmap
+        d["groups"] = groups
+        passes.append(d)
+    n_ops = w[i]; i += 1
+    ops = [(w[i + 2 * k] & 0xFFFFFFFF, w[i + 2 * k + 1] & 0xFFFFFFFF) for k in range(n_ops)]
+    i += 2 * n_ops
+    nf = w[i]; i += 1
+    fused = []
+    for _ in range(nf):
+        cnt = w[i]; i += 1
+        fused.append([(w[i + 2 * j], w[i + 2 * j + 1]) for j in range(cnt)])
+        i += 2 * cnt
+    return passes, ops, fused
+
+
+def rot(kind, t):
+    c, s = np.cos(t / 2), np.sin(t / 2)
+    if kind == RX:
+        return np.array([[c, -1j * s], [-1j * s, c]])
+    if kind == RY:
+        return np.array([[c, -s], [s, c]], dtype=complex)
+    return np.array([[c - 1j * s, 0], [0, c + 1j * s]])
+
+
+PAULI = {RX: np.array([[0, 1], [1, 0]], complex), RY: np.array([[0, -1j], [1j, 0]]),
+         RZ: np.array([[1, 0], [0, -1]], complex)}
+
+
+def apply1(psi, n, q, u):
+    v = psi.reshape(2 ** (n - 1 - q), 2, 2 ** q)
+    return np.einsum("ab,xbz->xaz", u, v).reshape(-1)
+
+
+def chain_sign(n, links):
+    x = np.arange(2 ** n, dtype=np.int64)
+    par = np.zeros(2 ** n, dtype=np.int64)
+    for q in range(n):
+        if (links >> q) & 1:
+            par ^= ((x >> q) & 1) & ((x >> (q + 1)) & 1)
+    return 1 - 2 * par
+
+
+def cz_sign(n, c, t):
+    x = np.arange(2 ** n, dtype=np.int64)
+    return 1 - 2 * (((x >> c) & 1) & ((x >> t) & 1))
+
+
+def observable(psi, n, xm, zm):
+    x = np.arange(2 ** n, dtype=np.int64)
+    xp = x ^ xm
+    ny = bin(xm & zm).count("1")
+    par = np.array([bin(int(v) & zm).count("1") & 1 for v in xp])
+    return (1j ** ny) * (1 - 2 * par) * psi[xp]
+
+
+def encode(x, n, n_eff):
+    psi = np.zeros(2 ** n_eff, complex)
+    psi[0] = 1
+    for q in range(n):
+        psi = apply1(psi, n_eff, q, rot(RY, float(x[q])))
+    return psi
+
+
+def run_forward(fwd, n, n_eff, theta, xrow, xm, zm):
+    passes, ops, fused = fwd
+    slots = {}
+    work = None
+    E = None
+    for pd in passes:
+        src = pd["psi_src"]
+        psi = encode(xrow, n, n_eff) if src == SRC_GENERATE else (slots[src] if src >= 0 else work).copy()
+        k = pd["op_begin"]
+        group = None
+        while k < pd["op_end"]:
+            w0, w1 = ops[k]; k += 1
+            code = w0 & 15
+            if code == OP_STEP:
+                group = pd["groups"][(w0 >> 4) & 3]
+            elif code == OP_U:
+                r, m = (w0 >> 4) & 3, w0 >> 8
+                u = np.eye(2, dtype=complex)
+                for kind, p in fused[m]:
+                    u = rot(kind, float(theta[p])) @ u
+                psi = apply1(psi, n_eff, pd["gmap"][group[r]], u)
+            elif code == OP_CHAIN:
+                psi = psi * chain_sign(n_eff, w1)
+            elif code == OP_CZ:
+                psi = psi * cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
+            elif code == OP_CKPT:
+                slots[w1] = psi.copy()
+            else:
+                raise AssertionError(f"unexpected forward op {code}")
+        dst = pd["psi_dst"]
+        if dst >= 0:
+            slots[dst] = psi.copy()
+        elif dst == BUF_WORK:
+            work = psi.copy()
+        if pd["flags"] & 1:
+            E = float(np.real(np.vdot(psi, observable(psi, n_eff, xm, zm))))
+    return E, slots
+
+
+def run_backward(bwd, n_eff, theta, slot_param, slot_kind, slots, xm, zm, dLdE):
+    passes, ops, _ = bwd
+    grad_slot = np.zeros(len(slot_param))
+    work = lam_buf = None
+    seen = np.zeros(len(slot_param), int)
+    for pd in passes:
+        src = pd["psi_src"]
+        psi = (slots[src] if src >= 0 else work).copy()
+        lam = 2 * dLdE * observable(psi, n_eff, xm, zm) if pd["lam_src"] == LAM_SEED else lam_buf.copy()
+        k = pd["op_begin"]
+        group = None
+        while k < pd["op_end"]:
+            w0, w1 = ops[k]; k += 1
+            code = w0 & 15
+            if code == OP_STEP:
+                group = pd["groups"][(w0 >> 4) & 3]
+            elif code == OP_G:
+                r, kind, slot = (w0 >> 4) & 3, (w0 >> 6) & 3, w1
+                assert kind == slot_kind[slot]
+                q = pd["gmap"][group[r]]
+                seen[slot] += 1
+                Pp = apply1(psi, n_eff, q, PAULI[kind])
+                grad_slot[slot] += 0.5 * np.imag(np.vdot(lam, Pp))
+                ud = rot(kind, float(theta[slot_param[slot]])).conj().T
+                psi = apply1(psi, n_eff, q, ud)
+                lam = apply1(lam, n_eff, q, ud)
+            elif code == OP_CHAIN:
+                s = chain_sign(n_eff, w1)
+                psi, lam = psi * s, lam * s
+            elif code == OP_CZ:
+                s = cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
+                psi, lam = psi * s, lam * s
+            elif code == OP_ANCHOR:
+                psi = slots[w1].copy()
+            else:
+                raise AssertionError(f"unexpected backward op {code}")
+        if pd["psi_dst"] == BUF_WORK:
+            work = psi
+        if pd["lam_dst"] == LAM_BUF:
+            lam_buf = lam
+    assert np.all(seen == 1), "every gradient slot must appear exactly once"
+    return grad_slot

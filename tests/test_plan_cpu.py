@@ -1,0 +1,176 @@
+"""Host-side checks of the library: exported symbols, argument checking and
+the fusion planner (via a complex128 interpreter of the exported programs,
+compared with the oracle). No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2603_02804_gb300 import build as qbuild
+from paper_2603_02804_gb300 import qfuse
+from tests import plan_interp as pi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    qbuild.build()
+    return qfuse.load()
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "qfuse.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:qf_status|const char\*|int32_t)\s+(qf_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = header_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(qfuse.SIGNATURES), "binding and header must declare the same entry points"
+
+
+def test_version_and_error_string(lib):
+    assert qfuse.qf_version() >= 100
+    with pytest.raises(qfuse.QFError) as e:
+        qfuse.qf_hea_create(0, 3)
+    assert e.value.status == qfuse.QF_ERR_INVALID_ARG
+    assert "n_qubits" in qfuse.qf_last_error()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=31, d=2), dict(n=4, d=-1),
+])
+def test_hea_create_rejects(bad):
+    with pytest.raises(qfuse.QFError):
+        qfuse.qf_hea_create(bad["n"], bad["d"])
+
+
+def test_circuit_create_rejects_bad_gates():
+    with pytest.raises(qfuse.QFError):
+        qfuse.qf_circuit_create(3, [(qfuse.QF_GATE_RY, 3, -1, 0)], 1)   # qubit out of range
+    with pytest.raises(qfuse.QFError):
+        qfuse.qf_circuit_create(3, [(qfuse.QF_GATE_RY, 0, -1, 5)], 1)   # param out of range
+    with pytest.raises(qfuse.QFError):
+        qfuse.qf_circuit_create(3, [(qfuse.QF_GATE_CZ, 1, 1, -1)], 0)   # CZ on one qubit
+    with pytest.raises(qfuse.QFError):
+        qfuse.qf_circuit_create(3, [(7, 0, -1, 0)], 1)                   # unknown kind
+
+
+def test_plan_rejects_bad_options():
+    h = qfuse.qf_hea_create(5, 2)
+    try:
+        for kw in (dict(tile_bits=3), dict(tile_bits=13), dict(path=5), dict(ckpt_layers=-1)):
+            with pytest.raises(qfuse.QFError):
+                qfuse.qf_plan(h, 4, host_only=True, **kw)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan(h, -1, host_only=True)
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+def test_host_only_plan_refuses_device_calls():
+    h = qfuse.qf_hea_create(5, 2)
+    try:
+        ws = qfuse.qf_plan(h, 4, host_only=True)
+        assert ws > 0
+        with pytest.raises(qfuse.QFError) as e:
+            qfuse.qf_forward(h, 0, 0, 4, qfuse.pauli("Z", 5), 0, 0, ws)
+        assert e.value.status in (qfuse.QF_ERR_WORKSPACE, qfuse.QF_ERR_INVALID_ARG)
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, oracle_circ=None):
+    info = qfuse.qf_plan_info(handle)
+    n_eff = info["n_eff"]
+    fwd = pi.parse(qfuse.qf_plan_export(handle, 0))
+    bwd = pi.parse(qfuse.qf_plan_export(handle, 1))
+    # every rotation gate appears exactly once in the fused forward entries
+    entries = sorted((k, p) for run in fwd[2] for (k, p) in run)
+    assert entries == sorted(zip(slot_kind, slot_param))
+    pq = qfuse.pauli(obs, n)
+    gp, Ep = orc.gradient(oracle_circ, theta, x, obs, per_sample=True)
+    for b in range(len(x)):
+        E, slots = pi.run_forward(fwd, n, n_eff, theta, x[b], pq.x_mask, pq.z_mask)
+        assert abs(E - Ep[b]) < tol
+        gs = pi.run_backward(bwd, n_eff, theta, slot_param, slot_kind, slots, pq.x_mask, pq.z_mask, 1.0)
+        g = np.zeros(len(theta))
+        np.add.at(g, slot_param, gs)
+        assert np.max(np.abs(g - gp[b])) < tol
+    return info
+
+
+@pytest.mark.parametrize("n,d,K,ck", [
+    (1, 2, 0, 0), (3, 3, 0, 0), (4, 2, 0, 0), (5, 3, 0, 1), (6, 4, 0, 2), (8, 3, 0, 0),
+    (10, 3, 0, 1), (12, 2, 0, 1), (13, 2, 0, 1), (14, 3, 8, 1), (9, 4, 6, 2), (11, 2, 5, 0),
+])
+def test_fused_plan_matches_oracle_hea(n, d, K, ck):
+    rng = np.random.default_rng(1000 + 37 * n + d)
+    h = qfuse.qf_hea_create(n, d)
+    try:
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True)
+        theta = rng.uniform(0, 2 * np.pi, 3 * n * d).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
+        c = orc.hea(n, d)
+        obs = "Z" if n < 3 else "ZXY"[: min(3, n)]
+        P = 3 * n * d
+        slot_param = list(range(P))
+        slot_kind = [orc.RY if (p % 3) == 1 else orc.RZ for p in range(P)]
+        info = interp_check(h, n, theta, x, obs, slot_param, slot_kind, oracle_circ=c)
+        if n <= 12 and K == 0:
+            assert info["n_passes"] == 1
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fused_plan_matches_oracle_random_gate_list(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 9))
+    rows, kinds = [], [orc.RX, orc.RY, orc.RZ, orc.CZ]
+    n_params = 7
+    for _ in range(40):
+        k = int(rng.choice(kinds))
+        if k == orc.CZ:
+            a, b = rng.choice(n, 2, replace=False)
+            rows.append((k, int(a), int(b), -1))
+        else:
+            rows.append((k, int(rng.integers(n)), -1, int(rng.integers(n_params))))
+    h = qfuse.qf_circuit_create(n, rows, n_params)
+    try:
+        qfuse.qf_plan(h, 3, tile_bits=int(rng.choice([0, 4, 5])), ckpt_layers=1, host_only=True)
+        theta = rng.uniform(0, 2 * np.pi, n_params).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (3, n)).astype(np.float32).astype(np.float64)
+        c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=n_params)
+        slot_param = [r[3] for r in rows if r[0] != orc.CZ]
+        slot_kind = [r[0] for r in rows if r[0] != orc.CZ]
+        obs = "".join(rng.choice(list("IZ"), size=n))
+        interp_check(h, n, theta, x, obs, slot_param, slot_kind, oracle_circ=c)
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+def test_plan_statistics_for_benchmark_shapes():
+    """Planner shape on the benchmark circuits: n = 12 is one pass (whole state
+    in one CTA); n = 16 and n = 20 stream tiles with a few passes per layer."""
+    out = {}
+    for n, d in ((12, 20), (16, 100), (20, 50)):
+        h = qfuse.qf_hea_create(n, d)
+        try:
+            qfuse.qf_plan(h, 1, ckpt_layers=10, host_only=True)
+            out[n] = qfuse.qf_plan_info(h)
+        finally:
+            qfuse.qf_circuit_destroy(h)
+    assert out[12]["n_passes"] == 1
+    # about one fused 2x2 per qubit and layer (RZ RY RZ -> one op)
+    assert 12 * 20 <= out[12]["n_fused_ops"] <= 12 * 21
+    assert out[12]["n_steps"] <= 2 * 20
+    # light-cone wedges: several layers per pass over HBM
+    assert out[16]["n_passes"] <= 100 // 2
+    assert out[20]["n_passes"] <= 50 // 1
