@@ -199,6 +199,40 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
                              double* loss_h, double* E_h, double* grad_h, void* ws_d,
                              size_t ws_bytes, void* stream);
 
+/* Size of the fixed device scratch used by qf_train_step_noalloc. */
+#define QF_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
+
+/* qf_train_step without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * e.g. code embedded in a host application that owns the whole device-memory
+ * budget and forbids new allocations after start-up (a real-time control or
+ * data-taking loop, a plugin running inside another framework's memory
+ * pool), and so can neither call cudaMalloc nor size a workspace per call.
+ *
+ * Instead of a caller workspace, the step uses one fixed block of device
+ * memory of QF_NOALLOC_MAX_BYTES (32 MiB) that the library reserves on every
+ * GPU where its device code is loaded and holds until the process exits. The
+ * caller still passes inputs and outputs exactly as for qf_train_step
+ * (theta_d, x_d, y_d, loss_d, E_d, grad_d: device pointers). The circuit must
+ * have been planned with qf_plan; a host_only plan is enough, because this
+ * call copies the plan's tables into the fixed block itself. It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Limits and behaviour:
+ *  - plan tables plus the step's buffers for `batch` samples must fit in
+ *    QF_NOALLOC_MAX_BYTES; otherwise QF_ERR_WORKSPACE is returned and
+ *    qf_last_error() states the bytes needed.
+ *  - the first call on a device looks up the block's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - every call shares the one block and it keeps the last call's contents;
+ *    each kernel writes every scratch element it later reads, so nothing needs
+ *    clearing. Calls that overlap on the GPU (other streams, other threads)
+ *    race on the block: serialise them. */
+qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float* x_d,
+                                const float* y_d, int64_t batch, int32_t loss_kind, qf_pauli obs,
+                                double* loss_d, double* E_d, double* grad_d, void* stream);
+
 /* Kernels launched by the most recent qf_forward + qf_backward (+ qf_loss
  * inside qf_train_step) on this handle; for launch accounting. */
 qf_status qf_launch_count(const qf_circuit* c, int64_t* launches);

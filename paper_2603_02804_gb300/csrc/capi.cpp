@@ -35,6 +35,22 @@ struct Layout {
   int64_t rows = 0;         // partial rows per sample (tiles or chunks)
 };
 
+// Plan tables on the device.
+struct DevTables {
+  const uint2* fwd_ops = nullptr;
+  const uint2* bwd_ops = nullptr;
+  const int32_t* fuse_off = nullptr;
+  const qf::FuseGate* fuse_gates = nullptr;
+  const int32_t* slot_param = nullptr;
+  const int32_t* param_off = nullptr;
+  const int32_t* param_slots = nullptr;
+};
+
+// Byte offsets of each table inside the blob.
+struct BlobOffsets {
+  size_t fwd = 0, bwd = 0, foff = 0, fg = 0, sp = 0, po = 0, ps = 0;
+};
+
 }  // namespace
 
 struct qf_circuit {
@@ -47,14 +63,10 @@ struct qf_circuit {
   qf::FusedPlan fp;
   qf::PerGatePlan gp;
   Layout L;
-  void* d_tables = nullptr;
-  const uint2* d_fwd_ops = nullptr;
-  const uint2* d_bwd_ops = nullptr;
-  const int32_t* d_fuse_off = nullptr;
-  const qf::FuseGate* d_fuse_gates = nullptr;
-  const int32_t* d_slot_param = nullptr;
-  const int32_t* d_param_off = nullptr;
-  const int32_t* d_param_slots = nullptr;
+  std::vector<char> blob;   // host image of the plan's device tables
+  BlobOffsets bo;
+  void* d_tables = nullptr; // device copy of blob (qf_plan)
+  DevTables dt;
   int64_t launches = 0;
   int64_t call_launches = 0;
   // pass-kernel timing (qf_profile)
@@ -95,9 +107,7 @@ void prof_end(qf_circuit* c, int k, int dir, int64_t launches, cudaStream_t st) 
 void free_tables(qf_circuit* c) {
   if (c->d_tables) cudaFree(c->d_tables);
   c->d_tables = nullptr;
-  c->d_fwd_ops = c->d_bwd_ops = nullptr;
-  c->d_fuse_off = c->d_slot_param = c->d_param_off = c->d_param_slots = nullptr;
-  c->d_fuse_gates = nullptr;
+  c->dt = DevTables();
 }
 
 int n_eff_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_eff : c->gp.n_eff; }
@@ -150,44 +160,58 @@ size_t push_table(std::vector<char>& blob, const std::vector<T>& v) {
   return at;
 }
 
-qf_status upload(qf_circuit* c) {
-  std::vector<char> blob;
-  size_t o_fwd = 0, o_bwd = 0, o_foff = 0, o_fg = 0, o_sp, o_po, o_ps;
+// Serialise the plan's device tables into c->blob (host memory).
+void build_blob(qf_circuit* c) {
+  std::vector<char>& blob = c->blob;
+  blob.clear();
+  BlobOffsets& o = c->bo;
+  o = BlobOffsets();
   if (c->path == QF_PATH_FUSED) {
-    o_fwd = push_table(blob, c->fp.fwd_ops);
-    o_bwd = push_table(blob, c->fp.bwd_ops);
-    o_foff = push_table(blob, c->fp.fuse_off);
-    o_fg = push_table(blob, c->fp.fuse_gates);
-    o_sp = push_table(blob, c->fp.slot_param);
-    o_po = push_table(blob, c->fp.param_off);
-    o_ps = push_table(blob, c->fp.param_slots);
+    o.fwd = push_table(blob, c->fp.fwd_ops);
+    o.bwd = push_table(blob, c->fp.bwd_ops);
+    o.foff = push_table(blob, c->fp.fuse_off);
+    o.fg = push_table(blob, c->fp.fuse_gates);
+    o.sp = push_table(blob, c->fp.slot_param);
+    o.po = push_table(blob, c->fp.param_off);
+    o.ps = push_table(blob, c->fp.param_slots);
   } else {
-    o_sp = push_table(blob, c->gp.slot_param);
-    o_po = push_table(blob, c->gp.param_off);
-    o_ps = push_table(blob, c->gp.param_slots);
+    o.sp = push_table(blob, c->gp.slot_param);
+    o.po = push_table(blob, c->gp.param_off);
+    o.ps = push_table(blob, c->gp.param_slots);
   }
+  blob.resize(al(std::max<size_t>(blob.size(), 1)));
+}
+
+// Table pointers for a device copy of c->blob starting at base.
+DevTables tables_at(const qf_circuit* c, void* base) {
+  char* b = static_cast<char*>(base);
+  DevTables t;
+  if (c->path == QF_PATH_FUSED) {
+    t.fwd_ops = reinterpret_cast<const uint2*>(b + c->bo.fwd);
+    t.bwd_ops = reinterpret_cast<const uint2*>(b + c->bo.bwd);
+    t.fuse_off = reinterpret_cast<const int32_t*>(b + c->bo.foff);
+    t.fuse_gates = reinterpret_cast<const qf::FuseGate*>(b + c->bo.fg);
+  }
+  t.slot_param = reinterpret_cast<const int32_t*>(b + c->bo.sp);
+  t.param_off = reinterpret_cast<const int32_t*>(b + c->bo.po);
+  t.param_slots = reinterpret_cast<const int32_t*>(b + c->bo.ps);
+  return t;
+}
+
+qf_status upload(qf_circuit* c) {
   void* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, blob.size());
+  cudaError_t e = cudaMalloc(&d, c->blob.size());
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(QF_ERR_OOM, std::string("cudaMalloc of plan tables failed: ") + cudaGetErrorString(e));
   }
-  e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(d, c->blob.data(), c->blob.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d);
     return fail(QF_ERR_CUDA, std::string("plan upload failed: ") + cudaGetErrorString(e));
   }
-  char* b = static_cast<char*>(d);
   c->d_tables = d;
-  if (c->path == QF_PATH_FUSED) {
-    c->d_fwd_ops = reinterpret_cast<const uint2*>(b + o_fwd);
-    c->d_bwd_ops = reinterpret_cast<const uint2*>(b + o_bwd);
-    c->d_fuse_off = reinterpret_cast<const int32_t*>(b + o_foff);
-    c->d_fuse_gates = reinterpret_cast<const qf::FuseGate*>(b + o_fg);
-  }
-  c->d_slot_param = reinterpret_cast<const int32_t*>(b + o_sp);
-  c->d_param_off = reinterpret_cast<const int32_t*>(b + o_po);
-  c->d_param_slots = reinterpret_cast<const int32_t*>(b + o_ps);
+  c->dt = tables_at(c, d);
   return QF_OK;
 }
 
@@ -244,18 +268,17 @@ bool local_xmask(const qf::PassDesc& pd, uint32_t xm, uint32_t* out) {
   return true;
 }
 
-qf_status fused_forward(qf_circuit* c, const float* theta, const float* x, int64_t B, const Obs& o,
-                        double* E, void* ws, cudaStream_t st) {
+qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, const float* x,
+                        int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st) {
   const qf::FusedPlan& P = c->fp;
-  const Layout& L = c->L;
   qf::PrepArgs pa{};
   pa.theta = theta;
   pa.n_fused = (int32_t)P.fuse_off.size() - 1;
-  pa.fuse_off = c->d_fuse_off;
-  pa.fuse_gates = c->d_fuse_gates;
+  pa.fuse_off = T.fuse_off;
+  pa.fuse_gates = T.fuse_gates;
   pa.mats = at<float4>(ws, L.mats);
   pa.n_slots = P.n_slots;
-  pa.slot_param = c->d_slot_param;
+  pa.slot_param = T.slot_param;
   pa.cs = at<float2>(ws, L.cs);
   pa.x = x;
   pa.B = B;
@@ -268,7 +291,7 @@ qf_status fused_forward(qf_circuit* c, const float* theta, const float* x, int64
   a.n_eff = P.n_eff;
   a.tps_log2 = P.n_eff - P.K;
   a.B = B;
-  a.ops = c->d_fwd_ops;
+  a.ops = T.fwd_ops;
   a.mats = pa.mats;
   a.cs = pa.cs;
   a.enc = pa.enc;
@@ -296,15 +319,14 @@ qf_status fused_forward(qf_circuit* c, const float* theta, const float* x, int64
   return QF_OK;
 }
 
-qf_status fused_backward(qf_circuit* c, const float* theta, int64_t B, const Obs& o, const double* dLdE,
-                         double* grad, int per_sample, void* ws, cudaStream_t st) {
+qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, int64_t B,
+                         const Obs& o, const double* dLdE, double* grad, int per_sample, void* ws, cudaStream_t st) {
   const qf::FusedPlan& P = c->fp;
-  const Layout& L = c->L;
   qf::PrepArgs pa{};
   pa.theta = theta;
   pa.n_fused = 0;
   pa.n_slots = P.n_slots;
-  pa.slot_param = c->d_slot_param;
+  pa.slot_param = T.slot_param;
   pa.cs = at<float2>(ws, L.cs);
   pa.B = 0;
   pa.n = c->circ.n;
@@ -315,7 +337,7 @@ qf_status fused_backward(qf_circuit* c, const float* theta, int64_t B, const Obs
   a.n_eff = P.n_eff;
   a.tps_log2 = P.n_eff - P.K;
   a.B = B;
-  a.ops = c->d_bwd_ops;
+  a.ops = T.bwd_ops;
   a.cs = pa.cs;
   a.work = at<float2>(ws, L.work);
   a.lam = at<float2>(ws, L.lam);
@@ -344,8 +366,8 @@ qf_status fused_backward(qf_circuit* c, const float* theta, int64_t B, const Obs
   g.slot_stride = P.n_slots;
   g.slot_step = 1;
   g.n_params = c->circ.n_params;
-  g.param_off = c->d_param_off;
-  g.param_slots = c->d_param_slots;
+  g.param_off = T.param_off;
+  g.param_slots = T.param_slots;
   g.per_sample = per_sample;
   g.grad = grad;
   QF_CU(qf::launch_g_reduce(g, st));
@@ -353,14 +375,13 @@ qf_status fused_backward(qf_circuit* c, const float* theta, int64_t B, const Obs
   return QF_OK;
 }
 
-qf_status pg_forward(qf_circuit* c, const float* theta, const float* x, int64_t B, const Obs& o, double* E,
-                     void* ws, cudaStream_t st) {
+qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, const float* x,
+                     int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st) {
   const qf::PerGatePlan& P = c->gp;
-  const Layout& L = c->L;
   qf::PrepArgs pa{};
   pa.theta = theta;
   pa.n_slots = P.n_slots;
-  pa.slot_param = c->d_slot_param;
+  pa.slot_param = T.slot_param;
   pa.cs = at<float2>(ws, L.cs);
   pa.x = x;
   pa.B = B;
@@ -395,14 +416,13 @@ qf_status pg_forward(qf_circuit* c, const float* theta, const float* x, int64_t 
   return QF_OK;
 }
 
-qf_status pg_backward(qf_circuit* c, const float* theta, int64_t B, const Obs& o, const double* dLdE,
-                      double* grad, int per_sample, void* ws, cudaStream_t st) {
+qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, int64_t B,
+                      const Obs& o, const double* dLdE, double* grad, int per_sample, void* ws, cudaStream_t st) {
   const qf::PerGatePlan& P = c->gp;
-  const Layout& L = c->L;
   qf::PrepArgs pa{};
   pa.theta = theta;
   pa.n_slots = P.n_slots;
-  pa.slot_param = c->d_slot_param;
+  pa.slot_param = T.slot_param;
   pa.cs = at<float2>(ws, L.cs);
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
@@ -439,8 +459,8 @@ qf_status pg_backward(qf_circuit* c, const float* theta, int64_t B, const Obs& o
   g.slot_stride = 1;
   g.slot_step = B * L.rows;
   g.n_params = c->circ.n_params;
-  g.param_off = c->d_param_off;
-  g.param_slots = c->d_param_slots;
+  g.param_off = T.param_off;
+  g.param_slots = T.param_slots;
   g.per_sample = per_sample;
   g.grad = grad;
   QF_CU(qf::launch_g_reduce(g, st));
@@ -541,6 +561,7 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
       c->fp = qf::FusedPlan();
     }
     c->L = make_layout(c, batch);
+    build_blob(c);
   } catch (const std::bad_alloc&) {
     return fail(QF_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
@@ -631,8 +652,8 @@ qf_status qf_forward(qf_circuit* c, const float* theta_d, const float* x_d, int6
   if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
   c->call_launches = 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  s = c->path == QF_PATH_FUSED ? fused_forward(c, theta_d, x_d, batch, o, E_d, ws_d, st)
-                               : pg_forward(c, theta_d, x_d, batch, o, E_d, ws_d, st);
+  s = c->path == QF_PATH_FUSED ? fused_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st)
+                               : pg_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st);
   c->launches = c->call_launches;
   return s;
 }
@@ -649,8 +670,9 @@ qf_status qf_backward(qf_circuit* c, const float* theta_d, const float* x_d, int
   if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
   c->call_launches = 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  s = c->path == QF_PATH_FUSED ? fused_backward(c, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st)
-                               : pg_backward(c, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st);
+  s = c->path == QF_PATH_FUSED
+          ? fused_backward(c, c->dt, c->L, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st)
+          : pg_backward(c, c->dt, c->L, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st);
   c->launches += c->call_launches;
   return s;
 }
@@ -703,6 +725,50 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
   if (P) QF_CU(cudaMemcpyAsync(grad_h, at<double>(ws_d, L.grad), (size_t)P * 8, cudaMemcpyDeviceToHost, st));
   QF_CU(cudaStreamSynchronize(st));
   return QF_OK;
+}
+
+qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float* x_d, const float* y_d,
+                                int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d,
+                                double* grad_d, void* stream) {
+  if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
+  if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan (call qf_plan, host_only is enough)");
+  if (batch < 0) return fail(QF_ERR_INVALID_ARG, "negative batch");
+  if (loss_kind != QF_LOSS_SUM && loss_kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
+  if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
+      (!grad_d && c->circ.n_params > 0) || (loss_kind == QF_LOSS_MSE && batch > 0 && !y_d))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  Obs o;
+  qf_status s = check_obs(c, obs, &o);
+  if (s != QF_OK) return s;
+  // buffers for this batch behind the plan tables, all inside the fixed block
+  const Layout L = make_layout(c, batch);
+  const size_t tbytes = c->blob.size();
+  const size_t need = tbytes + L.total;
+  if (need > (size_t)QF_NOALLOC_MAX_BYTES)
+    return fail(QF_ERR_WORKSPACE, "qf_train_step_noalloc needs " + std::to_string(need) +
+                                      " bytes of scratch for this circuit and batch, more than the fixed " +
+                                      std::to_string((size_t)QF_NOALLOC_MAX_BYTES) +
+                                      " (QF_NOALLOC_MAX_BYTES); use a smaller batch or qf_train_step");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QF_ERR_CUDA, std::string("pending CUDA error: ") + cudaGetErrorString(e));
+  void* scratch = nullptr;
+  size_t cap = 0;
+  QF_CU(qf::noalloc_scratch(&scratch, &cap));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  QF_CU(cudaMemcpyAsync(scratch, c->blob.data(), tbytes, cudaMemcpyHostToDevice, st));
+  const DevTables T = tables_at(c, scratch);
+  void* ws = static_cast<char*>(scratch) + tbytes;
+  c->call_launches = 0;
+  s = c->path == QF_PATH_FUSED ? fused_forward(c, T, L, theta_d, x_d, batch, o, E_d, ws, st)
+                               : pg_forward(c, T, L, theta_d, x_d, batch, o, E_d, ws, st);
+  if (s != QF_OK) return s;
+  double* dLdE = at<double>(ws, L.dLdE);
+  QF_CU(qf::launch_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, st));
+  c->call_launches++;
+  s = c->path == QF_PATH_FUSED ? fused_backward(c, T, L, theta_d, batch, o, dLdE, grad_d, 0, ws, st)
+                               : pg_backward(c, T, L, theta_d, batch, o, dLdE, grad_d, 0, ws, st);
+  c->launches = c->call_launches;
+  return s;
 }
 
 qf_status qf_profile(qf_circuit* c, int32_t on) {

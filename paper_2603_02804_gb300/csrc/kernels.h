@@ -83,4 +83,8 @@ cudaError_t pg_rot_bwd(const PerGateArgs& a, int kind, int q, const float2* cs, 
 cudaError_t pg_copy(const float2* src, float2* dst, int64_t n, cudaStream_t st);
 int32_t pg_chunks(int32_t n_eff);
 
+// Device address of the fixed scratch block on the current device
+// (QF_NOALLOC_MAX_BYTES bytes); looked up once per device.
+cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
+
 }  // namespace qf

@@ -69,6 +69,7 @@ SIGNATURES = {
     "qf_loss": ([_i32, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
     "qf_train_step": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
     "qf_train_step_host": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
+    "qf_train_step_noalloc": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp], _i32),
     "qf_launch_count": ([_vp, ctypes.POINTER(_i64)], _i32),
     "qf_profile": ([_vp, _i32], _i32),
     "qf_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
@@ -202,6 +203,14 @@ def qf_train_step(handle, theta, x, y, batch, loss_kind, obs, loss, E, grad, ws,
 def qf_train_step_host(handle, theta, x, y, batch, loss_kind, obs, loss, E, grad, ws, ws_bytes, stream=None):
     _check(load().qf_train_step_host(handle, _ptr(theta), _ptr(x), _ptr(y), batch, loss_kind, obs, _ptr(loss),
                                      _ptr(E), _ptr(grad), _ptr(ws), ws_bytes, _stream(stream)))
+
+
+def qf_train_step_noalloc(handle, theta, x, y, batch, loss_kind, obs, loss, E, grad, stream=None) -> None:
+    _check(load().qf_train_step_noalloc(handle, _ptr(theta), _ptr(x), _ptr(y), batch, loss_kind, obs, _ptr(loss),
+                                        _ptr(E), _ptr(grad), _stream(stream)))
+
+
+QF_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 
 
 def qf_launch_count(handle) -> int:
