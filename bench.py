@@ -66,13 +66,14 @@ def load_peaks():
 
 
 def algorithmic_flops(n, d, B):
-    """Method arithmetic per step in FP32 flops (a fused multiply-add = 2):
-    forward: one fused complex 2x2 per qubit and layer = 16 real FMA per pair
-    of amplitudes; adjoint: per rotation, un-apply psi (8 FMA per pair),
-    Im<lambda|P|psi> (4 FMA per pair), un-apply lambda (8 FMA per pair)."""
+    """Method arithmetic per step in FP32 flops (real multiplies + adds):
+    forward: one fused complex 2x2 per qubit and layer, 4 complex multiplies
+    and 2 complex adds = 28 flops per pair of amplitudes; adjoint: per
+    rotation, un-apply psi (12 flops per pair), un-apply lambda (12) and
+    Im<lambda|P|psi> accumulated (8) = 32 flops per pair."""
     pairs = B * (1 << (n - 1))
-    fwd = n * d * pairs * 16 * 2
-    bwd = 3 * n * d * pairs * 20 * 2
+    fwd = n * d * pairs * 28
+    bwd = 3 * n * d * pairs * 32
     return fwd, bwd
 
 
