@@ -93,7 +93,10 @@ typedef struct {
                           0 = 10 layers; a value >= depth keeps only psi_M       */
   int32_t host_only;   /* 1 = build the plan on the host only (no device tables;
                           forward/backward then fail with QF_ERR_WORKSPACE)      */
-  int32_t reserved[12];
+  int32_t program;     /* fused: 0 = round steps when the circuit allows (RZ/RY
+                          rotations, CZ on neighbouring qubits, tile >= 7 qubits),
+                          else generic steps; 1 = always generic steps           */
+  int32_t reserved[11];
 } qf_plan_opts;
 
 /* Summary of a plan (host-side numbers). */
@@ -152,11 +155,13 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
 
 /* Export the forward (direction 0) or backward (1) program for inspection:
  * writes up to cap int32 words to buf (may be NULL) and the full length to
- * *len. Layout: [n_passes, then per pass: 11 header words (op_begin, op_end,
- * psi_src, psi_dst, lam_src, lam_dst, flags, K, n_groups, outer_mask,
- * xm_local), 16 gmap words, 16 group words], then [n_ops, 2 words per op],
- * then [n_fused, per fused op: count, then count (kind, param) pairs].
- * Host only. */
+ * *len. Layout: [program kind (0 generic steps, 1 round steps), n_passes,
+ * then per pass: 11 header words (op_begin, op_end, psi_src, psi_dst,
+ * lam_src, lam_dst, flags, K, n_groups, outer_mask, xm_local), 16 gmap
+ * words, 16 group words], then [n_ops, 2 words per op], then [n_fused, per
+ * fused op: count, then count (kind, param) pairs], then [n round words of
+ * this direction, the words], then [n_terms, per gradient term: kind, count,
+ * count parameters]. Host only. */
 qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf,
                          int64_t cap, int64_t* len);
 

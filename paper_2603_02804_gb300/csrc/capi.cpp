@@ -41,14 +41,17 @@ struct DevTables {
   const uint2* bwd_ops = nullptr;
   const int32_t* fuse_off = nullptr;
   const qf::FuseGate* fuse_gates = nullptr;
-  const int32_t* slot_param = nullptr;
-  const int32_t* param_off = nullptr;
-  const int32_t* param_slots = nullptr;
+  const uint4* fwd_rounds = nullptr;
+  const uint4* bwd_rounds = nullptr;
+  const int32_t* term_off = nullptr;      // CSR term -> parameters
+  const int32_t* term_params = nullptr;
+  const int32_t* param_off = nullptr;     // CSR parameter -> terms
+  const int32_t* param_terms = nullptr;
 };
 
 // Byte offsets of each table inside the blob.
 struct BlobOffsets {
-  size_t fwd = 0, bwd = 0, foff = 0, fg = 0, sp = 0, po = 0, ps = 0;
+  size_t fwd = 0, bwd = 0, foff = 0, fg = 0, frd = 0, brd = 0, to = 0, tp = 0, po = 0, ps = 0;
 };
 
 }  // namespace
@@ -111,7 +114,7 @@ void free_tables(qf_circuit* c) {
 }
 
 int n_eff_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_eff : c->gp.n_eff; }
-int n_slots_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_slots : c->gp.n_slots; }
+int n_slots_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_terms : c->gp.n_slots; }
 
 Layout make_layout(const qf_circuit* c, int64_t B) {
   Layout L;
@@ -171,11 +174,17 @@ void build_blob(qf_circuit* c) {
     o.bwd = push_table(blob, c->fp.bwd_ops);
     o.foff = push_table(blob, c->fp.fuse_off);
     o.fg = push_table(blob, c->fp.fuse_gates);
-    o.sp = push_table(blob, c->fp.slot_param);
+    o.frd = push_table(blob, c->fp.fwd_rounds);
+    o.brd = push_table(blob, c->fp.bwd_rounds);
+    o.to = push_table(blob, c->fp.term_off);
+    o.tp = push_table(blob, c->fp.term_params);
     o.po = push_table(blob, c->fp.param_off);
-    o.ps = push_table(blob, c->fp.param_slots);
+    o.ps = push_table(blob, c->fp.param_terms);
   } else {
-    o.sp = push_table(blob, c->gp.slot_param);
+    std::vector<int32_t> toff(c->gp.n_slots + 1);
+    for (int t = 0; t <= c->gp.n_slots; ++t) toff[t] = t;
+    o.to = push_table(blob, toff);
+    o.tp = push_table(blob, c->gp.slot_param);
     o.po = push_table(blob, c->gp.param_off);
     o.ps = push_table(blob, c->gp.param_slots);
   }
@@ -191,10 +200,13 @@ DevTables tables_at(const qf_circuit* c, void* base) {
     t.bwd_ops = reinterpret_cast<const uint2*>(b + c->bo.bwd);
     t.fuse_off = reinterpret_cast<const int32_t*>(b + c->bo.foff);
     t.fuse_gates = reinterpret_cast<const qf::FuseGate*>(b + c->bo.fg);
+    t.fwd_rounds = reinterpret_cast<const uint4*>(b + c->bo.frd);
+    t.bwd_rounds = reinterpret_cast<const uint4*>(b + c->bo.brd);
   }
-  t.slot_param = reinterpret_cast<const int32_t*>(b + c->bo.sp);
+  t.term_off = reinterpret_cast<const int32_t*>(b + c->bo.to);
+  t.term_params = reinterpret_cast<const int32_t*>(b + c->bo.tp);
   t.param_off = reinterpret_cast<const int32_t*>(b + c->bo.po);
-  t.param_slots = reinterpret_cast<const int32_t*>(b + c->bo.ps);
+  t.param_terms = reinterpret_cast<const int32_t*>(b + c->bo.ps);
   return t;
 }
 
@@ -277,8 +289,9 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.fuse_off = T.fuse_off;
   pa.fuse_gates = T.fuse_gates;
   pa.mats = at<float4>(ws, L.mats);
-  pa.n_slots = P.n_slots;
-  pa.slot_param = T.slot_param;
+  pa.n_terms = n_slots_of(c);
+  pa.term_off = T.term_off;
+  pa.term_params = T.term_params;
   pa.cs = at<float2>(ws, L.cs);
   pa.x = x;
   pa.B = B;
@@ -292,6 +305,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.tps_log2 = P.n_eff - P.K;
   a.B = B;
   a.ops = T.fwd_ops;
+  a.rounds = P.rounds ? T.fwd_rounds : nullptr;
   a.mats = pa.mats;
   a.cs = pa.cs;
   a.enc = pa.enc;
@@ -303,7 +317,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.y_count = o.y;
   a.e_part = at<double>(ws, L.epart);
   a.g_part = at<double>(ws, L.gpart);
-  a.n_slots = P.n_slots;
+  a.n_slots = P.n_terms;
   const int prof = prof_begin(c, st);
   for (size_t pi = 0; pi < P.fwd.size(); ++pi) {
     a.pd = P.fwd[pi];
@@ -325,8 +339,9 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   qf::PrepArgs pa{};
   pa.theta = theta;
   pa.n_fused = 0;
-  pa.n_slots = P.n_slots;
-  pa.slot_param = T.slot_param;
+  pa.n_terms = n_slots_of(c);
+  pa.term_off = T.term_off;
+  pa.term_params = T.term_params;
   pa.cs = at<float2>(ws, L.cs);
   pa.B = 0;
   pa.n = c->circ.n;
@@ -338,6 +353,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.tps_log2 = P.n_eff - P.K;
   a.B = B;
   a.ops = T.bwd_ops;
+  a.rounds = P.rounds ? T.bwd_rounds : nullptr;
   a.cs = pa.cs;
   a.work = at<float2>(ws, L.work);
   a.lam = at<float2>(ws, L.lam);
@@ -348,7 +364,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.dLdE = dLdE;
   a.e_part = at<double>(ws, L.epart);
   a.g_part = at<double>(ws, L.gpart);
-  a.n_slots = P.n_slots;
+  a.n_slots = P.n_terms;
   const int prof = prof_begin(c, st);
   for (size_t pi = 0; pi < P.bwd.size(); ++pi) {
     a.pd = P.bwd[pi];
@@ -363,11 +379,11 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   g.g_part = a.g_part;
   g.B = B;
   g.tps = L.rows;
-  g.slot_stride = P.n_slots;
+  g.slot_stride = P.n_terms;
   g.slot_step = 1;
   g.n_params = c->circ.n_params;
   g.param_off = T.param_off;
-  g.param_slots = T.param_slots;
+  g.param_slots = T.param_terms;
   g.per_sample = per_sample;
   g.grad = grad;
   QF_CU(qf::launch_g_reduce(g, st));
@@ -380,8 +396,9 @@ qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const f
   const qf::PerGatePlan& P = c->gp;
   qf::PrepArgs pa{};
   pa.theta = theta;
-  pa.n_slots = P.n_slots;
-  pa.slot_param = T.slot_param;
+  pa.n_terms = n_slots_of(c);
+  pa.term_off = T.term_off;
+  pa.term_params = T.term_params;
   pa.cs = at<float2>(ws, L.cs);
   pa.x = x;
   pa.B = B;
@@ -421,8 +438,9 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
   const qf::PerGatePlan& P = c->gp;
   qf::PrepArgs pa{};
   pa.theta = theta;
-  pa.n_slots = P.n_slots;
-  pa.slot_param = T.slot_param;
+  pa.n_terms = n_slots_of(c);
+  pa.term_off = T.term_off;
+  pa.term_params = T.term_params;
   pa.cs = at<float2>(ws, L.cs);
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
@@ -460,7 +478,7 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
   g.slot_step = B * L.rows;
   g.n_params = c->circ.n_params;
   g.param_off = T.param_off;
-  g.param_slots = T.param_slots;
+  g.param_slots = T.param_terms;
   g.per_sample = per_sample;
   g.grad = grad;
   QF_CU(qf::launch_g_reduce(g, st));
@@ -543,6 +561,7 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
   if (o.tile_bits != 0 && (o.tile_bits < 4 || o.tile_bits > 12))
     return fail(QF_ERR_INVALID_ARG, "tile_bits must be 0 or in 4..12");
   if (o.ckpt_layers < 0) return fail(QF_ERR_INVALID_ARG, "negative checkpoint interval");
+  if (o.program != 0 && o.program != 1) return fail(QF_ERR_INVALID_ARG, "program must be 0 or 1");
   try {
     free_tables(c);
     c->planned = false;
@@ -553,6 +572,7 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     qf::PlanRequest req;
     req.tile_bits = o.tile_bits;
     req.ckpt_layers = c->ckpt_layers;
+    req.generic = o.program == 1;
     if (c->path == QF_PATH_FUSED) {
       c->fp = qf::plan_fused(c->circ, req);
       c->gp = qf::PerGatePlan();
@@ -589,7 +609,7 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
   info->state_bytes = c->L.state_elems * 8;
   if (c->path == QF_PATH_FUSED) {
     info->n_eff = c->fp.n_eff;
-    info->n_slots = c->fp.n_slots;
+    info->n_slots = c->fp.n_terms;
     info->tile_bits = c->fp.K;
     info->n_passes = (int32_t)c->fp.fwd.size();
     info->n_steps = c->fp.n_steps;
@@ -617,6 +637,7 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, i
   const auto& passes = direction == 0 ? P.fwd : P.bwd;
   const auto& ops = direction == 0 ? P.fwd_ops : P.bwd_ops;
   std::vector<int32_t> w;
+  w.push_back(P.rounds ? 1 : 0);
   w.push_back((int32_t)passes.size());
   for (const qf::PassDesc& pd : passes) {
     const int32_t hdr[11] = {pd.op_begin, pd.op_end, pd.psi_src, pd.psi_dst, pd.lam_src, pd.lam_dst,
@@ -636,6 +657,19 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, i
       w.push_back(P.fuse_gates[j].kind);
       w.push_back(P.fuse_gates[j].param);
     }
+  }
+  if (direction == 0) {
+    w.push_back((int32_t)P.fwd_rounds.size());
+    for (uint32_t v : P.fwd_rounds) w.push_back((int32_t)v);
+  } else {
+    w.push_back((int32_t)P.bwd_rounds.size());
+    for (int32_t v : P.bwd_rounds) w.push_back(v);
+  }
+  w.push_back(P.n_terms);
+  for (int t = 0; t < P.n_terms; ++t) {
+    w.push_back(P.term_kind[t]);
+    w.push_back(P.term_off[t + 1] - P.term_off[t]);
+    for (int j = P.term_off[t]; j < P.term_off[t + 1]; ++j) w.push_back(P.term_params[j]);
   }
   *len = (int64_t)w.size();
   if (buf) memcpy(buf, w.data(), sizeof(int32_t) * (size_t)std::min<int64_t>(cap, (int64_t)w.size()));

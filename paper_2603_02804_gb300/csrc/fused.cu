@@ -130,11 +130,134 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, uint32_t k) {
   }
 }
 
+// ---- round programs: pending CZ signs ------------------------------------------
+// A thread's 16 registers hold psi~ with psi = D psi~, where D = (-1)^(c0 +
+// sum_r A_r j_r) is the part of the CZ signs that is constant or linear in the
+// register index j (bit 4 of D: c0, bits 0..3: A). D commutes with every
+// diagonal gate; a gate on register bit r only sees the factor Z_r^(A_r),
+// which is folded into that gate. CZs between two register bits (quadratic in
+// j) are applied to the registers directly.
+//
+// Links L of one round, thread base index gb (register bits zero), register
+// bit positions p[r]: x = gb ^ y(j) with disjoint supports, so each link q
+// contributes gb_q gb_{q+1} (constant), gb_{q} y_{q+1} or y_q gb_{q+1} (linear)
+// or y_q y_{q+1} (between register bits).
+template <bool BWD>
+__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4],
+                                              uint32_t& D, float2 (&r)[16], float2 (&l)[16]) {
+  const uint32_t t1 = L & gb, t2 = L & (gb >> 1);
+  const uint32_t u = (t1 << 1) ^ t2;
+  const uint32_t A = ((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) |
+                     (((u >> p[3]) & 1u) << 3);
+  D ^= A | ((__popc(t2 & gb) & 1u) << 4);
+#pragma unroll
+  for (int rb = 0; rb < 3; ++rb) {
+    const int f = (int)(((bbits >> rb) & 1u) << 31);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (((j >> rb) & 3) != 3) continue;
+      r[j].x = __int_as_float(__float_as_int(r[j].x) ^ f);
+      r[j].y = __int_as_float(__float_as_int(r[j].y) ^ f);
+      if (BWD) {
+        l[j].x = __int_as_float(__float_as_int(l[j].x) ^ f);
+        l[j].y = __int_as_float(__float_as_int(l[j].y) ^ f);
+      }
+    }
+  }
+}
+
+// Multiply the registers by D (end of a step).
+template <bool BWD>
+__device__ __forceinline__ void apply_pending(uint32_t D, float2 (&r)[16], float2 (&l)[16]) {
+  uint32_t S = (D & 16u) ? 0xFFFFu : 0u;
+  S ^= (D & 1u) ? 0xAAAAu : 0u;
+  S ^= (D & 2u) ? 0xCCCCu : 0u;
+  S ^= (D & 4u) ? 0xF0F0u : 0u;
+  S ^= (D & 8u) ? 0xFF00u : 0u;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int f = (int)((S << (31 - j)) & 0x80000000u);
+    r[j].x = __int_as_float(__float_as_int(r[j].x) ^ f);
+    r[j].y = __int_as_float(__float_as_int(r[j].y) ^ f);
+    if (BWD) {
+      l[j].x = __int_as_float(__float_as_int(l[j].x) ^ f);
+      l[j].y = __int_as_float(__float_as_int(l[j].y) ^ f);
+    }
+  }
+}
+
+// Forward item on register bit R: U' = Z^a U Z^a (negated off-diagonal).
+template <int R>
+__device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 m0, float4 m1, uint32_t a) {
+  const int f = (int)(a << 31);
+  m0.z = __int_as_float(__float_as_int(m0.z) ^ f);
+  m0.w = __int_as_float(__float_as_int(m0.w) ^ f);
+  m1.x = __int_as_float(__float_as_int(m1.x) ^ f);
+  m1.y = __int_as_float(__float_as_int(m1.y) ^ f);
+  apply_u<R>(r, m0, m1);
+}
+
+// Backward item on register bit R: the merged RZ run (phase (cz, sz)), then
+// the RY ((cy, sy)); with a pending Z_R the RY un-applies as RY(+theta) and
+// its Im<lambda|Y|psi> changes sign. Returns both partials.
+template <int R>
+__device__ __forceinline__ void item_bwd(float2 (&p)[16], float2 (&l)[16], float2 czs, float2 cys, uint32_t a,
+                                         float& gz, float& gy) {
+  gz = bwd_gate<R, G_RZ>(p, l, czs.x, czs.y);
+  const int f = (int)(a << 31);
+  const float s = __int_as_float(__float_as_int(cys.y) ^ f);
+  gy = __int_as_float(__float_as_int(bwd_gate<R, G_RY>(p, l, cys.x, s)) ^ f);
+}
+
+// Reduce 8 per-thread values over `lanes` lanes (8, 16 or 32; whole-warp
+// call). Afterwards lane holds the lanes-sum of value *idx; the lanes with
+// (lane & (lanes/8 - 1)) == 0 hold the 8 distinct values.
+__device__ __forceinline__ float butterfly8(float (&v)[8], int lanes, int lane, int& idx) {
+  int o = lanes >> 1;
+  bool up = (lane & o) != 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = up ? v[i] : v[i + 4];
+    const float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+  idx = up ? 4 : 0;
+  o >>= 1;
+  up = (lane & o) != 0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = up ? v[i] : v[i + 2];
+    const float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+  idx += up ? 2 : 0;
+  o >>= 1;
+  up = (lane & o) != 0;
+  {
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+  idx += up ? 1 : 0;
+  for (o >>= 1; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
+
+__device__ __forceinline__ int32_t pick_term(uint4 tz, uint4 ty, int idx) {
+  const uint4 t = (idx & 4) ? ty : tz;
+  const uint32_t lo = (idx & 1) ? t.y : t.x, hi = (idx & 1) ? t.w : t.z;
+  return (int32_t)((idx & 2) ? hi : lo);
+}
+
+__device__ __forceinline__ float2 term_cs(const float2* cs, uint32_t t) {
+  return (int32_t)t >= 0 ? __ldg(cs + t) : make_float2(1.f, 0.f);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
-template <bool BWD>
-__global__ void __launch_bounds__(kThreads) pass_kernel(const PassArgs a) {
+template <bool BWD, bool ROUNDS>
+__global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const PassArgs a) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ uint32_t s_lg[256];
   __shared__ float s_red[2][kThreads / 32][kMaxStepSlots];
@@ -242,7 +365,89 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const PassArgs a) {
   while (pc < pd.op_end) {
     const uint2 op = __ldg(ops + pc++);
     const uint32_t code = op.x & 15u;
-    if (code == OP_STEP) {
+    if (ROUNDS && code == OP_STEP) {
+      // ---- round step: straight-line rounds over the 4 register bits
+      const int g = (op.x >> 4) & 3;
+      const int nr = (op.x >> 8) & 0xffff;
+      const uint32_t rb0 = op.y;
+      const uint32_t lb0 = s_grp[g][0], lb1 = s_grp[g][1], lb2 = s_grp[g][2], lb3 = s_grp[g][3];
+      const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
+      const uint32_t base = pdep32(tau, ((1u << K) - 1u) & ~gm);
+      const uint32_t pb = swz(base);
+      const uint32_t so[4] = {swz(1u << lb0), swz(1u << lb1), swz(1u << lb2), swz(1u << lb3)};
+      const uint32_t gb = gidx(base);
+      const uint32_t pos[4] = {s_gmap[lb0], s_gmap[lb1], s_gmap[lb2], s_gmap[lb3]};
+      float2 r[16];
+      float2 l[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        r[j] = tp[pb ^ reg_off(j, so)];
+        if (BWD) l[j] = tl[pb ^ reg_off(j, so)];
+      }
+      uint32_t D = 0;
+#pragma unroll 1
+      for (int k = 0; k < nr; ++k) {
+        if (!BWD) {
+          const uint4* rec = a.rounds + (size_t)(rb0 + k) * (kFwdRoundWords / 4);
+          const uint4 mi = __ldg(rec), lk = __ldg(rec + 1);
+          const float4 u00 = __ldg(a.mats + 2 * mi.x), u01 = __ldg(a.mats + 2 * mi.x + 1);
+          const float4 u10 = __ldg(a.mats + 2 * mi.y), u11 = __ldg(a.mats + 2 * mi.y + 1);
+          const float4 u20 = __ldg(a.mats + 2 * mi.z), u21 = __ldg(a.mats + 2 * mi.z + 1);
+          const float4 u30 = __ldg(a.mats + 2 * mi.w), u31 = __ldg(a.mats + 2 * mi.w + 1);
+          item_fwd<0>(r, u00, u01, D & 1u);
+          item_fwd<1>(r, u10, u11, (D >> 1) & 1u);
+          item_fwd<2>(r, u20, u21, (D >> 2) & 1u);
+          item_fwd<3>(r, u30, u31, (D >> 3) & 1u);
+          chain_pending<false>(lk.x, lk.y, gb, pos, D, r, l);
+        } else {
+          const uint4* rec = a.rounds + (size_t)(rb0 + k) * (kBwdRoundWords / 4);
+          const uint4 tz = __ldg(rec), ty = __ldg(rec + 1), lk = __ldg(rec + 2);
+          const float2 z0 = term_cs(a.cs, tz.x), z1 = term_cs(a.cs, tz.y), z2 = term_cs(a.cs, tz.z),
+                       z3 = term_cs(a.cs, tz.w);
+          const float2 y0 = term_cs(a.cs, ty.x), y1 = term_cs(a.cs, ty.y), y2 = term_cs(a.cs, ty.z),
+                       y3 = term_cs(a.cs, ty.w);
+          chain_pending<true>(lk.x, lk.y, gb, pos, D, r, l);
+          float v[8];
+          item_bwd<0>(r, l, z0, y0, D & 1u, v[0], v[4]);
+          item_bwd<1>(r, l, z1, y1, (D >> 1) & 1u, v[1], v[5]);
+          item_bwd<2>(r, l, z2, y2, (D >> 2) & 1u, v[2], v[6]);
+          item_bwd<3>(r, l, z3, y3, (D >> 3) & 1u, v[3], v[7]);
+          int idx;
+          const float sum = butterfly8(v, lanes, lane, idx);
+          const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
+          const int32_t term = pick_term(tz, ty, idx);
+          if (Tt >= 32) {
+            if (owner) {
+              s_red[buf][warp][k * 8 + idx] = sum;
+              if (warp == 0) s_slot[buf][k * 8 + idx] = term;
+            }
+          } else if (owner && active && term >= 0) {
+            a.g_part[tile * a.n_slots + term] = 0.5 * (double)sum;
+          }
+        }
+      }
+      apply_pending<BWD>(D, r, l);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        tp[pb ^ reg_off(j, so)] = r[j];
+        if (BWD) tl[pb ^ reg_off(j, so)] = l[j];
+      }
+      __syncthreads();
+      if (BWD && Tt >= 32) {
+        const int nk = nr * 8;
+        for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
+          const int tc = e / nk, kk = e - tc * nk;
+          const int64_t t2 = (int64_t)blockIdx.x * tiles_per_cta + tc;
+          const int32_t term = s_slot[buf][kk];
+          if (t2 < total_tiles && term >= 0) {
+            double sum = 0.0;
+            for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
+            a.g_part[t2 * a.n_slots + term] = 0.5 * sum;
+          }
+        }
+        buf ^= 1;
+      }
+    } else if (!ROUNDS && code == OP_STEP) {
       const int g = (op.x >> 4) & 3;
       const int nops = (op.x >> 8) & 0xffff;
       const int nk = (int)op.y;
@@ -429,13 +634,16 @@ __global__ void prep_kernel(const PrepArgs a) {
     return;
   }
   i -= a.n_fused;
-  if (i < a.n_slots) {
+  if (i < a.n_terms) {
+    // a term's angle is the sum of its parameters (a merged run of RZ gates)
+    double phi = 0.0;
+    for (int j = a.term_off[i]; j < a.term_off[i + 1]; ++j) phi += (double)a.theta[a.term_params[j]];
     double s, c;
-    sincos(0.5 * (double)a.theta[a.slot_param[i]], &s, &c);
+    sincos(0.5 * phi, &s, &c);
     a.cs[i] = make_float2((float)c, (float)s);
     return;
   }
-  i -= a.n_slots;
+  i -= a.n_terms;
   if (i < (int64_t)a.B * a.n_eff) {
     const int64_t bb = i / a.n_eff;
     const int q = (int)(i - bb * a.n_eff);
@@ -509,7 +717,7 @@ __global__ void loss_kernel(int kind, const double* E, const float* y, int64_t B
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.n_fused + a.n_slots + (int64_t)a.B * a.n_eff;
+  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff;
   if (total == 0) return cudaSuccess;
   const int blk = 256;
   prep_kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, st>>>(a);
@@ -522,16 +730,25 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
   const int64_t grid = (total_tiles + tiles_per_cta - 1) / tiles_per_cta;
   if (grid == 0) return cudaSuccess;
   const size_t smem = (size_t)(bwd ? 2 : 1) * kTileAmps * sizeof(float2);
+  const bool rounds = a.rounds != nullptr;
   if (bwd) {
-    static bool once = false;
-    if (!once) {
-      cudaError_t e = cudaFuncSetAttribute(pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // 64 KiB of dynamic shared memory needs the opt-in, once per device
+    static bool once[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !once[dev]) {
+      e = cudaFuncSetAttribute(pass_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pass_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      once = true;
+      once[dev] = true;
     }
-    pass_kernel<true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    if (rounds) pass_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    else pass_kernel<true, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   } else {
-    pass_kernel<false><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    if (rounds) pass_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    else pass_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -13,6 +13,7 @@ struct PassArgs {
   int32_t tps_log2;       // log2(tiles per sample) = n_eff - K
   int64_t B;              // samples in this call
   const uint2* ops;       // program of this direction
+  const uint4* rounds;    // round records of this direction (round programs)
   const float4* mats;     // fused 2x2 matrices, 2 float4 each
   const float2* cs;       // (cos, sin) of theta/2 per gradient slot
   const float2* enc;      // (cos, sin) of x/2, [B][n_eff]
@@ -34,8 +35,9 @@ struct PrepArgs {
   const int32_t* fuse_off;
   const FuseGate* fuse_gates;
   float4* mats;
-  int32_t n_slots;
-  const int32_t* slot_param;
+  int32_t n_terms;
+  const int32_t* term_off;     // CSR term -> parameters (angles summed)
+  const int32_t* term_params;
   float2* cs;
   const float* x;
   int64_t B;

@@ -9,6 +9,8 @@
 #include "planner.h"
 
 #include <algorithm>
+#include <cstdlib>
+#include <functional>
 #include <set>
 #include <stdexcept>
 #include <string>
@@ -125,9 +127,25 @@ int absorb_step(Sim& s, uint64_t group, int max_slots, std::vector<int>* out) {
   return rot * 64 + cz;
 }
 
+// One item of a round: the next run of rotations on one qubit, either a run
+// of diagonal rotations ("pre", when the qubit's next rotation is an RZ) or
+// one RY followed by the diagonal rotations that become ready after it.
+struct ItemRec {
+  std::vector<int> pre;
+  int y = -1;
+  std::vector<int> post;
+  bool empty() const { return pre.empty() && y < 0; }
+};
+
+struct RoundRec {
+  ItemRec it[4];
+  std::vector<int> czs;
+};
+
 struct StepRec {
   int group;
-  std::vector<int> gates;
+  std::vector<int> gates;        // every gate absorbed by the step
+  std::vector<RoundRec> rounds;  // round programs only
 };
 
 struct Tile {
@@ -174,6 +192,152 @@ int run_pass(Sim& s, const Tile& t, std::vector<StepRec>* steps) {
   return total;
 }
 
+// ---- round programs -------------------------------------------------------------
+// Rotations of every qubit in circuit order, with a cursor that only lags the
+// committed absorption state (simulated absorption may run ahead of it).
+struct QubitRots {
+  std::vector<std::vector<int>> rots;
+  std::vector<size_t> cursor;
+  int next(const Sim& s, int q) const {
+    const auto& l = rots[q];
+    size_t i = cursor[q];
+    while (i < l.size() && s.done[l[i]]) ++i;
+    return i < l.size() ? l[i] : -1;
+  }
+  void commit(const Sim& s) {
+    for (size_t q = 0; q < rots.size(); ++q)
+      while (cursor[q] < rots[q].size() && s.done[rots[q][cursor[q]]]) ++cursor[q];
+  }
+};
+
+bool ready(const Sim& s, int g) { return g >= 0 && !s.done[g] && s.indeg[g] == 0; }
+
+// Absorb the next item of qubit q; false if its next rotation is not ready.
+bool take_item(Sim& s, const QubitRots& qr, int q, ItemRec* it) {
+  int g = qr.next(s, q);
+  if (!ready(s, g)) return false;
+  const auto& gates = s.c->gates;
+  if (gates[g].kind == G_RZ) {
+    while (ready(s, g) && gates[g].kind == G_RZ) {
+      s.absorb(g);
+      it->pre.push_back(g);
+      g = qr.next(s, q);
+    }
+    return true;
+  }
+  s.absorb(g);
+  it->y = g;
+  g = qr.next(s, q);
+  while (ready(s, g) && gates[g].kind == G_RZ) {
+    s.absorb(g);
+    it->post.push_back(g);
+    g = qr.next(s, q);
+  }
+  return true;
+}
+
+bool has_rotations_left(const Sim& s, const QubitRots& qr, int q) { return qr.next(s, q) >= 0; }
+
+// One round on the group's qubits. full: every qubit of the group that still
+// has rotations must contribute an item. Ready CZs are absorbed at its end.
+bool form_round(Sim& s, const QubitRots& qr, const int (&qs)[4], bool full, RoundRec* rr, int* n_rot) {
+  const size_t mark = s.log.size();
+  RoundRec r;
+  int items = 0, want = 0, rot = 0;
+  for (int k = 0; k < 4; ++k) {
+    bool dup = false;
+    for (int j = 0; j < k; ++j) dup |= qs[j] == qs[k];
+    if (dup || qs[k] >= s.c->n) continue;
+    if (!has_rotations_left(s, qr, qs[k])) continue;
+    ++want;
+    if (take_item(s, qr, qs[k], &r.it[k])) {
+      ++items;
+      rot += (int)r.it[k].pre.size() + (r.it[k].y >= 0) + (int)r.it[k].post.size();
+    }
+  }
+  if (full && (items < want || items == 0)) {
+    s.undo_to(mark);
+    return false;
+  }
+  std::vector<int> cand(s.front.begin(), s.front.end());
+  for (int g : cand)
+    if (s.c->gates[g].kind == G_CZ && ready(s, g)) {
+      s.absorb(g);
+      r.czs.push_back(g);
+    }
+  if (items == 0 && r.czs.empty()) {
+    s.undo_to(mark);
+    return false;
+  }
+  if (rr) *rr = std::move(r);
+  if (n_rot) *n_rot = rot;
+  return true;
+}
+
+int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<StepRec>* steps, bool allow_partial) {
+  int total = 0;
+  auto group_qubits = [&](int gi, int (&qs)[4]) {
+    for (int k = 0; k < 4; ++k) qs[k] = t.local_to_global[t.groups[gi][k]];
+  };
+  for (;;) {
+    // prefer the group that absorbs the most full rounds (then the most rotations)
+    int best = -1, best_rounds = 0, best_rot = 0;
+    for (int gi = 0; gi < (int)t.groups.size(); ++gi) {
+      int qs[4];
+      group_qubits(gi, qs);
+      const size_t mark = s.log.size();
+      int nr = 0, rot = 0, r1;
+      while (nr < kMaxStepRounds && form_round(s, qr, qs, true, nullptr, &r1)) {
+        ++nr;
+        rot += r1;
+      }
+      s.undo_to(mark);
+      if (nr > best_rounds || (nr == best_rounds && rot > best_rot)) {
+        best = gi;
+        best_rounds = nr;
+        best_rot = rot;
+      }
+    }
+    bool partial = false;
+    if (best_rounds == 0) {
+      if (!allow_partial) break;
+      // no full round anywhere: one partial round in the group that absorbs most
+      best = -1;
+      best_rot = -1;
+      for (int gi = 0; gi < (int)t.groups.size(); ++gi) {
+        int qs[4];
+        group_qubits(gi, qs);
+        const size_t mark = s.log.size();
+        int r1 = 0;
+        if (form_round(s, qr, qs, false, nullptr, &r1) && r1 > best_rot) {
+          best = gi;
+          best_rot = r1;
+        }
+        s.undo_to(mark);
+      }
+      if (best < 0) break;
+      partial = true;
+    }
+    int qs[4];
+    group_qubits(best, qs);
+    StepRec st;
+    st.group = best;
+    const size_t mark = s.log.size();
+    for (int nr = 0; nr < (partial ? 1 : kMaxStepRounds); ++nr) {
+      RoundRec rr;
+      int r1 = 0;
+      if (!form_round(s, qr, qs, !partial, &rr, &r1)) break;
+      int pads = 0;
+      for (int k = 0; k < 4; ++k) pads += rr.it[k].empty();
+      total += 4 * r1 - pads;  // useful rotations, minus identity items
+      st.rounds.push_back(std::move(rr));
+    }
+    st.gates.assign(s.log.begin() + mark, s.log.end());
+    if (steps) steps->push_back(std::move(st));
+  }
+  return total;
+}
+
 // Candidate tiles for a multi-pass plan: low nibble {0..3} plus K-4 others.
 std::vector<std::vector<int>> tile_candidates(const Sim& s, int n_eff, int K) {
   std::vector<std::vector<int>> cands;
@@ -208,6 +372,28 @@ std::vector<std::vector<int>> tile_candidates(const Sim& s, int n_eff, int K) {
         for (int i = 0; i < h; ++i) c.push_back(b + i);
         cands.push_back(c);
       }
+  }
+  // unions of aligned 4-qubit chunks {4k..4k+3} (qubits of one chunk tend to
+  // advance together, so round steps on them stay full)
+  if (extra % 4 == 0 && extra > 0) {
+    std::vector<int> chunks;
+    for (int b = 4; b + 4 <= n_eff; b += 4) chunks.push_back(b);
+    const int need = extra / 4;
+    std::vector<int> pick(need);
+    std::function<void(int, int)> rec = [&](int at, int from) {
+      if (at == need) {
+        std::vector<int> c = {0, 1, 2, 3};
+        for (int b : pick)
+          for (int k = 0; k < 4; ++k) c.push_back(b + k);
+        cands.push_back(c);
+        return;
+      }
+      for (int i = from; i < (int)chunks.size(); ++i) {
+        pick[at] = chunks[i];
+        rec(at + 1, i + 1);
+      }
+    };
+    rec(0, 0);
   }
   for (auto& c : cands) std::sort(c.begin(), c.end());
   std::sort(cands.begin(), cands.end());
@@ -261,6 +447,15 @@ int ckpt_interval_gates(const Circuit& c, int ckpt_layers) {
   return (int)std::min<long>(g, 1L << 30);
 }
 
+// Round programs handle RZ / RY rotations and CZs on neighbouring qubits.
+static bool round_eligible(const Circuit& c) {
+  for (const Gate& g : c.gates) {
+    if (g.kind == G_RX) return false;
+    if (g.kind == G_CZ && std::abs(g.q0 - g.q1) != 1) return false;
+  }
+  return true;
+}
+
 static void fill_slots(const Circuit& c, std::vector<int32_t>& slot_param, std::vector<int32_t>& slot_kind,
                        std::vector<int32_t>& slot_gate, std::vector<int32_t>& param_off,
                        std::vector<int32_t>& param_slots) {
@@ -288,14 +483,35 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
   // a multi-pass tile needs at least one qubit beyond the low nibble
   if (P.n_eff > K && K < kRegBits + 1) K = kRegBits + 1;
   P.K = K;
-  fill_slots(c, P.slot_param, P.slot_kind, P.slot_gate, P.param_off, P.param_slots);
-  P.n_slots = (int)P.slot_param.size();
-  std::vector<int> slot_of_gate(c.gates.size(), -1);
-  for (int s = 0; s < P.n_slots; ++s) slot_of_gate[P.slot_gate[s]] = s;
+  P.rounds = !req.generic && K >= 7 && round_eligible(c);
+  // gradient terms: generic programs have one per rotation, in circuit order
+  std::vector<int> term_of_gate(c.gates.size(), -1);
+  P.term_off.assign(1, 0);
+  if (!P.rounds) {
+    for (int g = 0; g < (int)c.gates.size(); ++g)
+      if (is_rot(c.gates[g].kind)) {
+        term_of_gate[g] = (int)P.term_kind.size();
+        P.term_kind.push_back(c.gates[g].kind);
+        P.term_params.push_back(c.gates[g].param);
+        P.term_off.push_back((int32_t)P.term_params.size());
+      }
+  }
 
   const int M = (int)c.gates.size();
   Dag dag = build_dag(c);
   Sim sim(c, dag);
+  QubitRots qr;
+  qr.rots.assign(c.n, {});
+  qr.cursor.assign(c.n, 0);
+  for (int g = 0; g < M; ++g)
+    if (is_rot(c.gates[g].kind)) qr.rots[c.gates[g].q0].push_back(g);
+  // Round programs end a pass when no group can take a full round; partial
+  // rounds (identity-padded items) are used only when no tile progresses
+  // otherwise.
+  bool allow_partial = false;
+  auto pass_run = [&](const Tile& t, std::vector<StepRec>* steps) {
+    return P.rounds ? run_pass_rounds(sim, qr, t, steps, allow_partial) : run_pass(sim, t, steps);
+  };
 
   // checkpoint boundaries in gate-sequence positions
   const int G = ckpt_interval_gates(c, req.ckpt_layers);
@@ -312,28 +528,40 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
 
   while (sim.n_done < M || passes.empty()) {
     Tile tile;
-    if (P.n_eff <= K) {
-      std::vector<int> all;
-      for (int q = 0; q < P.n_eff; ++q) all.push_back(q);
-      tile = make_tile(all, K);
-    } else {
-      auto cands = tile_candidates(sim, P.n_eff, K);
-      int best = -1, best_score = -1;
-      for (int i = 0; i < (int)cands.size(); ++i) {
-        Tile t = make_tile(cands[i], K);
+    // one tile covers the state: partial rounds stay in the single pass
+    allow_partial = !P.rounds || P.n_eff <= K;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      int best_score = 0;
+      if (P.n_eff <= K) {
+        std::vector<int> all;
+        for (int q = 0; q < P.n_eff; ++q) all.push_back(q);
+        tile = make_tile(all, K);
         size_t mark = sim.log.size();
-        int sc = run_pass(sim, t, nullptr);
+        best_score = pass_run(tile, nullptr);
         sim.undo_to(mark);
-        if (sc > best_score) {
-          best_score = sc;
-          best = i;
+      } else {
+        auto cands = tile_candidates(sim, P.n_eff, K);
+        int best = -1;
+        best_score = -1;
+        for (int i = 0; i < (int)cands.size(); ++i) {
+          Tile t = make_tile(cands[i], K);
+          size_t mark = sim.log.size();
+          int sc = pass_run(t, nullptr);
+          sim.undo_to(mark);
+          if (sc > best_score) {
+            best_score = sc;
+            best = i;
+          }
         }
+        tile = make_tile(cands[best], K);
       }
-      tile = make_tile(cands[best], K);
+      if (best_score > 0 || allow_partial) break;
+      allow_partial = true;
     }
     PassRec pr;
     pr.tile = tile;
-    run_pass(sim, tile, &pr.steps);
+    pass_run(tile, &pr.steps);
+    qr.commit(sim);
     if (pr.steps.empty() && M > 0) throw std::runtime_error("planner made no progress");
     // checkpoints: after a step, once every gate before the next boundary is done
     // (recomputed from the absorption order of this pass)
@@ -361,6 +589,69 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
   // ---- emit forward and backward programs
   P.fuse_off.assign(1, 0);
   P.n_steps = 0;
+  if (P.rounds) P.fuse_off.push_back(0);  // fused entry 0 = identity (empty product)
+  using Item = std::vector<std::pair<uint32_t, uint32_t>>;
+  auto fuse_of = [&](const std::vector<int>& gates) -> uint32_t {
+    if (gates.empty()) return 0u;
+    for (int g : gates) P.fuse_gates.push_back({c.gates[g].kind, c.gates[g].param});
+    P.fuse_off.push_back((int32_t)P.fuse_gates.size());
+    return (uint32_t)P.fuse_off.size() - 2;
+  };
+  auto new_term = [&](const std::vector<int>& gates, int kind) -> int32_t {
+    if (gates.empty()) return -1;
+    const int32_t id = (int32_t)P.term_kind.size();
+    P.term_kind.push_back(kind);
+    for (int g : gates) P.term_params.push_back(c.gates[g].param);
+    P.term_off.push_back((int32_t)P.term_params.size());
+    return id;
+  };
+  // A round step: forward rounds in order; the backward step runs the same
+  // rounds in reverse, each one links first, then per item the RZ run and the RY.
+  auto emit_round_step = [&](const Tile& tile, const StepRec& st, std::vector<Item>& bwd_items) {
+    const std::vector<int>& gl = tile.groups[st.group];
+    int gq[4];
+    for (int r = 0; r < 4; ++r) gq[r] = tile.local_to_global[gl[r]];
+    const uint32_t fr0 = (uint32_t)(P.fwd_rounds.size() / kFwdRoundWords);
+    std::vector<std::vector<int32_t>> brs;
+    for (const RoundRec& rr : st.rounds) {
+      uint32_t links = 0;
+      for (int g : rr.czs) links ^= 1u << std::min(c.gates[g].q0, c.gates[g].q1);
+      uint32_t bbits = 0;
+      for (int r = 0; r < 3; ++r)
+        if (gq[r + 1] == gq[r] + 1 && ((links >> gq[r]) & 1u)) bbits |= 1u << r;
+      std::vector<uint32_t> fw(kFwdRoundWords, 0u);
+      std::vector<int32_t> bw(kBwdRoundWords, -1);
+      for (int r = 0; r < 4; ++r) {
+        const ItemRec& it = rr.it[r];
+        std::vector<int> fg = it.pre;
+        if (it.y >= 0) {
+          fg.push_back(it.y);
+          fg.insert(fg.end(), it.post.begin(), it.post.end());
+          bw[r] = new_term(it.post, G_RZ);
+          bw[4 + r] = new_term({it.y}, G_RY);
+        } else {
+          bw[r] = new_term(it.pre, G_RZ);
+        }
+        fw[r] = fuse_of(fg);
+      }
+      fw[4] = links;
+      fw[5] = bbits;
+      bw[8] = (int32_t)links;
+      bw[9] = (int32_t)bbits;
+      bw[10] = bw[11] = 0;
+      P.fwd_rounds.insert(P.fwd_rounds.end(), fw.begin(), fw.end());
+      brs.push_back(std::move(bw));
+    }
+    const uint32_t nr = (uint32_t)st.rounds.size();
+    if (nr == 0 || nr > (uint32_t)kMaxStepRounds) throw std::runtime_error("internal: bad round count");
+    P.fwd_ops.push_back(w0(OP_STEP, (uint32_t)st.group << 4 | nr << 8));
+    P.fwd_ops.push_back(fr0);
+    ++P.n_steps;
+    P.n_rounds += (int)nr;
+    const uint32_t br0 = (uint32_t)(P.bwd_rounds.size() / kBwdRoundWords);
+    for (auto it = brs.rbegin(); it != brs.rend(); ++it) P.bwd_rounds.insert(P.bwd_rounds.end(), it->begin(), it->end());
+    bwd_items.push_back({{w0(OP_STEP, (uint32_t)st.group << 4 | nr << 8), br0}});
+  };
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const PassRec& pr = passes[pi];
     std::vector<int> global_to_local(P.n_eff, -1);
@@ -386,6 +677,9 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
     int trailing_ckpt = -1;
     for (int si = 0; si < n_steps; ++si) {
       const StepRec& st = pr.steps[si];
+      if (P.rounds) {
+        emit_round_step(pr.tile, st, bwd_items);
+      } else {
       const std::vector<int>& gl = pr.tile.groups[st.group];
       auto reg_of = [&](int q) -> uint32_t {
         int lb = global_to_local[q];
@@ -486,7 +780,7 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
           const std::vector<int>& run = fruns[oi];
           for (int j = (int)run.size() - 1; j >= 0; --j) {
             const Gate& gt = c.gates[run[j]];
-            const int slot = slot_of_gate[run[j]];
+            const int slot = term_of_gate[run[j]];
             bops.push_back({w0(OP_G, r << 4 | (uint32_t)gt.kind << 6 | k << 8), (uint32_t)slot});
             ++k;
           }
@@ -499,6 +793,7 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
       item.push_back({w0(OP_STEP, (uint32_t)st.group << 4 | (uint32_t)bops.size() << 8), k});
       item.insert(item.end(), bops.begin(), bops.end());
       bwd_items.push_back(std::move(item));
+      }
       // checkpoint after this step
       const int ck = pr.ckpt_after_step[si];
       if (ck >= 0) {
@@ -544,6 +839,17 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
     const bool last_bwd = fi == 0;
     b.psi_dst = (last_bwd || f.psi_src >= 0) ? BUF_NONE : BUF_WORK;
     b.lam_dst = last_bwd ? BUF_NONE : LAM_BUF;
+  }
+  // parameter -> terms (a parameter used twice in one term is listed twice)
+  P.n_terms = (int)P.term_kind.size();
+  P.param_off.assign(c.n_params + 1, 0);
+  for (int32_t p : P.term_params) P.param_off[p + 1]++;
+  for (int p = 0; p < c.n_params; ++p) P.param_off[p + 1] += P.param_off[p];
+  P.param_terms.assign(P.term_params.size(), 0);
+  {
+    std::vector<int32_t> fill(P.param_off.begin(), P.param_off.end() - 1);
+    for (int t = 0; t < P.n_terms; ++t)
+      for (int j = P.term_off[t]; j < P.term_off[t + 1]; ++j) P.param_terms[fill[P.term_params[j]]++] = t;
   }
   return P;
 }

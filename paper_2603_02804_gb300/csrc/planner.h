@@ -22,18 +22,28 @@ struct Circuit {
 };
 
 // Result of fusion planning for one circuit.
+//
+// A gradient term is one (cos, sin) table entry and one reduced partial:
+// in a generic program every rotation is its own term; in a round program a
+// run of RZ gates on one qubit with nothing non-diagonal between them is one
+// term (they share the value (1/2) Im<lambda|Z|psi> and un-apply as one
+// phase), so a term lists the parameters whose angles it sums.
 struct FusedPlan {
-  int n_eff = 0;   // simulated qubits (>= 4)
-  int K = 0;       // tile bits
-  int n_slots = 0; // parametrised gates (gradient slots), numbered in circuit order
-  int n_ckpt = 0;  // checkpoint state slots including the final state
+  int n_eff = 0;    // simulated qubits (>= 4)
+  int K = 0;        // tile bits
+  bool rounds = false;  // round program (straight-line steps) instead of generic ops
+  int n_terms = 0;  // gradient terms
+  int n_ckpt = 0;   // checkpoint state slots including the final state
   int n_steps = 0;
+  int n_rounds = 0;
   std::vector<PassDesc> fwd, bwd;
   std::vector<uint32_t> fwd_ops, bwd_ops;   // 2 words per op
+  std::vector<uint32_t> fwd_rounds;         // kFwdRoundWords per round
+  std::vector<int32_t> bwd_rounds;          // kBwdRoundWords per round
   std::vector<int32_t> fuse_off;            // size n_fused + 1
   std::vector<FuseGate> fuse_gates;
-  std::vector<int32_t> slot_param, slot_kind, slot_gate;
-  std::vector<int32_t> param_off, param_slots;  // CSR param -> slots
+  std::vector<int32_t> term_off, term_params, term_kind;  // CSR term -> params
+  std::vector<int32_t> param_off, param_terms;            // CSR param -> terms
 };
 
 // Per-gate schedule (the unfused comparator path).
@@ -49,6 +59,7 @@ struct PerGatePlan {
 struct PlanRequest {
   int tile_bits = 0;     // 0 = auto
   int ckpt_layers = 10;  // checkpoint interval in layers
+  bool generic = false;  // force the generic step program
 };
 
 // Throws std::runtime_error with a message on invalid input.

@@ -35,6 +35,21 @@ enum OpCode : uint32_t {
   OP_ANCHOR = 7,  // bwd: reload psi of the tile from checkpoint slot w1
 };
 
+// Round programs: a step is OP_STEP {w0: group (bits 4-5) | rounds << 8,
+// w1: first round}; every round applies one item per register bit r = 0..3
+// and then the CZ links of the round.
+//   forward round, kFwdRoundWords words: m[4] (fused 2x2 index per register
+//     bit, 0 = identity), links, bbits (links between register bits r, r+1),
+//     2 pad words.
+//   backward round, kBwdRoundWords words: tz[4], ty[4] (term of the merged RZ
+//     run and of the RY of each item, -1 = none), links, bbits, 2 pad words.
+// A backward step runs its rounds in the order stored; each round applies the
+// links first, then per item the RZ run and then the RY (the exact reverse of
+// the forward round).
+constexpr int kFwdRoundWords = 8;
+constexpr int kBwdRoundWords = 12;
+constexpr int kMaxStepRounds = 4;   // 8 gradient values per round
+
 // Source / destination codes of a pass.
 enum : int32_t {
   SRC_GENERATE = -1,  // fwd: build psi_0 = (x) RY(x_q)|0> in place

@@ -41,7 +41,7 @@ class qf_pauli(ctypes.Structure):
 
 class qf_plan_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("ckpt_layers", ctypes.c_int32),
-                ("host_only", ctypes.c_int32), ("reserved", ctypes.c_int32 * 12)]
+                ("host_only", ctypes.c_int32), ("program", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
 
 
 class qf_plan_info_t(ctypes.Structure):
@@ -158,8 +158,8 @@ def qf_circuit_destroy(handle: int) -> None:
 
 
 def qf_plan(handle: int, batch: int, path: int = QF_PATH_FUSED, tile_bits: int = 0, ckpt_layers: int = 0,
-            host_only: bool = False) -> int:
-    o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only))
+            host_only: bool = False, program: int = 0) -> int:
+    o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program))
     ws = _sz()
     _check(load().qf_plan(handle, ctypes.byref(o), batch, ctypes.byref(ws)))
     return ws.value

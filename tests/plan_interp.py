@@ -2,8 +2,8 @@
 
 It executes the forward and backward programs exported by qf_plan_export with
 the same semantics as the pass kernels, but on whole complex128 state vectors,
-so the planner's fusion, ordering, checkpoint placement and reversal can be
-checked against the oracle without a GPU.
+so the planner's fusion, ordering, checkpoint placement, merged gradient terms
+and reversal can be checked against the oracle without a GPU.
 """
 from __future__ import annotations
 
@@ -13,33 +13,48 @@ OP_STEP, OP_U, OP_G, OP_CHAIN, OP_CZ, OP_CKPT, OP_ANCHOR = 1, 2, 3, 4, 5, 6, 7
 SRC_GENERATE, BUF_WORK, BUF_NONE = -1, -2, -3
 LAM_SEED, LAM_BUF = -1, -2
 RX, RY, RZ = 0, 1, 2
+FWD_ROUND_WORDS, BWD_ROUND_WORDS = 8, 12
+
+
+class Program:
+    pass
 
 
 def parse(words):
-    w = list(map(int, words))
+    w = [int(v) for v in words]
     i = 0
+    prog = Program()
+    prog.rounds_mode = w[i] == 1
+    i += 1
     n_pass = w[i]; i += 1
     passes = []
+    keys = ["op_begin", "op_end", "psi_src", "psi_dst", "lam_src", "lam_dst", "flags", "K", "n_groups",
+            "outer_mask", "xm_local"]
     for _ in range(n_pass):
-        hdr = w[i:i + 11]; i += 11
-        gmap = w[i:i + 16]; i += 16
-        groups = [w[i + 4 * g:i + 4 * g + 4] for g in range(4)]; i += 16
-        keys = ["op_begin", "op_end", "psi_src", "psi_dst", "lam_src", "lam_dst", "flags", "K", "n_groups",
-                "outer_mask", "xm_local"]
-        d = dict(zip(keys, hdr))
-        d["gmap"] = gmap
-        d["groups"] = groups
+        d = dict(zip(keys, w[i:i + 11])); i += 11
+        d["gmap"] = w[i:i + 16]; i += 16
+        d["groups"] = [w[i + 4 * g:i + 4 * g + 4] for g in range(4)]; i += 16
         passes.append(d)
     n_ops = w[i]; i += 1
-    ops = [(w[i + 2 * k] & 0xFFFFFFFF, w[i + 2 * k + 1] & 0xFFFFFFFF) for k in range(n_ops)]
+    prog.ops = [(w[i + 2 * k] & 0xFFFFFFFF, w[i + 2 * k + 1] & 0xFFFFFFFF) for k in range(n_ops)]
     i += 2 * n_ops
     nf = w[i]; i += 1
-    fused = []
+    prog.fused = []
     for _ in range(nf):
         cnt = w[i]; i += 1
-        fused.append([(w[i + 2 * j], w[i + 2 * j + 1]) for j in range(cnt)])
+        prog.fused.append([(w[i + 2 * j], w[i + 2 * j + 1]) for j in range(cnt)])
         i += 2 * cnt
-    return passes, ops, fused
+    nr = w[i]; i += 1
+    prog.round_words = w[i:i + nr]; i += nr
+    nt = w[i]; i += 1
+    prog.terms = []
+    for _ in range(nt):
+        kind, cnt = w[i], w[i + 1]
+        prog.terms.append((kind, w[i + 2:i + 2 + cnt]))
+        i += 2 + cnt
+    prog.passes = passes
+    assert i == len(w)
+    return prog
 
 
 def rot(kind, t):
@@ -90,27 +105,42 @@ def encode(x, n, n_eff):
     return psi
 
 
-def run_forward(fwd, n, n_eff, theta, xrow, xm, zm):
-    passes, ops, fused = fwd
+def fused_matrix(prog, m, theta):
+    u = np.eye(2, dtype=complex)
+    for kind, p in prog.fused[m]:
+        u = rot(kind, float(theta[p])) @ u
+    return u
+
+
+def term_angle(prog, t, theta):
+    return float(sum(float(theta[p]) for p in prog.terms[t][1]))
+
+
+def run_forward(prog, n, n_eff, theta, xrow, xm, zm):
     slots = {}
     work = None
     E = None
-    for pd in passes:
+    for pd in prog.passes:
         src = pd["psi_src"]
         psi = encode(xrow, n, n_eff) if src == SRC_GENERATE else (slots[src] if src >= 0 else work).copy()
         k = pd["op_begin"]
         group = None
         while k < pd["op_end"]:
-            w0, w1 = ops[k]; k += 1
+            w0, w1 = prog.ops[k]; k += 1
             code = w0 & 15
-            if code == OP_STEP:
+            if code == OP_STEP and prog.rounds_mode:
+                group = pd["groups"][(w0 >> 4) & 3]
+                nr = (w0 >> 8) & 0xFFFF
+                for j in range(nr):
+                    rec = prog.round_words[(w1 + j) * FWD_ROUND_WORDS:(w1 + j + 1) * FWD_ROUND_WORDS]
+                    for r in range(4):
+                        psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, rec[r], theta))
+                    psi = psi * chain_sign(n_eff, rec[4] & 0xFFFFFFFF)
+            elif code == OP_STEP:
                 group = pd["groups"][(w0 >> 4) & 3]
             elif code == OP_U:
                 r, m = (w0 >> 4) & 3, w0 >> 8
-                u = np.eye(2, dtype=complex)
-                for kind, p in fused[m]:
-                    u = rot(kind, float(theta[p])) @ u
-                psi = apply1(psi, n_eff, pd["gmap"][group[r]], u)
+                psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, m, theta))
             elif code == OP_CHAIN:
                 psi = psi * chain_sign(n_eff, w1)
             elif code == OP_CZ:
@@ -129,32 +159,50 @@ def run_forward(fwd, n, n_eff, theta, xrow, xm, zm):
     return E, slots
 
 
-def run_backward(bwd, n_eff, theta, slot_param, slot_kind, slots, xm, zm, dLdE):
-    passes, ops, _ = bwd
-    grad_slot = np.zeros(len(slot_param))
+def _grad_unapply(psi, lam, n_eff, q, kind, angle):
+    g = 0.5 * np.imag(np.vdot(lam, apply1(psi, n_eff, q, PAULI[kind])))
+    ud = rot(kind, angle).conj().T
+    return g, apply1(psi, n_eff, q, ud), apply1(lam, n_eff, q, ud)
+
+
+def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params):
+    """Per-parameter gradient; every gradient term must be visited once."""
+    grad_term = np.zeros(len(prog.terms))
+    seen = np.zeros(len(prog.terms), int)
     work = lam_buf = None
-    seen = np.zeros(len(slot_param), int)
-    for pd in passes:
+    for pd in prog.passes:
         src = pd["psi_src"]
         psi = (slots[src] if src >= 0 else work).copy()
         lam = 2 * dLdE * observable(psi, n_eff, xm, zm) if pd["lam_src"] == LAM_SEED else lam_buf.copy()
         k = pd["op_begin"]
         group = None
         while k < pd["op_end"]:
-            w0, w1 = ops[k]; k += 1
+            w0, w1 = prog.ops[k]; k += 1
             code = w0 & 15
-            if code == OP_STEP:
+            if code == OP_STEP and prog.rounds_mode:
+                group = pd["groups"][(w0 >> 4) & 3]
+                nr = (w0 >> 8) & 0xFFFF
+                for j in range(nr):
+                    rec = prog.round_words[(w1 + j) * BWD_ROUND_WORDS:(w1 + j + 1) * BWD_ROUND_WORDS]
+                    s = chain_sign(n_eff, rec[8] & 0xFFFFFFFF)
+                    psi, lam = psi * s, lam * s
+                    for r in range(4):
+                        q = pd["gmap"][group[r]]
+                        for t in (rec[r], rec[4 + r]):
+                            if t < 0:
+                                continue
+                            kind = prog.terms[t][0]
+                            g, psi, lam = _grad_unapply(psi, lam, n_eff, q, kind, term_angle(prog, t, theta))
+                            grad_term[t] += g
+                            seen[t] += 1
+            elif code == OP_STEP:
                 group = pd["groups"][(w0 >> 4) & 3]
             elif code == OP_G:
-                r, kind, slot = (w0 >> 4) & 3, (w0 >> 6) & 3, w1
-                assert kind == slot_kind[slot]
-                q = pd["gmap"][group[r]]
-                seen[slot] += 1
-                Pp = apply1(psi, n_eff, q, PAULI[kind])
-                grad_slot[slot] += 0.5 * np.imag(np.vdot(lam, Pp))
-                ud = rot(kind, float(theta[slot_param[slot]])).conj().T
-                psi = apply1(psi, n_eff, q, ud)
-                lam = apply1(lam, n_eff, q, ud)
+                r, kind, t = (w0 >> 4) & 3, (w0 >> 6) & 3, w1
+                assert kind == prog.terms[t][0]
+                g, psi, lam = _grad_unapply(psi, lam, n_eff, pd["gmap"][group[r]], kind, term_angle(prog, t, theta))
+                grad_term[t] += g
+                seen[t] += 1
             elif code == OP_CHAIN:
                 s = chain_sign(n_eff, w1)
                 psi, lam = psi * s, lam * s
@@ -169,5 +217,9 @@ def run_backward(bwd, n_eff, theta, slot_param, slot_kind, slots, xm, zm, dLdE):
             work = psi
         if pd["lam_dst"] == LAM_BUF:
             lam_buf = lam
-    assert np.all(seen == 1), "every gradient slot must appear exactly once"
-    return grad_slot
+    assert np.all(seen == 1), "every gradient term must appear exactly once"
+    grad = np.zeros(n_params)
+    for t, (_, params) in enumerate(prog.terms):
+        for p in params:
+            grad[p] += grad_term[t]
+    return grad

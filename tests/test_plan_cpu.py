@@ -92,29 +92,31 @@ def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, ora
     fwd = pi.parse(qfuse.qf_plan_export(handle, 0))
     bwd = pi.parse(qfuse.qf_plan_export(handle, 1))
     # every rotation gate appears exactly once in the fused forward entries
-    entries = sorted((k, p) for run in fwd[2] for (k, p) in run)
+    entries = sorted((k, p) for run in fwd.fused for (k, p) in run)
     assert entries == sorted(zip(slot_kind, slot_param))
+    # and exactly once in the gradient terms
+    assert sorted(p for _, ps in bwd.terms for p in ps) == sorted(slot_param)
     pq = qfuse.pauli(obs, n)
     gp, Ep = orc.gradient(oracle_circ, theta, x, obs, per_sample=True)
     for b in range(len(x)):
         E, slots = pi.run_forward(fwd, n, n_eff, theta, x[b], pq.x_mask, pq.z_mask)
         assert abs(E - Ep[b]) < tol
-        gs = pi.run_backward(bwd, n_eff, theta, slot_param, slot_kind, slots, pq.x_mask, pq.z_mask, 1.0)
-        g = np.zeros(len(theta))
-        np.add.at(g, slot_param, gs)
+        g = pi.run_backward(bwd, n_eff, theta, slots, pq.x_mask, pq.z_mask, 1.0, len(theta))
         assert np.max(np.abs(g - gp[b])) < tol
-    return info
+    return info, fwd.rounds_mode
 
 
+@pytest.mark.parametrize("program", [0, 1])
 @pytest.mark.parametrize("n,d,K,ck", [
-    (1, 2, 0, 0), (3, 3, 0, 0), (4, 2, 0, 0), (5, 3, 0, 1), (6, 4, 0, 2), (8, 3, 0, 0),
+    (1, 2, 0, 0), (3, 3, 0, 0), (4, 2, 0, 0), (5, 3, 0, 1), (6, 4, 0, 2), (7, 3, 0, 1), (8, 3, 0, 0),
     (10, 3, 0, 1), (12, 2, 0, 1), (13, 2, 0, 1), (14, 3, 8, 1), (9, 4, 6, 2), (11, 2, 5, 0),
+    (15, 4, 7, 1), (17, 3, 0, 1),
 ])
-def test_fused_plan_matches_oracle_hea(n, d, K, ck):
+def test_fused_plan_matches_oracle_hea(n, d, K, ck, program):
     rng = np.random.default_rng(1000 + 37 * n + d)
     h = qfuse.qf_hea_create(n, d)
     try:
-        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True)
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, program=program)
         theta = rng.uniform(0, 2 * np.pi, 3 * n * d).astype(np.float32).astype(np.float64)
         x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
         c = orc.hea(n, d)
@@ -122,9 +124,10 @@ def test_fused_plan_matches_oracle_hea(n, d, K, ck):
         P = 3 * n * d
         slot_param = list(range(P))
         slot_kind = [orc.RY if (p % 3) == 1 else orc.RZ for p in range(P)]
-        info = interp_check(h, n, theta, x, obs, slot_param, slot_kind, oracle_circ=c)
+        info, rounds = interp_check(h, n, theta, x, obs, slot_param, slot_kind, oracle_circ=c)
         if n <= 12 and K == 0:
             assert info["n_passes"] == 1
+        assert rounds == (program == 0 and info["tile_bits"] >= 7)
     finally:
         qfuse.qf_circuit_destroy(h)
 
@@ -169,8 +172,20 @@ def test_plan_statistics_for_benchmark_shapes():
             qfuse.qf_circuit_destroy(h)
     assert out[12]["n_passes"] == 1
     # about one fused 2x2 per qubit and layer (RZ RY RZ -> one op)
-    assert 12 * 20 <= out[12]["n_fused_ops"] <= 12 * 21
+    assert 12 * 20 <= out[12]["n_fused_ops"] <= 12 * 22
     assert out[12]["n_steps"] <= 2 * 20
-    # light-cone wedges: several layers per pass over HBM
-    assert out[16]["n_passes"] <= 100 // 2
-    assert out[20]["n_passes"] <= 50 // 1
+    # round programs: group-level light-cone staircases, so a pass over HBM
+    # covers about 2 layers at n = 16 and 1 layer at n = 20 with full rounds
+    assert out[16]["n_passes"] <= 0.6 * 100
+    assert out[20]["n_passes"] <= 1.1 * 50
+    for n, d in ((12, 20), (16, 100), (20, 50)):
+        h = qfuse.qf_hea_create(n, d)
+        try:
+            qfuse.qf_plan(h, 1, ckpt_layers=10, host_only=True)
+            prog = pi.parse(qfuse.qf_plan_export(h, 0))
+            assert prog.rounds_mode
+            words = prog.round_words
+            pads = sum(1 for k in range(len(words) // 8) for r in range(4) if words[8 * k + r] == 0)
+            assert pads == 0, (n, pads)
+        finally:
+            qfuse.qf_circuit_destroy(h)
