@@ -66,14 +66,16 @@ def load_peaks():
 
 
 def algorithmic_flops(n, d, B):
-    """Method arithmetic per step in FP32 flops (real multiplies + adds):
-    forward: one fused complex 2x2 per qubit and layer, 4 complex multiplies
-    and 2 complex adds = 28 flops per pair of amplitudes; adjoint: per
-    rotation, un-apply psi (12 flops per pair), un-apply lambda (12) and
-    Im<lambda|P|psi> accumulated (8) = 32 flops per pair."""
+    """Arithmetic per step in FP32 flops (a multiply or an add = 1, FMA = 2).
+    Forward: one fused complex 2x2 per qubit and layer = 4 complex multiplies
+    and 2 complex adds = 28 flops per pair of amplitudes. Adjoint: per qubit
+    and layer two gradient terms (the RY, and the run RZ_c(l) RZ_a(l+1), whose
+    gradients are equal and which un-apply as one phase), plus the first RZ of
+    every qubit; per term and pair: un-apply psi and lambda (12 FMA) and
+    Im<lambda|P|psi> (4 FMA) = 32 flops."""
     pairs = B * (1 << (n - 1))
     fwd = n * d * pairs * 28
-    bwd = 3 * n * d * pairs * 32
+    bwd = (2 * n * d + n) * pairs * 32
     return fwd, bwd
 
 

@@ -136,7 +136,7 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
   L.dLdE = take((size_t)B * 8);
   L.grad = take((size_t)P * 8);
   L.loss = take(8);
-  L.cs = take((size_t)S * 8);
+  L.cs = take((size_t)S * 16);  // (cos, sin) or shear parameters per term
   L.enc = take((size_t)B * n_eff * 8);
   L.work = take((size_t)L.state_elems * 8);
   L.lam = take((size_t)L.state_elems * 8);
@@ -280,8 +280,20 @@ bool local_xmask(const qf::PassDesc& pd, uint32_t xm, uint32_t* out) {
   return true;
 }
 
+// The backward's per-term table: (cos, sin) for generic programs, three-shear
+// parameters for round programs.
+void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, qf::PrepArgs& pa) {
+  pa.n_terms = n_slots_of(c);
+  pa.term_off = T.term_off;
+  pa.term_params = T.term_params;
+  if (c->path == QF_PATH_FUSED && c->fp.rounds) pa.shear = at<float4>(ws, L.cs);
+  else pa.cs = at<float2>(ws, L.cs);
+}
+
+// with_terms: also fill the backward's term table in the same prep launch
+// (used by the train step, where the backward follows with the same theta).
 qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, const float* x,
-                        int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st) {
+                        int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false) {
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa{};
   pa.theta = theta;
@@ -289,10 +301,8 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.fuse_off = T.fuse_off;
   pa.fuse_gates = T.fuse_gates;
   pa.mats = at<float4>(ws, L.mats);
-  pa.n_terms = n_slots_of(c);
-  pa.term_off = T.term_off;
-  pa.term_params = T.term_params;
-  pa.cs = at<float2>(ws, L.cs);
+  pa.n_terms = 0;  // the forward itself needs only the fused matrices and the encoding
+  if (with_terms) set_term_table(c, T, L, ws, pa);
   pa.x = x;
   pa.B = B;
   pa.n = c->circ.n;
@@ -333,21 +343,22 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   return QF_OK;
 }
 
+// with_prep = false: the term table was filled by the preceding forward.
 qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, int64_t B,
-                         const Obs& o, const double* dLdE, double* grad, int per_sample, void* ws, cudaStream_t st) {
+                         const Obs& o, const double* dLdE, double* grad, int per_sample, void* ws, cudaStream_t st,
+                         bool with_prep = true) {
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa{};
   pa.theta = theta;
   pa.n_fused = 0;
-  pa.n_terms = n_slots_of(c);
-  pa.term_off = T.term_off;
-  pa.term_params = T.term_params;
-  pa.cs = at<float2>(ws, L.cs);
+  set_term_table(c, T, L, ws, pa);
   pa.B = 0;
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
-  QF_CU(qf::launch_prep(pa, st));
-  c->call_launches++;
+  if (with_prep) {
+    QF_CU(qf::launch_prep(pa, st));
+    c->call_launches++;
+  }
   qf::PassArgs a{};
   a.n_eff = P.n_eff;
   a.tps_log2 = P.n_eff - P.K;
@@ -355,6 +366,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.ops = T.bwd_ops;
   a.rounds = P.rounds ? T.bwd_rounds : nullptr;
   a.cs = pa.cs;
+  a.shear = pa.shear;
   a.work = at<float2>(ws, L.work);
   a.lam = at<float2>(ws, L.lam);
   a.slots = at<float2>(ws, L.slots);
@@ -723,6 +735,27 @@ qf_status qf_loss(int32_t kind, const double* E_d, const float* y_d, int64_t bat
 qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d, const float* y_d, int64_t batch,
                         int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d, double* grad_d, void* ws_d,
                         size_t ws_bytes, void* stream) {
+  if (c && c->planned && c->path == QF_PATH_FUSED) {
+    // fused: one prep launch fills the forward's and the backward's tables
+    qf_status s = check_call(c, batch, ws_d, ws_bytes);
+    if (s != QF_OK) return s;
+    if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
+        (!grad_d && c->circ.n_params > 0))
+      return fail(QF_ERR_INVALID_ARG, "null data pointer");
+    Obs o;
+    if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->call_launches = 0;
+    s = fused_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
+    if (s != QF_OK) return s;
+    double* dLdE = at<double>(ws_d, c->L.dLdE);
+    s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+    if (s != QF_OK) return s;
+    c->call_launches++;
+    s = fused_backward(c, c->dt, c->L, theta_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
+    c->launches = c->call_launches;
+    return s;
+  }
   qf_status s = qf_forward(c, theta_d, x_d, batch, obs, E_d, ws_d, ws_bytes, stream);
   if (s != QF_OK) return s;
   double* dLdE = at<double>(ws_d, c->L.dLdE);

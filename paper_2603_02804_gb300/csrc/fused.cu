@@ -197,16 +197,54 @@ __device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 m0, float4 m1, 
   apply_u<R>(r, m0, m1);
 }
 
-// Backward item on register bit R: the merged RZ run (phase (cz, sz)), then
-// the RY ((cy, sy)); with a pending Z_R the RY un-applies as RY(+theta) and
-// its Im<lambda|Y|psi> changes sign. Returns both partials.
+// Un-apply one rotation on register bit R by three shears and return the
+// thread's sum of Im<lambda|P|psi> taken before it. A plane rotation by phi
+// equals x += a y; y += b x; x += a y with a = -tan(phi/2), b = sin(phi)
+// (exact; |a| <= 1 for |phi| <= pi/2), three FMAs per component.
+//   RZ: amplitudes with bit R = 0 are multiplied by e^{+iw/2} (a rotation of
+//   (re, im) by w/2), those with bit R = 1 by e^{-iw/2}; t = tan(w/4), s = sin(w/2).
+//   RY: (x, y) <- RY(w)^dagger (x, y) = rotation by -w/2: a = t, b = -s.
+template <int R, int KIND>
+__device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], const float t, const float s) {
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    float2 p0 = p[j], p1 = p[j1], l0 = l[j], l1 = l[j1];
+    if (KIND == G_RZ) {
+      acc += l0.x * p0.y - l0.y * p0.x - l1.x * p1.y + l1.y * p1.x;
+      p0.x = fmaf(-t, p0.y, p0.x); p0.y = fmaf(s, p0.x, p0.y); p0.x = fmaf(-t, p0.y, p0.x);
+      l0.x = fmaf(-t, l0.y, l0.x); l0.y = fmaf(s, l0.x, l0.y); l0.x = fmaf(-t, l0.y, l0.x);
+      p1.x = fmaf(t, p1.y, p1.x); p1.y = fmaf(-s, p1.x, p1.y); p1.x = fmaf(t, p1.y, p1.x);
+      l1.x = fmaf(t, l1.y, l1.x); l1.y = fmaf(-s, l1.x, l1.y); l1.x = fmaf(t, l1.y, l1.x);
+    } else {
+      acc += l1.x * p0.x + l1.y * p0.y - l0.x * p1.x - l0.y * p1.y;
+      p0.x = fmaf(t, p1.x, p0.x); p0.y = fmaf(t, p1.y, p0.y);
+      p1.x = fmaf(-s, p0.x, p1.x); p1.y = fmaf(-s, p0.y, p1.y);
+      p0.x = fmaf(t, p1.x, p0.x); p0.y = fmaf(t, p1.y, p0.y);
+      l0.x = fmaf(t, l1.x, l0.x); l0.y = fmaf(t, l1.y, l0.y);
+      l1.x = fmaf(-s, l0.x, l1.x); l1.y = fmaf(-s, l0.y, l1.y);
+      l0.x = fmaf(t, l1.x, l0.x); l0.y = fmaf(t, l1.y, l0.y);
+    }
+    p[j] = p0; p[j1] = p1; l[j] = l0; l[j1] = l1;
+  }
+  return acc;
+}
+
+// Backward item on register bit R: the merged RZ run, then the RY (shear
+// parameters (t, s, wrap parity)). With a pending Z_R the RY un-applies as
+// RY(+w) (t, s negated) and its Im<lambda|Y|psi> changes sign. The wrap
+// parities (u(phi) = -u(w) for odd k) go to the pending constant sign.
 template <int R>
-__device__ __forceinline__ void item_bwd(float2 (&p)[16], float2 (&l)[16], float2 czs, float2 cys, uint32_t a,
-                                         float& gz, float& gy) {
-  gz = bwd_gate<R, G_RZ>(p, l, czs.x, czs.y);
+__device__ __forceinline__ void item_bwd(float2 (&p)[16], float2 (&l)[16], float4 zq, float4 yq, uint32_t a,
+                                         uint32_t& D, float& gz, float& gy) {
+  gz = bwd_shear<R, G_RZ>(p, l, zq.x, zq.y);
   const int f = (int)(a << 31);
-  const float s = __int_as_float(__float_as_int(cys.y) ^ f);
-  gy = __int_as_float(__float_as_int(bwd_gate<R, G_RY>(p, l, cys.x, s)) ^ f);
+  const float t = __int_as_float(__float_as_int(yq.x) ^ f);
+  const float s = __int_as_float(__float_as_int(yq.y) ^ f);
+  gy = __int_as_float(__float_as_int(bwd_shear<R, G_RY>(p, l, t, s)) ^ f);
+  D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
 }
 
 // Reduce 8 per-thread values over `lanes` lanes (8, 16 or 32; whole-warp
@@ -249,8 +287,9 @@ __device__ __forceinline__ int32_t pick_term(uint4 tz, uint4 ty, int idx) {
   return (int32_t)((idx & 2) ? hi : lo);
 }
 
-__device__ __forceinline__ float2 term_cs(const float2* cs, uint32_t t) {
-  return (int32_t)t >= 0 ? __ldg(cs + t) : make_float2(1.f, 0.f);
+// Shear parameters of a term; a missing term (-1) is the identity (t = s = 0).
+__device__ __forceinline__ float4 term_shear(const float4* sh, uint32_t t) {
+  return (int32_t)t >= 0 ? __ldg(sh + t) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 }  // namespace
@@ -402,16 +441,16 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
         } else {
           const uint4* rec = a.rounds + (size_t)(rb0 + k) * (kBwdRoundWords / 4);
           const uint4 tz = __ldg(rec), ty = __ldg(rec + 1), lk = __ldg(rec + 2);
-          const float2 z0 = term_cs(a.cs, tz.x), z1 = term_cs(a.cs, tz.y), z2 = term_cs(a.cs, tz.z),
-                       z3 = term_cs(a.cs, tz.w);
-          const float2 y0 = term_cs(a.cs, ty.x), y1 = term_cs(a.cs, ty.y), y2 = term_cs(a.cs, ty.z),
-                       y3 = term_cs(a.cs, ty.w);
+          const float4 z0 = term_shear(a.shear, tz.x), z1 = term_shear(a.shear, tz.y),
+                       z2 = term_shear(a.shear, tz.z), z3 = term_shear(a.shear, tz.w);
+          const float4 y0 = term_shear(a.shear, ty.x), y1 = term_shear(a.shear, ty.y),
+                       y2 = term_shear(a.shear, ty.z), y3 = term_shear(a.shear, ty.w);
           chain_pending<true>(lk.x, lk.y, gb, pos, D, r, l);
           float v[8];
-          item_bwd<0>(r, l, z0, y0, D & 1u, v[0], v[4]);
-          item_bwd<1>(r, l, z1, y1, (D >> 1) & 1u, v[1], v[5]);
-          item_bwd<2>(r, l, z2, y2, (D >> 2) & 1u, v[2], v[6]);
-          item_bwd<3>(r, l, z3, y3, (D >> 3) & 1u, v[3], v[7]);
+          item_bwd<0>(r, l, z0, y0, D & 1u, D, v[0], v[4]);
+          item_bwd<1>(r, l, z1, y1, (D >> 1) & 1u, D, v[1], v[5]);
+          item_bwd<2>(r, l, z2, y2, (D >> 2) & 1u, D, v[2], v[6]);
+          item_bwd<3>(r, l, z3, y3, (D >> 3) & 1u, D, v[3], v[7]);
           int idx;
           const float sum = butterfly8(v, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
@@ -638,9 +677,19 @@ __global__ void prep_kernel(const PrepArgs a) {
     // a term's angle is the sum of its parameters (a merged run of RZ gates)
     double phi = 0.0;
     for (int j = a.term_off[i]; j < a.term_off[i + 1]; ++j) phi += (double)a.theta[a.term_params[j]];
-    double s, c;
-    sincos(0.5 * phi, &s, &c);
-    a.cs[i] = make_float2((float)c, (float)s);
+    if (a.shear) {
+      // u(phi) = (-1)^k u(w) with w = phi - 2 pi k in (-pi, pi]: the rotation by
+      // w/2 as three shears needs tan(w/4) (|.| <= 1) and sin(w/2)
+      const double two_pi = 6.283185307179586476925286766559;
+      const double k = rint(phi / two_pi);
+      const double w = phi - two_pi * k;
+      const int parity = ((long long)k) & 1;
+      a.shear[i] = make_float4((float)tan(0.25 * w), (float)sin(0.5 * w), __int_as_float(parity), 0.f);
+    } else {
+      double s, c;
+      sincos(0.5 * phi, &s, &c);
+      a.cs[i] = make_float2((float)c, (float)s);
+    }
     return;
   }
   i -= a.n_terms;
@@ -669,26 +718,23 @@ __global__ void e_reduce_kernel(const double* e_part, int64_t B, int tps, double
 // grad[p] (or grad[b][p]) = sum over tiles, then over the slots of p, in a
 // fixed order.
 __global__ void g_reduce_kernel(const GradReduceArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a.per_sample) {
-    if (i >= (int64_t)a.B * a.n_params) return;
-    const int64_t bb = i / a.n_params;
-    const int p = (int)(i - bb * a.n_params);
-    double s = 0.0;
-    for (int k = a.param_off[p]; k < a.param_off[p + 1]; ++k) {
-      const int slot = a.param_slots[k];
-      for (int64_t t = 0; t < a.tps; ++t) s += a.g_part[(bb * a.tps + t) * a.slot_stride + slot * a.slot_step];
-    }
-    a.grad[i] = s;
-  } else {
-    if (i >= a.n_params) return;
-    double s = 0.0;
-    for (int k = a.param_off[i]; k < a.param_off[i + 1]; ++k) {
-      const int slot = a.param_slots[k];
-      for (int64_t t = 0; t < (int64_t)a.B * a.tps; ++t) s += a.g_part[t * a.slot_stride + slot * a.slot_step];
-    }
-    a.grad[i] = s;
+  // one warp per output value; lane k sums rows k, k+32, ... and the warp
+  // combines the 32 lane sums in a fixed butterfly (bitwise repeatable)
+  const int64_t out = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_out = a.per_sample ? (int64_t)a.B * a.n_params : a.n_params;
+  if (out >= n_out) return;  // whole warps exit together
+  const int64_t bb = a.per_sample ? out / a.n_params : 0;
+  const int p = (int)(a.per_sample ? out - bb * a.n_params : out);
+  const int64_t rows = a.per_sample ? a.tps : (int64_t)a.B * a.tps;
+  const int64_t row0 = a.per_sample ? bb * a.tps : 0;
+  double s = 0.0;
+  for (int k = a.param_off[p]; k < a.param_off[p + 1]; ++k) {
+    const int64_t col = (int64_t)a.param_slots[k] * a.slot_step;
+    for (int64_t t = lane; t < rows; t += 32) s += a.g_part[(row0 + t) * a.slot_stride + col];
   }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) a.grad[out] = s;
 }
 
 // Loss and dL/dE in one block, fixed-order tree reduction.
@@ -762,7 +808,8 @@ cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E,
 cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st) {
   const int64_t n = a.per_sample ? (int64_t)a.B * a.n_params : a.n_params;
   if (n == 0) return cudaSuccess;
-  g_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+  const int64_t threads = n * 32;
+  g_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

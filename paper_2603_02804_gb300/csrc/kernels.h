@@ -15,7 +15,8 @@ struct PassArgs {
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs)
   const float4* mats;     // fused 2x2 matrices, 2 float4 each
-  const float2* cs;       // (cos, sin) of theta/2 per gradient slot
+  const float2* cs;       // (cos, sin) of theta/2 per gradient term (generic programs)
+  const float4* shear;    // three-shear parameters per gradient term (round programs)
   const float2* enc;      // (cos, sin) of x/2, [B][n_eff]
   float2* work;           // working state [B][2^n_eff]
   float2* lam;            // adjoint state [B][2^n_eff]
@@ -38,7 +39,9 @@ struct PrepArgs {
   int32_t n_terms;
   const int32_t* term_off;     // CSR term -> parameters (angles summed)
   const int32_t* term_params;
-  float2* cs;
+  float2* cs;                  // (cos, sin) of phi/2 per term, or
+  float4* shear;               // if non-null instead: (tan(w/4), sin(w/2), wrap parity, 0),
+                               // w = phi wrapped into (-pi, pi], phi = w + 2 pi k
   const float* x;
   int64_t B;
   int32_t n, n_eff;
