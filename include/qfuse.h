@@ -242,6 +242,53 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
  * inside qf_train_step) on this handle; for launch accounting. */
 qf_status qf_launch_count(const qf_circuit* c, int64_t* launches);
 
+/* ---- batched launch over many circuits ----------------------------------
+ * Many circuits of different widths, depths and batch sizes, trained in one
+ * persistent kernel launch: each work item (one sample, or a group of small
+ * samples, of one circuit) is taken by one CTA from a work queue ordered
+ * largest first, and that CTA runs the item's fused forward passes, its
+ * dL/dE and its fused adjoint passes (Secs. 3.2-3.3) with no waits on other
+ * CTAs. The loss is summed over every circuit; each circuit gets its own
+ * gradient. Per step: 4 kernels and one memset; capturable in a CUDA graph. */
+typedef struct qf_batch qf_batch;
+
+/* Build a batched launch. circuits[i] must be planned with QF_PATH_FUSED as
+ * round programs (qf_plan_info: tile_bits >= 7, RZ/RY rotations, CZ on
+ * neighbouring qubits; host_only plans are fine); batch[i] >= 1 samples of
+ * circuit i; obs[i] its observable; loss_kind QF_LOSS_SUM or QF_LOSS_MSE
+ * (mean over each circuit's samples, summed over circuits). Allocates the
+ * batch's device tables; the circuits must outlive the batch and not be
+ * re-planned. *workspace_bytes: size of the caller workspace. */
+qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const int64_t* batch,
+                          const qf_pauli* obs, int32_t loss_kind, size_t* workspace_bytes,
+                          qf_batch** out);
+
+/* Element offsets of each circuit in the concatenated buffers ([n + 1] each,
+ * any may be NULL): theta_off (float32 parameters; also float64 gradients),
+ * x_off (float32 [B_i][n_i] encodings), sample_off (E and y per sample). */
+qf_status qf_batch_layout(const qf_batch* b, int64_t* theta_off, int64_t* x_off, int64_t* sample_off);
+
+/* One training step of every circuit: theta_d, x_d, y_d (MSE only) are the
+ * concatenated inputs, E_d (float64 per sample), grad_d (float64 per
+ * parameter, dL/dtheta) and loss_d (float64 [1]) are written. */
+qf_status qf_batch_train_step(qf_batch* b, const float* theta_d, const float* x_d, const float* y_d,
+                              double* loss_d, double* E_d, double* grad_d, void* ws_d, size_t ws_bytes,
+                              void* stream);
+
+/* Capture one qf_batch_train_step with these buffers into a CUDA graph owned
+ * by the batch (runs one eager step first, then captures on `stream`, which
+ * must not be the legacy default stream). qf_batch_graph_launch replays it. */
+qf_status qf_batch_graph_capture(qf_batch* b, const float* theta_d, const float* x_d, const float* y_d,
+                                 double* loss_d, double* E_d, double* grad_d, void* ws_d,
+                                 size_t ws_bytes, void* stream);
+qf_status qf_batch_graph_launch(qf_batch* b, void* stream);
+
+/* Work items, total samples and total parameters of the batch. */
+qf_status qf_batch_info(const qf_batch* b, int64_t* n_items, int64_t* n_samples, int64_t* n_params);
+
+/* Free the batch's device tables and graph. NULL is accepted. */
+qf_status qf_batch_destroy(qf_batch* b);
+
 /* Start (on != 0) or stop timing the pass kernels of the following
  * qf_forward / qf_backward calls on this handle: a CUDA event pair is
  * recorded on the call's stream around the forward passes and around the

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <exception>
 #include <new>
 #include <stdexcept>
@@ -836,6 +837,345 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
                                : pg_backward(c, T, L, theta_d, batch, o, dLdE, grad_d, 0, ws, st);
   c->launches = c->call_launches;
   return s;
+}
+
+}  // extern "C"
+
+// ---- batched persistent launch over many circuits ---------------------------------
+struct qf_batch {
+  int n = 0;
+  std::vector<qf_circuit*> circ;
+  std::vector<int64_t> B;
+  std::vector<int64_t> theta_off, x_off, sample_off, grad_off;  // n + 1 each
+  std::vector<size_t> ws_off;
+  int32_t loss_kind = QF_LOSS_SUM;
+  size_t ws_total = 0, lterm_off = 0, queue_off = 0;
+  void* d_tables = nullptr;
+  qf::BatchArgs args{};
+  int64_t prep_total = 0, n_grad_out = 0;
+  int grid = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+template <class T>
+T* rel(size_t off) {  // a workspace-relative pointer (rebased by the kernels)
+  return reinterpret_cast<T*>(static_cast<uintptr_t>(off));
+}
+
+void batch_free(qf_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_tables) cudaFree(b->d_tables);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->d_tables = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const int64_t* batch,
+                          const qf_pauli* obs, int32_t loss_kind, size_t* workspace_bytes, qf_batch** out) {
+  if (!out || !workspace_bytes) return fail(QF_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (n_circuits <= 0 || !circuits || !batch || !obs) return fail(QF_ERR_INVALID_ARG, "empty or null circuit list");
+  if (loss_kind != QF_LOSS_SUM && loss_kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
+  qf_batch* b = nullptr;
+  try {
+    b = new qf_batch();
+    b->n = n_circuits;
+    b->loss_kind = loss_kind;
+    b->circ.assign(circuits, circuits + n_circuits);
+    b->B.assign(batch, batch + n_circuits);
+    b->theta_off.assign(n_circuits + 1, 0);
+    b->x_off.assign(n_circuits + 1, 0);
+    b->sample_off.assign(n_circuits + 1, 0);
+    b->grad_off.assign(n_circuits + 1, 0);
+    b->ws_off.assign(n_circuits, 0);
+    std::vector<Layout> lay(n_circuits);
+    std::vector<Obs> ob(n_circuits);
+    size_t ws = 0;
+    for (int i = 0; i < n_circuits; ++i) {
+      qf_circuit* c = b->circ[i];
+      const std::string at = " (circuit " + std::to_string(i) + ")";
+      if (!c || !c->planned) throw std::invalid_argument("circuit has no plan" + at);
+      if (c->path != QF_PATH_FUSED || !c->fp.rounds)
+        throw std::invalid_argument("batched launches need fused round programs (RZ/RY rotations, CZ on "
+                                    "neighbouring qubits, at least 7 qubits per tile)" + at);
+      if (b->B[i] < 1) throw std::invalid_argument("batch must be >= 1" + at);
+      if (check_obs(c, obs[i], &ob[i]) != QF_OK) throw std::invalid_argument(g_err + at);
+      for (const qf::PassDesc& pd : c->fp.fwd) {
+        uint32_t xl;
+        if ((pd.flags & qf::PF_EXPECT) && !local_xmask(pd, ob[i].x, &xl))
+          throw std::invalid_argument("observable X/Y qubits must lie in the last pass's tile" + at);
+      }
+      lay[i] = make_layout(c, b->B[i]);
+      b->ws_off[i] = ws;
+      ws += lay[i].total;
+      b->theta_off[i + 1] = b->theta_off[i] + c->circ.n_params;
+      b->x_off[i + 1] = b->x_off[i] + b->B[i] * c->circ.n;
+      b->sample_off[i + 1] = b->sample_off[i] + b->B[i];
+      b->grad_off[i + 1] = b->grad_off[i] + c->circ.n_params;
+    }
+    b->lterm_off = ws;
+    ws += al((size_t)b->sample_off[n_circuits] * 8);
+    b->queue_off = ws;
+    ws += 256;
+    b->ws_total = ws;
+
+    // ---- device tables: every circuit's plan tables and pass descriptors, the
+    // circuit records, the work items and the prefix offsets
+    std::vector<size_t> tab_off(n_circuits), fwd_off(n_circuits), bwd_off(n_circuits);
+    size_t o = 0;
+    for (int i = 0; i < n_circuits; ++i) {
+      tab_off[i] = o;
+      o = al(o + b->circ[i]->blob.size());
+      fwd_off[i] = o;
+      o = al(o + b->circ[i]->fp.fwd.size() * sizeof(qf::PassDesc));
+      bwd_off[i] = o;
+      o = al(o + b->circ[i]->fp.bwd.size() * sizeof(qf::PassDesc));
+    }
+    // work items: samples of one circuit; largest first
+    std::vector<qf::BatchItem> items;
+    std::vector<double> cost;
+    for (int i = 0; i < n_circuits; ++i) {
+      const qf::FusedPlan& P = b->circ[i]->fp;
+      const int tps_log2 = P.n_eff - P.K;
+      const int tpc = qf::kThreads >> (P.K - qf::kRegBits);
+      const int step = tps_log2 == 0 ? tpc : 1;
+      for (int64_t b0 = 0; b0 < b->B[i]; b0 += step) {
+        items.push_back({i, (int32_t)b0});
+        const double ns = (double)std::min<int64_t>(step, b->B[i] - b0);
+        cost.push_back(ns * std::ldexp(1.0, P.n_eff) * (double)std::max(P.n_rounds, 1));
+      }
+    }
+    std::vector<size_t> ord(items.size());
+    for (size_t k = 0; k < ord.size(); ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    const size_t circ_off = o;
+    o = al(o + n_circuits * sizeof(qf::BatchCircuit));
+    const size_t items_off = o;
+    o = al(o + items.size() * sizeof(qf::BatchItem));
+    const size_t prep_off = o;
+    o = al(o + (n_circuits + 1) * sizeof(int64_t));
+    const size_t gout_off = o;
+    o = al(o + (n_circuits + 1) * sizeof(int64_t));
+    const size_t total = o;
+
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return fail(QF_ERR_OOM, std::string("cudaMalloc of batch tables failed: ") + cudaGetErrorString(e));
+    }
+    b->d_tables = d;
+    char* base = static_cast<char*>(d);
+    std::vector<char> img(total, 0);
+    std::vector<qf::BatchCircuit> recs(n_circuits);
+    std::vector<int64_t> prep_pref(n_circuits + 1, 0), gout_pref(n_circuits + 1, 0);
+    for (int i = 0; i < n_circuits; ++i) {
+      qf_circuit* c = b->circ[i];
+      const qf::FusedPlan& P = c->fp;
+      const Layout& L = lay[i];
+      const size_t w0 = b->ws_off[i];
+      memcpy(img.data() + tab_off[i], c->blob.data(), c->blob.size());
+      std::vector<qf::PassDesc> fp = P.fwd, bp = P.bwd;
+      for (auto& pd : fp) {
+        pd.xm_local = 0;
+        if (pd.flags & qf::PF_EXPECT) local_xmask(pd, ob[i].x, &pd.xm_local);
+      }
+      for (auto& pd : bp) {
+        pd.xm_local = 0;
+        if (pd.lam_src == qf::LAM_SEED) local_xmask(pd, ob[i].x, &pd.xm_local);
+      }
+      memcpy(img.data() + fwd_off[i], fp.data(), fp.size() * sizeof(qf::PassDesc));
+      memcpy(img.data() + bwd_off[i], bp.data(), bp.size() * sizeof(qf::PassDesc));
+      const DevTables T = tables_at(c, base + tab_off[i]);
+      qf::BatchCircuit& r = recs[i];
+      qf::PassArgs a{};
+      a.n_eff = P.n_eff;
+      a.tps_log2 = P.n_eff - P.K;
+      a.B = b->B[i];
+      a.mats = rel<const float4>(w0 + L.mats);
+      a.enc = rel<const float2>(w0 + L.enc);
+      a.work = rel<float2>(w0 + L.work);
+      a.lam = rel<float2>(w0 + L.lam);
+      a.slots = rel<float2>(w0 + L.slots);
+      a.slot_stride = L.state_elems;
+      a.z_mask = ob[i].z;
+      a.y_count = ob[i].y;
+      a.dLdE = rel<const double>(w0 + L.dLdE);
+      a.e_part = rel<double>(w0 + L.epart);
+      a.g_part = rel<double>(w0 + L.gpart);
+      a.shear = rel<const float4>(w0 + L.cs);
+      a.n_slots = P.n_terms;
+      r.fa = a;
+      r.fa.ops = T.fwd_ops;
+      r.fa.rounds = T.fwd_rounds;
+      r.ba = a;
+      r.ba.ops = T.bwd_ops;
+      r.ba.rounds = T.bwd_rounds;
+      r.ba.g_accum = a.tps_log2 > 0 ? 1 : 0;
+      r.fwd = reinterpret_cast<const qf::PassDesc*>(base + fwd_off[i]);
+      r.bwd = reinterpret_cast<const qf::PassDesc*>(base + bwd_off[i]);
+      r.n_fwd = (int32_t)fp.size();
+      r.n_bwd = (int32_t)bp.size();
+      r.samples_per_item = a.tps_log2 == 0 ? (qf::kThreads >> (P.K - qf::kRegBits)) : 1;
+      r.loss_kind = loss_kind;
+      r.inv_B = 1.0 / (double)b->B[i];
+      r.theta_off = b->theta_off[i];
+      r.x_off = b->x_off[i];
+      r.sample_off = b->sample_off[i];
+      r.grad_off = b->grad_off[i];
+      qf::PrepArgs& p = r.prep;
+      p = qf::PrepArgs{};
+      p.n_fused = (int32_t)P.fuse_off.size() - 1;
+      p.fuse_off = T.fuse_off;
+      p.fuse_gates = T.fuse_gates;
+      p.mats = rel<float4>(w0 + L.mats);
+      p.n_terms = P.n_terms;
+      p.term_off = T.term_off;
+      p.term_params = T.term_params;
+      p.shear = rel<float4>(w0 + L.cs);
+      p.B = b->B[i];
+      p.n = c->circ.n;
+      p.n_eff = P.n_eff;
+      p.enc = rel<float2>(w0 + L.enc);
+      r.n_params = c->circ.n_params;
+      r.param_off = T.param_off;
+      r.param_terms = T.param_terms;
+      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff;
+      gout_pref[i + 1] = gout_pref[i] + c->circ.n_params;
+    }
+    memcpy(img.data() + circ_off, recs.data(), recs.size() * sizeof(qf::BatchCircuit));
+    for (size_t k = 0; k < ord.size(); ++k)
+      memcpy(img.data() + items_off + k * sizeof(qf::BatchItem), &items[ord[k]], sizeof(qf::BatchItem));
+    memcpy(img.data() + prep_off, prep_pref.data(), prep_pref.size() * sizeof(int64_t));
+    memcpy(img.data() + gout_off, gout_pref.data(), gout_pref.size() * sizeof(int64_t));
+    e = cudaMemcpy(d, img.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      batch_free(b);
+      delete b;
+      return fail(QF_ERR_CUDA, std::string("batch table upload failed: ") + cudaGetErrorString(e));
+    }
+    b->args = qf::BatchArgs{};
+    b->args.circ = reinterpret_cast<const qf::BatchCircuit*>(base + circ_off);
+    b->args.n_circ = n_circuits;
+    b->args.items = reinterpret_cast<const qf::BatchItem*>(base + items_off);
+    b->args.n_items = (int32_t)items.size();
+    b->args.prep_off = reinterpret_cast<const int64_t*>(base + prep_off);
+    b->args.grad_out_off = reinterpret_cast<const int64_t*>(base + gout_off);
+    b->args.n_samples = b->sample_off[n_circuits];
+    b->prep_total = prep_pref[n_circuits];
+    b->n_grad_out = gout_pref[n_circuits];
+    b->grid = qf::batch_grid();
+    if (b->grid <= 0) {
+      batch_free(b);
+      delete b;
+      return fail(QF_ERR_CUDA, "cannot query the device's SM count");
+    }
+  } catch (const std::bad_alloc&) {
+    if (b) {
+      batch_free(b);
+      delete b;
+    }
+    return fail(QF_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& ex) {
+    if (b) {
+      batch_free(b);
+      delete b;
+    }
+    return fail(QF_ERR_INVALID_ARG, ex.what());
+  }
+  *workspace_bytes = b->ws_total;
+  *out = b;
+  return QF_OK;
+}
+
+qf_status qf_batch_layout(const qf_batch* b, int64_t* theta_off, int64_t* x_off, int64_t* sample_off) {
+  if (!b) return fail(QF_ERR_INVALID_ARG, "null batch");
+  const size_t n = (size_t)b->n + 1;
+  if (theta_off) memcpy(theta_off, b->theta_off.data(), n * sizeof(int64_t));
+  if (x_off) memcpy(x_off, b->x_off.data(), n * sizeof(int64_t));
+  if (sample_off) memcpy(sample_off, b->sample_off.data(), n * sizeof(int64_t));
+  return QF_OK;
+}
+
+qf_status qf_batch_train_step(qf_batch* b, const float* theta_d, const float* x_d, const float* y_d,
+                              double* loss_d, double* E_d, double* grad_d, void* ws_d, size_t ws_bytes,
+                              void* stream) {
+  if (!b) return fail(QF_ERR_INVALID_ARG, "null batch");
+  if (!ws_d || ((uintptr_t)ws_d & 255) != 0) return fail(QF_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < b->ws_total) return fail(QF_ERR_WORKSPACE, "workspace smaller than qf_batch_create reported");
+  if (!theta_d || !x_d || !loss_d || !E_d || !grad_d || (b->loss_kind == QF_LOSS_MSE && !y_d))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QF_ERR_CUDA, std::string("pending CUDA error: ") + cudaGetErrorString(e));
+  qf::BatchArgs a = b->args;
+  a.ws = static_cast<char*>(ws_d);
+  a.theta = theta_d;
+  a.x = x_d;
+  a.y = y_d;
+  a.E = E_d;
+  a.grad = grad_d;
+  a.loss = loss_d;
+  a.lterm = reinterpret_cast<double*>(a.ws + b->lterm_off);
+  a.queue = reinterpret_cast<int32_t*>(a.ws + b->queue_off);
+  QF_CU(qf::launch_batch(a, b->grid, b->prep_total, b->n_grad_out, static_cast<cudaStream_t>(stream)));
+  return QF_OK;
+}
+
+qf_status qf_batch_graph_capture(qf_batch* b, const float* theta_d, const float* x_d, const float* y_d,
+                                 double* loss_d, double* E_d, double* grad_d, void* ws_d, size_t ws_bytes,
+                                 void* stream) {
+  if (!b) return fail(QF_ERR_INVALID_ARG, "null batch");
+  if (!stream) return fail(QF_ERR_INVALID_ARG, "capture needs a non-default stream");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  // one eager step first: per-device kernel attributes are set outside the capture
+  qf_status s = qf_batch_train_step(b, theta_d, x_d, y_d, loss_d, E_d, grad_d, ws_d, ws_bytes, stream);
+  if (s != QF_OK) return s;
+  QF_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  s = qf_batch_train_step(b, theta_d, x_d, y_d, loss_d, E_d, grad_d, ws_d, ws_bytes, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (s != QF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(QF_ERR_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+  b->graph = g;
+  QF_CU(cudaGraphInstantiate(&b->exec, g, 0));
+  return QF_OK;
+}
+
+qf_status qf_batch_graph_launch(qf_batch* b, void* stream) {
+  if (!b || !b->exec) return fail(QF_ERR_INVALID_ARG, "no captured graph (call qf_batch_graph_capture)");
+  QF_CU(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
+  return QF_OK;
+}
+
+qf_status qf_batch_info(const qf_batch* b, int64_t* n_items, int64_t* n_samples, int64_t* n_params) {
+  if (!b) return fail(QF_ERR_INVALID_ARG, "null batch");
+  if (n_items) *n_items = b->args.n_items;
+  if (n_samples) *n_samples = b->args.n_samples;
+  if (n_params) *n_params = b->n_grad_out;
+  return QF_OK;
+}
+
+qf_status qf_batch_destroy(qf_batch* b) {
+  if (!b) return QF_OK;
+  batch_free(b);
+  delete b;
+  return QF_OK;
 }
 
 qf_status qf_profile(qf_circuit* c, int32_t on) {

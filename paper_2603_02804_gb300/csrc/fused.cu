@@ -295,15 +295,27 @@ __device__ __forceinline__ float4 term_shear(const float4* sh, uint32_t t) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Static shared memory of a pass (the tiles themselves are dynamic).
+struct PassShared {
+  uint32_t lg[256];
+  float red[2][kThreads / 32][kMaxStepSlots];
+  int32_t slot[2][kMaxStepSlots];
+  double dred[kThreads / 32];
+  uint32_t gmap[16];
+  uint32_t grp[4][4];
+};
+
+// One CTA's share of a pass: tiles first_tile .. first_tile + tiles_per_cta-1
+// (tile = sample * tiles_per_sample + tile within the sample). Ends with a
+// barrier, so a CTA may call it again for another pass or tile range.
 template <bool BWD, bool ROUNDS>
-__global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const PassArgs a) {
-  extern __shared__ __align__(16) float2 smem[];
-  __shared__ uint32_t s_lg[256];
-  __shared__ float s_red[2][kThreads / 32][kMaxStepSlots];
-  __shared__ int32_t s_slot[2][kMaxStepSlots];
-  __shared__ double s_dred[kThreads / 32];
-  __shared__ uint32_t s_gmap[16];
-  __shared__ uint32_t s_grp[4][4];
+__device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_tile, float2* smem, PassShared& sh) {
+  uint32_t (&s_lg)[256] = sh.lg;
+  float (&s_red)[2][kThreads / 32][kMaxStepSlots] = sh.red;
+  int32_t (&s_slot)[2][kMaxStepSlots] = sh.slot;
+  double (&s_dred)[kThreads / 32] = sh.dred;
+  uint32_t (&s_gmap)[16] = sh.gmap;
+  uint32_t (&s_grp)[4][4] = sh.grp;
 
   const PassDesc& pd = a.pd;
   const int K = pd.K;
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
   const uint32_t tau = (uint32_t)(tid & (Tt - 1));
   const int tiles_per_cta = kThreads >> tl2;
   const int64_t total_tiles = (int64_t)a.B << a.tps_log2;
-  const int64_t tile = (int64_t)blockIdx.x * tiles_per_cta + tile_in_cta;
+  const int64_t tile = first_tile + tile_in_cta;
   const bool active = tile < total_tiles;
   const int64_t b = active ? (tile >> a.tps_log2) : 0;
   const uint32_t t_in = active ? (uint32_t)(tile & ((1ll << a.tps_log2) - 1)) : 0u;
@@ -472,11 +484,28 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
         if (BWD) tl[pb ^ reg_off(j, so)] = l[j];
       }
       __syncthreads();
-      if (BWD && Tt >= 32) {
+      if (BWD && Tt >= 32 && a.g_accum) {
+        // every tile of this call belongs to one sample: one thread per term sums
+        // the tiles in order and adds to the sample's row (stored by its tile 0)
+        const int nk = nr * 8;
+        const int64_t b2 = first_tile >> a.tps_log2;
+        const bool first = (first_tile & ((1ll << a.tps_log2) - 1)) == 0;
+        for (int kk = tid; kk < nk; kk += kThreads) {
+          const int32_t term = s_slot[buf][kk];
+          if (term < 0) continue;
+          double sum = 0.0;
+          for (int tc = 0; tc < tiles_per_cta; ++tc)
+            if (first_tile + tc < total_tiles)
+              for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
+          double* dst = a.g_part + b2 * a.n_slots + term;
+          *dst = first ? 0.5 * sum : *dst + 0.5 * sum;
+        }
+        buf ^= 1;
+      } else if (BWD && Tt >= 32) {
         const int nk = nr * 8;
         for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
           const int tc = e / nk, kk = e - tc * nk;
-          const int64_t t2 = (int64_t)blockIdx.x * tiles_per_cta + tc;
+          const int64_t t2 = first_tile + tc;
           const int32_t term = s_slot[buf][kk];
           if (t2 < total_tiles && term >= 0) {
             double sum = 0.0;
@@ -557,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
       if (BWD && Tt >= 32) {
         for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
           const int tc = e / nk, kk = e - tc * nk;
-          const int64_t t2 = (int64_t)blockIdx.x * tiles_per_cta + tc;
+          const int64_t t2 = first_tile + tc;
           if (t2 < total_tiles) {
             double sum = 0.0;
             for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
@@ -614,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
       if (lane == 0) s_dred[warp] = d;
       __syncthreads();
       if (tid < tiles_per_cta) {
-        const int64_t t2 = (int64_t)blockIdx.x * tiles_per_cta + tid;
+        const int64_t t2 = first_tile + tid;
         if (t2 < total_tiles) {
           double sum = 0.0;
           for (int w = 0; w < wpt; ++w) sum += s_dred[tid * wpt + w];
@@ -625,14 +654,29 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
       a.e_part[tile] = d;
     }
   }
+  __syncthreads();
+}
+
+template <bool BWD, bool ROUNDS>
+__global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ PassShared sh;
+  pass_cta<BWD, ROUNDS>(a, (int64_t)blockIdx.x * (kThreads >> (a.pd.K - kRegBits)), smem, sh);
 }
 
 // ---------------------------------------------------------------------------
 // Gate tables from theta in float64, rounded once to float32:
 //   fused 2x2 products (forward), (cos, sin) of theta/2 per slot (backward),
 //   (cos, sin) of x/2 per sample and qubit (encoding).
+__device__ void prep_one(const PrepArgs& a, int64_t i);
+
 __global__ void prep_kernel(const PrepArgs a) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  prep_one(a, i);
+}
+
+// Element i of the tables: fused matrices, then terms, then encodings.
+__device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (i < a.n_fused) {
     double u[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {1, 0}}};  // [row][col][re/im]
     for (int j = a.fuse_off[i]; j < a.fuse_off[i + 1]; ++j) {
@@ -759,6 +803,195 @@ __global__ void loss_kernel(int kind, const double* E, const float* y, int64_t B
     __syncthreads();
   }
   if (threadIdx.x == 0) loss[0] = kind == 1 ? red[0] / (double)B : red[0];
+}
+
+// ---- batched persistent launch -------------------------------------------------
+namespace {
+
+template <class T>
+__device__ __forceinline__ T* rebase(T* p, char* base) {
+  return reinterpret_cast<T*>(base + reinterpret_cast<uintptr_t>(p));
+}
+template <class T>
+__device__ __forceinline__ const T* rebase(const T* p, char* base) {
+  return reinterpret_cast<const T*>(base + reinterpret_cast<uintptr_t>(p));
+}
+
+__device__ __forceinline__ int find_circuit(const int64_t* off, int n, int64_t i) {
+  int lo = 0, hi = n;  // off[lo] <= i < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Copy a circuit's pass arguments into shared memory with pass descriptor pd
+// and the workspace pointers rebased.
+__device__ void load_args(PassArgs& dst, const PassArgs& src, const PassDesc& pd, char* ws) {
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(&src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(PassArgs) / 4); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dst.pd = pd;
+    dst.mats = rebase(dst.mats, ws);
+    dst.shear = rebase(dst.shear, ws);
+    dst.enc = rebase(dst.enc, ws);
+    dst.work = rebase(dst.work, ws);
+    dst.lam = rebase(dst.lam, ws);
+    dst.slots = rebase(dst.slots, ws);
+    dst.dLdE = rebase(dst.dLdE, ws);
+    dst.e_part = rebase(dst.e_part, ws);
+    dst.g_part = rebase(dst.g_part, ws);
+  }
+  __syncthreads();
+}
+
+__device__ void run_item_pass(bool bwd, const PassArgs& a, int32_t b0) {
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ PassShared sh;
+  const int tpc = kThreads >> (a.pd.K - kRegBits);
+  if (a.tps_log2 == 0) {
+    // a tile is a sample: the item's samples b0 .. b0 + tpc - 1 in one call
+    if (bwd) pass_cta<true, true>(a, b0, smem, sh);
+    else pass_cta<false, true>(a, b0, smem, sh);
+  } else {
+    const int64_t tps = 1ll << a.tps_log2;
+    for (int64_t t = 0; t < tps; t += tpc) {
+      if (bwd) pass_cta<true, true>(a, (int64_t)b0 * tps + t, smem, sh);
+      else pass_cta<false, true>(a, (int64_t)b0 * tps + t, smem, sh);
+    }
+  }
+}
+
+}  // namespace
+
+__global__ void batch_prep_kernel(const BatchArgs a, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int c = find_circuit(a.prep_off, a.n_circ, i);
+  PrepArgs p = a.circ[c].prep;
+  p.theta = a.theta + a.circ[c].theta_off;
+  p.x = a.x + a.circ[c].x_off;
+  p.mats = rebase(p.mats, a.ws);
+  p.shear = rebase(p.shear, a.ws);
+  p.enc = rebase(p.enc, a.ws);
+  prep_one(p, i - a.prep_off[c]);
+}
+
+// Persistent kernel: CTAs take work items (one sample, or a group of small
+// samples, of one circuit; largest first) from an atomic queue and run the
+// item's forward passes, its loss derivative and its adjoint passes
+// themselves, so items never wait on each other.
+__global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs a) {
+  __shared__ PassArgs s_a;
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= a.n_items) return;
+    const BatchItem item = a.items[it];
+    const BatchCircuit& C = a.circ[item.c];
+    for (int p = 0; p < C.n_fwd; ++p) {
+      load_args(s_a, C.fa, C.fwd[p], a.ws);
+      run_item_pass(false, s_a, item.b0);
+    }
+    // E and dL/dE of the item's samples (their tiles were written by this CTA)
+    {
+      const int64_t B = C.fa.B;
+      const int64_t tps = 1ll << C.fa.tps_log2;
+      const int ns = (int)min((int64_t)C.samples_per_item, B - item.b0);
+      if ((int)threadIdx.x < ns) {
+        const int64_t b = item.b0 + threadIdx.x;
+        const double* ep = rebase(C.fa.e_part, a.ws) + b * tps;
+        double e = 0.0;
+        for (int64_t t = 0; t < tps; ++t) e += ep[t];
+        const int64_t s = C.sample_off + b;
+        a.E[s] = e;
+        double g = 1.0, lt = e;
+        if (C.loss_kind == 1) {
+          const double dd = e - (double)a.y[s];
+          g = 2.0 * dd * C.inv_B;
+          lt = dd * dd * C.inv_B;
+        }
+        const_cast<double*>(rebase(C.ba.dLdE, a.ws))[b] = g;  // the item's own workspace row
+        a.lterm[s] = lt;
+      }
+      __syncthreads();
+    }
+    for (int p = 0; p < C.n_bwd; ++p) {
+      load_args(s_a, C.ba, C.bwd[p], a.ws);
+      run_item_pass(true, s_a, item.b0);
+    }
+  }
+}
+
+// grad[o], o over every circuit's parameters: one warp per value, fixed order.
+__global__ void batch_g_reduce_kernel(const BatchArgs a, int64_t n_out) {
+  const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= n_out) return;
+  const int c = find_circuit(a.grad_out_off, a.n_circ, o);
+  const BatchCircuit& C = a.circ[c];
+  const int p = (int)(o - a.grad_out_off[c]);
+  const double* gp = rebase(C.ba.g_part, a.ws);
+  const int64_t rows = C.ba.g_accum ? C.ba.B : (C.ba.B << C.ba.tps_log2);
+  double s = 0.0;
+  for (int k = C.param_off[p]; k < C.param_off[p + 1]; ++k) {
+    const int term = C.param_terms[k];
+    for (int64_t r = lane; r < rows; r += 32) s += gp[r * C.ba.n_slots + term];
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) a.grad[C.grad_off + p] = s;
+}
+
+__global__ void batch_loss_kernel(const BatchArgs a) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < a.n_samples; i += blockDim.x) s += a.lterm[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.loss[0] = red[0];
+}
+
+int batch_grid() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return 2 * sms;
+}
+
+cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64_t n_grad_out, cudaStream_t st) {
+  static bool once[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)kTileAmps * sizeof(float2);
+  if (dev >= 0 && dev < 64 && !once[dev]) {
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    once[dev] = true;
+  }
+  if (prep_total > 0) batch_prep_kernel<<<(unsigned)((prep_total + 255) / 256), 256, 0, st>>>(a, prep_total);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+  if (a.n_items > 0) {
+    const int g = grid < a.n_items ? grid : a.n_items;
+    batch_kernel<<<(unsigned)g, kThreads, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (n_grad_out > 0) batch_g_reduce_kernel<<<(unsigned)((n_grad_out * 32 + 255) / 256), 256, 0, st>>>(a, n_grad_out);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  batch_loss_kernel<<<1, 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 // ---- launchers ----------------------------------------------------------------

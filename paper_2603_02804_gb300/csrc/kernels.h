@@ -26,8 +26,9 @@ struct PassArgs {
   uint32_t y_count;       // number of Y factors (phase i^y_count)
   const double* dLdE;     // [B]
   double* e_part;         // [B * tiles per sample]
-  double* g_part;         // [B * tiles per sample][n_slots]
+  double* g_part;         // [B * tiles per sample][n_slots], or [B][n_slots] when g_accum
   int32_t n_slots;
+  int32_t g_accum;        // round programs: add the partials of a sample's tiles into one row
 };
 
 struct PrepArgs {
@@ -67,6 +68,54 @@ cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E,
 cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st);
 cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
                         cudaStream_t st);
+
+// ---- batched persistent launch ------------------------------------------------
+// Pointers into the workspace are stored as byte offsets from its base and
+// rebased in the kernels; theta/x/y/E/grad are element offsets into the
+// caller's concatenated buffers. Plan tables are absolute device pointers.
+struct BatchCircuit {
+  PassArgs fa, ba;            // forward / backward arguments (pd set per pass)
+  const PassDesc* fwd;        // forward passes (observable folded in)
+  const PassDesc* bwd;
+  int32_t n_fwd, n_bwd;
+  int32_t samples_per_item;   // samples of one work item (tiles per CTA when a tile is a sample)
+  int32_t loss_kind;          // QF_LOSS_SUM or QF_LOSS_MSE
+  double inv_B;
+  int64_t theta_off, x_off, sample_off, grad_off;
+  PrepArgs prep;              // theta, x relative to the caller buffers; tables ws-relative
+  int32_t n_params;
+  const int32_t* param_off;   // parameter -> gradient terms
+  const int32_t* param_terms;
+};
+
+struct BatchItem {
+  int32_t c;   // circuit
+  int32_t b0;  // first sample
+};
+
+struct BatchArgs {
+  const BatchCircuit* circ;
+  int32_t n_circ;
+  const BatchItem* items;
+  int32_t n_items;
+  int32_t* queue;              // work-queue head (zeroed before each launch)
+  char* ws;
+  const float* theta;
+  const float* x;
+  const float* y;
+  double* E;
+  double* grad;
+  double* loss;
+  double* lterm;               // per-sample loss terms (workspace)
+  const int64_t* prep_off;     // [n_circ + 1]
+  const int64_t* grad_out_off; // [n_circ + 1]
+  int64_t n_samples;
+};
+
+// prep, work-queue reset, persistent forward+adjoint, gradient and loss
+// reductions: 4 kernels and one memset on `st`.
+cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64_t n_grad_out, cudaStream_t st);
+int batch_grid();
 
 // ---- per-gate comparator ------------------------------------------------------
 struct PerGateArgs {

@@ -70,6 +70,14 @@ SIGNATURES = {
     "qf_train_step": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
     "qf_train_step_host": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
     "qf_train_step_noalloc": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp], _i32),
+    "qf_batch_create": ([_i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(qf_pauli), _i32,
+                         ctypes.POINTER(_sz), ctypes.POINTER(_vp)], _i32),
+    "qf_batch_layout": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i32),
+    "qf_batch_train_step": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
+    "qf_batch_graph_capture": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
+    "qf_batch_graph_launch": ([_vp, _vp], _i32),
+    "qf_batch_info": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i32),
+    "qf_batch_destroy": ([_vp], _i32),
     "qf_launch_count": ([_vp, ctypes.POINTER(_i64)], _i32),
     "qf_profile": ([_vp, _i32], _i32),
     "qf_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
@@ -211,6 +219,48 @@ def qf_train_step_noalloc(handle, theta, x, y, batch, loss_kind, obs, loss, E, g
 
 
 QF_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
+
+
+def qf_batch_create(circuits, batch, obs, loss_kind=QF_LOSS_SUM):
+    """Returns (batch handle, workspace bytes)."""
+    n = len(circuits)
+    hs = (_vp * n)(*circuits)
+    bs = (_i64 * n)(*[int(v) for v in batch])
+    ob = (qf_pauli * n)(*obs)
+    ws = _sz()
+    h = _vp()
+    _check(load().qf_batch_create(n, hs, bs, ob, loss_kind, ctypes.byref(ws), ctypes.byref(h)))
+    return h.value, ws.value
+
+
+def qf_batch_layout(handle, n):
+    t, x, s = (_i64 * (n + 1))(), (_i64 * (n + 1))(), (_i64 * (n + 1))()
+    _check(load().qf_batch_layout(handle, t, x, s))
+    return list(t), list(x), list(s)
+
+
+def qf_batch_train_step(handle, theta, x, y, loss, E, grad, ws, ws_bytes, stream=None) -> None:
+    _check(load().qf_batch_train_step(handle, _ptr(theta), _ptr(x), _ptr(y), _ptr(loss), _ptr(E), _ptr(grad),
+                                      _ptr(ws), ws_bytes, _stream(stream)))
+
+
+def qf_batch_graph_capture(handle, theta, x, y, loss, E, grad, ws, ws_bytes, stream) -> None:
+    _check(load().qf_batch_graph_capture(handle, _ptr(theta), _ptr(x), _ptr(y), _ptr(loss), _ptr(E), _ptr(grad),
+                                         _ptr(ws), ws_bytes, _stream(stream)))
+
+
+def qf_batch_graph_launch(handle, stream) -> None:
+    _check(load().qf_batch_graph_launch(handle, _stream(stream)))
+
+
+def qf_batch_info(handle) -> dict:
+    a, b, c = _i64(), _i64(), _i64()
+    _check(load().qf_batch_info(handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"n_items": a.value, "n_samples": b.value, "n_params": c.value}
+
+
+def qf_batch_destroy(handle) -> None:
+    _check(load().qf_batch_destroy(handle))
 
 
 def qf_launch_count(handle) -> int:

@@ -161,3 +161,69 @@ class HEA(torch.nn.Module):
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         return QFuseFn.apply(self.theta, x.to(device=self.sim.device, dtype=torch.float32), self.sim)
+
+
+class Batch:
+    """Many hardware-efficient-ansatz circuits trained in one persistent launch.
+
+    specs: list of (n_qubits, n_layers, batch). tile_bits: None (12, the
+    whole state for n <= 12), an int, or a callable (n, d, B) -> K, e.g. an
+    autotuner's choice. Inputs and outputs are concatenated over circuits in
+    spec order (offsets from `layout()`).
+    """
+
+    def __init__(self, specs, loss: str = "sum", obs="Z", ckpt_layers: int = 0, tile_bits=None, device=None):
+        _cuda_check()
+        self.device = torch.device(device or "cuda")
+        self.specs = [(int(n), int(d), int(B)) for n, d, B in specs]
+        self.loss = loss
+        self.handles = []
+        pauli_list = []
+        for n, d, B in self.specs:
+            h = qfuse.qf_hea_create(n, d, qfuse.QF_ENT_CHAIN)
+            self.handles.append(h)
+            K = tile_bits(n, d, B) if callable(tile_bits) else (tile_bits or 0)
+            qfuse.qf_plan(h, B, qfuse.QF_PATH_FUSED, K, ckpt_layers, host_only=True)
+            pauli_list.append(qfuse.pauli(obs, n) if not isinstance(obs, qfuse.qf_pauli) else obs)
+        with torch.cuda.device(self.device):
+            self.handle, self.ws_bytes = qfuse.qf_batch_create(self.handles, [B for _, _, B in self.specs],
+                                                               pauli_list, _LOSS[loss])
+            self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
+        self.theta_off, self.x_off, self.sample_off = qfuse.qf_batch_layout(self.handle, len(self.specs))
+        info = qfuse.qf_batch_info(self.handle)
+        self.n_items = info["n_items"]
+        self.n_samples = info["n_samples"]
+        self.n_params = info["n_params"]
+        self._graph_stream = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                qfuse.qf_batch_destroy(h)
+            except Exception:
+                pass
+        for c in getattr(self, "handles", []):
+            try:
+                qfuse.qf_circuit_destroy(c)
+            except Exception:
+                pass
+
+    def outputs(self):
+        z = lambda k: torch.empty(k, dtype=torch.float64, device=self.device)
+        return z(1), z(self.n_samples), z(self.n_params)
+
+    def train_step(self, theta, x, y=None, out=None):
+        loss, E, g = out if out is not None else self.outputs()
+        qfuse.qf_batch_train_step(self.handle, theta, x, y, loss, E, g, self.ws, self.ws_bytes,
+                                  torch.cuda.current_stream(self.device))
+        return loss, E, g
+
+    def capture(self, theta, x, y, out, stream):
+        """Capture one step with these buffers into a CUDA graph (replay())."""
+        loss, E, g = out
+        self._graph_stream = stream
+        qfuse.qf_batch_graph_capture(self.handle, theta, x, y, loss, E, g, self.ws, self.ws_bytes, stream)
+
+    def replay(self):
+        qfuse.qf_batch_graph_launch(self.handle, self._graph_stream)
