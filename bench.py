@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
     return ap.parse_args()
@@ -196,8 +196,98 @@ def run_reference(args, w):
     return 0
 
 
+def run_mixed(args):
+    """512 uneven circuits (n 8..18, d 10..200, B 1..64) trained by one
+    persistent launch per step; eager steps and CUDA-graph replays timed."""
+    import torch
+    from paper_2603_02804_gb300 import build as qbuild
+    from paper_2603_02804_gb300.autotune import Autotuner
+    from paper_2603_02804_gb300.torch_api import Batch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    peaks, peak_src = load_peaks()
+    circs = workloads.mixed_circuits(512, seed=104 + 1000 * rank)
+    specs = [(c.n, c.d, c.B) for c in circs]
+    tuner = Autotuner(path=os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None)
+    t0 = time.perf_counter()
+    bt = Batch(specs, loss="sum", tile_bits=tuner)
+    tune_s = time.perf_counter() - t0
+    cat = lambda arrs: torch.from_numpy(np.concatenate([a.reshape(-1) for a in arrs])).cuda()
+    theta, x = cat([c.theta for c in circs]), cat([c.x for c in circs])
+    out = bt.outputs()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bt.train_step(theta, x, out=out)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            starts[k].record(stream)
+            bt.train_step(theta, x, out=out)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    gs = torch.cuda.Stream()
+    with torch.cuda.stream(gs):
+        bt.capture(theta, x, None, out, gs)
+    gs.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(gs)
+    for _ in range(args.steps):
+        bt.replay()
+    g1.record(gs)
+    gs.synchronize()
+    graph_ms = g0.elapsed_time(g1)
+    # end to end from pinned host buffers
+    th_h = theta.cpu().pin_memory()
+    x_h = x.cpu().pin_memory()
+    res_h = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in out]
+    e0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 4)):
+        theta.copy_(th_h, non_blocking=True)
+        x.copy_(x_h, non_blocking=True)
+        bt.train_step(theta, x, out=out)
+        for h, d in zip(res_h, out):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+    e_dt = (time.perf_counter() - e0) / max(1, args.steps // 4)
+    fl = sum(sum(algorithmic_flops(n, d, B)) for n, d, B in specs)
+    ms = total_ms / args.steps
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = fl / (ms / 1e3) / 1e12
+    line = {
+        "metric": "fwd+grad samples/s", "value": bt.n_samples * world / (ms / 1e3), "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": "mixed512: 512 HEA circuits n~U{8..18} d~U{10..200} B~U{1..64}, L=sum E, obs=Z0, "
+                               "one persistent launch per step", "samples_per_step": bt.n_samples,
+                   "work_items": bt.n_items, "tile_bits": "autotuned", "tune_s": tune_s,
+                   "l2": "inputs larger than L2 (workspace %.1f GB)" % (bt.ws_bytes / 1e9)},
+        "graph": {"value": bt.n_samples * world * args.steps / (graph_ms / 1e3), "unit": "samples/s",
+                  "ms_per_step": graph_ms / args.steps},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "batch_kernel (whole step: prep + persistent + reductions)"},
+        "e2e": {"value": bt.n_samples * world / e_dt, "unit": "samples/s",
+                "h2d_bytes_per_step": theta.numel() * 4 + x.numel() * 4,
+                "d2h_bytes_per_step": sum(t.numel() * 8 for t in out)},
+        "gpu_launches": 4 * args.steps,
+        "per_gate": None, "cpu_baseline": None, "clocks": clk.summary(),
+        "autotune": tuner.cache,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "mixed512":
+        return run_mixed(args)
     w = workloads.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

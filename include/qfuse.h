@@ -150,6 +150,22 @@ qf_status qf_circuit_destroy(qf_circuit* c);
 qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch,
                   size_t* workspace_bytes);
 
+/* The paper's checkpoint memory model (Sec. 3.4, Eqs. 5-8): with checkpoint
+ * blocks of b layers, d layers and k state vectors stored per layer of the
+ * active block (k = l_var + l_const for per-gate autograd, Eq. 5;
+ * k = ceil(l_var / alpha) for fused gates, Eq. 7), peak storage is
+ * (k b + d / b) state vectors. Returns that count; *b_best (may be NULL)
+ * receives the minimiser sqrt(d / k) (Eqs. 6 and 8). Host only. */
+double qf_mem_model(double k, double d, double b, double* b_best);
+
+/* Plan like qf_plan, choosing the checkpoint interval from memory: the
+ * smallest interval c (most checkpoints, least reversal drift) whose
+ * workspace for `batch` samples fits in mem_bytes. *ckpt_layers receives c
+ * (0 and QF_ERR_WORKSPACE when even one checkpoint of psi_M does not fit).
+ * opts->ckpt_layers is ignored. */
+qf_status qf_plan_fit(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t mem_bytes,
+                      int32_t* ckpt_layers, size_t* workspace_bytes);
+
 /* Fill *info with the current plan's summary. */
 qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
 

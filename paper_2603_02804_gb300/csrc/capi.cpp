@@ -609,6 +609,45 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
   return QF_OK;
 }
 
+double qf_mem_model(double k, double d, double b, double* b_best) {
+  if (b_best) *b_best = (k > 0 && d > 0) ? std::sqrt(d / k) : 0.0;
+  if (b <= 0) return 0.0;
+  return k * b + d / b;
+}
+
+qf_status qf_plan_fit(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t mem_bytes, int32_t* ckpt_layers,
+                      size_t* workspace_bytes) {
+  if (!c || !ckpt_layers) return fail(QF_ERR_INVALID_ARG, "null argument");
+  *ckpt_layers = 0;
+  qf_plan_opts o{};
+  if (opts) o = *opts;
+  const int d = c->circ.layers > 0 ? c->circ.layers : std::max(1, (int)c->circ.gates.size());
+  // the workspace shrinks as the interval grows: binary search on a host-only plan
+  auto ws_for = [&](int cl, size_t* ws) -> qf_status {
+    qf_plan_opts t = o;
+    t.ckpt_layers = cl;
+    t.host_only = 1;
+    return qf_plan(c, &t, batch, ws);
+  };
+  size_t ws = 0;
+  qf_status s = ws_for(d, &ws);
+  if (s != QF_OK) return s;
+  if (ws > mem_bytes) return fail(QF_ERR_WORKSPACE, "even a plan with only the final state does not fit");
+  int lo = 1, hi = d;  // hi fits
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if ((s = ws_for(mid, &ws)) != QF_OK) return s;
+    if (ws <= mem_bytes) hi = mid;
+    else lo = mid + 1;
+  }
+  qf_plan_opts fin = o;
+  fin.ckpt_layers = hi;
+  if ((s = qf_plan(c, &fin, batch, &ws)) != QF_OK) return s;
+  *ckpt_layers = hi;
+  if (workspace_bytes) *workspace_bytes = ws;
+  return QF_OK;
+}
+
 qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
   if (!c || !info) return fail(QF_ERR_INVALID_ARG, "null argument");
   if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan");

@@ -63,6 +63,10 @@ SIGNATURES = {
     "qf_circuit_destroy": ([_vp], _i32),
     "qf_plan": ([_vp, ctypes.POINTER(qf_plan_opts), _i64, ctypes.POINTER(_sz)], _i32),
     "qf_plan_info": ([_vp, ctypes.POINTER(qf_plan_info_t)], _i32),
+    "qf_mem_model": ([ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+                     ctypes.c_double),
+    "qf_plan_fit": ([_vp, ctypes.POINTER(qf_plan_opts), _i64, _sz, ctypes.POINTER(_i32), ctypes.POINTER(_sz)],
+                    _i32),
     "qf_plan_export": ([_vp, _i32, ctypes.POINTER(_i32), _i64, ctypes.POINTER(_i64)], _i32),
     "qf_forward": ([_vp, _vp, _vp, _i64, qf_pauli, _vp, _vp, _sz, _vp], _i32),
     "qf_backward": ([_vp, _vp, _vp, _i64, qf_pauli, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
@@ -171,6 +175,23 @@ def qf_plan(handle: int, batch: int, path: int = QF_PATH_FUSED, tile_bits: int =
     ws = _sz()
     _check(load().qf_plan(handle, ctypes.byref(o), batch, ctypes.byref(ws)))
     return ws.value
+
+
+def qf_mem_model(k: float, d: float, b: float):
+    """(stored state vectors k b + d / b, minimising block size sqrt(d / k))."""
+    best = ctypes.c_double()
+    m = load().qf_mem_model(float(k), float(d), float(b), ctypes.byref(best))
+    return m, best.value
+
+
+def qf_plan_fit(handle: int, batch: int, mem_bytes: int, path: int = QF_PATH_FUSED, tile_bits: int = 0,
+                host_only: bool = False, program: int = 0):
+    """Plan with the smallest checkpoint interval that fits mem_bytes: (c, workspace bytes)."""
+    o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program))
+    c = _i32()
+    ws = _sz()
+    _check(load().qf_plan_fit(handle, ctypes.byref(o), batch, mem_bytes, ctypes.byref(c), ctypes.byref(ws)))
+    return c.value, ws.value
 
 
 def qf_plan_info(handle: int) -> dict:

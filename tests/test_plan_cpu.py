@@ -24,7 +24,7 @@ def lib():
 
 def header_symbols():
     src = open(os.path.join(ROOT, "include", "qfuse.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:qf_status|const char\*|int32_t)\s+(qf_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:qf_status|const char\*|int32_t|double)\s+(qf_\w+)\s*\(", src, re.M)))
 
 
 def test_library_exports_every_declared_symbol(lib):
