@@ -284,10 +284,86 @@ def run_mixed(args):
     return 0
 
 
+def run_epoch(args, w):
+    """Large workload (n=20, d=1000, 1000 samples): micro-batches of `mb`
+    samples with the checkpoint interval chosen from free HBM; one step = one
+    epoch over all samples (gradients summed over micro-batches)."""
+    import torch
+    from paper_2603_02804_gb300 import build as qbuild
+    from paper_2603_02804_gb300 import qfuse
+    from paper_2603_02804_gb300.torch_api import Simulator
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    peaks, peak_src = load_peaks()
+    theta_np, x_np, _ = workloads.make_inputs(w)
+    N = w.B
+    mb = int(w.extra.get("micro_batch", 100))
+    free, _ = torch.cuda.mem_get_info()
+    h = qfuse.qf_hea_create(w.n, w.d)
+    c, ws_need = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True)
+    qfuse.qf_circuit_destroy(h)
+    sim = Simulator(w.n, w.d, mb, ckpt_layers=c, obs=w.obs)
+    theta = torch.from_numpy(theta_np).cuda()
+    xs = [torch.from_numpy(x_np[i:i + mb]).cuda() for i in range(0, N, mb)]
+    grad = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def epoch():
+        grad.zero_()
+        for xb in xs:
+            _, _, g = sim.train_step(theta, xb, loss=w.loss)
+            grad.add_(g)
+
+    for _ in range(max(1, args.warmup // 3)):
+        sim.train_step(theta, xs[0], loss=w.loss)
+    torch.cuda.synchronize()
+    qfuse.qf_profile(sim.handle, True)
+    qfuse.qf_profile_read(sim.handle)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            epoch()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    prof = qfuse.qf_profile_read(sim.handle)
+    ms = t0.elapsed_time(t1) / args.steps
+    info = sim.info()
+    fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, mb)
+    bwd_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
+    n_bwd = info["n_passes"]
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ach = (bwd_fl / n_bwd) / (bwd_ms / 1e3) / 1e12
+    bytes_bwd = 32 * mb * (1 << w.n)  # read + write psi and lambda per adjoint pass
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    line = {
+        "metric": "fwd+grad samples/s", "value": N * world / (ms / 1e3), "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d}, {N} samples per step (epoch) in micro-batches "
+                               f"of {mb}, L=sum E, obs=Z0", "ckpt_layers_from_memory": c,
+                   "workspace_gb": sim.ws_bytes / 1e9, "passes": info["n_passes"],
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                     "traffic": None, "kernel": "pass_kernel<true,true> (fused adjoint)",
+                     "bwd_pass_ms": bwd_ms,
+                     "hbm": {"achieved_gbs": bytes_bwd / (bwd_ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
+                             "frac": bytes_bwd / (bwd_ms / 1e3) / 1e9 / hbm_gbs, "peak_source": peak_src}},
+        "gpu_launches": None, "per_gate": None, "cpu_baseline": None, "e2e": None, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "mixed512":
         return run_mixed(args)
+    if args.workload == "hea20":
+        return run_epoch(args, workloads.WORKLOADS["hea20"])
     w = workloads.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
