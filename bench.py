@@ -401,10 +401,12 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
+    from paper_2603_02804_gb300 import dp
+
     def step(s):
         loss, E, g = s.train_step(theta, x, y, loss=w.loss)
         if world > 1:
-            dist.all_reduce(g)  # data-parallel gradient sum over ranks
+            dp.allreduce_sum(g)  # data-parallel gradient sum over ranks (NCCL)
         return g
 
     def timed(s, K):
