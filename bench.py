@@ -46,7 +46,23 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
+    ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
     return ap.parse_args()
+
+
+def override(w, args):
+    """A smaller case of the same workload for profiling (batch / depth)."""
+    import dataclasses
+    kw = {}
+    if args.batch:
+        kw["B"] = args.batch
+        extra = dict(w.extra)
+        extra["micro_batch"] = min(int(extra.get("micro_batch", args.batch)), args.batch)
+        kw["extra"] = extra
+    if args.depth:
+        kw["d"] = args.depth
+    return dataclasses.replace(w, **kw) if kw else w
 
 
 def dist_env():
@@ -316,8 +332,8 @@ def run_epoch(args, w):
             _, _, g = sim.train_step(theta, xb, loss=w.loss)
             grad.add_(g)
 
-    for _ in range(max(1, args.warmup // 3)):
-        sim.train_step(theta, xs[0], loss=w.loss)
+    sim.train_step(theta, xs[0], loss=w.loss)
+    epoch()  # warm every kernel of the timed epoch (library and torch)
     torch.cuda.synchronize()
     qfuse.qf_profile(sim.handle, True)
     qfuse.qf_profile_read(sim.handle)
@@ -363,8 +379,8 @@ def main():
     if args.workload == "mixed512":
         return run_mixed(args)
     if args.workload == "hea20":
-        return run_epoch(args, workloads.WORKLOADS["hea20"])
-    w = workloads.WORKLOADS[args.workload]
+        return run_epoch(args, override(workloads.WORKLOADS["hea20"], args))
+    w = override(workloads.WORKLOADS[args.workload], args)
     if args.impl == "reference":
         return run_reference(args, w)
     if args.warmup < 3:
