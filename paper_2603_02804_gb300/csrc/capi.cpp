@@ -29,6 +29,7 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t theta = 0, x = 0, y = 0, E = 0, dLdE = 0, grad = 0, loss = 0;  // staging
   size_t mats = 0, cs = 0, enc = 0;
+  size_t rpf = 0, rpb = 0;  // round-ordered item parameters (round programs)
   size_t work = 0, lam = 0, slots = 0;
   size_t epart = 0, gpart = 0;
   size_t total = 0;
@@ -144,6 +145,10 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
   if (c->path == QF_PATH_FUSED) {
     const int n_fused = (int)c->fp.fuse_off.size() - 1;
     L.mats = take((size_t)std::max(n_fused, 0) * 32);
+    if (c->fp.rounds) {
+      L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 128);
+      L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * 128);
+    }
     L.slots = take((size_t)c->fp.n_ckpt * L.state_elems * 8);
     L.rows = 1ll << (c->fp.n_eff - c->fp.K);
   } else {
@@ -287,8 +292,14 @@ void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, vo
   pa.n_terms = n_slots_of(c);
   pa.term_off = T.term_off;
   pa.term_params = T.term_params;
-  if (c->path == QF_PATH_FUSED && c->fp.rounds) pa.shear = at<float4>(ws, L.cs);
-  else pa.cs = at<float2>(ws, L.cs);
+  if (c->path == QF_PATH_FUSED && c->fp.rounds) {
+    pa.shear = at<float4>(ws, L.cs);
+    pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
+    pa.rpb_src = T.bwd_rounds;
+    pa.rpb = at<float4>(ws, L.rpb);
+  } else {
+    pa.cs = at<float2>(ws, L.cs);
+  }
 }
 
 // with_terms: also fill the backward's term table in the same prep launch
@@ -304,6 +315,11 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.mats = at<float4>(ws, L.mats);
   pa.n_terms = 0;  // the forward itself needs only the fused matrices and the encoding
   if (with_terms) set_term_table(c, T, L, ws, pa);
+  if (P.rounds) {
+    pa.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
+    pa.rpf_src = T.fwd_rounds;
+    pa.rpf = at<float4>(ws, L.rpf);
+  }
   pa.x = x;
   pa.B = B;
   pa.n = c->circ.n;
@@ -317,6 +333,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.B = B;
   a.ops = T.fwd_ops;
   a.rounds = P.rounds ? T.fwd_rounds : nullptr;
+  a.rpar = P.rounds ? at<float4>(ws, L.rpf) : nullptr;
   a.mats = pa.mats;
   a.cs = pa.cs;
   a.enc = pa.enc;
@@ -366,6 +383,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.B = B;
   a.ops = T.bwd_ops;
   a.rounds = P.rounds ? T.bwd_rounds : nullptr;
+  a.rpar = P.rounds ? at<float4>(ws, L.rpb) : nullptr;
   a.cs = pa.cs;
   a.shear = pa.shear;
   a.work = at<float2>(ws, L.work);
@@ -1056,9 +1074,11 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       r.fa = a;
       r.fa.ops = T.fwd_ops;
       r.fa.rounds = T.fwd_rounds;
+      r.fa.rpar = rel<const float4>(w0 + L.rpf);
       r.ba = a;
       r.ba.ops = T.bwd_ops;
       r.ba.rounds = T.bwd_rounds;
+      r.ba.rpar = rel<const float4>(w0 + L.rpb);
       r.ba.g_accum = a.tps_log2 > 0 ? 1 : 0;
       r.fwd = reinterpret_cast<const qf::PassDesc*>(base + fwd_off[i]);
       r.bwd = reinterpret_cast<const qf::PassDesc*>(base + bwd_off[i]);
@@ -1085,10 +1105,16 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       p.n = c->circ.n;
       p.n_eff = P.n_eff;
       p.enc = rel<float2>(w0 + L.enc);
+      p.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
+      p.rpf_src = T.fwd_rounds;
+      p.rpf = rel<float4>(w0 + L.rpf);
+      p.n_rpb = (int32_t)(P.bwd_rounds.size() / qf::kBwdRoundWords);
+      p.rpb_src = T.bwd_rounds;
+      p.rpb = rel<float4>(w0 + L.rpb);
       r.n_params = c->circ.n_params;
       r.param_off = T.param_off;
       r.param_terms = T.param_terms;
-      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff;
+      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff + 4ll * p.n_rpf + 8ll * p.n_rpb;
       gout_pref[i + 1] = gout_pref[i] + c->circ.n_params;
     }
     memcpy(img.data() + circ_off, recs.data(), recs.size() * sizeof(qf::BatchCircuit));

@@ -281,22 +281,28 @@ __device__ __forceinline__ float butterfly8(float (&v)[8], int lanes, int lane, 
   return v[0];
 }
 
-__device__ __forceinline__ int32_t pick_term(uint4 tz, uint4 ty, int idx) {
-  const uint4 t = (idx & 4) ? ty : tz;
-  const uint32_t lo = (idx & 1) ? t.y : t.x, hi = (idx & 1) ? t.w : t.z;
-  return (int32_t)((idx & 2) ? hi : lo);
+// 16-byte asynchronous copy global -> shared (L2 only), and its fences.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
-
-// Shear parameters of a term; a missing term (-1) is the identity (t = s = 0).
-__device__ __forceinline__ float4 term_shear(const float4* sh, uint32_t t) {
-  return (int32_t)t >= 0 ? __ldg(sh + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Static shared memory of a pass (the tiles themselves are dynamic).
+// Parameters of one round step, staged from the round-ordered tables: per
+// round 8 float4 (forward: the 4 items' fused 2x2s; backward: the shear
+// parameters of tz[0..3], ty[0..3]) and the round record.
+struct StepPar {
+  float4 v[kMaxStepRounds][8];
+  uint4 rec[kMaxStepRounds * (kBwdRoundWords / 4)];
+};
+
 struct PassShared {
+  StepPar par[2];
   uint32_t lg[256];
   float red[2][kThreads / 32][kMaxStepSlots];
   int32_t slot[2][kMaxStepSlots];
@@ -307,8 +313,9 @@ struct PassShared {
 
 // One CTA's share of a pass: tiles first_tile .. first_tile + tiles_per_cta-1
 // (tile = sample * tiles_per_sample + tile within the sample). Ends with a
-// barrier, so a CTA may call it again for another pass or tile range.
-template <bool BWD, bool ROUNDS>
+// barrier, so a CTA may call it again for another pass or tile range. LOADS:
+// tile loads in flight per thread and state (8 = the whole tile at once).
+template <bool BWD, bool ROUNDS, int LOADS = 8>
 __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_tile, float2* smem, PassShared& sh) {
   uint32_t (&s_lg)[256] = sh.lg;
   float (&s_red)[2][kThreads / 32][kMaxStepSlots] = sh.red;
@@ -357,6 +364,28 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
     if (code >= 0) return a.slots + (int64_t)code * a.slot_stride + sbase;
     return a.work + sbase;
   };
+  // (warp 0) the next round step at or after op q: its first round and count
+  auto next_step = [&](int32_t q, uint32_t& rb, int& nr) -> bool {
+    for (; q < pd.op_end; ++q) {
+      const uint2 o = __ldg(a.ops + q);
+      if ((o.x & 15u) == OP_STEP) {
+        rb = o.y;
+        nr = (int)((o.x >> 8) & 0xffffu);
+        return true;
+      }
+    }
+    return false;
+  };
+  // (warp 0) asynchronous copy of rounds rb .. rb+nr-1 into sh.par[pb]
+  auto stage = [&](int pb, uint32_t rb, int nr) {
+    constexpr int RW4 = (BWD ? kBwdRoundWords : kFwdRoundWords) / 4;
+    const int nv = nr * 8, n_all = nv + nr * RW4;
+    for (int e = lane; e < n_all; e += 32) {
+      if (e < nv) cp_async16(&sh.par[pb].v[0][0] + e, a.rpar + (size_t)rb * 8 + e);
+      else cp_async16(&sh.par[pb].rec[e - nv], a.rounds + (size_t)rb * RW4 + (e - nv));
+    }
+    cp_async_commit();
+  };
 
   // ---- bring psi (and lambda) in -------------------------------------------
   const int32_t psrc = pd.psi_src;
@@ -375,21 +404,43 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       const float2 f0 = __ldg(e);
       if (active) st_pair(tp, i, make_float4(pr * f0.x, 0.f, pr * f0.y, 0.f));
     }
-  } else {
+  } else if (active) {
+    // issue every load of the tile (psi, and lambda) before the first store
     const float2* src = state_ptr(psrc);
+    const bool two = BWD && pd.lam_src == LAM_BUF;
+    const float2* lsrc = a.lam + sbase;
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
-      if (active) st_pair(tp, i, *reinterpret_cast<const float4*>(src + gidx(i)));
+    for (int i0 = 0; i0 < 8; i0 += LOADS) {
+      float4 vp[LOADS], vl[LOADS];
+#pragma unroll
+      for (int it = 0; it < LOADS; ++it) {
+        const uint32_t g = gidx(2u * ((uint32_t)(i0 + it) * Tt + tau));
+        vp[it] = __ldcg(reinterpret_cast<const float4*>(src + g));
+        if (two) vl[it] = __ldcg(reinterpret_cast<const float4*>(lsrc + g));
+      }
+#pragma unroll
+      for (int it = 0; it < LOADS; ++it) {
+        const uint32_t i = 2u * ((uint32_t)(i0 + it) * Tt + tau);
+        st_pair(tp, i, vp[it]);
+        if (two) st_pair(tl, i, vl[it]);
+      }
     }
   }
-  if (BWD && pd.lam_src == LAM_BUF) {
+  if (BWD && pd.lam_src == LAM_BUF && psrc == SRC_GENERATE && active) {
     const float2* src = a.lam + sbase;
 #pragma unroll
     for (int it = 0; it < 8; ++it) {
       const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
-      if (active) st_pair(tl, i, *reinterpret_cast<const float4*>(src + gidx(i)));
+      st_pair(tl, i, __ldcg(reinterpret_cast<const float4*>(src + gidx(i))));
     }
+  }
+  // round programs: stage the first step's parameters
+  int sb = 0;
+  if (ROUNDS && warp == 0) {
+    uint32_t rb;
+    int nr;
+    if (next_step(pd.op_begin, rb, nr)) stage(0, rb, nr);
+    cp_async_wait_all();
   }
   __syncthreads();
   if (BWD && pd.lam_src == LAM_SEED) {
@@ -420,7 +471,13 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       // ---- round step: straight-line rounds over the 4 register bits
       const int g = (op.x >> 4) & 3;
       const int nr = (op.x >> 8) & 0xffff;
-      const uint32_t rb0 = op.y;
+      if (warp == 0) {
+        // prefetch the next step's parameters while this one runs
+        uint32_t rb;
+        int nr2;
+        if (next_step(pc, rb, nr2)) stage(sb ^ 1, rb, nr2);
+      }
+      const StepPar& P = sh.par[sb];
       const uint32_t lb0 = s_grp[g][0], lb1 = s_grp[g][1], lb2 = s_grp[g][2], lb3 = s_grp[g][3];
       const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
       const uint32_t base = pdep32(tau, ((1u << K) - 1u) & ~gm);
@@ -439,34 +496,25 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
 #pragma unroll 1
       for (int k = 0; k < nr; ++k) {
         if (!BWD) {
-          const uint4* rec = a.rounds + (size_t)(rb0 + k) * (kFwdRoundWords / 4);
-          const uint4 mi = __ldg(rec), lk = __ldg(rec + 1);
-          const float4 u00 = __ldg(a.mats + 2 * mi.x), u01 = __ldg(a.mats + 2 * mi.x + 1);
-          const float4 u10 = __ldg(a.mats + 2 * mi.y), u11 = __ldg(a.mats + 2 * mi.y + 1);
-          const float4 u20 = __ldg(a.mats + 2 * mi.z), u21 = __ldg(a.mats + 2 * mi.z + 1);
-          const float4 u30 = __ldg(a.mats + 2 * mi.w), u31 = __ldg(a.mats + 2 * mi.w + 1);
-          item_fwd<0>(r, u00, u01, D & 1u);
-          item_fwd<1>(r, u10, u11, (D >> 1) & 1u);
-          item_fwd<2>(r, u20, u21, (D >> 2) & 1u);
-          item_fwd<3>(r, u30, u31, (D >> 3) & 1u);
+          const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];
+          item_fwd<0>(r, P.v[k][0], P.v[k][1], D & 1u);
+          item_fwd<1>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u);
+          item_fwd<2>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u);
+          item_fwd<3>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u);
           chain_pending<false>(lk.x, lk.y, gb, pos, D, r, l);
         } else {
-          const uint4* rec = a.rounds + (size_t)(rb0 + k) * (kBwdRoundWords / 4);
-          const uint4 tz = __ldg(rec), ty = __ldg(rec + 1), lk = __ldg(rec + 2);
-          const float4 z0 = term_shear(a.shear, tz.x), z1 = term_shear(a.shear, tz.y),
-                       z2 = term_shear(a.shear, tz.z), z3 = term_shear(a.shear, tz.w);
-          const float4 y0 = term_shear(a.shear, ty.x), y1 = term_shear(a.shear, ty.y),
-                       y2 = term_shear(a.shear, ty.z), y3 = term_shear(a.shear, ty.w);
+          const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];
           chain_pending<true>(lk.x, lk.y, gb, pos, D, r, l);
           float v[8];
-          item_bwd<0>(r, l, z0, y0, D & 1u, D, v[0], v[4]);
-          item_bwd<1>(r, l, z1, y1, (D >> 1) & 1u, D, v[1], v[5]);
-          item_bwd<2>(r, l, z2, y2, (D >> 2) & 1u, D, v[2], v[6]);
-          item_bwd<3>(r, l, z3, y3, (D >> 3) & 1u, D, v[3], v[7]);
+          item_bwd<0>(r, l, P.v[k][0], P.v[k][4], D & 1u, D, v[0], v[4]);
+          item_bwd<1>(r, l, P.v[k][1], P.v[k][5], (D >> 1) & 1u, D, v[1], v[5]);
+          item_bwd<2>(r, l, P.v[k][2], P.v[k][6], (D >> 2) & 1u, D, v[2], v[6]);
+          item_bwd<3>(r, l, P.v[k][3], P.v[k][7], (D >> 3) & 1u, D, v[3], v[7]);
           int idx;
           const float sum = butterfly8(v, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
-          const int32_t term = pick_term(tz, ty, idx);
+          const int32_t term =
+              reinterpret_cast<const int32_t*>(&P.rec[k * (kBwdRoundWords / 4)])[idx];
           if (Tt >= 32) {
             if (owner) {
               s_red[buf][warp][k * 8 + idx] = sum;
@@ -483,7 +531,9 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         tp[pb ^ reg_off(j, so)] = r[j];
         if (BWD) tl[pb ^ reg_off(j, so)] = l[j];
       }
+      if (warp == 0) cp_async_wait_all();
       __syncthreads();
+      sb ^= 1;
       if (BWD && Tt >= 32 && a.g_accum) {
         // every tile of this call belongs to one sample: one thread per term sums
         // the tiles in order and adds to the sample's row (stored by its tile 0)
@@ -675,63 +725,84 @@ __global__ void prep_kernel(const PrepArgs a) {
   prep_one(a, i);
 }
 
-// Element i of the tables: fused matrices, then terms, then encodings.
+namespace {
+
+// Fused 2x2 product of fused entry m (float64, rounded once to float32).
+__device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1) {
+  double u[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {1, 0}}};  // [row][col][re/im]
+  for (int j = a.fuse_off[m]; j < a.fuse_off[m + 1]; ++j) {
+    const FuseGate fg = a.fuse_gates[j];
+    double s, c;
+    sincos(0.5 * (double)a.theta[fg.param], &s, &c);
+    // g = c I - i s P
+    double g[2][2][2];
+    if (fg.kind == G_RX) {
+      g[0][0][0] = c; g[0][0][1] = 0; g[0][1][0] = 0; g[0][1][1] = -s;
+      g[1][0][0] = 0; g[1][0][1] = -s; g[1][1][0] = c; g[1][1][1] = 0;
+    } else if (fg.kind == G_RY) {
+      g[0][0][0] = c; g[0][0][1] = 0; g[0][1][0] = -s; g[0][1][1] = 0;
+      g[1][0][0] = s; g[1][0][1] = 0; g[1][1][0] = c; g[1][1][1] = 0;
+    } else {
+      g[0][0][0] = c; g[0][0][1] = -s; g[0][1][0] = 0; g[0][1][1] = 0;
+      g[1][0][0] = 0; g[1][0][1] = 0; g[1][1][0] = c; g[1][1][1] = s;
+    }
+    double t[2][2][2];
+    for (int r = 0; r < 2; ++r)
+      for (int k = 0; k < 2; ++k) {
+        double re = 0, im = 0;
+        for (int q = 0; q < 2; ++q) {
+          re += g[r][q][0] * u[q][k][0] - g[r][q][1] * u[q][k][1];
+          im += g[r][q][0] * u[q][k][1] + g[r][q][1] * u[q][k][0];
+        }
+        t[r][k][0] = re;
+        t[r][k][1] = im;
+      }
+    for (int r = 0; r < 2; ++r)
+      for (int k = 0; k < 2; ++k) {
+        u[r][k][0] = t[r][k][0];
+        u[r][k][1] = t[r][k][1];
+      }
+  }
+  m0 = make_float4((float)u[0][0][0], (float)u[0][0][1], (float)u[0][1][0], (float)u[0][1][1]);
+  m1 = make_float4((float)u[1][0][0], (float)u[1][0][1], (float)u[1][1][0], (float)u[1][1][1]);
+}
+
+// A term's angle is the sum of its parameters (a merged run of RZ gates).
+__device__ double term_angle(const PrepArgs& a, int64_t t) {
+  double phi = 0.0;
+  for (int j = a.term_off[t]; j < a.term_off[t + 1]; ++j) phi += (double)a.theta[a.term_params[j]];
+  return phi;
+}
+
+// u(phi) = (-1)^k u(w) with w = phi - 2 pi k in (-pi, pi]: the rotation by w/2
+// as three shears needs tan(w/4) (|.| <= 1) and sin(w/2); a missing term (-1)
+// is the identity (all zero).
+__device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
+  if (t < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const double phi = term_angle(a, t);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double k = rint(phi / two_pi);
+  const double w = phi - two_pi * k;
+  const int parity = ((long long)k) & 1;
+  return make_float4((float)tan(0.25 * w), (float)sin(0.5 * w), __int_as_float(parity), 0.f);
+}
+
+}  // namespace
+
+// Element i of the tables: fused matrices, terms, encodings, then (round
+// programs) the forward and backward round parameters in round order.
 __device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (i < a.n_fused) {
-    double u[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {1, 0}}};  // [row][col][re/im]
-    for (int j = a.fuse_off[i]; j < a.fuse_off[i + 1]; ++j) {
-      const FuseGate fg = a.fuse_gates[j];
-      double s, c;
-      sincos(0.5 * (double)a.theta[fg.param], &s, &c);
-      // g = c I - i s P
-      double g[2][2][2];
-      if (fg.kind == G_RX) {
-        g[0][0][0] = c; g[0][0][1] = 0; g[0][1][0] = 0; g[0][1][1] = -s;
-        g[1][0][0] = 0; g[1][0][1] = -s; g[1][1][0] = c; g[1][1][1] = 0;
-      } else if (fg.kind == G_RY) {
-        g[0][0][0] = c; g[0][0][1] = 0; g[0][1][0] = -s; g[0][1][1] = 0;
-        g[1][0][0] = s; g[1][0][1] = 0; g[1][1][0] = c; g[1][1][1] = 0;
-      } else {
-        g[0][0][0] = c; g[0][0][1] = -s; g[0][1][0] = 0; g[0][1][1] = 0;
-        g[1][0][0] = 0; g[1][0][1] = 0; g[1][1][0] = c; g[1][1][1] = s;
-      }
-      double t[2][2][2];
-      for (int r = 0; r < 2; ++r)
-        for (int k = 0; k < 2; ++k) {
-          double re = 0, im = 0;
-          for (int m = 0; m < 2; ++m) {
-            re += g[r][m][0] * u[m][k][0] - g[r][m][1] * u[m][k][1];
-            im += g[r][m][0] * u[m][k][1] + g[r][m][1] * u[m][k][0];
-          }
-          t[r][k][0] = re;
-          t[r][k][1] = im;
-        }
-      for (int r = 0; r < 2; ++r)
-        for (int k = 0; k < 2; ++k) {
-          u[r][k][0] = t[r][k][0];
-          u[r][k][1] = t[r][k][1];
-        }
-    }
-    a.mats[2 * i] = make_float4((float)u[0][0][0], (float)u[0][0][1], (float)u[0][1][0], (float)u[0][1][1]);
-    a.mats[2 * i + 1] = make_float4((float)u[1][0][0], (float)u[1][0][1], (float)u[1][1][0], (float)u[1][1][1]);
+    fused_u(a, i, a.mats[2 * i], a.mats[2 * i + 1]);
     return;
   }
   i -= a.n_fused;
   if (i < a.n_terms) {
-    // a term's angle is the sum of its parameters (a merged run of RZ gates)
-    double phi = 0.0;
-    for (int j = a.term_off[i]; j < a.term_off[i + 1]; ++j) phi += (double)a.theta[a.term_params[j]];
     if (a.shear) {
-      // u(phi) = (-1)^k u(w) with w = phi - 2 pi k in (-pi, pi]: the rotation by
-      // w/2 as three shears needs tan(w/4) (|.| <= 1) and sin(w/2)
-      const double two_pi = 6.283185307179586476925286766559;
-      const double k = rint(phi / two_pi);
-      const double w = phi - two_pi * k;
-      const int parity = ((long long)k) & 1;
-      a.shear[i] = make_float4((float)tan(0.25 * w), (float)sin(0.5 * w), __int_as_float(parity), 0.f);
+      a.shear[i] = term_shear_of(a, (int32_t)i);
     } else {
       double s, c;
-      sincos(0.5 * phi, &s, &c);
+      sincos(0.5 * term_angle(a, i), &s, &c);
       a.cs[i] = make_float2((float)c, (float)s);
     }
     return;
@@ -747,6 +818,24 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     } else {
       a.enc[i] = make_float2(1.f, 0.f);  // padding qubit stays |0>
     }
+    return;
+  }
+  i -= (int64_t)a.B * a.n_eff;
+  if (i < 4ll * a.n_rpf) {
+    // forward round r, item k: word k of the record is the fused entry
+    const int64_t r = i >> 2;
+    const int k = (int)(i & 3);
+    const uint32_t m = reinterpret_cast<const uint32_t*>(a.rpf_src)[r * kFwdRoundWords + k];
+    fused_u(a, m, a.rpf[r * 8 + 2 * k], a.rpf[r * 8 + 2 * k + 1]);
+    return;
+  }
+  i -= 4ll * a.n_rpf;
+  if (i < 8ll * a.n_rpb) {
+    // backward round r, slot k: tz[0..3] then ty[0..3]
+    const int64_t r = i >> 3;
+    const int k = (int)(i & 7);
+    const int32_t t = reinterpret_cast<const int32_t*>(a.rpb_src)[r * kBwdRoundWords + k];
+    a.rpb[i] = term_shear_of(a, t);
   }
 }
 
@@ -837,6 +926,7 @@ __device__ void load_args(PassArgs& dst, const PassArgs& src, const PassDesc& pd
   if (threadIdx.x == 0) {
     dst.pd = pd;
     dst.mats = rebase(dst.mats, ws);
+    dst.rpar = rebase(dst.rpar, ws);
     dst.shear = rebase(dst.shear, ws);
     dst.enc = rebase(dst.enc, ws);
     dst.work = rebase(dst.work, ws);
@@ -855,13 +945,13 @@ __device__ void run_item_pass(bool bwd, const PassArgs& a, int32_t b0) {
   const int tpc = kThreads >> (a.pd.K - kRegBits);
   if (a.tps_log2 == 0) {
     // a tile is a sample: the item's samples b0 .. b0 + tpc - 1 in one call
-    if (bwd) pass_cta<true, true>(a, b0, smem, sh);
-    else pass_cta<false, true>(a, b0, smem, sh);
+    if (bwd) pass_cta<true, true, 2>(a, b0, smem, sh);
+    else pass_cta<false, true, 2>(a, b0, smem, sh);
   } else {
     const int64_t tps = 1ll << a.tps_log2;
     for (int64_t t = 0; t < tps; t += tpc) {
-      if (bwd) pass_cta<true, true>(a, (int64_t)b0 * tps + t, smem, sh);
-      else pass_cta<false, true>(a, (int64_t)b0 * tps + t, smem, sh);
+      if (bwd) pass_cta<true, true, 2>(a, (int64_t)b0 * tps + t, smem, sh);
+      else pass_cta<false, true, 2>(a, (int64_t)b0 * tps + t, smem, sh);
     }
   }
 }
@@ -876,6 +966,8 @@ __global__ void batch_prep_kernel(const BatchArgs a, int64_t total) {
   p.theta = a.theta + a.circ[c].theta_off;
   p.x = a.x + a.circ[c].x_off;
   p.mats = rebase(p.mats, a.ws);
+  p.rpf = rebase(p.rpf, a.ws);
+  p.rpb = rebase(p.rpb, a.ws);
   p.shear = rebase(p.shear, a.ws);
   p.enc = rebase(p.enc, a.ws);
   prep_one(p, i - a.prep_off[c]);
@@ -996,7 +1088,7 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff;
+  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + 4ll * a.n_rpf + 8ll * a.n_rpb;
   if (total == 0) return cudaSuccess;
   const int blk = 256;
   prep_kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, st>>>(a);

@@ -14,6 +14,7 @@ struct PassArgs {
   int64_t B;              // samples in this call
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs)
+  const float4* rpar;     // per-round item parameters, 8 float4 per round (round programs)
   const float4* mats;     // fused 2x2 matrices, 2 float4 each
   const float2* cs;       // (cos, sin) of theta/2 per gradient term (generic programs)
   const float4* shear;    // three-shear parameters per gradient term (round programs)
@@ -47,6 +48,13 @@ struct PrepArgs {
   int64_t B;
   int32_t n, n_eff;
   float2* enc;
+  // round programs: the parameters of every round gathered in round order
+  int32_t n_rpf;               // forward rounds
+  const uint4* rpf_src;        // forward round records (fused index per item)
+  float4* rpf;                 // [n_rpf][8]: item k's fused 2x2 at 2k, 2k+1
+  int32_t n_rpb;               // backward rounds
+  const uint4* rpb_src;        // backward round records (tz[4], ty[4] terms)
+  float4* rpb;                 // [n_rpb][8]: shear parameters of tz[0..3], ty[0..3]
 };
 
 struct GradReduceArgs {
