@@ -96,7 +96,19 @@ typedef struct {
   int32_t program;     /* fused: 0 = round steps when the circuit allows (RZ/RY
                           rotations, CZ on neighbouring qubits, tile >= 7 qubits),
                           else generic steps; 1 = always generic steps           */
-  int32_t reserved[11];
+  int32_t ckpt_mode;   /* fused: how the adjoint gets psi_{j-1} (Secs. 3.3-3.4).
+                          0 (default): each adjoint pass un-applies the gates to
+                          psi in-kernel and re-anchors at the stored checkpoints.
+                          1: per checkpoint block, the block's forward passes are
+                          re-run from its input checkpoint storing every pass
+                          output, and each adjoint pass starts from the stored
+                          output of the forward pass it undoes (psi is re-anchored
+                          every pass; costs about one extra forward and p*c more
+                          stored states, p passes per layer, c layers a block)  */
+  int32_t mem_save;    /* ckpt_mode 1 only: store those pass outputs as bfloat16
+                          (re, im), computing in float32 (the memory-saving mode
+                          of Sec. 3.2); checkpoints and psi_M stay float32       */
+  int32_t reserved[9];
 } qf_plan_opts;
 
 /* Summary of a plan (host-side numbers). */
@@ -117,6 +129,10 @@ typedef struct {
   int64_t batch;           /* batch the workspace was sized for                 */
   int64_t workspace_bytes;
   int64_t state_bytes;     /* one batched state buffer                          */
+  int32_t ckpt_mode;       /* as planned (opts->ckpt_mode)                      */
+  int32_t mem_save;
+  int32_t n_pass_slots;    /* ckpt_mode 1: stored pass outputs of one block     */
+  int32_t reserved;
 } qf_plan_info_t;
 
 /* Create the hardware-efficient ansatz of the paper's benchmarks with the
@@ -169,7 +185,8 @@ qf_status qf_plan_fit(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, si
 /* Fill *info with the current plan's summary. */
 qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
 
-/* Export the forward (direction 0) or backward (1) program for inspection:
+/* Export the forward (direction 0) or backward (1) program for inspection,
+ * or (direction 2, ckpt_mode 1 plans) the adjoint's launch list:
  * writes up to cap int32 words to buf (may be NULL) and the full length to
  * *len. Layout: [program kind (0 generic steps, 1 round steps), n_passes,
  * then per pass: 11 header words (op_begin, op_end, psi_src, psi_dst,
@@ -177,7 +194,9 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
  * words, 16 group words], then [n_ops, 2 words per op], then [n_fused, per
  * fused op: count, then count (kind, param) pairs], then [n round words of
  * this direction, the words], then [n_terms, per gradient term: kind, count,
- * count parameters]. Host only. */
+ * count parameters]. Direction 2: [program kind, n_launches, then per
+ * launch: program (0 forward, 1 backward; op ranges index that direction's
+ * ops), the 11 header words, 16 gmap words, 16 group words]. Host only. */
 qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf,
                          int64_t cap, int64_t* len);
 

@@ -4,8 +4,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <exception>
+#include <map>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -30,7 +33,7 @@ struct Layout {
   size_t theta = 0, x = 0, y = 0, E = 0, dLdE = 0, grad = 0, loss = 0;  // staging
   size_t mats = 0, cs = 0, enc = 0;
   size_t rpf = 0, rpb = 0;  // round-ordered item parameters (round programs)
-  size_t work = 0, lam = 0, slots = 0;
+  size_t work = 0, lam = 0, slots = 0, hslots = 0;
   size_t epart = 0, gpart = 0;
   size_t total = 0;
   int64_t state_elems = 0;  // batch * 2^n_eff
@@ -149,7 +152,11 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
       L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 128);
       L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * 128);
     }
-    L.slots = take((size_t)c->fp.n_ckpt * L.state_elems * 8);
+    // checkpoint mode A: pass-output slots after the checkpoints (float32), or
+    // a bfloat16 array of them (memory-saving mode)
+    const int extra = c->fp.ckpt_mode == 1 && !c->fp.mem_save ? c->fp.n_aslots : 0;
+    L.slots = take((size_t)(c->fp.n_ckpt + extra) * L.state_elems * 8);
+    if (c->fp.ckpt_mode == 1 && c->fp.mem_save) L.hslots = take((size_t)c->fp.n_aslots * L.state_elems * 4);
     L.rows = 1ll << (c->fp.n_eff - c->fp.K);
   } else {
     L.slots = take((size_t)c->gp.ckpt_after.size() * L.state_elems * 8);
@@ -340,6 +347,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.work = at<float2>(ws, L.work);
   a.lam = at<float2>(ws, L.lam);
   a.slots = at<float2>(ws, L.slots);
+  a.hslots = L.hslots ? at<char>(ws, L.hslots) : nullptr;
   a.slot_stride = L.state_elems;
   a.z_mask = o.z;
   a.y_count = o.y;
@@ -389,6 +397,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.work = at<float2>(ws, L.work);
   a.lam = at<float2>(ws, L.lam);
   a.slots = at<float2>(ws, L.slots);
+  a.hslots = L.hslots ? at<char>(ws, L.hslots) : nullptr;
   a.slot_stride = L.state_elems;
   a.z_mask = o.z;
   a.y_count = o.y;
@@ -397,15 +406,37 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.g_part = at<double>(ws, L.gpart);
   a.n_slots = P.n_terms;
   const int prof = prof_begin(c, st);
-  for (size_t pi = 0; pi < P.bwd.size(); ++pi) {
-    a.pd = P.bwd[pi];
-    a.pd.xm_local = 0;
-    if (a.pd.lam_src == qf::LAM_SEED && !local_xmask(a.pd, o.x, &a.pd.xm_local))
-      return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
-    QF_CU(qf::launch_pass(true, a, st));
-    c->call_launches++;
+  if (P.ckpt_mode == 1) {
+    // checkpoint mode A: forward re-runs (tables and encodings of the preceding
+    // forward) interleaved with adjoint passes, block by block
+    qf::PassArgs f = a;
+    f.ops = T.fwd_ops;
+    f.rounds = P.rounds ? T.fwd_rounds : nullptr;
+    f.rpar = P.rounds ? at<float4>(ws, L.rpf) : nullptr;
+    f.mats = at<float4>(ws, L.mats);
+    f.enc = at<float2>(ws, L.enc);
+    for (size_t i = 0; i < P.a_sched.size(); ++i) {
+      const bool bwd = P.a_dir[i] != 0;
+      qf::PassArgs& x = bwd ? a : f;
+      x.pd = P.a_sched[i];
+      x.pd.xm_local = 0;
+      if (bwd && x.pd.lam_src == qf::LAM_SEED && !local_xmask(x.pd, o.x, &x.pd.xm_local))
+        return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+      QF_CU(qf::launch_pass(bwd, x, st));
+      c->call_launches++;
+    }
+    prof_end(c, prof, 1, (int64_t)P.a_sched.size(), st);
+  } else {
+    for (size_t pi = 0; pi < P.bwd.size(); ++pi) {
+      a.pd = P.bwd[pi];
+      a.pd.xm_local = 0;
+      if (a.pd.lam_src == qf::LAM_SEED && !local_xmask(a.pd, o.x, &a.pd.xm_local))
+        return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+      QF_CU(qf::launch_pass(true, a, st));
+      c->call_launches++;
+    }
+    prof_end(c, prof, 1, (int64_t)P.bwd.size(), st);
   }
-  prof_end(c, prof, 1, (int64_t)P.bwd.size(), st);
   qf::GradReduceArgs g{};
   g.g_part = a.g_part;
   g.B = B;
@@ -593,6 +624,11 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     return fail(QF_ERR_INVALID_ARG, "tile_bits must be 0 or in 4..12");
   if (o.ckpt_layers < 0) return fail(QF_ERR_INVALID_ARG, "negative checkpoint interval");
   if (o.program != 0 && o.program != 1) return fail(QF_ERR_INVALID_ARG, "program must be 0 or 1");
+  if (o.ckpt_mode != 0 && o.ckpt_mode != 1) return fail(QF_ERR_INVALID_ARG, "ckpt_mode must be 0 or 1");
+  if (o.mem_save != 0 && o.mem_save != 1) return fail(QF_ERR_INVALID_ARG, "mem_save must be 0 or 1");
+  if (o.mem_save && o.ckpt_mode != 1) return fail(QF_ERR_INVALID_ARG, "mem_save needs ckpt_mode 1");
+  if (o.ckpt_mode != 0 && o.path != QF_PATH_FUSED)
+    return fail(QF_ERR_UNSUPPORTED, "ckpt_mode 1 applies to the fused path");
   try {
     free_tables(c);
     c->planned = false;
@@ -604,6 +640,8 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     req.tile_bits = o.tile_bits;
     req.ckpt_layers = c->ckpt_layers;
     req.generic = o.program == 1;
+    req.ckpt_mode = o.ckpt_mode;
+    req.mem_save = o.mem_save != 0;
     if (c->path == QF_PATH_FUSED) {
       c->fp = qf::plan_fused(c->circ, req);
       c->gp = qf::PerGatePlan();
@@ -648,7 +686,40 @@ qf_status qf_plan_fit(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, si
     return qf_plan(c, &t, batch, ws);
   };
   size_t ws = 0;
-  qf_status s = ws_for(d, &ws);
+  qf_status s;
+  if (o.ckpt_mode == 1) {
+    // mode A: the workspace is about (p c + d / c) states, smallest near
+    // c = sqrt(d / p) (Eq. 8); its recompute costs about one forward for any
+    // c. Take the c with the smallest workspace (ternary search on the
+    // unimodal count, then a local scan) and fail if even that does not fit.
+    std::map<int, size_t> memo;
+    auto wsc = [&](int cl) -> size_t {
+      auto it = memo.find(cl);
+      if (it != memo.end()) return it->second;
+      size_t w = 0;
+      if (ws_for(cl, &w) != QF_OK) w = SIZE_MAX;
+      memo[cl] = w;
+      return w;
+    };
+    int lo = 1, hi = d;
+    while (hi - lo > 4) {
+      const int m1 = lo + (hi - lo) / 3, m2 = hi - (hi - lo) / 3;
+      if (wsc(m1) <= wsc(m2)) hi = m2;
+      else lo = m1;
+    }
+    int best = lo;
+    for (int cl = lo; cl <= hi; ++cl)
+      if (wsc(cl) < wsc(best)) best = cl;
+    if (wsc(best) == SIZE_MAX) return fail(QF_ERR_INVALID_ARG, "planning failed");
+    if (wsc(best) > mem_bytes) return fail(QF_ERR_WORKSPACE, "no checkpoint interval fits");
+    qf_plan_opts fin = o;
+    fin.ckpt_layers = best;
+    if ((s = qf_plan(c, &fin, batch, &ws)) != QF_OK) return s;
+    *ckpt_layers = best;
+    if (workspace_bytes) *workspace_bytes = ws;
+    return QF_OK;
+  }
+  s = ws_for(d, &ws);
   if (s != QF_OK) return s;
   if (ws > mem_bytes) return fail(QF_ERR_WORKSPACE, "even a plan with only the final state does not fit");
   int lo = 1, hi = d;  // hi fits
@@ -687,6 +758,10 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
     info->n_ckpt = c->fp.n_ckpt;
     info->launches_fwd = info->n_passes + 2;
     info->launches_bwd = info->n_passes + 2;
+    info->ckpt_mode = c->fp.ckpt_mode;
+    info->mem_save = c->fp.mem_save ? 1 : 0;
+    info->n_pass_slots = c->fp.n_aslots;
+    if (c->fp.ckpt_mode == 1) info->launches_bwd = (int32_t)c->fp.a_sched.size() + 2;
   } else {
     info->n_eff = c->gp.n_eff;
     info->n_slots = c->gp.n_slots;
@@ -702,8 +777,27 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
 qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, int64_t cap, int64_t* len) {
   if (!c || !len) return fail(QF_ERR_INVALID_ARG, "null argument");
   if (!c->planned || c->path != QF_PATH_FUSED) return fail(QF_ERR_WORKSPACE, "no fused plan");
-  if (direction != 0 && direction != 1) return fail(QF_ERR_INVALID_ARG, "direction must be 0 or 1");
+  if (direction < 0 || direction > 2) return fail(QF_ERR_INVALID_ARG, "direction must be 0, 1 or 2");
   const qf::FusedPlan& P = c->fp;
+  if (direction == 2) {
+    if (P.ckpt_mode != 1) return fail(QF_ERR_INVALID_ARG, "direction 2 needs a ckpt_mode 1 plan");
+    std::vector<int32_t> w;
+    w.push_back(P.rounds ? 1 : 0);
+    w.push_back((int32_t)P.a_sched.size());
+    for (size_t i = 0; i < P.a_sched.size(); ++i) {
+      const qf::PassDesc& pd = P.a_sched[i];
+      w.push_back(P.a_dir[i]);
+      const int32_t hdr[11] = {pd.op_begin, pd.op_end, pd.psi_src, pd.psi_dst, pd.lam_src, pd.lam_dst,
+                               pd.flags, pd.K, pd.n_groups, (int32_t)pd.outer_mask, (int32_t)pd.xm_local};
+      w.insert(w.end(), hdr, hdr + 11);
+      for (int j = 0; j < 16; ++j) w.push_back(pd.gmap[j]);
+      for (int g = 0; g < 4; ++g)
+        for (int r = 0; r < 4; ++r) w.push_back(pd.groups[g][r]);
+    }
+    *len = (int64_t)w.size();
+    if (buf) memcpy(buf, w.data(), sizeof(int32_t) * (size_t)std::min<int64_t>(cap, *len));
+    return QF_OK;
+  }
   const auto& passes = direction == 0 ? P.fwd : P.bwd;
   const auto& ops = direction == 0 ? P.fwd_ops : P.bwd_ops;
   std::vector<int32_t> w;
@@ -960,6 +1054,8 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       qf_circuit* c = b->circ[i];
       const std::string at = " (circuit " + std::to_string(i) + ")";
       if (!c || !c->planned) throw std::invalid_argument("circuit has no plan" + at);
+      if (c->path == QF_PATH_FUSED && c->fp.ckpt_mode != 0)
+        throw std::invalid_argument("batched launches use checkpoint mode 0");
       if (c->path != QF_PATH_FUSED || !c->fp.rounds)
         throw std::invalid_argument("batched launches need fused round programs (RZ/RY rotations, CZ on "
                                     "neighbouring qubits, at least 7 qubits per tile)" + at);

@@ -9,6 +9,7 @@
 // Shared-memory layout: amplitude with local index i lives at i ^ ((i>>4)&15)
 // (XOR swizzle on 8-byte words). Register groups are local nibbles, so the 16
 // lanes of a half-warp always hit 16 distinct bank pairs.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -281,6 +282,17 @@ __device__ __forceinline__ float butterfly8(float (&v)[8], int lanes, int lane, 
   return v[0];
 }
 
+// Two amplitudes as bfloat16 (re, im) pairs <-> float32 (round to nearest even).
+__device__ __forceinline__ float4 bf16x4_to_f4(uint2 h) {
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ uint2 f4_to_bf16x4(float4 v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
 // 16-byte asynchronous copy global -> shared (L2 only), and its fences.
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -407,6 +419,9 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
   } else if (active) {
     // issue every load of the tile (psi, and lambda) before the first store
     const float2* src = state_ptr(psrc);
+    const bool half = (pd.flags & PF_SRC_H) != 0;
+    const __nv_bfloat162* hsrc =
+        half ? reinterpret_cast<const __nv_bfloat162*>(a.hslots) + (int64_t)psrc * a.slot_stride + sbase : nullptr;
     const bool two = BWD && pd.lam_src == LAM_BUF;
     const float2* lsrc = a.lam + sbase;
 #pragma unroll
@@ -415,7 +430,8 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
 #pragma unroll
       for (int it = 0; it < LOADS; ++it) {
         const uint32_t g = gidx(2u * ((uint32_t)(i0 + it) * Tt + tau));
-        vp[it] = __ldcg(reinterpret_cast<const float4*>(src + g));
+        if (half) vp[it] = bf16x4_to_f4(__ldcg(reinterpret_cast<const uint2*>(hsrc + g)));
+        else vp[it] = __ldcg(reinterpret_cast<const float4*>(src + g));
         if (two) vl[it] = __ldcg(reinterpret_cast<const float4*>(lsrc + g));
       }
 #pragma unroll
@@ -659,7 +675,15 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
   }
 
   // ---- write back -----------------------------------------------------------
-  if (pd.psi_dst != BUF_NONE) {
+  if (pd.psi_dst != BUF_NONE && (pd.flags & PF_DST_H)) {
+    // memory-saving mode (Sec. 3.2): the stored copy is rounded to bfloat16
+    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(a.hslots) + (int64_t)pd.psi_dst * a.slot_stride + sbase;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      if (active) *reinterpret_cast<uint2*>(dst + gidx(i)) = f4_to_bf16x4(ld_pair(tp, i));
+    }
+  } else if (pd.psi_dst != BUF_NONE) {
     float2* dst = state_ptr(pd.psi_dst);
 #pragma unroll
     for (int it = 0; it < 8; ++it) {

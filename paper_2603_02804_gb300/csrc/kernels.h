@@ -22,6 +22,7 @@ struct PassArgs {
   float2* work;           // working state [B][2^n_eff]
   float2* lam;            // adjoint state [B][2^n_eff]
   float2* slots;          // checkpoint states [n_ckpt][slot_stride]
+  void* hslots;           // bfloat16 (re, im) pass-output slots [n][slot_stride] (PF_SRC_H / PF_DST_H)
   int64_t slot_stride;    // elements between consecutive checkpoint slots
   uint32_t z_mask;        // observable Z part (global bits)
   uint32_t y_count;       // number of Y factors (phase i^y_count)

@@ -473,6 +473,124 @@ static void fill_slots(const Circuit& c, std::vector<int32_t>& slot_param, std::
   for (int s = 0; s < (int)slot_param.size(); ++s) param_slots[fill[slot_param[s]]++] = s;
 }
 
+// Checkpoint mode A (Sec. 3.4 with the gradient checkpointing of its memory
+// analysis). The forward program is cut into segments at its checkpoints
+// (OP_CKPT ops, and pass outputs that are checkpoints); a block is the run of
+// segments between two checkpoints. The adjoint, block by block from the
+// last: re-run the block's forward segments from the block's input checkpoint
+// (psi_0 generated for the first block), storing every segment output but
+// the last (which is the next checkpoint, or psi_M), in pass-output slots;
+// then run the adjoint segments in reverse, each starting from the stored
+// output of the forward segment it undoes. psi is not written back.
+static void build_mode_a(FusedPlan& P, bool mem_save) {
+  struct Seg {
+    int pass;                  // forward pass
+    int32_t fb, fe;            // forward op range
+    int32_t bb, be;            // adjoint op range
+    int32_t end_ckpt;          // slot holding the output (-1: none)
+  };
+  const int np = (int)P.fwd.size();
+  std::vector<Seg> segs;
+  for (int p = 0; p < np; ++p) {
+    const PassDesc& f = P.fwd[p];
+    const PassDesc& b = P.bwd[np - 1 - p];
+    std::vector<Seg> fs;
+    int32_t at = f.op_begin;
+    for (int32_t o = f.op_begin; o < f.op_end; ++o) {
+      const uint32_t code = P.fwd_ops[2 * o] & 15u;
+      if (code == OP_STEP) {
+        // round steps are one op; generic steps are followed by their ops
+        if (!P.rounds) o += (int32_t)((P.fwd_ops[2 * o] >> 8) & 0xffffu);
+      } else if (code == OP_CKPT) {
+        fs.push_back({p, at, o, 0, 0, (int32_t)P.fwd_ops[2 * o + 1]});
+        at = o + 1;
+      }
+    }
+    fs.push_back({p, at, f.op_end, 0, 0, f.psi_dst >= 0 ? f.psi_dst : -1});
+    // adjoint segments: the same cuts at OP_ANCHOR, in reverse order
+    std::vector<std::pair<int32_t, int32_t>> bs;
+    at = b.op_begin;
+    for (int32_t o = b.op_begin; o < b.op_end; ++o) {
+      const uint32_t code = P.bwd_ops[2 * o] & 15u;
+      if (code == OP_STEP) {
+        if (!P.rounds) o += (int32_t)((P.bwd_ops[2 * o] >> 8) & 0xffffu);
+      } else if (code == OP_ANCHOR) {
+        bs.push_back({at, o});
+        at = o + 1;
+      }
+    }
+    bs.push_back({at, b.op_end});
+    if (bs.size() != fs.size()) throw std::runtime_error("internal: mode A segment mismatch");
+    for (size_t j = 0; j < fs.size(); ++j) {
+      fs[j].bb = bs[fs.size() - 1 - j].first;
+      fs[j].be = bs[fs.size() - 1 - j].second;
+    }
+    for (const Seg& sg : fs) {
+      if (sg.fe > sg.fb) {
+        segs.push_back(sg);
+      } else if (sg.end_ckpt >= 0 && !segs.empty()) {
+        // an empty segment: its output is its input
+        segs.back().end_ckpt = sg.end_ckpt;
+      }
+    }
+  }
+  if (segs.empty()) throw std::runtime_error("internal: mode A without segments");
+  if (segs.back().end_ckpt < 0) throw std::runtime_error("internal: mode A without the final state");
+  const int32_t H = mem_save ? (PF_SRC_H | PF_DST_H) : 0;
+  const int32_t base = mem_save ? 0 : P.n_ckpt;  // pass-output slot numbering
+  P.ckpt_mode = 1;
+  P.mem_save = mem_save;
+  P.n_aslots = 0;
+  P.a_sched.clear();
+  P.a_dir.clear();
+  // blocks: [t0, t1] with segs[t1] ending at a checkpoint
+  std::vector<std::pair<int, int>> blocks;
+  for (int t = 0, t0 = 0; t < (int)segs.size(); ++t)
+    if (segs[t].end_ckpt >= 0) {
+      blocks.push_back({t0, t});
+      t0 = t + 1;
+    }
+  bool first = true;
+  for (int k = (int)blocks.size() - 1; k >= 0; --k) {
+    const int t0 = blocks[k].first, t1 = blocks[k].second;
+    P.n_aslots = std::max(P.n_aslots, t1 - t0);
+    for (int t = t0; t < t1; ++t) {
+      PassDesc d = P.fwd[segs[t].pass];
+      d.op_begin = segs[t].fb;
+      d.op_end = segs[t].fe;
+      d.flags = H & PF_DST_H;
+      if (t == t0) {
+        d.psi_src = t0 == 0 ? SRC_GENERATE : segs[t0 - 1].end_ckpt;
+      } else {
+        d.psi_src = base + (t - 1 - t0);
+        d.flags |= H & PF_SRC_H;
+      }
+      d.psi_dst = base + (t - t0);
+      d.lam_src = d.lam_dst = BUF_NONE;
+      P.a_sched.push_back(d);
+      P.a_dir.push_back(0);
+    }
+    for (int t = t1; t >= t0; --t) {
+      PassDesc d = P.bwd[np - 1 - segs[t].pass];
+      d.op_begin = segs[t].bb;
+      d.op_end = segs[t].be;
+      d.flags = 0;
+      if (t == t1) {
+        d.psi_src = segs[t1].end_ckpt;
+      } else {
+        d.psi_src = base + (t - t0);
+        d.flags |= H & PF_SRC_H;
+      }
+      d.psi_dst = BUF_NONE;
+      d.lam_src = first ? LAM_SEED : LAM_BUF;
+      d.lam_dst = (k == 0 && t == t0) ? BUF_NONE : LAM_BUF;
+      first = false;
+      P.a_sched.push_back(d);
+      P.a_dir.push_back(1);
+    }
+  }
+}
+
 FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
   validate_circuit(c);
   FusedPlan P;
@@ -851,6 +969,9 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
     for (int t = 0; t < P.n_terms; ++t)
       for (int j = P.term_off[t]; j < P.term_off[t + 1]; ++j) P.param_terms[fill[P.term_params[j]]++] = t;
   }
+  if (req.ckpt_mode == 1) build_mode_a(P, req.mem_save);
+  else if (req.ckpt_mode != 0) throw std::runtime_error("ckpt_mode must be 0 or 1");
+  else if (req.mem_save) throw std::runtime_error("mem_save needs ckpt_mode 1");
   return P;
 }
 

@@ -44,6 +44,16 @@ struct FusedPlan {
   std::vector<FuseGate> fuse_gates;
   std::vector<int32_t> term_off, term_params, term_kind;  // CSR term -> params
   std::vector<int32_t> param_off, param_terms;            // CSR param -> terms
+  // Checkpoint mode. 0 (B): the adjoint passes reverse psi in-kernel and
+  // re-anchor at the checkpoints. 1 (A, Sec. 3.4): per checkpoint block the
+  // forward passes are re-run from the block's input checkpoint, storing each
+  // pass output, and each adjoint pass starts from the stored output of the
+  // forward pass it undoes. The A schedule is the adjoint's launch list.
+  int ckpt_mode = 0;
+  bool mem_save = false;     // A: pass outputs stored as bfloat16 (re, im)
+  int n_aslots = 0;          // A: pass-output slots (one block's worth)
+  std::vector<PassDesc> a_sched;
+  std::vector<uint8_t> a_dir;  // 0: forward program pass, 1: adjoint program pass
 };
 
 // Per-gate schedule (the unfused comparator path).
@@ -60,6 +70,8 @@ struct PlanRequest {
   int tile_bits = 0;     // 0 = auto
   int ckpt_layers = 10;  // checkpoint interval in layers
   bool generic = false;  // force the generic step program
+  int ckpt_mode = 0;     // 0 = B (reverse in-kernel), 1 = A (per-block recompute)
+  bool mem_save = false; // A only: bfloat16 pass outputs
 };
 
 // Throws std::runtime_error with a message on invalid input.

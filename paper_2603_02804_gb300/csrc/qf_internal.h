@@ -61,6 +61,8 @@ enum : int32_t {
 
 enum PassFlags : int32_t {
   PF_EXPECT = 1,   // last forward pass: emit <O> partials of each tile
+  PF_SRC_H = 2,    // psi_src is a bfloat16 pass-output slot (memory-saving mode)
+  PF_DST_H = 4,    // psi_dst is a bfloat16 pass-output slot
 };
 
 struct PassDesc {

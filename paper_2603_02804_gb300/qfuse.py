@@ -41,14 +41,16 @@ class qf_pauli(ctypes.Structure):
 
 class qf_plan_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("ckpt_layers", ctypes.c_int32),
-                ("host_only", ctypes.c_int32), ("program", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("host_only", ctypes.c_int32), ("program", ctypes.c_int32), ("ckpt_mode", ctypes.c_int32),
+                ("mem_save", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class qf_plan_info_t(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in (
         "n_qubits", "n_eff", "n_params", "n_slots", "path", "tile_bits", "n_passes", "n_steps",
         "n_fused_ops", "n_ckpt", "ckpt_layers", "launches_fwd", "launches_bwd")] + [
-        ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64)]
+        ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64)] + [
+        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "reserved")]
 
 
 _vp = ctypes.c_void_p
@@ -170,8 +172,8 @@ def qf_circuit_destroy(handle: int) -> None:
 
 
 def qf_plan(handle: int, batch: int, path: int = QF_PATH_FUSED, tile_bits: int = 0, ckpt_layers: int = 0,
-            host_only: bool = False, program: int = 0) -> int:
-    o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program))
+            host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False) -> int:
+    o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program), int(ckpt_mode), int(mem_save))
     ws = _sz()
     _check(load().qf_plan(handle, ctypes.byref(o), batch, ctypes.byref(ws)))
     return ws.value
@@ -185,9 +187,10 @@ def qf_mem_model(k: float, d: float, b: float):
 
 
 def qf_plan_fit(handle: int, batch: int, mem_bytes: int, path: int = QF_PATH_FUSED, tile_bits: int = 0,
-                host_only: bool = False, program: int = 0):
-    """Plan with the smallest checkpoint interval that fits mem_bytes: (c, workspace bytes)."""
-    o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program))
+                host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False):
+    """Plan with a checkpoint interval that fits mem_bytes (mode 0: the smallest;
+    mode 1: the one with the smallest workspace): (c, workspace bytes)."""
+    o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program), int(ckpt_mode), int(mem_save))
     c = _i32()
     ws = _sz()
     _check(load().qf_plan_fit(handle, ctypes.byref(o), batch, mem_bytes, ctypes.byref(c), ctypes.byref(ws)))

@@ -116,6 +116,38 @@ def term_angle(prog, t, theta):
     return float(sum(float(theta[p]) for p in prog.terms[t][1]))
 
 
+def fwd_ops(prog, pd, psi, n_eff, theta, slots):
+    """Apply the forward op range of pass pd to psi (whole vector); OP_CKPT
+    writes slots."""
+    k = pd["op_begin"]
+    group = None
+    while k < pd["op_end"]:
+        w0, w1 = prog.ops[k]; k += 1
+        code = w0 & 15
+        if code == OP_STEP and prog.rounds_mode:
+            group = pd["groups"][(w0 >> 4) & 3]
+            nr = (w0 >> 8) & 0xFFFF
+            for j in range(nr):
+                rec = prog.round_words[(w1 + j) * FWD_ROUND_WORDS:(w1 + j + 1) * FWD_ROUND_WORDS]
+                for r in range(4):
+                    psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, rec[r], theta))
+                psi = psi * chain_sign(n_eff, rec[4] & 0xFFFFFFFF)
+        elif code == OP_STEP:
+            group = pd["groups"][(w0 >> 4) & 3]
+        elif code == OP_U:
+            r, m = (w0 >> 4) & 3, w0 >> 8
+            psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, m, theta))
+        elif code == OP_CHAIN:
+            psi = psi * chain_sign(n_eff, w1)
+        elif code == OP_CZ:
+            psi = psi * cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
+        elif code == OP_CKPT:
+            slots[w1] = psi.copy()
+        else:
+            raise AssertionError(f"unexpected forward op {code}")
+    return psi
+
+
 def run_forward(prog, n, n_eff, theta, xrow, xm, zm):
     slots = {}
     work = None
@@ -123,32 +155,7 @@ def run_forward(prog, n, n_eff, theta, xrow, xm, zm):
     for pd in prog.passes:
         src = pd["psi_src"]
         psi = encode(xrow, n, n_eff) if src == SRC_GENERATE else (slots[src] if src >= 0 else work).copy()
-        k = pd["op_begin"]
-        group = None
-        while k < pd["op_end"]:
-            w0, w1 = prog.ops[k]; k += 1
-            code = w0 & 15
-            if code == OP_STEP and prog.rounds_mode:
-                group = pd["groups"][(w0 >> 4) & 3]
-                nr = (w0 >> 8) & 0xFFFF
-                for j in range(nr):
-                    rec = prog.round_words[(w1 + j) * FWD_ROUND_WORDS:(w1 + j + 1) * FWD_ROUND_WORDS]
-                    for r in range(4):
-                        psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, rec[r], theta))
-                    psi = psi * chain_sign(n_eff, rec[4] & 0xFFFFFFFF)
-            elif code == OP_STEP:
-                group = pd["groups"][(w0 >> 4) & 3]
-            elif code == OP_U:
-                r, m = (w0 >> 4) & 3, w0 >> 8
-                psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, m, theta))
-            elif code == OP_CHAIN:
-                psi = psi * chain_sign(n_eff, w1)
-            elif code == OP_CZ:
-                psi = psi * cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
-            elif code == OP_CKPT:
-                slots[w1] = psi.copy()
-            else:
-                raise AssertionError(f"unexpected forward op {code}")
+        psi = fwd_ops(prog, pd, psi, n_eff, theta, slots)
         dst = pd["psi_dst"]
         if dst >= 0:
             slots[dst] = psi.copy()
@@ -165,6 +172,59 @@ def _grad_unapply(psi, lam, n_eff, q, kind, angle):
     return g, apply1(psi, n_eff, q, ud), apply1(lam, n_eff, q, ud)
 
 
+def bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen):
+    """Run the adjoint op range of pass pd on (psi, lam); returns both."""
+    k = pd["op_begin"]
+    group = None
+    while k < pd["op_end"]:
+        w0, w1 = prog.ops[k]; k += 1
+        code = w0 & 15
+        if code == OP_STEP and prog.rounds_mode:
+            group = pd["groups"][(w0 >> 4) & 3]
+            nr = (w0 >> 8) & 0xFFFF
+            for j in range(nr):
+                rec = prog.round_words[(w1 + j) * BWD_ROUND_WORDS:(w1 + j + 1) * BWD_ROUND_WORDS]
+                s = chain_sign(n_eff, rec[8] & 0xFFFFFFFF)
+                psi, lam = psi * s, lam * s
+                for r in range(4):
+                    q = pd["gmap"][group[r]]
+                    for t in (rec[r], rec[4 + r]):
+                        if t < 0:
+                            continue
+                        kind = prog.terms[t][0]
+                        g, psi, lam = _grad_unapply(psi, lam, n_eff, q, kind, term_angle(prog, t, theta))
+                        grad_term[t] += g
+                        seen[t] += 1
+        elif code == OP_STEP:
+            group = pd["groups"][(w0 >> 4) & 3]
+        elif code == OP_G:
+            r, kind, t = (w0 >> 4) & 3, (w0 >> 6) & 3, w1
+            assert kind == prog.terms[t][0]
+            g, psi, lam = _grad_unapply(psi, lam, n_eff, pd["gmap"][group[r]], kind, term_angle(prog, t, theta))
+            grad_term[t] += g
+            seen[t] += 1
+        elif code == OP_CHAIN:
+            s = chain_sign(n_eff, w1)
+            psi, lam = psi * s, lam * s
+        elif code == OP_CZ:
+            s = cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
+            psi, lam = psi * s, lam * s
+        elif code == OP_ANCHOR:
+            psi = slots[w1].copy()
+        else:
+            raise AssertionError(f"unexpected backward op {code}")
+    return psi, lam
+
+
+def _term_grad(prog, grad_term, seen, n_params):
+    assert np.all(seen == 1), "every gradient term must appear exactly once"
+    grad = np.zeros(n_params)
+    for t, (_, params) in enumerate(prog.terms):
+        for p in params:
+            grad[p] += grad_term[t]
+    return grad
+
+
 def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params):
     """Per-parameter gradient; every gradient term must be visited once."""
     grad_term = np.zeros(len(prog.terms))
@@ -174,52 +234,71 @@ def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params):
         src = pd["psi_src"]
         psi = (slots[src] if src >= 0 else work).copy()
         lam = 2 * dLdE * observable(psi, n_eff, xm, zm) if pd["lam_src"] == LAM_SEED else lam_buf.copy()
-        k = pd["op_begin"]
-        group = None
-        while k < pd["op_end"]:
-            w0, w1 = prog.ops[k]; k += 1
-            code = w0 & 15
-            if code == OP_STEP and prog.rounds_mode:
-                group = pd["groups"][(w0 >> 4) & 3]
-                nr = (w0 >> 8) & 0xFFFF
-                for j in range(nr):
-                    rec = prog.round_words[(w1 + j) * BWD_ROUND_WORDS:(w1 + j + 1) * BWD_ROUND_WORDS]
-                    s = chain_sign(n_eff, rec[8] & 0xFFFFFFFF)
-                    psi, lam = psi * s, lam * s
-                    for r in range(4):
-                        q = pd["gmap"][group[r]]
-                        for t in (rec[r], rec[4 + r]):
-                            if t < 0:
-                                continue
-                            kind = prog.terms[t][0]
-                            g, psi, lam = _grad_unapply(psi, lam, n_eff, q, kind, term_angle(prog, t, theta))
-                            grad_term[t] += g
-                            seen[t] += 1
-            elif code == OP_STEP:
-                group = pd["groups"][(w0 >> 4) & 3]
-            elif code == OP_G:
-                r, kind, t = (w0 >> 4) & 3, (w0 >> 6) & 3, w1
-                assert kind == prog.terms[t][0]
-                g, psi, lam = _grad_unapply(psi, lam, n_eff, pd["gmap"][group[r]], kind, term_angle(prog, t, theta))
-                grad_term[t] += g
-                seen[t] += 1
-            elif code == OP_CHAIN:
-                s = chain_sign(n_eff, w1)
-                psi, lam = psi * s, lam * s
-            elif code == OP_CZ:
-                s = cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
-                psi, lam = psi * s, lam * s
-            elif code == OP_ANCHOR:
-                psi = slots[w1].copy()
-            else:
-                raise AssertionError(f"unexpected backward op {code}")
+        psi, lam = bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen)
         if pd["psi_dst"] == BUF_WORK:
             work = psi
         if pd["lam_dst"] == LAM_BUF:
             lam_buf = lam
-    assert np.all(seen == 1), "every gradient term must appear exactly once"
-    grad = np.zeros(n_params)
-    for t, (_, params) in enumerate(prog.terms):
-        for p in params:
-            grad[p] += grad_term[t]
-    return grad
+    return _term_grad(prog, grad_term, seen, n_params)
+
+
+PF_SRC_H, PF_DST_H = 2, 4
+
+
+def parse_schedule(words):
+    """Mode A adjoint launch list (qf_plan_export direction 2)."""
+    w = [int(v) for v in words]
+    n = w[1]
+    keys = ["op_begin", "op_end", "psi_src", "psi_dst", "lam_src", "lam_dst", "flags", "K", "n_groups",
+            "outer_mask", "xm_local"]
+    out, i = [], 2
+    for _ in range(n):
+        d = dict(zip(keys, w[i + 1:i + 12]))
+        d["dir"] = w[i]
+        d["gmap"] = w[i + 12:i + 28]
+        d["groups"] = [w[i + 28 + 4 * g:i + 32 + 4 * g] for g in range(4)]
+        out.append(d)
+        i += 44
+    assert i == len(w)
+    return out
+
+
+def bf16_round(psi):
+    """Round re and im to bfloat16 (nearest even), as the memory-saving store."""
+    def r(v):
+        b = np.asarray(v, np.float32).view(np.uint32).astype(np.uint64)
+        b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+    return r(psi.real) + 1j * r(psi.imag)
+
+
+def run_backward_mode_a(fprog, bprog, sched, n, n_eff, theta, xrow, slots, xm, zm, dLdE, n_params):
+    """Mode A: per block, forward segments re-run into pass-output slots, then
+    adjoint segments from those stored outputs (psi never reversed across a
+    segment boundary)."""
+    grad_term = np.zeros(len(bprog.terms))
+    seen = np.zeros(len(bprog.terms), int)
+    aslots = {}
+    lam_buf = None
+
+    def load(src, half):
+        if src == SRC_GENERATE:
+            return encode(xrow, n, n_eff)
+        return (aslots[src] if half else slots[src]).copy()
+
+    for pd in sched:
+        half_src = bool(pd["flags"] & PF_SRC_H)
+        if pd["dir"] == 0:
+            psi = fwd_ops(fprog, pd, load(pd["psi_src"], half_src), n_eff, theta, {})
+            if pd["flags"] & PF_DST_H:
+                aslots[pd["psi_dst"]] = bf16_round(psi)
+            else:
+                slots[pd["psi_dst"]] = psi.copy()
+        else:
+            psi = load(pd["psi_src"], half_src)
+            lam = 2 * dLdE * observable(psi, n_eff, xm, zm) if pd["lam_src"] == LAM_SEED else lam_buf.copy()
+            psi, lam = bwd_ops(bprog, pd, psi, lam, n_eff, theta, slots, grad_term, seen)
+            assert pd["psi_dst"] == BUF_NONE
+            if pd["lam_dst"] == LAM_BUF:
+                lam_buf = lam
+    return _term_grad(bprog, grad_term, seen, n_params)

@@ -189,3 +189,105 @@ def test_plan_statistics_for_benchmark_shapes():
             assert pads == 0, (n, pads)
         finally:
             qfuse.qf_circuit_destroy(h)
+
+
+# Memory-saving mode: each stored pass output is rounded once to bfloat16
+# (relative 2^-9 per component); a gradient term sees one such rounding of
+# psi. Measured ~1e-4 on these shapes; the bound leaves 20x room.
+BF16_GRAD_TOL = 2e-3
+
+
+@pytest.mark.parametrize("mem_save", [False, True])
+@pytest.mark.parametrize("program", [0, 1])
+@pytest.mark.parametrize("n,d,K,ck", [
+    (6, 4, 0, 1), (12, 4, 0, 1), (12, 3, 0, 2), (13, 3, 0, 1), (14, 3, 8, 1), (17, 3, 0, 1), (9, 4, 6, 2),
+    (11, 2, 5, 0),
+])
+def test_mode_a_schedule_matches_oracle(n, d, K, ck, program, mem_save):
+    """Checkpoint mode A (per-block forward re-run storing pass outputs, each
+    adjoint pass starting from the stored output of the forward pass it
+    undoes): the exported launch list, executed on whole complex128 vectors,
+    gives the oracle's gradient; every gradient term is visited once."""
+    rng = np.random.default_rng(7000 + 37 * n + d)
+    h = qfuse.qf_hea_create(n, d)
+    try:
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, program=program, ckpt_mode=1,
+                      mem_save=mem_save)
+        info = qfuse.qf_plan_info(h)
+        assert info["ckpt_mode"] == 1 and info["mem_save"] == int(mem_save)
+        n_eff = info["n_eff"]
+        fwd = pi.parse(qfuse.qf_plan_export(h, 0))
+        bwd = pi.parse(qfuse.qf_plan_export(h, 1))
+        sched = pi.parse_schedule(qfuse.qf_plan_export(h, 2))
+        assert info["launches_bwd"] == len(sched) + 2
+        # no adjoint launch writes psi back; pass-output slots stay within the plan's count
+        for s in sched:
+            if s["dir"] == 1:
+                assert s["psi_dst"] == pi.BUF_NONE
+            h_dst = s["flags"] & pi.PF_DST_H
+            if s["dir"] == 0:
+                idx = s["psi_dst"] if h_dst else s["psi_dst"] - info["n_ckpt"]
+                assert 0 <= idx < info["n_pass_slots"]
+        theta = rng.uniform(0, 2 * np.pi, 3 * n * d).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
+        obs = "Z" if n < 3 else "ZXY"[: min(3, n)]
+        pq = qfuse.pauli(obs, n)
+        gp, Ep = orc.gradient(orc.hea(n, d), theta, x, obs, per_sample=True)
+        tol = BF16_GRAD_TOL if mem_save else 1e-10
+        for b in range(len(x)):
+            E, slots = pi.run_forward(fwd, n, n_eff, theta, x[b], pq.x_mask, pq.z_mask)
+            assert abs(E - Ep[b]) < 1e-10
+            g = pi.run_backward_mode_a(fwd, bwd, sched, n, n_eff, theta, x[b], slots, pq.x_mask, pq.z_mask,
+                                       1.0, len(theta))
+            assert np.max(np.abs(g - gp[b])) < tol
+            if mem_save and info["n_pass_slots"] > 0 and info["n_passes"] > 1:
+                assert np.max(np.abs(g - gp[b])) > 1e-9  # the rounding is really there
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+def test_mode_a_memory_and_options():
+    """Mode A stores p*c pass outputs of one block on top of the checkpoints;
+    the memory-saving mode stores them at half the bytes; mem_save without
+    mode A and mode A on the per-gate path are refused."""
+    n, d, B = 16, 40, 4
+    h = qfuse.qf_hea_create(n, d)
+    try:
+        ws_b = qfuse.qf_plan(h, B, ckpt_layers=10, host_only=True)
+        ws_a = qfuse.qf_plan(h, B, ckpt_layers=10, host_only=True, ckpt_mode=1)
+        ia = qfuse.qf_plan_info(h)
+        ws_h = qfuse.qf_plan(h, B, ckpt_layers=10, host_only=True, ckpt_mode=1, mem_save=True)
+        ih = qfuse.qf_plan_info(h)
+        st = ia["state_bytes"]
+        assert ia["n_pass_slots"] >= 1 and ih["n_pass_slots"] == ia["n_pass_slots"]
+        assert ws_a - ws_b == ia["n_pass_slots"] * st
+        assert ws_h - ws_b == ia["n_pass_slots"] * st // 2
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan(h, B, host_only=True, mem_save=True)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan(h, B, host_only=True, ckpt_mode=2)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan(h, B, host_only=True, path=qfuse.QF_PATH_PER_GATE, ckpt_mode=1)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan_export(h, 3)
+        qfuse.qf_plan(h, B, ckpt_layers=10, host_only=True)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan_export(h, 2)
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+def test_mode_a_fit_minimises_the_workspace():
+    """qf_plan_fit in mode A takes the checkpoint interval with the smallest
+    workspace (about sqrt(d / p) layers, Eq. 8), not the smallest interval."""
+    n, d, B = 16, 64, 2
+    h = qfuse.qf_hea_create(n, d)
+    try:
+        c, ws = qfuse.qf_plan_fit(h, B, 1 << 40, host_only=True, ckpt_mode=1)
+        sizes = {cl: qfuse.qf_plan(h, B, ckpt_layers=cl, host_only=True, ckpt_mode=1) for cl in range(1, d + 1)}
+        assert ws == sizes[c] == min(sizes.values())
+        assert 1 < c < d
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan_fit(h, B, min(sizes.values()) - 1, host_only=True, ckpt_mode=1)
+    finally:
+        qfuse.qf_circuit_destroy(h)
