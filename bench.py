@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
+    ap.add_argument("--tc", action="store_true", help="forward rounds on the tensor cores (3xTF32)")
+    ap.add_argument("--ckpt-mode", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--mem-save", action="store_true", help="checkpoint mode 1 with bfloat16 pass outputs")
+    ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core / mode-1 variant timings")
     return ap.parse_args()
 
 
@@ -413,7 +417,8 @@ def main():
     x = torch.from_numpy(x_np).to(dev)
     y = torch.from_numpy(y_np).to(dev) if y_np is not None else None
     ckpt = w.ckpt_layers or 0
-    sim = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs)
+    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
+    sim = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs, **opts)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
@@ -484,6 +489,32 @@ def main():
            "frac": 4 * state_bytes / (ms_per_step / 1e3) / 1e9 / hbm_gbs,
            "note": "state of this workload fits in L2; the path is ALU-bound, see roofline"}
 
+    # ---- the same step with the tensor-core forward and with checkpoint mode 1
+    variants = None
+    if not args.no_variants and world == 1:
+        variants = {}
+        for name, kw in (("tc_path", dict(tc_path=True)), ("ckpt_mode_1", dict(ckpt_mode=1)),
+                         ("ckpt_mode_1_mem_save", dict(ckpt_mode=1, mem_save=True))):
+            if kw == opts:
+                continue
+            try:
+                vs = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs, **kw)
+            except qfuse.QFError as err:
+                variants[name] = {"unavailable": str(err)}
+                continue
+            for _ in range(args.warmup):
+                step(vs)
+            torch.cuda.synchronize()
+            qfuse.qf_profile(vs.handle, True)
+            qfuse.qf_profile_read(vs.handle)
+            K = min(args.steps, 200)
+            v_ms, _ = timed(vs, K)
+            vp = qfuse.qf_profile_read(vs.handle)
+            variants[name] = {"value": w.B * K / (v_ms / 1e3), "unit": "samples/s", "ms_per_step": v_ms / K,
+                              "fwd_ms_per_step": vp["fwd_ms"] / K, "bwd_ms_per_step": vp["bwd_ms"] / K,
+                              "device_status": qfuse.qf_device_status(stream)}
+            del vs
+
     # ---- unfused per-gate comparator on the same GPU
     per_gate = None
     if not args.no_per_gate:
@@ -525,10 +556,12 @@ def main():
             "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} [RZ,RY,RZ + CZ chain], RY(x) encoding, "
                                    f"batch={w.B}/GPU, loss={w.loss}, obs=Z0",
                        "path": "fused", "tile_bits": info["tile_bits"], "passes": info["n_passes"],
+                       "tc_path": bool(args.tc), "ckpt_mode": args.ckpt_mode, "mem_save": bool(args.mem_save),
                        "ckpt_layers": info["ckpt_layers"], "parallelism": f"dp{world}",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "per_gate": per_gate,
             "speedup_vs_per_gate": (value / per_gate["value"]) if per_gate else None,
+            "variants": variants,
             "roofline": roofline,
             "hbm": hbm,
             "e2e": e2e,

@@ -108,7 +108,14 @@ typedef struct {
   int32_t mem_save;    /* ckpt_mode 1 only: store those pass outputs as bfloat16
                           (re, im), computing in float32 (the memory-saving mode
                           of Sec. 3.2); checkpoints and psi_M stay float32       */
-  int32_t reserved[9];
+  int32_t tc_path;     /* fused: 1 = forward passes (and mode-1 re-runs) apply
+                          each round of 4 single-qubit gates as a 32x32 real
+                          block on the tensor cores, split-precision 3xTF32 with
+                          float32 accumulation; needs round programs and
+                          12-qubit tiles (n >= 12), else QF_ERR_UNSUPPORTED.
+                          The paper has no tensor-core path (Sec. 3.2 fuses the
+                          unitaries, applied here as dense blocks)               */
+  int32_t reserved[8];
 } qf_plan_opts;
 
 /* Summary of a plan (host-side numbers). */
@@ -132,7 +139,7 @@ typedef struct {
   int32_t ckpt_mode;       /* as planned (opts->ckpt_mode)                      */
   int32_t mem_save;
   int32_t n_pass_slots;    /* ckpt_mode 1: stored pass outputs of one block     */
-  int32_t reserved;
+  int32_t tc_path;
 } qf_plan_info_t;
 
 /* Create the hardware-efficient ansatz of the paper's benchmarks with the
@@ -337,6 +344,13 @@ qf_status qf_profile(qf_circuit* c, int32_t on);
  * NULL. */
 qf_status qf_profile_read(qf_circuit* c, double* fwd_ms, int64_t* fwd_launches, double* bwd_ms,
                           int64_t* bwd_launches);
+
+/* Read and clear the device error word after the work queued on `stream`
+ * (synchronises the stream). *code: 0 = no error; 1 = a bounded wait inside
+ * a kernel gave up (the tensor-core path waits on its MMA completions with an
+ * iteration limit instead of spinning forever; results of that launch are
+ * invalid). Has no counterpart in the paper. */
+qf_status qf_device_status(void* stream, int32_t* code);
 
 /* Thread-local description of the last error ("" if none). */
 const char* qf_last_error(void);

@@ -33,6 +33,7 @@ struct Layout {
   size_t theta = 0, x = 0, y = 0, E = 0, dLdE = 0, grad = 0, loss = 0;  // staging
   size_t mats = 0, cs = 0, enc = 0;
   size_t rpf = 0, rpb = 0;  // round-ordered item parameters (round programs)
+  size_t mats64 = 0, tcb = 0;  // tensor-core path: float64 fused 2x2s, per-round B blocks
   size_t work = 0, lam = 0, slots = 0, hslots = 0;
   size_t epart = 0, gpart = 0;
   size_t total = 0;
@@ -67,6 +68,7 @@ struct qf_circuit {
   bool host_only = false;
   int path = QF_PATH_FUSED;
   int ckpt_layers = 10;
+  bool tc = false;          // forward rounds on the tensor cores
   int64_t batch = 0;
   qf::FusedPlan fp;
   qf::PerGatePlan gp;
@@ -151,6 +153,10 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     if (c->fp.rounds) {
       L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 128);
       L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * 128);
+    }
+    if (c->tc) {
+      L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
+      L.tcb = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 2048 * 4);
     }
     // checkpoint mode A: pass-output slots after the checkpoints (float32), or
     // a bfloat16 array of them (memory-saving mode)
@@ -327,6 +333,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
     pa.rpf_src = T.fwd_rounds;
     pa.rpf = at<float4>(ws, L.rpf);
   }
+  if (c->tc) pa.mats64 = at<double>(ws, L.mats64);
   pa.x = x;
   pa.B = B;
   pa.n = c->circ.n;
@@ -334,11 +341,17 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.enc = at<float2>(ws, L.enc);
   QF_CU(qf::launch_prep(pa, st));
   c->call_launches++;
+  if (c->tc) {
+    QF_CU(qf::launch_tc_tables(T.fwd_rounds, (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords), pa.mats64,
+                               at<float>(ws, L.tcb), st));
+    c->call_launches++;
+  }
   qf::PassArgs a{};
   a.n_eff = P.n_eff;
   a.tps_log2 = P.n_eff - P.K;
   a.B = B;
   a.ops = T.fwd_ops;
+  a.tcb = c->tc ? at<float>(ws, L.tcb) : nullptr;
   a.rounds = P.rounds ? T.fwd_rounds : nullptr;
   a.rpar = P.rounds ? at<float4>(ws, L.rpf) : nullptr;
   a.mats = pa.mats;
@@ -360,7 +373,8 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
     a.pd.xm_local = 0;
     if ((a.pd.flags & qf::PF_EXPECT) && !local_xmask(a.pd, o.x, &a.pd.xm_local))
       return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
-    QF_CU(qf::launch_pass(false, a, st));
+    if (c->tc) QF_CU(qf::launch_pass_tc(a, st));
+    else QF_CU(qf::launch_pass(false, a, st));
     c->call_launches++;
   }
   prof_end(c, prof, 0, (int64_t)P.fwd.size(), st);
@@ -415,6 +429,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
     f.rpar = P.rounds ? at<float4>(ws, L.rpf) : nullptr;
     f.mats = at<float4>(ws, L.mats);
     f.enc = at<float2>(ws, L.enc);
+    f.tcb = c->tc ? at<float>(ws, L.tcb) : nullptr;
     for (size_t i = 0; i < P.a_sched.size(); ++i) {
       const bool bwd = P.a_dir[i] != 0;
       qf::PassArgs& x = bwd ? a : f;
@@ -422,7 +437,8 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
       x.pd.xm_local = 0;
       if (bwd && x.pd.lam_src == qf::LAM_SEED && !local_xmask(x.pd, o.x, &x.pd.xm_local))
         return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
-      QF_CU(qf::launch_pass(bwd, x, st));
+      if (c->tc && !bwd) QF_CU(qf::launch_pass_tc(x, st));
+      else QF_CU(qf::launch_pass(bwd, x, st));
       c->call_launches++;
     }
     prof_end(c, prof, 1, (int64_t)P.a_sched.size(), st);
@@ -552,6 +568,13 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
 
 extern "C" {
 
+qf_status qf_device_status(void* stream, int32_t* code) {
+  if (!code) return fail(QF_ERR_INVALID_ARG, "null argument");
+  *code = 0;
+  QF_CU(qf::device_status(code, static_cast<cudaStream_t>(stream)));
+  return QF_OK;
+}
+
 const char* qf_last_error(void) { return g_err.c_str(); }
 
 int32_t qf_version(void) { return 100; }
@@ -629,6 +652,8 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
   if (o.mem_save && o.ckpt_mode != 1) return fail(QF_ERR_INVALID_ARG, "mem_save needs ckpt_mode 1");
   if (o.ckpt_mode != 0 && o.path != QF_PATH_FUSED)
     return fail(QF_ERR_UNSUPPORTED, "ckpt_mode 1 applies to the fused path");
+  if (o.tc_path != 0 && o.tc_path != 1) return fail(QF_ERR_INVALID_ARG, "tc_path must be 0 or 1");
+  if (o.tc_path && o.path != QF_PATH_FUSED) return fail(QF_ERR_UNSUPPORTED, "tc_path applies to the fused path");
   try {
     free_tables(c);
     c->planned = false;
@@ -642,15 +667,23 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     req.generic = o.program == 1;
     req.ckpt_mode = o.ckpt_mode;
     req.mem_save = o.mem_save != 0;
+    c->tc = false;
     if (c->path == QF_PATH_FUSED) {
       c->fp = qf::plan_fused(c->circ, req);
       c->gp = qf::PerGatePlan();
+      if (o.tc_path) {
+        if (!c->fp.rounds || c->fp.K != qf::kMaxTileBits)
+          throw std::domain_error("tc_path needs round programs with 12-qubit tiles (n >= 12, RZ/RY, chain CZs)");
+        c->tc = true;
+      }
     } else {
       c->gp = qf::plan_per_gate(c->circ, req);
       c->fp = qf::FusedPlan();
     }
     c->L = make_layout(c, batch);
     build_blob(c);
+  } catch (const std::domain_error& e) {
+    return fail(QF_ERR_UNSUPPORTED, e.what());
   } catch (const std::bad_alloc&) {
     return fail(QF_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
@@ -761,6 +794,8 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
     info->ckpt_mode = c->fp.ckpt_mode;
     info->mem_save = c->fp.mem_save ? 1 : 0;
     info->n_pass_slots = c->fp.n_aslots;
+    info->tc_path = c->tc ? 1 : 0;
+    if (c->tc) info->launches_fwd += 1;  // the B-block table
     if (c->fp.ckpt_mode == 1) info->launches_bwd = (int32_t)c->fp.a_sched.size() + 2;
   } else {
     info->n_eff = c->gp.n_eff;
@@ -1054,8 +1089,8 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       qf_circuit* c = b->circ[i];
       const std::string at = " (circuit " + std::to_string(i) + ")";
       if (!c || !c->planned) throw std::invalid_argument("circuit has no plan" + at);
-      if (c->path == QF_PATH_FUSED && c->fp.ckpt_mode != 0)
-        throw std::invalid_argument("batched launches use checkpoint mode 0");
+      if (c->path == QF_PATH_FUSED && (c->fp.ckpt_mode != 0 || c->tc))
+        throw std::invalid_argument("batched launches use checkpoint mode 0 on the CUDA cores" + at);
       if (c->path != QF_PATH_FUSED || !c->fp.rounds)
         throw std::invalid_argument("batched launches need fused round programs (RZ/RY rotations, CZ on "
                                     "neighbouring qubits, at least 7 qubits per tile)" + at);

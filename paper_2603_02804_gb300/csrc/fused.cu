@@ -17,6 +17,10 @@
 
 namespace qf {
 
+// Sticky device error word (1: a bounded wait gave up); read and cleared by
+// qf_device_status.
+__device__ int g_qf_device_status = 0;
+
 namespace {
 
 __device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 4) & 15u); }
@@ -301,10 +305,6 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// Static shared memory of a pass (the tiles themselves are dynamic).
 // Parameters of one round step, staged from the round-ordered tables: per
 // round 8 float4 (forward: the 4 items' fused 2x2s; backward: the shear
 // parameters of tz[0..3], ty[0..3]) and the round record.
@@ -313,6 +313,200 @@ struct StepPar {
   uint4 rec[kMaxStepRounds * (kBwdRoundWords / 4)];
 };
 
+// ---- tensor-core block path (tcgen05) --------------------------------------------
+// A forward round applies u3 (x) u2 (x) u1 (x) u0 to the 16 amplitudes of a
+// register group: a 16x16 complex block, i.e. a 32x32 real matrix on the
+// (re, im) vector. A warpgroup's 128 columns (one per thread) form the MMA's
+// M = 128 rows: D[m][n] = sum_k A[m][k] B[n][k], A = the columns' amplitudes
+// (k < 16: re of amplitude k, else im of amplitude k - 16) in tensor memory,
+// B = the round's real matrix (K-major, in shared memory), D in tensor memory.
+// Split precision (3xTF32): A = Ah + Al, B = Bh + Bl with TF32 parts, and
+// D = Ah Bh + Ah Bl + Al Bh accumulated in float32.
+constexpr int kTcCols = 256;            // tensor-memory columns per CTA
+constexpr int kTcWgCols = 96;           // per warpgroup: D, A hi, A lo (32 each)
+constexpr int kTcBFloats = 2 * 1024;    // one round's B: hi then lo, 32x32 each
+constexpr long long kTcSpinLimit = 1ll << 26;
+
+// idesc for kind::tf32: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12 = 2),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Shared-memory descriptor, K-major without swizzle: 8-row x 16-byte core
+// matrices; LBO = 128 B between core matrices along K, SBO = 1024 B between
+// 8-row groups; version 1 (bit 46).
+__device__ __forceinline__ uint64_t tc_bdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cvt_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.u32 p, %3, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %4, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(acc), "r"(kTcIdesc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+// Wait for the mbarrier phase with the given parity; false after the spin limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t addr = smem_u32(mbar);
+  for (long long it = 0; it < kTcSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+#define QF_R8(b) "%" #b "0, %" #b "1, %" #b "2, %" #b "3, %" #b "4, %" #b "5, %" #b "6, %" #b "7"
+
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t u[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
+        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
+        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(u[k]);
+}
+
+// Per-CTA state of the tensor-core path.
+struct TcCtx {
+  uint32_t tmem;    // tensor-memory base (lane 0, first column)
+  uint64_t* mbar;   // [2] one per warpgroup, in shared memory
+  float* bsm;       // B staging: [2][kMaxStepRounds][kTcBFloats]
+};
+
+// Sign mask over the 16 register indices j of the round's CZ links (x = gb ^
+// y(j)): constant part, parts linear in one register bit, and links between
+// two register bits (bbits).
+__device__ __forceinline__ uint32_t cz_mask16(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4]) {
+  const uint32_t t1 = L & gb, t2 = L & (gb >> 1);
+  const uint32_t u = (t1 << 1) ^ t2;
+  uint32_t S = (__popc(t2 & gb) & 1u) ? 0xFFFFu : 0u;
+  S ^= ((u >> p[0]) & 1u) ? 0xAAAAu : 0u;
+  S ^= ((u >> p[1]) & 1u) ? 0xCCCCu : 0u;
+  S ^= ((u >> p[2]) & 1u) ? 0xF0F0u : 0u;
+  S ^= ((u >> p[3]) & 1u) ? 0xFF00u : 0u;
+  S ^= (bbits & 1u) ? 0x8888u : 0u;
+  S ^= (bbits & 2u) ? 0xC0C0u : 0u;
+  S ^= (bbits & 4u) ? 0xF000u : 0u;
+  return S;
+}
+
+// The rounds of one forward step on the tensor cores. r holds the thread's 16
+// amplitudes (its column) on entry and exit. Warpgroup wg issues its own MMAs
+// (M = its 128 columns) and waits on its own mbarrier; ph tracks the phase.
+__device__ __forceinline__ void tc_rounds(const TcCtx& tc, const StepPar& P, int nr, const float* bst, uint32_t gb,
+                                          const uint32_t (&pos)[4], float2 (&r)[16], uint32_t& ph, int tid) {
+  const int wg = tid >> 7, wq = (tid >> 5) & 3;
+  const uint32_t col0 = tc.tmem + (uint32_t)(wg * kTcWgCols);
+  const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+  const uint32_t d_col = col0, ah_col = col0 + 32, al_col = col0 + 64;
+  float x[32];
+  float n0 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    x[j] = r[j].x;
+    x[16 + j] = r[j].y;
+    n0 = fmaf(x[j], x[j], fmaf(x[16 + j], x[16 + j], n0));
+  }
+#pragma unroll 1
+  for (int k = 0; k < nr; ++k) {
+    {
+      uint32_t hi[32], lo[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        hi[q] = cvt_tf32(x[q]);
+        lo[q] = cvt_tf32(x[q] - __uint_as_float(hi[q]));
+      }
+      tc_st32(ah_col | lane_off, hi);
+      tc_st32(al_col | lane_off, lo);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
+    if ((tid & 127) == 0) {
+      tc_fence_after();
+      const uint32_t bh = smem_u32(bst + (size_t)k * kTcBFloats), bl = bh + 4096u;
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr) {
+        const uint32_t a = pr == 2 ? al_col : ah_col;
+        const uint32_t b = pr == 1 ? bl : bh;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          tc_mma(d_col, a + 8u * kk, tc_bdesc(b + 256u * kk), (pr | kk) != 0 ? 1u : 0u);
+      }
+      tc_commit(tc.mbar + wg);
+    }
+    if (!mbar_wait(tc.mbar + wg, ph)) atomicExch(&g_qf_device_status, 1);
+    ph ^= 1u;
+    tc_fence_after();
+    tc_ld32(d_col | lane_off, x);
+    // CZ links after this round's rotations
+    const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];
+    const uint32_t S = cz_mask16(lk.x, lk.y, gb, pos);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int f = (int)((S << (31 - j)) & 0x80000000u);
+      x[j] = __int_as_float(__float_as_int(x[j]) ^ f);
+      x[16 + j] = __int_as_float(__float_as_int(x[16 + j]) ^ f);
+    }
+  }
+  tc_fence_before();
+  // The step acts on the column by a unitary (rotations and CZ signs), so its
+  // norm is invariant; the tensor cores' float32 accumulation rounds toward
+  // zero and shrinks it by a few ulp per round. Restore the norm.
+  float n1 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) n1 = fmaf(x[q], x[q], n1);
+  const float sc = n1 > 0.f ? sqrtf(n0 / n1) : 1.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) r[j] = make_float2(x[j] * sc, x[16 + j] * sc);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Static shared memory of a pass (the tiles themselves are dynamic).
 struct PassShared {
   StepPar par[2];
   uint32_t lg[256];
@@ -327,8 +521,9 @@ struct PassShared {
 // (tile = sample * tiles_per_sample + tile within the sample). Ends with a
 // barrier, so a CTA may call it again for another pass or tile range. LOADS:
 // tile loads in flight per thread and state (8 = the whole tile at once).
-template <bool BWD, bool ROUNDS, int LOADS = 8>
-__device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_tile, float2* smem, PassShared& sh) {
+template <bool BWD, bool ROUNDS, int LOADS = 8, bool TC = false>
+__device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_tile, float2* smem, PassShared& sh,
+                                         const TcCtx* tc = nullptr) {
   uint32_t (&s_lg)[256] = sh.lg;
   float (&s_red)[2][kThreads / 32][kMaxStepSlots] = sh.red;
   int32_t (&s_slot)[2][kMaxStepSlots] = sh.slot;
@@ -388,6 +583,16 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
     }
     return false;
   };
+  // (tensor-core path, every thread) asynchronous copy of the B blocks of
+  // rounds rb .. rb+nr-1 into staging buffer bb
+  auto stage_b = [&](int bb, uint32_t rb, int nr) {
+    const int n16 = nr * kTcBFloats / 4;
+    const float* src = a.tcb + (size_t)rb * kTcBFloats;
+    float* dst = tc->bsm + (size_t)bb * kMaxStepRounds * kTcBFloats;
+    for (int e = tid; e < n16; e += kThreads) cp_async16(dst + 4 * e, src + 4 * e);
+    cp_async_commit();
+  };
+  uint32_t ph = 0;  // tensor-core path: mbarrier phase of this thread's warpgroup
   // (warp 0) asynchronous copy of rounds rb .. rb+nr-1 into sh.par[pb]
   auto stage = [&](int pb, uint32_t rb, int nr) {
     constexpr int RW4 = (BWD ? kBwdRoundWords : kFwdRoundWords) / 4;
@@ -458,6 +663,13 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
     if (next_step(pd.op_begin, rb, nr)) stage(0, rb, nr);
     cp_async_wait_all();
   }
+  if (TC) {
+    uint32_t rb;
+    int nr;
+    if (next_step(pd.op_begin, rb, nr)) stage_b(0, rb, nr);
+    cp_async_wait_all();
+    fence_proxy_async();  // B is read by the tensor cores (async proxy)
+  }
   __syncthreads();
   if (BWD && pd.lam_src == LAM_SEED) {
     // lambda_M = 2 (dL/dE_b) O psi_M (Eq. 4); (O psi)_x = i^{#Y} (-1)^{|(x^xm)&zm|} psi_{x^xm}
@@ -493,6 +705,11 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         int nr2;
         if (next_step(pc, rb, nr2)) stage(sb ^ 1, rb, nr2);
       }
+      if (TC) {
+        uint32_t rb;
+        int nr2;
+        if (next_step(pc, rb, nr2)) stage_b(sb ^ 1, rb, nr2);
+      }
       const StepPar& P = sh.par[sb];
       const uint32_t lb0 = s_grp[g][0], lb1 = s_grp[g][1], lb2 = s_grp[g][2], lb3 = s_grp[g][3];
       const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
@@ -509,6 +726,9 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         if (BWD) l[j] = tl[pb ^ reg_off(j, so)];
       }
       uint32_t D = 0;
+      if constexpr (TC) {
+        tc_rounds(*tc, P, nr, tc->bsm + (size_t)sb * kMaxStepRounds * kTcBFloats, gb, pos, r, ph, tid);
+      } else {
 #pragma unroll 1
       for (int k = 0; k < nr; ++k) {
         if (!BWD) {
@@ -542,12 +762,18 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         }
       }
       apply_pending<BWD>(D, r, l);
+      }  // CUDA-core rounds
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         tp[pb ^ reg_off(j, so)] = r[j];
         if (BWD) tl[pb ^ reg_off(j, so)] = l[j];
       }
-      if (warp == 0) cp_async_wait_all();
+      if (TC) {
+        cp_async_wait_all();
+        fence_proxy_async();
+      } else if (warp == 0) {
+        cp_async_wait_all();
+      }
       __syncthreads();
       sb ^= 1;
       if (BWD && Tt >= 32 && a.g_accum) {
@@ -738,6 +964,70 @@ __global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const Pa
   pass_cta<BWD, ROUNDS>(a, (int64_t)blockIdx.x * (kThreads >> (a.pd.K - kRegBits)), smem, sh);
 }
 
+// Forward pass with the rounds on the tensor cores: one 12-qubit tile per
+// CTA (two warpgroups of 128 columns). Dynamic shared memory: the tile, then
+// two B staging buffers of kMaxStepRounds rounds.
+__global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ PassShared sh;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < 2; ++w)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[w])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  TcCtx ctx{tmem_slot, mbar, reinterpret_cast<float*>(smem + kTileAmps)};
+  pass_cta<false, true, 8, true>(a, (int64_t)blockIdx.x, smem, sh, &ctx);
+  // pass_cta ends with a barrier; every tensor-memory access is complete
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kTcCols) : "memory");
+}
+
+// B blocks: element (n, k) of round r, n = output (re i | im i), k = input
+// (re j | im j): U = u3 (x) u2 (x) u1 (x) u0 of the round's fused 2x2s,
+// U[i][j] = prod_b u_b[i_b][j_b]; B[re i][re j] = Re U, B[re i][im j] = -Im U,
+// B[im i][re j] = Im U, B[im i][im j] = Re U. Stored K-major (8-row x 16-byte
+// core matrices, 128 B apart along K, 1024 B between row groups), TF32 hi at
+// [0, 1024) and lo at [1024, 2048) of the round's block.
+__global__ void tc_table_kernel(const uint4* fwd_rounds, int32_t n_rounds, const double* mats64, float* tcb) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n_rounds * 1024) return;
+  const int64_t r = e >> 10;
+  const int n = (int)((e >> 5) & 31), k = (int)(e & 31);
+  const int i = n & 15, j = k & 15;
+  const uint4 m = fwd_rounds[r * (kFwdRoundWords / 4)];
+  const uint32_t mm[4] = {m.x, m.y, m.z, m.w};
+  double re = 1.0, im = 0.0;
+  for (int b = 0; b < 4; ++b) {
+    const double* u = mats64 + 8 * (size_t)mm[b];
+    const int ib = (i >> b) & 1, jb = (j >> b) & 1;
+    const double ur = u[(ib * 2 + jb) * 2], ui = u[(ib * 2 + jb) * 2 + 1];
+    const double t = re * ur - im * ui;
+    im = re * ui + im * ur;
+    re = t;
+  }
+  const bool ro = n < 16, ri = k < 16;
+  const double v = ro ? (ri ? re : -im) : (ri ? im : re);
+  const float vf = (float)v;
+  const uint32_t hi = cvt_tf32(vf);
+  const uint32_t lo = cvt_tf32((float)(v - (double)__uint_as_float(hi)));
+  const int off = (n >> 3) * 256 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+  tcb[r * kTcBFloats + off] = __uint_as_float(hi);
+  tcb[r * kTcBFloats + 1024 + off] = __uint_as_float(lo);
+}
+
 // ---------------------------------------------------------------------------
 // Gate tables from theta in float64, rounded once to float32:
 //   fused 2x2 products (forward), (cos, sin) of theta/2 per slot (backward),
@@ -752,7 +1042,7 @@ __global__ void prep_kernel(const PrepArgs a) {
 namespace {
 
 // Fused 2x2 product of fused entry m (float64, rounded once to float32).
-__device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1) {
+__device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1, double* u64 = nullptr) {
   double u[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {1, 0}}};  // [row][col][re/im]
   for (int j = a.fuse_off[m]; j < a.fuse_off[m + 1]; ++j) {
     const FuseGate fg = a.fuse_gates[j];
@@ -789,6 +1079,8 @@ __device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1) {
   }
   m0 = make_float4((float)u[0][0][0], (float)u[0][0][1], (float)u[0][1][0], (float)u[0][1][1]);
   m1 = make_float4((float)u[1][0][0], (float)u[1][0][1], (float)u[1][1][0], (float)u[1][1][1]);
+  if (u64)
+    for (int q = 0; q < 8; ++q) u64[q] = u[q >> 2][(q >> 1) & 1][q & 1];
 }
 
 // A term's angle is the sum of its parameters (a merged run of RZ gates).
@@ -817,7 +1109,7 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
 // programs) the forward and backward round parameters in round order.
 __device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (i < a.n_fused) {
-    fused_u(a, i, a.mats[2 * i], a.mats[2 * i + 1]);
+    fused_u(a, i, a.mats[2 * i], a.mats[2 * i + 1], a.mats64 ? a.mats64 + 8 * i : nullptr);
     return;
   }
   i -= a.n_fused;
@@ -1146,6 +1438,44 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
     else pass_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_pass_tc(const PassArgs& a, cudaStream_t st) {
+  if (a.pd.K != kMaxTileBits || a.rounds == nullptr || a.tcb == nullptr) return cudaErrorInvalidValue;
+  const int64_t grid = (int64_t)a.B << a.tps_log2;
+  if (grid == 0) return cudaSuccess;
+  const size_t smem = (size_t)kTileAmps * sizeof(float2) + (size_t)2 * kMaxStepRounds * kTcBFloats * sizeof(float);
+  static bool once[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !once[dev]) {
+    e = cudaFuncSetAttribute(tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    once[dev] = true;
+  }
+  tc_pass_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_tables(const uint4* fwd_rounds, int32_t n_rounds, const double* mats64, float* tcb,
+                             cudaStream_t st) {
+  const int64_t total = (int64_t)n_rounds * 1024;
+  if (total == 0) return cudaSuccess;
+  tc_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(fwd_rounds, n_rounds, mats64, tcb);
+  return cudaGetLastError();
+}
+
+cudaError_t device_status(int32_t* code, cudaStream_t st) {
+  int32_t v = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_qf_device_status, sizeof(v), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  *code = v;
+  const int32_t zero = 0;
+  e = cudaMemcpyToSymbolAsync(g_qf_device_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
 }
 
 cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st) {

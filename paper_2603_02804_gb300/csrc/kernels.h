@@ -15,6 +15,7 @@ struct PassArgs {
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs)
   const float4* rpar;     // per-round item parameters, 8 float4 per round (round programs)
+  const float* tcb;       // tensor-core path: per-round 32x32 real blocks, TF32 hi then lo, K-major
   const float4* mats;     // fused 2x2 matrices, 2 float4 each
   const float2* cs;       // (cos, sin) of theta/2 per gradient term (generic programs)
   const float4* shear;    // three-shear parameters per gradient term (round programs)
@@ -39,6 +40,7 @@ struct PrepArgs {
   const int32_t* fuse_off;
   const FuseGate* fuse_gates;
   float4* mats;
+  double* mats64;              // if non-null: the fused 2x2s in float64 too, 8 doubles each
   int32_t n_terms;
   const int32_t* term_off;     // CSR term -> parameters (angles summed)
   const int32_t* term_params;
@@ -73,6 +75,13 @@ struct GradReduceArgs {
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
 cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st);
+// Forward pass on the tensor cores (round programs, 12-qubit tiles).
+cudaError_t launch_pass_tc(const PassArgs& a, cudaStream_t st);
+// Per-round B blocks of the tensor-core path from the float64 fused 2x2s.
+cudaError_t launch_tc_tables(const uint4* fwd_rounds, int32_t n_rounds, const double* mats64, float* tcb,
+                             cudaStream_t st);
+// Read and clear the device error word (1: a bounded wait gave up).
+cudaError_t device_status(int32_t* code, cudaStream_t st);
 cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st);
 cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st);
 cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,

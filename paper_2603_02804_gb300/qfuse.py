@@ -42,7 +42,7 @@ class qf_pauli(ctypes.Structure):
 class qf_plan_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("ckpt_layers", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("program", ctypes.c_int32), ("ckpt_mode", ctypes.c_int32),
-                ("mem_save", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("mem_save", ctypes.c_int32), ("tc_path", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class qf_plan_info_t(ctypes.Structure):
@@ -50,7 +50,7 @@ class qf_plan_info_t(ctypes.Structure):
         "n_qubits", "n_eff", "n_params", "n_slots", "path", "tile_bits", "n_passes", "n_steps",
         "n_fused_ops", "n_ckpt", "ckpt_layers", "launches_fwd", "launches_bwd")] + [
         ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64)] + [
-        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "reserved")]
+        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "tc_path")]
 
 
 _vp = ctypes.c_void_p
@@ -88,6 +88,7 @@ SIGNATURES = {
     "qf_profile": ([_vp, _i32], _i32),
     "qf_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)], _i32),
+    "qf_device_status": ([_vp, ctypes.POINTER(_i32)], _i32),
     "qf_last_error": ([], ctypes.c_char_p),
     "qf_version": ([], _i32),
 }
@@ -172,8 +173,10 @@ def qf_circuit_destroy(handle: int) -> None:
 
 
 def qf_plan(handle: int, batch: int, path: int = QF_PATH_FUSED, tile_bits: int = 0, ckpt_layers: int = 0,
-            host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False) -> int:
-    o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program), int(ckpt_mode), int(mem_save))
+            host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False,
+            tc_path: bool = False) -> int:
+    o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program), int(ckpt_mode), int(mem_save),
+                     int(tc_path))
     ws = _sz()
     _check(load().qf_plan(handle, ctypes.byref(o), batch, ctypes.byref(ws)))
     return ws.value
@@ -187,10 +190,12 @@ def qf_mem_model(k: float, d: float, b: float):
 
 
 def qf_plan_fit(handle: int, batch: int, mem_bytes: int, path: int = QF_PATH_FUSED, tile_bits: int = 0,
-                host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False):
+                host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False,
+                tc_path: bool = False):
     """Plan with a checkpoint interval that fits mem_bytes (mode 0: the smallest;
     mode 1: the one with the smallest workspace): (c, workspace bytes)."""
-    o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program), int(ckpt_mode), int(mem_save))
+    o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program), int(ckpt_mode), int(mem_save),
+                     int(tc_path))
     c = _i32()
     ws = _sz()
     _check(load().qf_plan_fit(handle, ctypes.byref(o), batch, mem_bytes, ctypes.byref(c), ctypes.byref(ws)))
@@ -302,6 +307,13 @@ def qf_profile_read(handle) -> dict:
     fl, bl = _i64(), _i64()
     _check(load().qf_profile_read(handle, ctypes.byref(fm), ctypes.byref(fl), ctypes.byref(bm), ctypes.byref(bl)))
     return {"fwd_ms": fm.value, "fwd_launches": fl.value, "bwd_ms": bm.value, "bwd_launches": bl.value}
+
+
+def qf_device_status(stream=None) -> int:
+    """Read and clear the device error word (0: none; 1: a bounded wait gave up)."""
+    code = _i32()
+    _check(load().qf_device_status(_stream(stream), ctypes.byref(code)))
+    return code.value
 
 
 def qf_last_error() -> str:

@@ -35,11 +35,13 @@ class Simulator:
     ``ckpt_mode`` 0 reverses psi in the adjoint passes between checkpoints;
     1 re-runs each checkpoint block's forward storing the pass outputs
     (bfloat16 with ``mem_save``), as in the paper's checkpointed scheme.
+    ``tc_path`` runs the forward rounds as split-precision blocks on the
+    tensor cores (12-qubit tiles, n >= 12).
     """
 
     def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
                  tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
-                 device=None, ckpt_mode: int = 0, mem_save: bool = False):
+                 device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False):
         _cuda_check()
         self.device = torch.device(device or "cuda")
         if gates is None:
@@ -53,7 +55,7 @@ class Simulator:
         self.obs = qfuse.pauli(obs, n) if not isinstance(obs, qfuse.qf_pauli) else obs
         with torch.cuda.device(self.device):
             self.ws_bytes = qfuse.qf_plan(self.handle, batch, _PATHS[path], tile_bits, ckpt_layers,
-                                          ckpt_mode=ckpt_mode, mem_save=mem_save)
+                                          ckpt_mode=ckpt_mode, mem_save=mem_save, tc_path=tc_path)
             self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
         self.batch = batch
         self._fwd_id = 0

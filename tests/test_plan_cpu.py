@@ -291,3 +291,27 @@ def test_mode_a_fit_minimises_the_workspace():
             qfuse.qf_plan_fit(h, B, min(sizes.values()) - 1, host_only=True, ckpt_mode=1)
     finally:
         qfuse.qf_circuit_destroy(h)
+
+
+def test_tc_path_options():
+    """The tensor-core path needs round programs on 12-qubit tiles."""
+    h = qfuse.qf_hea_create(8, 3)
+    try:
+        with pytest.raises(qfuse.QFError) as e:
+            qfuse.qf_plan(h, 2, host_only=True, tc_path=True)
+        assert e.value.status == qfuse.QF_ERR_UNSUPPORTED
+    finally:
+        qfuse.qf_circuit_destroy(h)
+    h = qfuse.qf_hea_create(12, 3)
+    try:
+        ws0 = qfuse.qf_plan(h, 2, host_only=True)
+        ws1 = qfuse.qf_plan(h, 2, host_only=True, tc_path=True)
+        info = qfuse.qf_plan_info(h)
+        assert info["tc_path"] == 1 and ws1 > ws0
+        assert info["launches_fwd"] == info["n_passes"] + 3
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan(h, 2, host_only=True, tc_path=True, program=1)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_plan(h, 2, host_only=True, tc_path=True, path=qfuse.QF_PATH_PER_GATE)
+    finally:
+        qfuse.qf_circuit_destroy(h)
