@@ -321,10 +321,11 @@ def run_epoch(args, w):
     N = w.B
     mb = int(w.extra.get("micro_batch", 100))
     free, _ = torch.cuda.mem_get_info()
+    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
     h = qfuse.qf_hea_create(w.n, w.d)
-    c, ws_need = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True)
+    c, ws_need = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True, **opts)
     qfuse.qf_circuit_destroy(h)
-    sim = Simulator(w.n, w.d, mb, ckpt_layers=c, obs=w.obs)
+    sim = Simulator(w.n, w.d, mb, ckpt_layers=c, obs=w.obs, **opts)
     theta = torch.from_numpy(theta_np).cuda()
     xs = [torch.from_numpy(x_np[i:i + mb]).cuda() for i in range(0, N, mb)]
     grad = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
@@ -364,6 +365,8 @@ def run_epoch(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d}, {N} samples per step (epoch) in micro-batches "
                                f"of {mb}, L=sum E, obs=Z0", "ckpt_layers_from_memory": c,
+                   "ckpt_mode": args.ckpt_mode, "mem_save": bool(args.mem_save), "tc_path": bool(args.tc),
+                   "fwd_ms_per_step": prof["fwd_ms"] / args.steps, "bwd_ms_per_step": prof["bwd_ms"] / args.steps,
                    "workspace_gb": sim.ws_bytes / 1e9, "passes": info["n_passes"],
                    "l2": "inputs larger than L2"},
         "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
