@@ -35,6 +35,9 @@ from paper_2603_02804_gb300 import workloads  # noqa: E402
 WORKLOAD = "hea12"
 FP32_LANES_PER_SM = 128
 N_SM = 152
+# DRAM bytes (read + write) of one adjoint pass launch from an ncu capture of the current kernel build
+# (profiles/pass_kernels_hea12.md); None where no capture of the current build exists.
+ADJOINT_TRAFFIC_BYTES = {"hea12": 16_860_672}
 
 
 def parse():
@@ -478,7 +481,8 @@ def main():
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     achieved = bwd_per_launch / (bwd_launch_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak,
+                "traffic": ADJOINT_TRAFFIC_BYTES.get(w.name) if not (args.tc or args.ckpt_mode) else None,
                 "kernel": "pass_kernel<true> (fused adjoint)",
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz",
                 "fwd_kernel": {"achieved": (fwd_fl / info["n_passes"]) / (fwd_launch_ms / 1e3) / 1e12,

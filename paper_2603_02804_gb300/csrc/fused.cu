@@ -1388,7 +1388,7 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64
     if (e != cudaSuccess) return e;
     once[dev] = true;
   }
-  if (prep_total > 0) batch_prep_kernel<<<(unsigned)((prep_total + 255) / 256), 256, 0, st>>>(a, prep_total);
+  if (prep_total > 0) batch_prep_kernel<<<(unsigned)((prep_total + 63) / 64), 64, 0, st>>>(a, prep_total);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
   if (a.n_items > 0) {
@@ -1406,7 +1406,8 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
   const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + 4ll * a.n_rpf + 8ll * a.n_rpb;
   if (total == 0) return cudaSuccess;
-  const int blk = 256;
+  // float64 work per element: small blocks spread it over more SMs
+  const int blk = 64;
   prep_kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, st>>>(a);
   return cudaGetLastError();
 }
