@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 # DRAM bytes (read + write) of one adjoint pass launch from an ncu capture of the current kernel build
 # (profiles/pass_kernels_hea12.md); None where no capture of the current build exists.
-ADJOINT_TRAFFIC_BYTES = {"hea12": 16_860_672}
+ADJOINT_TRAFFIC_BYTES = {}
 
 
 def parse():

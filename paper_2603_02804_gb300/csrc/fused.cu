@@ -212,6 +212,8 @@ __device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 m0, float4 m1, 
 template <int R, int KIND>
 __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], const float t, const float s) {
   float acc = 0.f;
+  float2 accp = make_float2(0.f, 0.f), accm = make_float2(0.f, 0.f);
+  const float2 t2 = make_float2(t, t), ms2 = make_float2(-s, -s);
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     if (j & (1 << R)) continue;
@@ -224,16 +226,21 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
       p1.x = fmaf(t, p1.y, p1.x); p1.y = fmaf(-s, p1.x, p1.y); p1.x = fmaf(t, p1.y, p1.x);
       l1.x = fmaf(t, l1.y, l1.x); l1.y = fmaf(-s, l1.x, l1.y); l1.x = fmaf(t, l1.y, l1.x);
     } else {
-      acc += l1.x * p0.x + l1.y * p0.y - l0.x * p1.x - l0.y * p1.y;
-      p0.x = fmaf(t, p1.x, p0.x); p0.y = fmaf(t, p1.y, p0.y);
-      p1.x = fmaf(-s, p0.x, p1.x); p1.y = fmaf(-s, p0.y, p1.y);
-      p0.x = fmaf(t, p1.x, p0.x); p0.y = fmaf(t, p1.y, p0.y);
-      l0.x = fmaf(t, l1.x, l0.x); l0.y = fmaf(t, l1.y, l0.y);
-      l1.x = fmaf(-s, l0.x, l1.x); l1.y = fmaf(-s, l0.y, l1.y);
-      l0.x = fmaf(t, l1.x, l0.x); l0.y = fmaf(t, l1.y, l0.y);
+      // RY is real: the same shear acts on re and im, so each step is one
+      // packed FFMA2 on the (re, im) pair; Im<lambda|Y|psi> per pair is
+      // l1 . p0 - l0 . p1 (component-wise products, two packed accumulators).
+      accp = __ffma2_rn(l1, p0, accp);
+      accm = __ffma2_rn(l0, p1, accm);
+      p0 = __ffma2_rn(t2, p1, p0);
+      p1 = __ffma2_rn(ms2, p0, p1);
+      p0 = __ffma2_rn(t2, p1, p0);
+      l0 = __ffma2_rn(t2, l1, l0);
+      l1 = __ffma2_rn(ms2, l0, l1);
+      l0 = __ffma2_rn(t2, l1, l0);
     }
     p[j] = p0; p[j1] = p1; l[j] = l0; l[j1] = l1;
   }
+  if (KIND != G_RZ) acc = (accp.x + accp.y) - (accm.x + accm.y);
   return acc;
 }
 
