@@ -57,6 +57,13 @@ typedef int32_t qf_status;
 #define QF_ENT_CHAIN 0 /* CZ(0,1), CZ(1,2), ..., CZ(n-2,n-1)            */
 #define QF_ENT_RING 1  /* the chain plus CZ(n-1, 0)                       */
 
+/* Input encodings (how psi_0 is formed for each sample). */
+#define QF_ENC_RY_X 0     /* psi_0 = (x) RY(x_q)|0>, x: float32 [batch][n] angles     */
+#define QF_ENC_STATE_IN 1 /* psi_0 given: x is complex64 [batch][2^n] as float32
+                             (re, im) pairs, e.g. the random initial states of the
+                             paper's measurements (Sec. 4); used as given (the
+                             library does not normalise it)                          */
+
 /* Execution paths. */
 #define QF_PATH_FUSED 0    /* fused forward / fused adjoint (Secs. 3.2-3.3) */
 #define QF_PATH_PER_GATE 1 /* one kernel per gate; the unfused comparator   */
@@ -78,7 +85,11 @@ typedef struct {
 
 /* Pauli-string observable O = i^{#Y} X^{x_mask} Z^{z_mask}: bit q of x_mask
  * (z_mask) set means an X (Z) factor on qubit q; both bits set is a Y
- * (Y = iXZ, Appendix B.2). */
+ * (Y = iXZ, Appendix B.2). Evaluated matrix-free: (O psi)_x =
+ * i^{#Y} (-1)^{|(x ^ x_mask) & z_mask|} psi_{x ^ x_mask}. When every X/Y qubit
+ * lies in the last pass's tile the expectation and the adjoint seed are fused
+ * into the last forward / first adjoint pass; otherwise each is one extra
+ * pass over the state. */
 typedef struct {
   uint64_t x_mask;
   uint64_t z_mask;
@@ -145,20 +156,21 @@ typedef struct {
 /* Create the hardware-efficient ansatz of the paper's benchmarks with the
  * gate set of this build: every layer applies RZ, RY, RZ to every qubit and
  * then the entangler (Sec. 4.2 and the ansatz figure; RZ,RY,RZ + CZ chain per
- * layer). The data encoding RY(x_q)|0> on every qubit precedes layer 0.
- * Parameter index of rotation g in {0: first RZ, 1: RY, 2: second RZ} on
- * qubit q of layer l is l*3n + 3q + g, so theta has 3*n*n_layers entries.
- * n_qubits in 1..30, n_layers >= 0. *out receives a new handle (free with
- * qf_circuit_destroy). */
-qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler,
+ * layer). `encoding` (QF_ENC_*) forms psi_0: RY(x_q)|0> on every qubit, or a
+ * given state. Parameter index of rotation g in {0: first RZ, 1: RY, 2:
+ * second RZ} on qubit q of layer l is l*3n + 3q + g, so theta has
+ * 3*n*n_layers entries. n_qubits in 1..30, n_layers >= 0. *out receives a new
+ * handle (free with qf_circuit_destroy). */
+qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler, int32_t encoding,
                         qf_circuit** out);
 
-/* Create a circuit from a gate list applied in order after the RY(x)
- * encoding (Sec. 2.1: U = U_M ... U_1). Supported kinds: QF_GATE_RX/RY/RZ
+/* Create a circuit from a gate list applied in order after the encoding
+ * (Sec. 2.1: U = U_M ... U_1). Supported kinds: QF_GATE_RX/RY/RZ
  * (param in 0..n_params-1; several gates may share a parameter, their
- * gradients add) and QF_GATE_CZ (param -1). The gate array is copied. */
+ * gradients add) and QF_GATE_CZ (param -1). The gate array is copied.
+ * `encoding` as for qf_hea_create. */
 qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_gates,
-                            int32_t n_params, qf_circuit** out);
+                            int32_t n_params, int32_t encoding, qf_circuit** out);
 
 /* Destroy a handle and the device tables its plan owns. NULL is accepted. */
 qf_status qf_circuit_destroy(qf_circuit* c);
@@ -209,9 +221,11 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf,
 
 /* Forward expectations E_b = <psi_M|O|psi_M> (Eq. 1) for b < batch.
  * theta_d: float32 [n_params]; x_d: float32 [batch][n_qubits] encoding
- * angles; E_d: float64 [batch] (written). The final state and the
- * checkpoints stay in the workspace for a following qf_backward with the
- * same theta, x, batch and observable. batch <= the planned batch. */
+ * angles (QF_ENC_RY_X), or the initial states, complex64 [batch][2^n_qubits]
+ * (QF_ENC_STATE_IN; qf_backward needs the same x_d); E_d: float64 [batch]
+ * (written). The final state and the checkpoints stay in the workspace for a
+ * following qf_backward with the same theta, x, batch and observable.
+ * batch <= the planned batch. */
 qf_status qf_forward(qf_circuit* c, const float* theta_d, const float* x_d, int64_t batch,
                      qf_pauli obs, double* E_d, void* ws_d, size_t ws_bytes, void* stream);
 

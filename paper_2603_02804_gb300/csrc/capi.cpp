@@ -68,6 +68,7 @@ struct qf_circuit {
   bool host_only = false;
   int path = QF_PATH_FUSED;
   int ckpt_layers = 10;
+  int encoding = QF_ENC_RY_X;
   bool tc = false;          // forward rounds on the tensor cores
   int64_t batch = 0;
   qf::FusedPlan fp;
@@ -121,6 +122,11 @@ void free_tables(qf_circuit* c) {
 }
 
 int n_eff_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_eff : c->gp.n_eff; }
+// Bytes of one batch of inputs: angles [B][n] float32, or states [B][2^n] complex64.
+size_t x_bytes(const qf_circuit* c, int64_t B) {
+  return c->encoding == QF_ENC_STATE_IN ? (size_t)B * ((size_t)1 << c->circ.n) * 8 : (size_t)B * c->circ.n * 4;
+}
+
 int n_slots_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_terms : c->gp.n_slots; }
 
 Layout make_layout(const qf_circuit* c, int64_t B) {
@@ -137,7 +143,7 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     return at;
   };
   L.theta = take((size_t)P * 4);
-  L.x = take((size_t)B * c->circ.n * 4);
+  L.x = take(x_bytes(c, B));
   L.y = take((size_t)B * 4);
   L.E = take((size_t)B * 8);
   L.dLdE = take((size_t)B * 8);
@@ -299,6 +305,13 @@ bool local_xmask(const qf::PassDesc& pd, uint32_t xm, uint32_t* out) {
   return true;
 }
 
+// Given initial states (QF_ENC_STATE_IN) are read by the pass that would
+// generate psi_0.
+void set_input(const qf_circuit* c, const float* x, qf::PassArgs& a) {
+  a.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const float2*>(x) : nullptr;
+  a.n_in = c->circ.n;
+}
+
 // The backward's per-term table: (cos, sin) for generic programs, three-shear
 // parameters for round programs.
 void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, qf::PrepArgs& pa) {
@@ -335,7 +348,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   }
   if (c->tc) pa.mats64 = at<double>(ws, L.mats64);
   pa.x = x;
-  pa.B = B;
+  pa.B = c->encoding == QF_ENC_RY_X ? B : 0;  // given states need no encoding table
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
   pa.enc = at<float2>(ws, L.enc);
@@ -352,6 +365,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.B = B;
   a.ops = T.fwd_ops;
   a.tcb = c->tc ? at<float>(ws, L.tcb) : nullptr;
+  set_input(c, x, a);
   a.rounds = P.rounds ? T.fwd_rounds : nullptr;
   a.rpar = P.rounds ? at<float4>(ws, L.rpf) : nullptr;
   a.mats = pa.mats;
@@ -368,25 +382,42 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.g_part = at<double>(ws, L.gpart);
   a.n_slots = P.n_terms;
   const int prof = prof_begin(c, st);
+  int32_t full_expect = -1;  // slot of psi_M when the observable reaches outside the last tile
   for (size_t pi = 0; pi < P.fwd.size(); ++pi) {
     a.pd = P.fwd[pi];
     a.pd.xm_local = 0;
-    if ((a.pd.flags & qf::PF_EXPECT) && !local_xmask(a.pd, o.x, &a.pd.xm_local))
-      return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+    if ((a.pd.flags & qf::PF_EXPECT) && !local_xmask(a.pd, o.x, &a.pd.xm_local)) {
+      a.pd.flags &= ~qf::PF_EXPECT;
+      full_expect = a.pd.psi_dst;
+    }
     if (c->tc) QF_CU(qf::launch_pass_tc(a, st));
     else QF_CU(qf::launch_pass(false, a, st));
     c->call_launches++;
   }
   prof_end(c, prof, 0, (int64_t)P.fwd.size(), st);
+  if (full_expect >= 0) {
+    QF_CU(qf::launch_expect_full(a.slots + (int64_t)full_expect * a.slot_stride, P.n_eff, B, L.rows, o.x, o.z,
+                                 o.y, a.e_part, st));
+    c->call_launches++;
+  }
   QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
   c->call_launches++;
   return QF_OK;
 }
 
+// Observable reaching outside the seeding pass's tile: lambda_M for every
+// amplitude as its own pass (psi_M from the pass's source slot).
+cudaError_t seed_full(qf_circuit* c, const qf::FusedPlan& P, const qf::PassArgs& a, int64_t B, const Obs& o,
+                      cudaStream_t st) {
+  c->call_launches++;
+  return qf::launch_seed_full(a.slots + (int64_t)a.pd.psi_src * a.slot_stride, a.lam, P.n_eff, B, o.x, o.z, o.y,
+                              a.dLdE, st);
+}
+
 // with_prep = false: the term table was filled by the preceding forward.
-qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, int64_t B,
-                         const Obs& o, const double* dLdE, double* grad, int per_sample, void* ws, cudaStream_t st,
-                         bool with_prep = true) {
+qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, const float* x,
+                         int64_t B, const Obs& o, const double* dLdE, double* grad, int per_sample, void* ws,
+                         cudaStream_t st, bool with_prep = true) {
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa{};
   pa.theta = theta;
@@ -430,13 +461,16 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
     f.mats = at<float4>(ws, L.mats);
     f.enc = at<float2>(ws, L.enc);
     f.tcb = c->tc ? at<float>(ws, L.tcb) : nullptr;
+    set_input(c, x, f);
     for (size_t i = 0; i < P.a_sched.size(); ++i) {
       const bool bwd = P.a_dir[i] != 0;
       qf::PassArgs& x = bwd ? a : f;
       x.pd = P.a_sched[i];
       x.pd.xm_local = 0;
-      if (bwd && x.pd.lam_src == qf::LAM_SEED && !local_xmask(x.pd, o.x, &x.pd.xm_local))
-        return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+      if (bwd && x.pd.lam_src == qf::LAM_SEED && !local_xmask(x.pd, o.x, &x.pd.xm_local)) {
+        QF_CU(seed_full(c, P, x, B, o, st));
+        x.pd.lam_src = qf::LAM_BUF;
+      }
       if (c->tc && !bwd) QF_CU(qf::launch_pass_tc(x, st));
       else QF_CU(qf::launch_pass(bwd, x, st));
       c->call_launches++;
@@ -446,8 +480,10 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
     for (size_t pi = 0; pi < P.bwd.size(); ++pi) {
       a.pd = P.bwd[pi];
       a.pd.xm_local = 0;
-      if (a.pd.lam_src == qf::LAM_SEED && !local_xmask(a.pd, o.x, &a.pd.xm_local))
-        return fail(QF_ERR_UNSUPPORTED, "observable X/Y qubits must lie in the last pass's tile");
+      if (a.pd.lam_src == qf::LAM_SEED && !local_xmask(a.pd, o.x, &a.pd.xm_local)) {
+        QF_CU(seed_full(c, P, a, B, o, st));
+        a.pd.lam_src = qf::LAM_BUF;
+      }
       QF_CU(qf::launch_pass(true, a, st));
       c->call_launches++;
     }
@@ -479,7 +515,7 @@ qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const f
   pa.term_params = T.term_params;
   pa.cs = at<float2>(ws, L.cs);
   pa.x = x;
-  pa.B = B;
+  pa.B = c->encoding == QF_ENC_RY_X ? B : 0;
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
   pa.enc = at<float2>(ws, L.enc);
@@ -487,7 +523,8 @@ qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const f
   c->call_launches++;
   qf::PerGateArgs a{P.n_eff, B, at<float2>(ws, L.work), at<float2>(ws, L.lam), (int32_t)L.rows};
   if (B == 0) return QF_OK;
-  QF_CU(qf::pg_encode(a, pa.enc, st));
+  if (c->encoding == QF_ENC_STATE_IN) QF_CU(qf::pg_load_states(a, reinterpret_cast<const float2*>(x), c->circ.n, st));
+  else QF_CU(qf::pg_encode(a, pa.enc, st));
   c->call_launches++;
   size_t k = 0;
   int slot = 0;
@@ -579,11 +616,14 @@ const char* qf_last_error(void) { return g_err.c_str(); }
 
 int32_t qf_version(void) { return 100; }
 
-qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler, qf_circuit** out) {
+qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler, int32_t encoding,
+                        qf_circuit** out) {
   if (!out) return fail(QF_ERR_INVALID_ARG, "null output pointer");
   *out = nullptr;
+  if (encoding != QF_ENC_RY_X && encoding != QF_ENC_STATE_IN) return fail(QF_ERR_INVALID_ARG, "unknown encoding");
   try {
     qf_circuit* c = new qf_circuit();
+    c->encoding = encoding;
     try {
       qf::build_hea(c->circ, n_qubits, n_layers, entangler);
     } catch (...) {
@@ -600,12 +640,14 @@ qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler, q
 }
 
 qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_gates, int32_t n_params,
-                            qf_circuit** out) {
+                            int32_t encoding, qf_circuit** out) {
   if (!out) return fail(QF_ERR_INVALID_ARG, "null output pointer");
   *out = nullptr;
   if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(QF_ERR_INVALID_ARG, "bad gate array");
+  if (encoding != QF_ENC_RY_X && encoding != QF_ENC_STATE_IN) return fail(QF_ERR_INVALID_ARG, "unknown encoding");
   try {
     qf_circuit* c = new qf_circuit();
+    c->encoding = encoding;
     c->circ.n = n_qubits;
     c->circ.n_params = n_params;
     for (int i = 0; i < n_gates; ++i) {
@@ -894,17 +936,18 @@ qf_status qf_forward(qf_circuit* c, const float* theta_d, const float* x_d, int6
 qf_status qf_backward(qf_circuit* c, const float* theta_d, const float* x_d, int64_t batch, qf_pauli obs,
                       const double* dLdE_d, double* grad_d, int32_t per_sample, void* ws_d, size_t ws_bytes,
                       void* stream) {
-  (void)x_d;
   qf_status s = check_call(c, batch, ws_d, ws_bytes);
   if (s != QF_OK) return s;
   if ((!theta_d && c->circ.n_params > 0) || (!dLdE_d && batch > 0) || (!grad_d && c->circ.n_params > 0))
     return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  if (!x_d && batch > 0 && c->encoding == QF_ENC_STATE_IN && c->path == QF_PATH_FUSED && c->fp.ckpt_mode == 1)
+    return fail(QF_ERR_INVALID_ARG, "checkpoint mode 1 re-runs the forward from the given states: x_d is needed");
   Obs o;
   if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
   c->call_launches = 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   s = c->path == QF_PATH_FUSED
-          ? fused_backward(c, c->dt, c->L, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st)
+          ? fused_backward(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st)
           : pg_backward(c, c->dt, c->L, theta_d, batch, o, dLdE_d, grad_d, per_sample, ws_d, st);
   c->launches += c->call_launches;
   return s;
@@ -939,7 +982,7 @@ qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d, c
     s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
     if (s != QF_OK) return s;
     c->call_launches++;
-    s = fused_backward(c, c->dt, c->L, theta_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
+    s = fused_backward(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
     c->launches = c->call_launches;
     return s;
   }
@@ -969,7 +1012,7 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
   float* yd = at<float>(ws_d, L.y);
   const int P = c->circ.n_params;
   if (P) QF_CU(cudaMemcpyAsync(th, theta_h, (size_t)P * 4, cudaMemcpyHostToDevice, st));
-  if (batch) QF_CU(cudaMemcpyAsync(xd, x_h, (size_t)batch * c->circ.n * 4, cudaMemcpyHostToDevice, st));
+  if (batch) QF_CU(cudaMemcpyAsync(xd, x_h, x_bytes(c, batch), cudaMemcpyHostToDevice, st));
   if (batch && loss_kind == QF_LOSS_MSE) QF_CU(cudaMemcpyAsync(yd, y_h, (size_t)batch * 4, cudaMemcpyHostToDevice, st));
   s = qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, L.loss), at<double>(ws_d, L.E),
                     at<double>(ws_d, L.grad), ws_d, ws_bytes, stream);
@@ -1019,7 +1062,7 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
   double* dLdE = at<double>(ws, L.dLdE);
   QF_CU(qf::launch_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, st));
   c->call_launches++;
-  s = c->path == QF_PATH_FUSED ? fused_backward(c, T, L, theta_d, batch, o, dLdE, grad_d, 0, ws, st)
+  s = c->path == QF_PATH_FUSED ? fused_backward(c, T, L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws, st)
                                : pg_backward(c, T, L, theta_d, batch, o, dLdE, grad_d, 0, ws, st);
   c->launches = c->call_launches;
   return s;
@@ -1089,6 +1132,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       qf_circuit* c = b->circ[i];
       const std::string at = " (circuit " + std::to_string(i) + ")";
       if (!c || !c->planned) throw std::invalid_argument("circuit has no plan" + at);
+      if (c->encoding != QF_ENC_RY_X) throw std::invalid_argument("batched launches take RY(x) encodings" + at);
       if (c->path == QF_PATH_FUSED && (c->fp.ckpt_mode != 0 || c->tc))
         throw std::invalid_argument("batched launches use checkpoint mode 0 on the CUDA cores" + at);
       if (c->path != QF_PATH_FUSED || !c->fp.rounds)

@@ -613,7 +613,24 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
 
   // ---- bring psi (and lambda) in -------------------------------------------
   const int32_t psrc = pd.psi_src;
-  if (psrc == SRC_GENERATE) {
+  if (psrc == SRC_GENERATE && a.psi_in) {
+    // given initial states [B][2^n_in]; padding qubits (n_in <= bit < n_eff) are |0>
+    const int64_t din = 1ll << a.n_in;
+    const float2* src = a.psi_in + b * din;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const uint32_t i = 2u * ((uint32_t)it * Tt + tau);
+      const uint32_t g = gidx(i);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a.n_in == a.n_eff) {
+        v = __ldcg(reinterpret_cast<const float4*>(src + g));
+      } else if ((int64_t)g < din) {
+        const float2 u0 = src[g], u1 = (int64_t)g + 1 < din ? src[g + 1] : make_float2(0.f, 0.f);
+        v = make_float4(u0.x, u0.y, u1.x, u1.y);
+      }
+      if (active) st_pair(tp, i, v);
+    }
+  } else if (psrc == SRC_GENERATE) {
     // psi_0 = (x) RY(x_q)|0>: a_x = prod_q (bit q of x ? sin(x_q/2) : cos(x_q/2))
     const float2* e = a.enc + b * a.n_eff;
 #pragma unroll 1
@@ -1445,6 +1462,68 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
     if (rounds) pass_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else pass_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   }
+  return cudaGetLastError();
+}
+
+// ---- observables whose X/Y qubits lie outside the tile (App. B.2) ---------------
+// E partials: CTA (b, t) sums Re(conj(a_x) (O a)_x) over amplitudes
+// x in [t*4096, (t+1)*4096) of sample b, with (O a)_x = i^{#Y} (-1)^{|(x^xm)&zm|} a_{x^xm};
+// one fp64 partial per CTA, the same [B][rows] layout as the pass kernels.
+__global__ void __launch_bounds__(kThreads) expect_full_kernel(const float2* psi, int n_eff, int64_t rows,
+                                                               uint32_t xm, uint32_t zm, uint32_t yc,
+                                                               double* e_part) {
+  __shared__ double red[kThreads / 32];
+  const int64_t dim = 1ll << n_eff;
+  const int64_t chunk = dim / rows;
+  const int64_t b = blockIdx.x / rows, t = blockIdx.x - b * rows;
+  const float2* s = psi + b * dim;
+  float acc = 0.f;
+  for (int64_t k = threadIdx.x; k < chunk; k += kThreads) {
+    const uint32_t x = (uint32_t)(t * chunk + k), xp = x ^ xm;
+    const float2 v = s[x];
+    const float2 w = mul_ipow(s[xp], yc);
+    acc += flip(v.x * w.x + v.y * w.y, __popc(xp & zm) & 1u);
+  }
+  double d = (double)acc;
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) sum += red[w];
+    e_part[blockIdx.x] = sum;
+  }
+}
+
+// Adjoint seed lambda_x = 2 (dL/dE_b) (O psi_M)_x (Eq. 4) for every amplitude.
+__global__ void seed_full_kernel(const float2* psi, float2* lam, int n_eff, int64_t B, uint32_t xm, uint32_t zm,
+                                 uint32_t yc, const double* dLdE) {
+  const int64_t dim = 1ll << n_eff;
+  const int64_t total = B * dim;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i >> n_eff;
+    const uint32_t x = (uint32_t)(i & (dim - 1)), xp = x ^ xm;
+    const float scale = (float)(2.0 * dLdE[b]);
+    const float2 v = mul_ipow(psi[b * dim + xp], yc);
+    const uint32_t sg = __popc(xp & zm) & 1u;
+    lam[i] = make_float2(flip(v.x, sg) * scale, flip(v.y, sg) * scale);
+  }
+}
+
+cudaError_t launch_expect_full(const float2* psi, int n_eff, int64_t B, int64_t rows, uint32_t xm, uint32_t zm,
+                               uint32_t yc, double* e_part, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  expect_full_kernel<<<(unsigned)(B * rows), kThreads, 0, st>>>(psi, n_eff, rows, xm, zm, yc, e_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_full(const float2* psi, float2* lam, int n_eff, int64_t B, uint32_t xm, uint32_t zm,
+                             uint32_t yc, const double* dLdE, cudaStream_t st) {
+  const int64_t total = B << n_eff;
+  if (total == 0) return cudaSuccess;
+  const int64_t want = (total + kThreads - 1) / kThreads;
+  const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+  seed_full_kernel<<<grid, kThreads, 0, st>>>(psi, lam, n_eff, B, xm, zm, yc, dLdE);
   return cudaGetLastError();
 }
 

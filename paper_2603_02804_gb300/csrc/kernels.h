@@ -20,6 +20,8 @@ struct PassArgs {
   const float2* cs;       // (cos, sin) of theta/2 per gradient term (generic programs)
   const float4* shear;    // three-shear parameters per gradient term (round programs)
   const float2* enc;      // (cos, sin) of x/2, [B][n_eff]
+  const float2* psi_in;   // given initial states [B][2^n_in] (QF_ENC_STATE_IN), else null
+  int32_t n_in;           // qubits of the given states (<= n_eff; padding qubits |0>)
   float2* work;           // working state [B][2^n_eff]
   float2* lam;            // adjoint state [B][2^n_eff]
   float2* slots;          // checkpoint states [n_ckpt][slot_stride]
@@ -80,6 +82,12 @@ cudaError_t launch_pass_tc(const PassArgs& a, cudaStream_t st);
 // Per-round B blocks of the tensor-core path from the float64 fused 2x2s.
 cudaError_t launch_tc_tables(const uint4* fwd_rounds, int32_t n_rounds, const double* mats64, float* tcb,
                              cudaStream_t st);
+// Observables with X/Y qubits outside the pass's tile: E partials [B][rows]
+// and the adjoint seed, each as a full pass over the state.
+cudaError_t launch_expect_full(const float2* psi, int n_eff, int64_t B, int64_t rows, uint32_t xm, uint32_t zm,
+                               uint32_t yc, double* e_part, cudaStream_t st);
+cudaError_t launch_seed_full(const float2* psi, float2* lam, int n_eff, int64_t B, uint32_t xm, uint32_t zm,
+                             uint32_t yc, const double* dLdE, cudaStream_t st);
 // Read and clear the device error word (1: a bounded wait gave up).
 cudaError_t device_status(int32_t* code, cudaStream_t st);
 cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st);
@@ -144,6 +152,7 @@ struct PerGateArgs {
   int32_t chunks;       // partial rows per sample
 };
 cudaError_t pg_encode(const PerGateArgs& a, const float2* enc, cudaStream_t st);
+cudaError_t pg_load_states(const PerGateArgs& a, const float2* in, int n_in, cudaStream_t st);
 cudaError_t pg_rot(const PerGateArgs& a, int kind, int q, const float2* cs, int slot, cudaStream_t st);
 cudaError_t pg_cz(const PerGateArgs& a, int c, int t, bool both, cudaStream_t st);
 cudaError_t pg_expect(const PerGateArgs& a, uint32_t x_mask, uint32_t z_mask, uint32_t y_count,

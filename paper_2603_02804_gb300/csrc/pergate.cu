@@ -75,6 +75,16 @@ __global__ void pg_encode_kernel(const PerGateArgs a, const float2* enc) {
   }
 }
 
+// Given initial states [B][2^n_in] into [B][2^n_eff] (padding qubits |0>).
+__global__ void pg_load_states_kernel(const PerGateArgs a, const float2* in, int n_in) {
+  const int64_t dim = 1ll << a.n_eff, din = 1ll << n_in;
+  const int64_t total = (int64_t)a.B * dim;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / dim, x = i - b * dim;
+    a.psi[i] = x < din ? in[b * din + x] : make_float2(0.f, 0.f);
+  }
+}
+
 template <int KIND>
 __global__ void pg_rot_kernel(const PerGateArgs a, int q, const float2* cs, int slot) {
   const float2 csv = __ldg(cs + slot);
@@ -235,6 +245,11 @@ int32_t pg_chunks(int32_t n_eff) {
 
 cudaError_t pg_encode(const PerGateArgs& a, const float2* enc, cudaStream_t st) {
   pg_encode_kernel<<<grid_for(a.B << (a.n_eff - 1)), kPgThreads, 0, st>>>(a, enc);
+  return cudaGetLastError();
+}
+
+cudaError_t pg_load_states(const PerGateArgs& a, const float2* in, int n_in, cudaStream_t st) {
+  pg_load_states_kernel<<<grid_for(a.B << a.n_eff), kPgThreads, 0, st>>>(a, in, n_in);
   return cudaGetLastError();
 }
 

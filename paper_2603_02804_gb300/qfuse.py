@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libqfuse.so")
 QF_OK, QF_ERR_INVALID_ARG, QF_ERR_UNSUPPORTED, QF_ERR_WORKSPACE, QF_ERR_OOM, QF_ERR_CUDA, QF_ERR_TIMEOUT = range(7)
 QF_GATE_RX, QF_GATE_RY, QF_GATE_RZ, QF_GATE_CZ = range(4)
 QF_ENT_CHAIN, QF_ENT_RING = 0, 1
+QF_ENC_RY_X, QF_ENC_STATE_IN = 0, 1
 QF_PATH_FUSED, QF_PATH_PER_GATE = 0, 1
 QF_LOSS_SUM, QF_LOSS_MSE = 0, 1
 
@@ -60,8 +61,8 @@ _sz = ctypes.c_size_t
 
 # C signature table: name -> (argtypes, restype)
 SIGNATURES = {
-    "qf_hea_create": ([_i32, _i32, _i32, ctypes.POINTER(_vp)], _i32),
-    "qf_circuit_create": ([_i32, ctypes.POINTER(qf_gate), _i32, _i32, ctypes.POINTER(_vp)], _i32),
+    "qf_hea_create": ([_i32, _i32, _i32, _i32, ctypes.POINTER(_vp)], _i32),
+    "qf_circuit_create": ([_i32, ctypes.POINTER(qf_gate), _i32, _i32, _i32, ctypes.POINTER(_vp)], _i32),
     "qf_circuit_destroy": ([_vp], _i32),
     "qf_plan": ([_vp, ctypes.POINTER(qf_plan_opts), _i64, ctypes.POINTER(_sz)], _i32),
     "qf_plan_info": ([_vp, ctypes.POINTER(qf_plan_info_t)], _i32),
@@ -155,16 +156,16 @@ def pauli(obs, n: int) -> qf_pauli:
 
 
 # ---- entry points (same names as the C-ABI) -------------------------------------
-def qf_hea_create(n_qubits: int, n_layers: int, entangler: int = QF_ENT_CHAIN) -> int:
+def qf_hea_create(n_qubits: int, n_layers: int, entangler: int = QF_ENT_CHAIN, encoding: int = QF_ENC_RY_X) -> int:
     h = _vp()
-    _check(load().qf_hea_create(n_qubits, n_layers, entangler, ctypes.byref(h)))
+    _check(load().qf_hea_create(n_qubits, n_layers, entangler, encoding, ctypes.byref(h)))
     return h.value
 
 
-def qf_circuit_create(n_qubits: int, gates, n_params: int) -> int:
+def qf_circuit_create(n_qubits: int, gates, n_params: int, encoding: int = QF_ENC_RY_X) -> int:
     arr = (qf_gate * max(len(gates), 1))(*[qf_gate(*map(int, g)) for g in gates])
     h = _vp()
-    _check(load().qf_circuit_create(n_qubits, arr, len(gates), n_params, ctypes.byref(h)))
+    _check(load().qf_circuit_create(n_qubits, arr, len(gates), n_params, encoding, ctypes.byref(h)))
     return h.value
 
 

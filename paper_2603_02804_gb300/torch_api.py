@@ -19,6 +19,7 @@ from . import qfuse
 _PATHS = {"fused": qfuse.QF_PATH_FUSED, "per_gate": qfuse.QF_PATH_PER_GATE}
 _ENT = {"chain": qfuse.QF_ENT_CHAIN, "ring": qfuse.QF_ENT_RING}
 _LOSS = {"sum": qfuse.QF_LOSS_SUM, "mse": qfuse.QF_LOSS_MSE}
+_ENC = {"angles": qfuse.QF_ENC_RY_X, "state": qfuse.QF_ENC_STATE_IN}
 _ids = itertools.count(1)
 
 
@@ -41,14 +42,16 @@ class Simulator:
 
     def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
                  tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
-                 device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False):
+                 device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False,
+                 encoding: str = "angles"):
         _cuda_check()
         self.device = torch.device(device or "cuda")
+        self.encoding = encoding
         if gates is None:
-            self.handle = qfuse.qf_hea_create(n, d, _ENT[entangler])
+            self.handle = qfuse.qf_hea_create(n, d, _ENT[entangler], _ENC[encoding])
             self.n_params = 3 * n * d
         else:
-            self.handle = qfuse.qf_circuit_create(n, gates, n_params)
+            self.handle = qfuse.qf_circuit_create(n, gates, n_params, _ENC[encoding])
             self.n_params = n_params
         self.n, self.d = n, d
         self.path = path
@@ -79,11 +82,17 @@ class Simulator:
         return torch.cuda.current_stream(self.device)
 
     def _check(self, theta, x):
-        if theta.dtype != torch.float32 or x.dtype != torch.float32:
-            raise TypeError("theta and x must be float32")
+        if self.encoding == "state":
+            # initial states: complex64 [B, 2^n] (passed to the library as float32 pairs)
+            if x.dtype != torch.complex64 or x.dim() != 2 or x.shape[1] != 1 << self.n:
+                raise TypeError("x must be complex64 [B, 2^n] initial states")
+        elif x.dtype != torch.float32 or x.dim() != 2 or x.shape[1] != self.n:
+            raise TypeError("x must be float32 [B, n] encoding angles")
+        if theta.dtype != torch.float32:
+            raise TypeError("theta must be float32")
         if not (theta.is_cuda and x.is_cuda and theta.is_contiguous() and x.is_contiguous()):
             raise ValueError("theta and x must be contiguous CUDA tensors")
-        if theta.numel() != self.n_params or x.dim() != 2 or x.shape[1] != self.n or x.shape[0] > self.batch:
+        if theta.numel() != self.n_params or x.shape[0] > self.batch:
             raise ValueError("shape mismatch with the planned circuit")
 
     def forward(self, theta: torch.Tensor, x: torch.Tensor) -> torch.Tensor:

@@ -140,3 +140,26 @@ def mixed_circuits(count: int = 512, seed: int = 104, n_range=(8, 18), d_range=(
             x = np.zeros((0, n), np.float32)
         out.append(MixedCircuit(i, n, d, B, theta, x))
     return out
+
+
+def xyz_ring_gates(n: int, d: int) -> list[tuple[int, int, int, int]]:
+    """The ansatz of the paper's throughput measurements (Sec. 4.2): every
+    layer applies Rx, Ry, Rz to every qubit, then CZ(q, q+1) for q < n-1 and
+    CZ(n-1, 0) (a ring; for n = 2 the single CZ). Rows (kind, q0, q1, param)
+    with kinds 0 RX, 1 RY, 2 RZ, 3 CZ; parameter l*3n + 3q + g, g in
+    {0: Rx, 1: Ry, 2: Rz}."""
+    rows = []
+    for layer in range(d):
+        for q in range(n):
+            for g in range(3):
+                rows.append((g, q, -1, layer * 3 * n + 3 * q + g))
+        for q in range(n - 1):
+            rows.append((3, q, q + 1, -1))
+        if n > 2:
+            rows.append((3, n - 1, 0, -1))
+    return rows
+
+
+def ixyz(n: int) -> str:
+    """O = IXYZ IXYZ ... truncated to n letters, letter k on qubit k (Sec. 4.2)."""
+    return ("IXYZ" * ((n + 3) // 4))[:n]

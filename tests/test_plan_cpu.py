@@ -315,3 +315,30 @@ def test_tc_path_options():
             qfuse.qf_plan(h, 2, host_only=True, tc_path=True, path=qfuse.QF_PATH_PER_GATE)
     finally:
         qfuse.qf_circuit_destroy(h)
+
+
+def test_encoding_argument_and_input_sizes():
+    """QF_ENC_STATE_IN takes complex64 [B][2^n] states: the host-buffer staging
+    grows accordingly; unknown encodings are refused."""
+    h0 = qfuse.qf_hea_create(10, 2)
+    h1 = qfuse.qf_hea_create(10, 2, qfuse.QF_ENT_CHAIN, qfuse.QF_ENC_STATE_IN)
+    try:
+        ws0 = qfuse.qf_plan(h0, 4, host_only=True)
+        ws1 = qfuse.qf_plan(h1, 4, host_only=True)
+        assert ws1 - ws0 >= 4 * (1 << 10) * 8 - 4 * 10 * 4 - 256
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_hea_create(10, 2, qfuse.QF_ENT_CHAIN, 7)
+        with pytest.raises(qfuse.QFError):
+            qfuse.qf_circuit_create(3, [(qfuse.QF_GATE_RY, 0, -1, 0)], 1, 5)
+    finally:
+        qfuse.qf_circuit_destroy(h0)
+        qfuse.qf_circuit_destroy(h1)
+
+
+def test_xyz_ring_ansatz_rows():
+    from paper_2603_02804_gb300 import workloads
+    rows = workloads.xyz_ring_gates(5, 2)
+    assert len(rows) == 2 * (15 + 5)
+    assert rows[:3] == [(0, 0, -1, 0), (1, 0, -1, 1), (2, 0, -1, 2)]
+    assert rows[15:20] == [(3, 0, 1, -1), (3, 1, 2, -1), (3, 2, 3, -1), (3, 3, 4, -1), (3, 4, 0, -1)]
+    assert workloads.ixyz(6) == "IXYZIX"
