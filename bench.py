@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512", "paper_hea"])
+    ap.add_argument("--qubits", type=int, default=29, help="paper_hea: number of qubits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
@@ -384,8 +385,102 @@ def run_epoch(args, w):
     return 0
 
 
+PAPER_SEC42_SAMPLES_PER_S = {29: 3.57}  # fused, GH200, HEA d=1 (Sec. 4.2); other hardware: context only
+
+
+def run_paper(args):
+    """The paper's throughput measurement (Sec. 4.2): HEA with d = 1 layer of Rx, Ry, Rz on every qubit
+    and a CZ ring, applied to random normalised initial states, O = IXYZ IXYZ ..., L = sum_b E_b, the
+    batch as large as fits in memory; one step = forward + loss + adjoint + gradient reduction."""
+    import torch
+    from paper_2603_02804_gb300 import build as qbuild
+    from paper_2603_02804_gb300 import qfuse
+    from paper_2603_02804_gb300.torch_api import Simulator
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    peaks, peak_src = load_peaks()
+    n, d = args.qubits, 1
+    rows = workloads.xyz_ring_gates(n, d)
+    P = 3 * n * d
+    obs = workloads.ixyz(n)
+    state_bytes = (1 << n) * 8
+    h = qfuse.qf_circuit_create(n, rows, P, qfuse.QF_ENC_STATE_IN)
+    ws1 = qfuse.qf_plan(h, 1, host_only=True, host_staging=False)
+    qfuse.qf_circuit_destroy(h)
+    free, _ = torch.cuda.mem_get_info()
+    B = args.batch or max(1, int(0.85 * free) // (ws1 + state_bytes))
+    sim = Simulator(n, 0, B, gates=rows, n_params=P, obs=obs, encoding="state", host_staging=False)
+    theta = torch.from_numpy(workloads.draw_theta(P, 401)).cuda()
+    # random normalised states drawn on the device (seeded), one sample at a time
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(402 + 1000 * rank)
+    psi0 = torch.empty(B, 1 << n, dtype=torch.complex64, device="cuda")
+    for b in range(B):
+        re = torch.randn(1 << n, generator=gen, device="cuda")
+        im = torch.randn(1 << n, generator=gen, device="cuda")
+        z = torch.complex(re, im)
+        psi0[b] = z / torch.linalg.vector_norm(z)
+        del re, im, z
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        sim.train_step(theta, psi0, loss="sum")
+    torch.cuda.synchronize()
+    qfuse.qf_profile(sim.handle, True)
+    qfuse.qf_profile_read(sim.handle)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            sim.train_step(theta, psi0, loss="sum")
+            launches += sim.launches()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    prof = qfuse.qf_profile_read(sim.handle)
+    status = qfuse.qf_device_status(stream)
+    ms = t0.elapsed_time(t1) / args.steps
+    info = sim.info()
+    nf = nb = info["n_passes"]
+    amps = B * (1 << n)
+    # algorithmic bytes: forward passes 16 B/amp (read + write psi), E 8 B/amp (psi_M once), seed 16 B/amp,
+    # adjoint passes 32 B/amp (psi and lambda read + write) but the last reads only
+    step_bytes = amps * (16 * nf + 8 + 16 + 32 * nb - 16)
+    bwd_bytes = amps * (16 + 32 * (nb - 1) + 16)
+    bwd_ms = prof["bwd_ms"] / args.steps
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    value = B * world / (ms / 1e3)
+    ref = PAPER_SEC42_SAMPLES_PER_S.get(n)
+    line = {
+        "metric": "fwd+grad samples/s", "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / ref) if ref else None, "dtype": "f32",
+        "data": "synthetic: random normalised complex Gaussian states (seeded, drawn on the device), "
+                "theta~U[0,2pi)",
+        "config": {"workload": f"paper_hea: n={n} d=1 [Rx,Ry,Rz + CZ ring], random initial states, "
+                               f"O=IXYZ..., L=sum E, batch={B} (largest that fits)",
+                   "passes_per_direction": nf, "workspace_gb": sim.ws_bytes / 1e9,
+                   "baseline_note": "vs_baseline divides by the paper's GH200 number for this workload (Sec. 4.2)"
+                   if ref else None, "l2": "inputs larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": bwd_bytes / (bwd_ms / 1e3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                     "frac": bwd_bytes / (bwd_ms / 1e3) / 1e9 / hbm_gbs, "traffic": None,
+                     "kernel": "adjoint phase (seed + adjoint pass kernels)", "peak_source": peak_src,
+                     "step": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / 1e3) / 1e9,
+                              "frac": step_bytes / (ms / 1e3) / 1e9 / hbm_gbs},
+                     "fwd_ms_per_step": prof["fwd_ms"] / args.steps, "bwd_ms_per_step": bwd_ms},
+        "gpu_launches": launches, "device_status": status, "per_gate": None, "cpu_baseline": None, "e2e": None,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "paper_hea":
+        return run_paper(args)
     if args.workload == "mixed512":
         return run_mixed(args)
     if args.workload == "hea20":

@@ -126,7 +126,10 @@ typedef struct {
                           12-qubit tiles (n >= 12), else QF_ERR_UNSUPPORTED.
                           The paper has no tensor-core path (Sec. 3.2 fuses the
                           unitaries, applied here as dense blocks)               */
-  int32_t reserved[8];
+  int32_t no_host_staging; /* 1: leave out the workspace's host-input staging
+                          (x, theta, y and outputs of qf_train_step_host, which
+                          then fails); for device-resident inputs of large states */
+  int32_t reserved[7];
 } qf_plan_opts;
 
 /* Summary of a plan (host-side numbers). */

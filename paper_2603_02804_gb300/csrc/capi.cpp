@@ -69,6 +69,7 @@ struct qf_circuit {
   int path = QF_PATH_FUSED;
   int ckpt_layers = 10;
   int encoding = QF_ENC_RY_X;
+  bool staging = true;      // workspace holds host-input staging (qf_train_step_host)
   bool tc = false;          // forward rounds on the tensor cores
   int64_t batch = 0;
   qf::FusedPlan fp;
@@ -142,8 +143,9 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     o += al(bytes);
     return at;
   };
+  const int64_t Bs = c->staging ? B : 0;  // staged inputs of the host-buffer step
   L.theta = take((size_t)P * 4);
-  L.x = take(x_bytes(c, B));
+  L.x = take(x_bytes(c, Bs));
   L.y = take((size_t)B * 4);
   L.E = take((size_t)B * 8);
   L.dLdE = take((size_t)B * 8);
@@ -702,6 +704,7 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     c->path = o.path;
     c->ckpt_layers = o.ckpt_layers > 0 ? o.ckpt_layers : 10;
     c->host_only = o.host_only != 0;
+    c->staging = o.no_host_staging == 0;
     c->batch = batch;
     qf::PlanRequest req;
     req.tile_bits = o.tile_bits;
@@ -1002,6 +1005,7 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
                              double* grad_h, void* ws_d, size_t ws_bytes, void* stream) {
   qf_status s = check_call(c, batch, ws_d, ws_bytes);
   if (s != QF_OK) return s;
+  if (!c->staging) return fail(QF_ERR_UNSUPPORTED, "the plan was made with no_host_staging");
   if ((!theta_h && c->circ.n_params > 0) || (!x_h && batch > 0) || !loss_h || (!grad_h && c->circ.n_params > 0) ||
       (loss_kind == QF_LOSS_MSE && batch > 0 && !y_h))
     return fail(QF_ERR_INVALID_ARG, "null host pointer");

@@ -982,7 +982,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
 }
 
 template <bool BWD, bool ROUNDS>
-__global__ void __launch_bounds__(kThreads, ROUNDS ? 2 : 1) pass_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) pass_kernel(const PassArgs a) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ PassShared sh;
   pass_cta<BWD, ROUNDS>(a, (int64_t)blockIdx.x * (kThreads >> (a.pd.K - kRegBits)), smem, sh);

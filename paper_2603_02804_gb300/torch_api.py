@@ -43,7 +43,7 @@ class Simulator:
     def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
                  tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
                  device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False,
-                 encoding: str = "angles"):
+                 encoding: str = "angles", host_staging: bool = True):
         _cuda_check()
         self.device = torch.device(device or "cuda")
         self.encoding = encoding
@@ -58,7 +58,8 @@ class Simulator:
         self.obs = qfuse.pauli(obs, n) if not isinstance(obs, qfuse.qf_pauli) else obs
         with torch.cuda.device(self.device):
             self.ws_bytes = qfuse.qf_plan(self.handle, batch, _PATHS[path], tile_bits, ckpt_layers,
-                                          ckpt_mode=ckpt_mode, mem_save=mem_save, tc_path=tc_path)
+                                          ckpt_mode=ckpt_mode, mem_save=mem_save, tc_path=tc_path,
+                                          host_staging=host_staging)
             self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
         self.batch = batch
         self._fwd_id = 0
