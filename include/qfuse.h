@@ -214,9 +214,10 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
  * then per pass: 11 header words (op_begin, op_end, psi_src, psi_dst,
  * lam_src, lam_dst, flags, K, n_groups, outer_mask, xm_local), 16 gmap
  * words, 16 group words], then [n_ops, 2 words per op], then [n_fused, per
- * fused op: count, then count (kind, param) pairs], then [n round words of
- * this direction, the words], then [n_terms, per gradient term: kind, count,
- * count parameters]. Direction 2: [program kind, n_launches, then per
+ * fused op: count, then count (kind, param, angle as 2 words) gates, param -1
+ * for a constant angle], then [n round words of this direction, the words],
+ * then [n_terms, per gradient term: kind, count, count parameters, constant
+ * angle as 2 words]. Doubles are exported as (low, high) words of their bits. Direction 2: [program kind, n_launches, then per
  * launch: program (0 forward, 1 backward; op ranges index that direction's
  * ops), the 11 header words, 16 gmap words, 16 group words]. Host only. */
 qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf,
@@ -368,6 +369,13 @@ qf_status qf_profile_read(qf_circuit* c, double* fwd_ms, int64_t* fwd_launches, 
  * iteration limit instead of spinning forever; results of that launch are
  * invalid). Has no counterpart in the paper. */
 qf_status qf_device_status(void* stream, int32_t* code);
+
+/* Check of the failure path of the bounded waits: launches one thread that
+ * waits on an mbarrier nothing arrives at, gives up after `spin_limit` polls
+ * (1..2^20, well under a second) and records the timeout in the device error
+ * word; a following qf_device_status then reports 1 and the context stays
+ * usable. No paper counterpart. */
+qf_status qf_check_bounded_wait(void* stream, int64_t spin_limit);
 
 /* Thread-local description of the last error ("" if none). */
 const char* qf_last_error(void);

@@ -51,13 +51,14 @@ struct DevTables {
   const uint4* bwd_rounds = nullptr;
   const int32_t* term_off = nullptr;      // CSR term -> parameters
   const int32_t* term_params = nullptr;
+  const double* term_const = nullptr;     // constant part of each term's angle (fused plans)
   const int32_t* param_off = nullptr;     // CSR parameter -> terms
   const int32_t* param_terms = nullptr;
 };
 
 // Byte offsets of each table inside the blob.
 struct BlobOffsets {
-  size_t fwd = 0, bwd = 0, foff = 0, fg = 0, frd = 0, brd = 0, to = 0, tp = 0, po = 0, ps = 0;
+  size_t fwd = 0, bwd = 0, foff = 0, fg = 0, frd = 0, brd = 0, to = 0, tp = 0, tcst = 0, po = 0, ps = 0;
 };
 
 }  // namespace
@@ -205,6 +206,7 @@ void build_blob(qf_circuit* c) {
     o.brd = push_table(blob, c->fp.bwd_rounds);
     o.to = push_table(blob, c->fp.term_off);
     o.tp = push_table(blob, c->fp.term_params);
+    o.tcst = push_table(blob, c->fp.term_const);
     o.po = push_table(blob, c->fp.param_off);
     o.ps = push_table(blob, c->fp.param_terms);
   } else {
@@ -229,6 +231,7 @@ DevTables tables_at(const qf_circuit* c, void* base) {
     t.fuse_gates = reinterpret_cast<const qf::FuseGate*>(b + c->bo.fg);
     t.fwd_rounds = reinterpret_cast<const uint4*>(b + c->bo.frd);
     t.bwd_rounds = reinterpret_cast<const uint4*>(b + c->bo.brd);
+    t.term_const = reinterpret_cast<const double*>(b + c->bo.tcst);
   }
   t.term_off = reinterpret_cast<const int32_t*>(b + c->bo.to);
   t.term_params = reinterpret_cast<const int32_t*>(b + c->bo.tp);
@@ -320,6 +323,7 @@ void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, vo
   pa.n_terms = n_slots_of(c);
   pa.term_off = T.term_off;
   pa.term_params = T.term_params;
+  pa.term_const = T.term_const;
   if (c->path == QF_PATH_FUSED && c->fp.rounds) {
     pa.shear = at<float4>(ws, L.cs);
     pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
@@ -515,6 +519,7 @@ qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const f
   pa.n_terms = n_slots_of(c);
   pa.term_off = T.term_off;
   pa.term_params = T.term_params;
+  pa.term_const = T.term_const;
   pa.cs = at<float2>(ws, L.cs);
   pa.x = x;
   pa.B = c->encoding == QF_ENC_RY_X ? B : 0;
@@ -558,6 +563,7 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
   pa.n_terms = n_slots_of(c);
   pa.term_off = T.term_off;
   pa.term_params = T.term_params;
+  pa.term_const = T.term_const;
   pa.cs = at<float2>(ws, L.cs);
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
@@ -606,6 +612,12 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
 }  // namespace
 
 extern "C" {
+
+qf_status qf_check_bounded_wait(void* stream, int64_t spin_limit) {
+  if (spin_limit < 1 || spin_limit > (1 << 20)) return fail(QF_ERR_INVALID_ARG, "spin_limit must be in 1..2^20");
+  QF_CU(qf::bounded_wait_probe((long long)spin_limit, static_cast<cudaStream_t>(stream)));
+  return QF_OK;
+}
 
 qf_status qf_device_status(void* stream, int32_t* code) {
   if (!code) return fail(QF_ERR_INVALID_ARG, "null argument");
@@ -854,6 +866,18 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
   return QF_OK;
 }
 
+}  // extern "C"
+
+// A double as two int32 words (low, high) of its bit pattern.
+static void push_double(std::vector<int32_t>& w, double v) {
+  int32_t b[2];
+  memcpy(b, &v, sizeof(v));
+  w.push_back(b[0]);
+  w.push_back(b[1]);
+}
+
+extern "C" {
+
 qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, int64_t cap, int64_t* len) {
   if (!c || !len) return fail(QF_ERR_INVALID_ARG, "null argument");
   if (!c->planned || c->path != QF_PATH_FUSED) return fail(QF_ERR_WORKSPACE, "no fused plan");
@@ -900,6 +924,7 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, i
     for (int j = P.fuse_off[m]; j < P.fuse_off[m + 1]; ++j) {
       w.push_back(P.fuse_gates[j].kind);
       w.push_back(P.fuse_gates[j].param);
+      push_double(w, P.fuse_gates[j].angle);
     }
   }
   if (direction == 0) {
@@ -914,6 +939,7 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, i
     w.push_back(P.term_kind[t]);
     w.push_back(P.term_off[t + 1] - P.term_off[t]);
     for (int j = P.term_off[t]; j < P.term_off[t + 1]; ++j) w.push_back(P.term_params[j]);
+    push_double(w, P.term_const[t]);
   }
   *len = (int64_t)w.size();
   if (buf) memcpy(buf, w.data(), sizeof(int32_t) * (size_t)std::min<int64_t>(cap, (int64_t)w.size()));
@@ -1279,6 +1305,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       p.n_terms = P.n_terms;
       p.term_off = T.term_off;
       p.term_params = T.term_params;
+      p.term_const = T.term_const;
       p.shear = rel<float4>(w0 + L.cs);
       p.B = b->B[i];
       p.n = c->circ.n;

@@ -147,11 +147,20 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, uint32_t k) {
 // bit positions p[r]: x = gb ^ y(j) with disjoint supports, so each link q
 // contributes gb_q gb_{q+1} (constant), gb_{q} y_{q+1} or y_q gb_{q+1} (linear)
 // or y_q y_{q+1} (between register bits).
+// Link q couples qubit q with q+1 mod n (link n-1 is a ring's CZ(n-1, 0); it
+// never joins two register bits), hence the n-bit rotations.
+__device__ __forceinline__ void link_terms(uint32_t L, uint32_t gb, int n, uint32_t& t2, uint32_t& u) {
+  const uint32_t nmask = n >= 32 ? ~0u : ((1u << n) - 1u);
+  const uint32_t t1 = L & gb;
+  t2 = L & (((gb >> 1) | ((gb & 1u) << (n - 1))) & nmask);
+  u = (((t1 << 1) | (t1 >> (n - 1))) & nmask) ^ t2;
+}
+
 template <bool BWD>
-__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4],
+__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4], int n,
                                               uint32_t& D, float2 (&r)[16], float2 (&l)[16]) {
-  const uint32_t t1 = L & gb, t2 = L & (gb >> 1);
-  const uint32_t u = (t1 << 1) ^ t2;
+  uint32_t t2, u;
+  link_terms(L, gb, n, t2, u);
   const uint32_t A = ((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) |
                      (((u >> p[3]) & 1u) << 3);
   D ^= A | ((__popc(t2 & gb) & 1u) << 4);
@@ -425,9 +434,9 @@ struct TcCtx {
 // Sign mask over the 16 register indices j of the round's CZ links (x = gb ^
 // y(j)): constant part, parts linear in one register bit, and links between
 // two register bits (bbits).
-__device__ __forceinline__ uint32_t cz_mask16(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4]) {
-  const uint32_t t1 = L & gb, t2 = L & (gb >> 1);
-  const uint32_t u = (t1 << 1) ^ t2;
+__device__ __forceinline__ uint32_t cz_mask16(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4], int n) {
+  uint32_t t2, u;
+  link_terms(L, gb, n, t2, u);
   uint32_t S = (__popc(t2 & gb) & 1u) ? 0xFFFFu : 0u;
   S ^= ((u >> p[0]) & 1u) ? 0xAAAAu : 0u;
   S ^= ((u >> p[1]) & 1u) ? 0xCCCCu : 0u;
@@ -443,7 +452,7 @@ __device__ __forceinline__ uint32_t cz_mask16(uint32_t L, uint32_t bbits, uint32
 // amplitudes (its column) on entry and exit. Warpgroup wg issues its own MMAs
 // (M = its 128 columns) and waits on its own mbarrier; ph tracks the phase.
 __device__ __forceinline__ void tc_rounds(const TcCtx& tc, const StepPar& P, int nr, const float* bst, uint32_t gb,
-                                          const uint32_t (&pos)[4], float2 (&r)[16], uint32_t& ph, int tid) {
+                                          const uint32_t (&pos)[4], int n, float2 (&r)[16], uint32_t& ph, int tid) {
   const int wg = tid >> 7, wq = (tid >> 5) & 3;
   const uint32_t col0 = tc.tmem + (uint32_t)(wg * kTcWgCols);
   const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
@@ -490,7 +499,7 @@ __device__ __forceinline__ void tc_rounds(const TcCtx& tc, const StepPar& P, int
     tc_ld32(d_col | lane_off, x);
     // CZ links after this round's rotations
     const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];
-    const uint32_t S = cz_mask16(lk.x, lk.y, gb, pos);
+    const uint32_t S = cz_mask16(lk.x, lk.y, gb, pos, n);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int f = (int)((S << (31 - j)) & 0x80000000u);
@@ -751,7 +760,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       }
       uint32_t D = 0;
       if constexpr (TC) {
-        tc_rounds(*tc, P, nr, tc->bsm + (size_t)sb * kMaxStepRounds * kTcBFloats, gb, pos, r, ph, tid);
+        tc_rounds(*tc, P, nr, tc->bsm + (size_t)sb * kMaxStepRounds * kTcBFloats, gb, pos, a.n_eff, r, ph, tid);
       } else {
 #pragma unroll 1
       for (int k = 0; k < nr; ++k) {
@@ -761,10 +770,10 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
           item_fwd<1>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u);
           item_fwd<2>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u);
           item_fwd<3>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u);
-          chain_pending<false>(lk.x, lk.y, gb, pos, D, r, l);
+          chain_pending<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
         } else {
           const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];
-          chain_pending<true>(lk.x, lk.y, gb, pos, D, r, l);
+          chain_pending<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
           float v[8];
           item_bwd<0>(r, l, P.v[k][0], P.v[k][4], D & 1u, D, v[0], v[4]);
           item_bwd<1>(r, l, P.v[k][1], P.v[k][5], (D >> 1) & 1u, D, v[1], v[5]);
@@ -1071,7 +1080,7 @@ __device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1, do
   for (int j = a.fuse_off[m]; j < a.fuse_off[m + 1]; ++j) {
     const FuseGate fg = a.fuse_gates[j];
     double s, c;
-    sincos(0.5 * (double)a.theta[fg.param], &s, &c);
+    sincos(0.5 * (fg.param >= 0 ? (double)a.theta[fg.param] : fg.angle), &s, &c);
     // g = c I - i s P
     double g[2][2][2];
     if (fg.kind == G_RX) {
@@ -1109,7 +1118,7 @@ __device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1, do
 
 // A term's angle is the sum of its parameters (a merged run of RZ gates).
 __device__ double term_angle(const PrepArgs& a, int64_t t) {
-  double phi = 0.0;
+  double phi = a.term_const ? a.term_const[t] : 0.0;
   for (int j = a.term_off[t]; j < a.term_off[t + 1]; ++j) phi += (double)a.theta[a.term_params[j]];
   return phi;
 }
@@ -1550,6 +1559,32 @@ cudaError_t launch_tc_tables(const uint4* fwd_rounds, int32_t n_rounds, const do
   const int64_t total = (int64_t)n_rounds * 1024;
   if (total == 0) return cudaSuccess;
   tc_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(fwd_rounds, n_rounds, mats64, tcb);
+  return cudaGetLastError();
+}
+
+// Failure-path check of the bounded waits: one thread waits on an mbarrier
+// that nothing arrives at, gives up after `limit` polls and records the
+// timeout in the device error word, exactly as the tensor-core path would.
+__global__ void bounded_wait_probe_kernel(long long limit) {
+  __shared__ __align__(8) uint64_t mbar;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const uint32_t addr = smem_u32(&mbar);
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(0u)
+        : "memory");
+    if (done) return;
+  }
+  atomicExch(&g_qf_device_status, 1);
+}
+
+cudaError_t bounded_wait_probe(long long limit, cudaStream_t st) {
+  if (limit < 1 || limit > (1ll << 20)) return cudaErrorInvalidValue;
+  bounded_wait_probe_kernel<<<1, 1, 0, st>>>(limit);
   return cudaGetLastError();
 }
 

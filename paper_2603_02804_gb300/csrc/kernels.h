@@ -46,6 +46,7 @@ struct PrepArgs {
   int32_t n_terms;
   const int32_t* term_off;     // CSR term -> parameters (angles summed)
   const int32_t* term_params;
+  const double* term_const;    // constant part of each term's angle (may be null)
   float2* cs;                  // (cos, sin) of phi/2 per term, or
   float4* shear;               // if non-null instead: (tan(w/4), sin(w/2), wrap parity, 0),
                                // w = phi wrapped into (-pi, pi], phi = w + 2 pi k
@@ -88,6 +89,8 @@ cudaError_t launch_expect_full(const float2* psi, int n_eff, int64_t B, int64_t 
                                uint32_t yc, double* e_part, cudaStream_t st);
 cudaError_t launch_seed_full(const float2* psi, float2* lam, int n_eff, int64_t B, uint32_t xm, uint32_t zm,
                              uint32_t yc, const double* dLdE, cudaStream_t st);
+// One bounded wait on an mbarrier nothing arrives at (records a timeout).
+cudaError_t bounded_wait_probe(long long limit, cudaStream_t st);
 // Read and clear the device error word (1: a bounded wait gave up).
 cudaError_t device_status(int32_t* code, cudaStream_t st);
 cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st);

@@ -448,12 +448,36 @@ int ckpt_interval_gates(const Circuit& c, int ckpt_layers) {
 }
 
 // Round programs handle RZ / RY rotations and CZs on neighbouring qubits.
+// Round programs take RZ / RY rotations (RX is rewritten, below) and CZs on
+// neighbouring qubits, plus the ring's CZ(n-1, 0) when n >= 5 (then qubits
+// 0 and n-1 never share a register group).
 static bool round_eligible(const Circuit& c) {
   for (const Gate& g : c.gates) {
-    if (g.kind == G_RX) return false;
-    if (g.kind == G_CZ && std::abs(g.q0 - g.q1) != 1) return false;
+    if (g.kind != G_CZ) continue;
+    const int dq = std::abs(g.q0 - g.q1);
+    if (dq != 1 && !(c.n >= 5 && dq == c.n - 1)) return false;
   }
   return true;
+}
+
+// RX(t) = RZ(-pi/2) RY(t) RZ(pi/2) (RZ(pi/2) acts first): exact, and the
+// gradient with respect to t is that of the RY. The constant RZs carry no
+// parameter (param -1) and merge into the RZ runs around them.
+static Circuit rewrite_rx(const Circuit& c) {
+  Circuit r = c;
+  r.gates.clear();
+  const double half_pi = 1.5707963267948966192313216916398;
+  for (const Gate& g : c.gates) {
+    if (g.kind != G_RX) {
+      r.gates.push_back(g);
+      continue;
+    }
+    r.gates.push_back({G_RZ, g.q0, -1, -1, half_pi});
+    r.gates.push_back({G_RY, g.q0, -1, g.param, 0.0});
+    r.gates.push_back({G_RZ, g.q0, -1, -1, -half_pi});
+  }
+  if (c.layers > 0 && !c.gates.empty()) r.gates_per_layer = (int)r.gates.size() / c.layers;
+  return r;
 }
 
 static void fill_slots(const Circuit& c, std::vector<int32_t>& slot_param, std::vector<int32_t>& slot_kind,
@@ -591,17 +615,19 @@ static void build_mode_a(FusedPlan& P, bool mem_save) {
   }
 }
 
-FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
-  validate_circuit(c);
+FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
+  validate_circuit(c_in);
   FusedPlan P;
-  P.n_eff = std::max(c.n, kRegBits);
+  P.n_eff = std::max(c_in.n, kRegBits);
   int K = req.tile_bits > 0 ? req.tile_bits : kMaxTileBits;
   if (K < kRegBits || K > kMaxTileBits) throw std::runtime_error("tile_bits must be in 4..12");
   K = std::min(K, P.n_eff);
   // a multi-pass tile needs at least one qubit beyond the low nibble
   if (P.n_eff > K && K < kRegBits + 1) K = kRegBits + 1;
   P.K = K;
-  P.rounds = !req.generic && K >= 7 && round_eligible(c);
+  P.rounds = !req.generic && K >= 7 && round_eligible(c_in);
+  const Circuit rewritten = P.rounds ? rewrite_rx(c_in) : Circuit();
+  const Circuit& c = P.rounds ? rewritten : c_in;
   // gradient terms: generic programs have one per rotation, in circuit order
   std::vector<int> term_of_gate(c.gates.size(), -1);
   P.term_off.assign(1, 0);
@@ -612,6 +638,7 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
         P.term_kind.push_back(c.gates[g].kind);
         P.term_params.push_back(c.gates[g].param);
         P.term_off.push_back((int32_t)P.term_params.size());
+        P.term_const.push_back(0.0);
       }
   }
 
@@ -711,7 +738,7 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
   using Item = std::vector<std::pair<uint32_t, uint32_t>>;
   auto fuse_of = [&](const std::vector<int>& gates) -> uint32_t {
     if (gates.empty()) return 0u;
-    for (int g : gates) P.fuse_gates.push_back({c.gates[g].kind, c.gates[g].param});
+    for (int g : gates) P.fuse_gates.push_back({c.gates[g].kind, c.gates[g].param, c.gates[g].angle});
     P.fuse_off.push_back((int32_t)P.fuse_gates.size());
     return (uint32_t)P.fuse_off.size() - 2;
   };
@@ -719,8 +746,13 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
     if (gates.empty()) return -1;
     const int32_t id = (int32_t)P.term_kind.size();
     P.term_kind.push_back(kind);
-    for (int g : gates) P.term_params.push_back(c.gates[g].param);
+    double cst = 0.0;
+    for (int g : gates) {
+      if (c.gates[g].param >= 0) P.term_params.push_back(c.gates[g].param);
+      else cst += c.gates[g].angle;
+    }
     P.term_off.push_back((int32_t)P.term_params.size());
+    P.term_const.push_back(cst);
     return id;
   };
   // A round step: forward rounds in order; the backward step runs the same
@@ -733,7 +765,10 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
     std::vector<std::vector<int32_t>> brs;
     for (const RoundRec& rr : st.rounds) {
       uint32_t links = 0;
-      for (int g : rr.czs) links ^= 1u << std::min(c.gates[g].q0, c.gates[g].q1);
+      for (int g : rr.czs) {
+        const int a = std::min(c.gates[g].q0, c.gates[g].q1), b = std::max(c.gates[g].q0, c.gates[g].q1);
+        links ^= 1u << (b == a + 1 ? a : b);  // the ring's CZ(n-1, 0) is link n-1
+      }
       uint32_t bbits = 0;
       for (int r = 0; r < 3; ++r)
         if (gq[r + 1] == gq[r] + 1 && ((links >> gq[r]) & 1u)) bbits |= 1u << r;
@@ -847,7 +882,7 @@ FusedPlan plan_fused(const Circuit& c, const PlanRequest& req) {
             --left;
           }
           if (!run.empty()) {
-            for (int g : run) P.fuse_gates.push_back({c.gates[g].kind, c.gates[g].param});
+            for (int g : run) P.fuse_gates.push_back({c.gates[g].kind, c.gates[g].param, c.gates[g].angle});
             P.fuse_off.push_back((int32_t)P.fuse_gates.size());
             const uint32_t mi = (uint32_t)P.fuse_off.size() - 2;
             fops.push_back({w0(OP_U, reg_of(q) << 4 | mi << 8), 0u});

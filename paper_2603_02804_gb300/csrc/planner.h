@@ -11,6 +11,7 @@ namespace qf {
 
 struct Gate {
   int32_t kind, q0, q1, param;
+  double angle = 0.0;  // constant rotation angle when param < 0 (planner-internal gates only)
 };
 
 struct Circuit {
@@ -43,6 +44,7 @@ struct FusedPlan {
   std::vector<int32_t> fuse_off;            // size n_fused + 1
   std::vector<FuseGate> fuse_gates;
   std::vector<int32_t> term_off, term_params, term_kind;  // CSR term -> params
+  std::vector<double> term_const;                         // constant angle of each term
   std::vector<int32_t> param_off, param_terms;            // CSR param -> terms
   // Checkpoint mode. 0 (B): the adjoint passes reverse psi in-kernel and
   // re-anchor at the checkpoints. 1 (A, Sec. 3.4): per checkpoint block the

@@ -82,7 +82,8 @@ struct PassDesc {
 // fuse_gate[fuse_off[m] .. fuse_off[m+1]) applied in that order.
 struct FuseGate {
   int32_t kind;
-  int32_t param;
+  int32_t param;   // theta index, or -1 for a constant angle
+  double angle;    // the constant angle when param < 0
 };
 
 }  // namespace qf

@@ -91,6 +91,7 @@ SIGNATURES = {
     "qf_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)], _i32),
     "qf_device_status": ([_vp, ctypes.POINTER(_i32)], _i32),
+    "qf_check_bounded_wait": ([_vp, _i64], _i32),
     "qf_last_error": ([], ctypes.c_char_p),
     "qf_version": ([], _i32),
 }
@@ -316,6 +317,11 @@ def qf_device_status(stream=None) -> int:
     code = _i32()
     _check(load().qf_device_status(_stream(stream), ctypes.byref(code)))
     return code.value
+
+
+def qf_check_bounded_wait(spin_limit: int, stream=None) -> None:
+    """Launch one bounded wait that times out (records 1 in the device error word)."""
+    _check(load().qf_check_bounded_wait(_stream(stream), spin_limit))
 
 
 def qf_last_error() -> str:

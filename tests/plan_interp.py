@@ -20,6 +20,10 @@ class Program:
     pass
 
 
+def _double(lo, hi):
+    return float(np.array([lo & 0xFFFFFFFF, hi & 0xFFFFFFFF], np.uint32).view(np.float64)[0])
+
+
 def parse(words):
     w = [int(v) for v in words]
     i = 0
@@ -42,16 +46,19 @@ def parse(words):
     prog.fused = []
     for _ in range(nf):
         cnt = w[i]; i += 1
-        prog.fused.append([(w[i + 2 * j], w[i + 2 * j + 1]) for j in range(cnt)])
-        i += 2 * cnt
+        prog.fused.append([(w[i + 4 * j], w[i + 4 * j + 1], _double(w[i + 4 * j + 2], w[i + 4 * j + 3]))
+                           for j in range(cnt)])
+        i += 4 * cnt
     nr = w[i]; i += 1
     prog.round_words = w[i:i + nr]; i += nr
     nt = w[i]; i += 1
     prog.terms = []
+    prog.term_const = []
     for _ in range(nt):
         kind, cnt = w[i], w[i + 1]
         prog.terms.append((kind, w[i + 2:i + 2 + cnt]))
-        i += 2 + cnt
+        prog.term_const.append(_double(w[i + 2 + cnt], w[i + 3 + cnt]))
+        i += 4 + cnt
     prog.passes = passes
     assert i == len(w)
     return prog
@@ -76,11 +83,13 @@ def apply1(psi, n, q, u):
 
 
 def chain_sign(n, links):
+    """Signs of the CZ links of a round: link q couples qubits q and q+1 mod n
+    (link n-1 is a ring's CZ(n-1, 0))."""
     x = np.arange(2 ** n, dtype=np.int64)
     par = np.zeros(2 ** n, dtype=np.int64)
     for q in range(n):
         if (links >> q) & 1:
-            par ^= ((x >> q) & 1) & ((x >> (q + 1)) & 1)
+            par ^= ((x >> q) & 1) & ((x >> ((q + 1) % n)) & 1)
     return 1 - 2 * par
 
 
@@ -107,13 +116,13 @@ def encode(x, n, n_eff):
 
 def fused_matrix(prog, m, theta):
     u = np.eye(2, dtype=complex)
-    for kind, p in prog.fused[m]:
-        u = rot(kind, float(theta[p])) @ u
+    for kind, p, angle in prog.fused[m]:
+        u = rot(kind, float(theta[p]) if p >= 0 else angle) @ u
     return u
 
 
 def term_angle(prog, t, theta):
-    return float(sum(float(theta[p]) for p in prog.terms[t][1]))
+    return float(sum(float(theta[p]) for p in prog.terms[t][1])) + prog.term_const[t]
 
 
 def fwd_ops(prog, pd, psi, n_eff, theta, slots):

@@ -92,8 +92,14 @@ def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, ora
     fwd = pi.parse(qfuse.qf_plan_export(handle, 0))
     bwd = pi.parse(qfuse.qf_plan_export(handle, 1))
     # every rotation gate appears exactly once in the fused forward entries
-    entries = sorted((k, p) for run in fwd.fused for (k, p) in run)
-    assert entries == sorted(zip(slot_kind, slot_param))
+    entries = sorted((k, p) for run in fwd.fused for (k, p, _) in run)
+    expect = []
+    for k, p in zip(slot_kind, slot_param):
+        if fwd.rounds_mode and k == orc.RX:  # round programs run RX(t) as RZ(-pi/2) RY(t) RZ(pi/2)
+            expect += [(orc.RZ, -1), (orc.RY, p), (orc.RZ, -1)]
+        else:
+            expect.append((k, p))
+    assert entries == sorted(expect)
     # and exactly once in the gradient terms
     assert sorted(p for _, ps in bwd.terms for p in ps) == sorted(slot_param)
     pq = qfuse.pauli(obs, n)
@@ -342,3 +348,28 @@ def test_xyz_ring_ansatz_rows():
     assert rows[:3] == [(0, 0, -1, 0), (1, 0, -1, 1), (2, 0, -1, 2)]
     assert rows[15:20] == [(3, 0, 1, -1), (3, 1, 2, -1), (3, 2, 3, -1), (3, 3, 4, -1), (3, 4, 0, -1)]
     assert workloads.ixyz(6) == "IXYZIX"
+
+
+@pytest.mark.parametrize("program", [0, 1])
+@pytest.mark.parametrize("n,d,K,ck", [(5, 2, 0, 0), (7, 3, 0, 1), (9, 2, 0, 0), (13, 2, 0, 1), (14, 2, 8, 1),
+                                      (17, 2, 0, 0)])
+def test_xyz_ring_ansatz_plans_match_oracle(n, d, K, ck, program):
+    """The paper's Rx, Ry, Rz + CZ-ring ansatz: round programs (RX rewritten as
+    RZ RY RZ with constant angles, the ring's CZ(n-1, 0) as link n-1) and
+    generic programs both give the oracle's expectations and gradients."""
+    from paper_2603_02804_gb300 import workloads
+    rng = np.random.default_rng(900 + 7 * n + d)
+    rows = workloads.xyz_ring_gates(n, d)
+    P = 3 * n * d
+    h = qfuse.qf_circuit_create(n, rows, P)
+    try:
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, program=program)
+        theta = rng.uniform(0, 2 * np.pi, P).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
+        c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=P)
+        slot_param = [r[3] for r in rows if r[0] != orc.CZ]
+        slot_kind = [r[0] for r in rows if r[0] != orc.CZ]
+        info, rounds = interp_check(h, n, theta, x, "ZXY"[: min(3, n)], slot_param, slot_kind, oracle_circ=c)
+        assert rounds == (program == 0 and info["tile_bits"] >= 7)
+    finally:
+        qfuse.qf_circuit_destroy(h)
