@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 # DRAM bytes (read + write) of one adjoint pass launch from an ncu capture of the current kernel build
 # (profiles/pass_kernels_hea12.md); None where no capture of the current build exists.
-ADJOINT_TRAFFIC_BYTES = {}
+ADJOINT_TRAFFIC_BYTES = {"hea12": 16_860_160}
 
 
 def parse():
@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512", "paper_hea"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512", "paper_hea", "fusion_sweep"])
     ap.add_argument("--qubits", type=int, default=29, help="paper_hea: number of qubits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
@@ -477,10 +477,67 @@ def run_paper(args):
     return 0
 
 
+def run_fusion_sweep(args):
+    """Sec. 4.1: time of m consecutive single-qubit gates (Rx, Ry, Rz repeating) on every qubit of a
+    20-qubit state, batch 100, random initial states, forward alone and forward + adjoint, as m grows."""
+    import torch
+    from paper_2603_02804_gb300 import build as qbuild
+    from paper_2603_02804_gb300 import qfuse
+    from paper_2603_02804_gb300.torch_api import Simulator
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    n, B = 20, args.batch or 100
+    obs = workloads.ixyz(n)
+    psi0 = torch.from_numpy(workloads.draw_state(B, n, 4101)).cuda()
+    stream = torch.cuda.current_stream()
+    rows_out = []
+    for m in (1, 3, 6, 9, 18, 36, 72):
+        rows = workloads.consecutive_gates(n, m)
+        P = n * m
+        sim = Simulator(n, 0, B, gates=rows, n_params=P, obs=obs, encoding="state", host_staging=False)
+        theta = torch.from_numpy(workloads.draw_theta(P, 4100 + m)).cuda()
+        for _ in range(3):
+            sim.train_step(theta, psi0, loss="sum")
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        K = args.steps
+        ev[0].record(stream)
+        for _ in range(K):
+            sim.forward(theta, psi0)
+        ev[1].record(stream)
+        for _ in range(K):
+            sim.train_step(theta, psi0, loss="sum")
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fwd = ev[0].elapsed_time(ev[1]) / K
+        step = ev[1].elapsed_time(ev[2]) / K
+        info = sim.info()
+        rows_out.append({"m": m, "gates": n * m, "passes": info["n_passes"], "fwd_ms": fwd, "fwd_bwd_ms": step,
+                         "bwd_ms": step - fwd, "fwd_us_per_gate": 1e3 * fwd / (n * m),
+                         "fwd_bwd_us_per_gate": 1e3 * step / (n * m), "samples_per_s": B / (step / 1e3),
+                         "workspace_gb": sim.ws_bytes / 1e9})
+        del sim
+    last = rows_out[-1]
+    line = {"metric": "fwd+grad samples/s", "value": last["samples_per_s"], "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": 3, "ms_per_step": last["fwd_bwd_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: random normalised complex Gaussian states, theta~U[0,2pi)",
+            "config": {"workload": f"fusion_sweep: n={n}, batch={B}, m consecutive Rx,Ry,Rz gates per qubit, "
+                                   "O=IXYZ..., L=sum E (value at the largest m)", "l2": "inputs larger than L2"},
+            "sweep": rows_out, "roofline": None, "gpu_launches": None, "cpu_baseline": None, "e2e": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "paper_hea":
         return run_paper(args)
+    if args.workload == "fusion_sweep":
+        return run_fusion_sweep(args)
     if args.workload == "mixed512":
         return run_mixed(args)
     if args.workload == "hea20":

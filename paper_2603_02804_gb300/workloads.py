@@ -163,3 +163,10 @@ def xyz_ring_gates(n: int, d: int) -> list[tuple[int, int, int, int]]:
 def ixyz(n: int) -> str:
     """O = IXYZ IXYZ ... truncated to n letters, letter k on qubit k (Sec. 4.2)."""
     return ("IXYZ" * ((n + 3) // 4))[:n]
+
+
+def consecutive_gates(n: int, m: int) -> list[tuple[int, int, int, int]]:
+    """The fusion-depth circuit of Sec. 4.1: m consecutive single-qubit gates on
+    every qubit in the repeating order Rx, Ry, Rz (no entangler); parameter
+    q*m + k for the k-th gate on qubit q. Rows as in xyz_ring_gates."""
+    return [(k % 3, q, -1, q * m + k) for q in range(n) for k in range(m)]

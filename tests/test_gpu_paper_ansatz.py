@@ -102,3 +102,21 @@ def test_n20_paper_ansatz_depth1():
     gr, Er = oracle_states(c, theta, psi0, obs)
     assert np.max(np.abs(E - Er)) < TOL
     assert np.max(np.abs(g - gr)) < TOL
+
+
+@pytest.mark.parametrize("m", [1, 9, 20])
+def test_consecutive_gates_fusion_depth(m):
+    """The fusion-depth circuit of Sec. 4.1 (m consecutive Rx, Ry, Rz gates on
+    every qubit), n = 14 so that it takes two tiles."""
+    n, B = 14, 3
+    rows = workloads.consecutive_gates(n, m)
+    P = n * m
+    rng = np.random.default_rng(3000 + m)
+    theta = rng.uniform(0, 2 * np.pi, P).astype(np.float32)
+    psi0 = workloads.draw_state(B, n, 3001 + m)
+    obs = workloads.ixyz(n)
+    E, g, _ = run(n, 0, theta, psi0, obs, encoding="state", gates=rows, n_params=P)
+    c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=P)
+    gr, Er = oracle_states(c, theta, psi0, obs)
+    assert np.max(np.abs(E - Er)) < TOL
+    assert np.max(np.abs(g - gr)) < TOL

@@ -373,3 +373,10 @@ def test_xyz_ring_ansatz_plans_match_oracle(n, d, K, ck, program):
         assert rounds == (program == 0 and info["tile_bits"] >= 7)
     finally:
         qfuse.qf_circuit_destroy(h)
+
+
+def test_consecutive_gates_rows():
+    from paper_2603_02804_gb300 import workloads
+    rows = workloads.consecutive_gates(3, 4)
+    assert rows[:5] == [(0, 0, -1, 0), (1, 0, -1, 1), (2, 0, -1, 2), (0, 0, -1, 3), (0, 1, -1, 4)]
+    assert len(rows) == 12 and sorted(r[3] for r in rows) == list(range(12))
