@@ -345,7 +345,10 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.fuse_off = T.fuse_off;
   pa.fuse_gates = T.fuse_gates;
   pa.mats = at<float4>(ws, L.mats);
-  pa.n_terms = 0;  // the forward itself needs only the fused matrices and the encoding
+  pa.n_terms = 0;  // the forward needs the fused matrices, the encoding and the round parameters
+  pa.term_off = T.term_off;  // round parameters are built from the gradient terms
+  pa.term_params = T.term_params;
+  pa.term_const = T.term_const;
   if (with_terms) set_term_table(c, T, L, ws, pa);
   if (P.rounds) {
     pa.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);

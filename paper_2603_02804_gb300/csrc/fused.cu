@@ -200,15 +200,33 @@ __device__ __forceinline__ void apply_pending(uint32_t D, float2 (&r)[16], float
   }
 }
 
-// Forward item on register bit R: U' = Z^a U Z^a (negated off-diagonal).
+// Forward item on register bit R: the RY, then the RZ run (the adjoint item
+// run forward). yq, zq: the terms' shear parameters (t, s, wrap parity) of the
+// un-apply direction; applying is the rotation the other way, (t, s) ->
+// (-t, -s). A pending Z_R turns RY(w) into RY(-w); the wrap parities go to
+// the pending constant sign.
 template <int R>
-__device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 m0, float4 m1, uint32_t a) {
+__device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D) {
   const int f = (int)(a << 31);
-  m0.z = __int_as_float(__float_as_int(m0.z) ^ f);
-  m0.w = __int_as_float(__float_as_int(m0.w) ^ f);
-  m1.x = __int_as_float(__float_as_int(m1.x) ^ f);
-  m1.y = __int_as_float(__float_as_int(m1.y) ^ f);
-  apply_u<R>(r, m0, m1);
+  const float2 T = make_float2(-__int_as_float(__float_as_int(yq.x) ^ f), 0.f);
+  const float2 t2 = make_float2(T.x, T.x), ms2 = make_float2(__int_as_float(__float_as_int(yq.y) ^ f),
+                                                               __int_as_float(__float_as_int(yq.y) ^ f));
+  const float t = zq.x, s = zq.y;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    float2 p0 = r[j], p1 = r[j1];
+    // RY(w) on (p0, p1): rotation by +w/2 as three packed shears
+    p0 = __ffma2_rn(t2, p1, p0);
+    p1 = __ffma2_rn(ms2, p0, p1);
+    p0 = __ffma2_rn(t2, p1, p0);
+    // RZ run: bit-R-clear amplitude times e^{-iw/2}, set one times e^{+iw/2}
+    p0.x = fmaf(t, p0.y, p0.x); p0.y = fmaf(-s, p0.x, p0.y); p0.x = fmaf(t, p0.y, p0.x);
+    p1.x = fmaf(-t, p1.y, p1.x); p1.y = fmaf(s, p1.x, p1.y); p1.x = fmaf(-t, p1.y, p1.x);
+    r[j] = p0; r[j1] = p1;
+  }
+  D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
 }
 
 // Un-apply one rotation on register bit R by three shears and return the
@@ -324,9 +342,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Parameters of one round step, staged from the round-ordered tables: per
 // round 8 float4 (forward: the 4 items' fused 2x2s; backward: the shear
 // parameters of tz[0..3], ty[0..3]) and the round record.
+constexpr int kMaxRoundWords = kFwdRoundWords > kBwdRoundWords ? kFwdRoundWords : kBwdRoundWords;
 struct StepPar {
   float4 v[kMaxStepRounds][8];
-  uint4 rec[kMaxStepRounds * (kBwdRoundWords / 4)];
+  uint4 rec[kMaxStepRounds * (kMaxRoundWords / 4)];
 };
 
 // ---- tensor-core block path (tcgen05) --------------------------------------------
@@ -766,10 +785,10 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       for (int k = 0; k < nr; ++k) {
         if (!BWD) {
           const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];
-          item_fwd<0>(r, P.v[k][0], P.v[k][1], D & 1u);
-          item_fwd<1>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u);
-          item_fwd<2>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u);
-          item_fwd<3>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u);
+          item_fwd<0>(r, P.v[k][0], P.v[k][1], D & 1u, D);
+          item_fwd<1>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u, D);
+          item_fwd<2>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u, D);
+          item_fwd<3>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u, D);
           chain_pending<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
         } else {
           const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];
@@ -1171,11 +1190,12 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   }
   i -= (int64_t)a.B * a.n_eff;
   if (i < 4ll * a.n_rpf) {
-    // forward round r, item k: word k of the record is the fused entry
+    // forward round r, item k: shear parameters of its RY term and RZ-run term
     const int64_t r = i >> 2;
     const int k = (int)(i & 3);
-    const uint32_t m = reinterpret_cast<const uint32_t*>(a.rpf_src)[r * kFwdRoundWords + k];
-    fused_u(a, m, a.rpf[r * 8 + 2 * k], a.rpf[r * 8 + 2 * k + 1]);
+    const int32_t* rec = reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords;
+    a.rpf[r * 8 + 2 * k] = term_shear_of(a, rec[12 + k]);
+    a.rpf[r * 8 + 2 * k + 1] = term_shear_of(a, rec[8 + k]);
     return;
   }
   i -= 4ll * a.n_rpf;

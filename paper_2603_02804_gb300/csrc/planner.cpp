@@ -789,6 +789,7 @@ FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
       }
       fw[4] = links;
       fw[5] = bbits;
+      for (int r = 0; r < 8; ++r) fw[8 + r] = (uint32_t)bw[r];  // the items' terms (forward shears)
       bw[8] = (int32_t)links;
       bw[9] = (int32_t)bbits;
       bw[10] = bw[11] = 0;

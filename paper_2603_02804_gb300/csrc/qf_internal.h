@@ -40,13 +40,14 @@ enum OpCode : uint32_t {
 // and then the CZ links of the round.
 //   forward round, kFwdRoundWords words: m[4] (fused 2x2 index per register
 //     bit, 0 = identity), links, bbits (links between register bits r, r+1),
-//     2 pad words.
+//     2 pad words, tz[4], ty[4] (the items' gradient terms, as below).
 //   backward round, kBwdRoundWords words: tz[4], ty[4] (term of the merged RZ
 //     run and of the RY of each item, -1 = none), links, bbits, 2 pad words.
-// A backward step runs its rounds in the order stored; each round applies the
-// links first, then per item the RZ run and then the RY (the exact reverse of
-// the forward round).
-constexpr int kFwdRoundWords = 8;
+// An item is an RZ run alone or an RY followed by an RZ run. A forward round
+// applies per item the RY and then the RZ run, then the links; a backward step
+// runs its rounds in the order stored, each applying the links first, then per
+// item the RZ run and then the RY (the exact reverse).
+constexpr int kFwdRoundWords = 16;
 constexpr int kBwdRoundWords = 12;
 constexpr int kMaxStepRounds = 4;   // 8 gradient values per round
 

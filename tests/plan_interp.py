@@ -13,7 +13,7 @@ OP_STEP, OP_U, OP_G, OP_CHAIN, OP_CZ, OP_CKPT, OP_ANCHOR = 1, 2, 3, 4, 5, 6, 7
 SRC_GENERATE, BUF_WORK, BUF_NONE = -1, -2, -3
 LAM_SEED, LAM_BUF = -1, -2
 RX, RY, RZ = 0, 1, 2
-FWD_ROUND_WORDS, BWD_ROUND_WORDS = 8, 12
+FWD_ROUND_WORDS, BWD_ROUND_WORDS = 16, 12
 
 
 class Program:

@@ -191,7 +191,8 @@ def test_plan_statistics_for_benchmark_shapes():
             prog = pi.parse(qfuse.qf_plan_export(h, 0))
             assert prog.rounds_mode
             words = prog.round_words
-            pads = sum(1 for k in range(len(words) // 8) for r in range(4) if words[8 * k + r] == 0)
+            W = pi.FWD_ROUND_WORDS
+            pads = sum(1 for k in range(len(words) // W) for r in range(4) if words[W * k + r] == 0)
             assert pads == 0, (n, pads)
         finally:
             qfuse.qf_circuit_destroy(h)
