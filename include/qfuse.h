@@ -52,6 +52,7 @@ typedef int32_t qf_status;
 #define QF_GATE_RY 1
 #define QF_GATE_RZ 2
 #define QF_GATE_CZ 3
+#define QF_GATE_CNOT 4 /* q0 control, q1 target (App. B.1); fused into generic steps */
 
 /* Entangler of the hardware-efficient ansatz. */
 #define QF_ENT_CHAIN 0 /* CZ(0,1), CZ(1,2), ..., CZ(n-2,n-1)            */
@@ -170,7 +171,8 @@ qf_status qf_hea_create(int32_t n_qubits, int32_t n_layers, int32_t entangler, i
 /* Create a circuit from a gate list applied in order after the encoding
  * (Sec. 2.1: U = U_M ... U_1). Supported kinds: QF_GATE_RX/RY/RZ
  * (param in 0..n_params-1; several gates may share a parameter, their
- * gradients add) and QF_GATE_CZ (param -1). The gate array is copied.
+ * gradients add), QF_GATE_CZ and QF_GATE_CNOT (param -1). The gate array is
+ * copied.
  * `encoding` as for qf_hea_create. */
 qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_gates,
                             int32_t n_params, int32_t encoding, qf_circuit** out);

@@ -542,6 +542,8 @@ qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const f
     const qf::Gate& gt = c->circ.gates[g];
     if (gt.kind == qf::G_CZ) {
       QF_CU(qf::pg_cz(a, gt.q0, gt.q1, false, st));
+    } else if (gt.kind == qf::G_CNOT) {
+      QF_CU(qf::pg_cnot(a, gt.q0, gt.q1, false, st));
     } else {
       QF_CU(qf::pg_rot(a, gt.kind, gt.q0, pa.cs, slot++, st));
     }
@@ -589,6 +591,8 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
       const qf::Gate& gt = c->circ.gates[g];
       if (gt.kind == qf::G_CZ) {
         QF_CU(qf::pg_cz(a, gt.q0, gt.q1, true, st));
+      } else if (gt.kind == qf::G_CNOT) {
+        QF_CU(qf::pg_cnot(a, gt.q0, gt.q1, true, st));
       } else {
         QF_CU(qf::pg_rot_bwd(a, gt.kind, gt.q0, pa.cs, slot, gpart + (int64_t)slot * B * L.rows, st));
         --slot;
@@ -669,7 +673,7 @@ qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_ga
     c->circ.n_params = n_params;
     for (int i = 0; i < n_gates; ++i) {
       qf::Gate g{gates[i].kind, gates[i].q0, gates[i].q1, gates[i].param};
-      if (g.kind == qf::G_CZ) g.param = -1;
+      if (g.kind == qf::G_CZ || g.kind == qf::G_CNOT) g.param = -1;
       else g.q1 = -1;
       c->circ.gates.push_back(g);
     }

@@ -120,6 +120,28 @@ __device__ __forceinline__ float bwd_dispatch_r(uint32_t r, float2 (&p)[16], flo
   }
 }
 
+// CNOT with its target on register bit RT: swap the target pairs whose
+// control is 1 (control: register bit cb when creg, else bit cb of the
+// thread's base index gb). Self-inverse, so the adjoint applies the same.
+template <int RT, bool BWD>
+__device__ __forceinline__ void cnot_regs(float2 (&r)[16], float2 (&l)[16], bool creg, uint32_t cb, uint32_t gb) {
+  const uint32_t cg = (gb >> cb) & 1u;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << RT)) continue;
+    const int j1 = j | (1 << RT);
+    const bool on = creg ? (((uint32_t)j >> cb) & 1u) != 0 : cg != 0;
+    const float2 a = r[j], b = r[j1];
+    r[j] = on ? b : a;
+    r[j1] = on ? a : b;
+    if (BWD) {
+      const float2 c = l[j], d = l[j1];
+      l[j] = on ? d : c;
+      l[j1] = on ? c : d;
+    }
+  }
+}
+
 __device__ __forceinline__ uint32_t reg_off(uint32_t j, const uint32_t (&o)[4]) {
   return ((j & 1u) ? o[0] : 0u) ^ ((j & 2u) ? o[1] : 0u) ^ ((j & 4u) ? o[2] : 0u) ^
          ((j & 8u) ? o[3] : 0u);
@@ -904,6 +926,15 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
             if (tid == 0) s_slot[buf][ks] = (int32_t)o.y;
           } else if (active && (lane & (Tt - 1)) == 0) {
             a.g_part[tile * a.n_slots + o.y] = 0.5 * (double)acc;
+          }
+        } else if (oc == OP_CNOT) {
+          const bool creg = ((o.y >> 8) & 1u) != 0;
+          const uint32_t cb = o.y & 0xffu;
+          switch ((o.x >> 4) & 3u) {
+            case 0: cnot_regs<0, BWD>(r, l, creg, cb, gb); break;
+            case 1: cnot_regs<1, BWD>(r, l, creg, cb, gb); break;
+            case 2: cnot_regs<2, BWD>(r, l, creg, cb, gb); break;
+            default: cnot_regs<3, BWD>(r, l, creg, cb, gb); break;
           }
         } else if (oc == OP_CHAIN || oc == OP_CZ) {
           const uint32_t links = o.y, c0 = o.y & 0xffu, c1 = (o.y >> 8) & 0xffu;

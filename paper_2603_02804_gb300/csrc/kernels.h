@@ -158,6 +158,7 @@ cudaError_t pg_encode(const PerGateArgs& a, const float2* enc, cudaStream_t st);
 cudaError_t pg_load_states(const PerGateArgs& a, const float2* in, int n_in, cudaStream_t st);
 cudaError_t pg_rot(const PerGateArgs& a, int kind, int q, const float2* cs, int slot, cudaStream_t st);
 cudaError_t pg_cz(const PerGateArgs& a, int c, int t, bool both, cudaStream_t st);
+cudaError_t pg_cnot(const PerGateArgs& a, int c, int t, bool both, cudaStream_t st);
 cudaError_t pg_expect(const PerGateArgs& a, uint32_t x_mask, uint32_t z_mask, uint32_t y_count,
                       double* e_part, cudaStream_t st);
 cudaError_t pg_seed(const PerGateArgs& a, uint32_t x_mask, uint32_t z_mask, uint32_t y_count,

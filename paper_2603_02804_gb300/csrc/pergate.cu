@@ -85,6 +85,33 @@ __global__ void pg_load_states_kernel(const PerGateArgs a, const float2* in, int
   }
 }
 
+// CNOT(c, t): swap the amplitude pairs over bit t whose bit c is 1 (psi, and
+// lambda when both): self-inverse, no gradient.
+__global__ void pg_cnot_kernel(const PerGateArgs a, int c, int t, int both) {
+  const int64_t dim = 1ll << a.n_eff;
+  const int64_t per = dim >> 2;  // pairs with bit c = 1
+  const int64_t total = (int64_t)a.B * per;
+  const int lo = c < t ? c : t, hi = c < t ? t : c;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / per;
+    uint64_t k = (uint64_t)(i - b * per);
+    // insert zero bits at lo and hi, then set the control bit
+    k = ((k >> lo) << (lo + 1)) | (k & ((1ull << lo) - 1));
+    k = ((k >> hi) << (hi + 1)) | (k & ((1ull << hi) - 1));
+    const uint64_t x0 = k | (1ull << c), x1 = x0 | (1ull << t);
+    float2* p = a.psi + b * dim;
+    const float2 u = p[x0];
+    p[x0] = p[x1];
+    p[x1] = u;
+    if (both) {
+      float2* q = a.lam + b * dim;
+      const float2 v = q[x0];
+      q[x0] = q[x1];
+      q[x1] = v;
+    }
+  }
+}
+
 template <int KIND>
 __global__ void pg_rot_kernel(const PerGateArgs a, int q, const float2* cs, int slot) {
   const float2 csv = __ldg(cs + slot);
@@ -259,6 +286,11 @@ cudaError_t pg_rot(const PerGateArgs& a, int kind, int q, const float2* cs, int 
   if (kind == G_RZ) pg_rot_kernel<G_RZ><<<g, kPgThreads, 0, st>>>(a, q, cs, slot);
   else if (kind == G_RY) pg_rot_kernel<G_RY><<<g, kPgThreads, 0, st>>>(a, q, cs, slot);
   else pg_rot_kernel<G_RX><<<g, kPgThreads, 0, st>>>(a, q, cs, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t pg_cnot(const PerGateArgs& a, int c, int t, bool both, cudaStream_t st) {
+  pg_cnot_kernel<<<grid_for(a.B << (a.n_eff - 2)), kPgThreads, 0, st>>>(a, c, t, both ? 1 : 0);
   return cudaGetLastError();
 }
 

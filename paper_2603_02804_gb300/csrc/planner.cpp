@@ -38,7 +38,7 @@ Dag build_dag(const Circuit& c) {
   std::vector<std::vector<int>> diag_since(c.n);
   for (int g = 0; g < M; ++g) {
     const Gate& gt = c.gates[g];
-    int qs[2] = {gt.q0, gt.kind == G_CZ ? gt.q1 : -1};
+    int qs[2] = {gt.q0, (gt.kind == G_CZ || gt.kind == G_CNOT) ? gt.q1 : -1};
     std::vector<int> deps;
     for (int q : qs) {
       if (q < 0) continue;
@@ -113,6 +113,10 @@ int absorb_step(Sim& s, uint64_t group, int max_slots, std::vector<int>* out) {
       if (s.done[g] || s.indeg[g] != 0) continue;
       const Gate& gt = s.c->gates[g];
       if (gt.kind == G_CZ) {
+        ++cz;
+      } else if (gt.kind == G_CNOT) {
+        // a permutation of the target's register pairs; the control may be any qubit
+        if (!((group >> gt.q1) & 1)) continue;
         ++cz;
       } else {
         if (!((group >> gt.q0) & 1)) continue;
@@ -430,8 +434,8 @@ void validate_circuit(const Circuit& c) {
     const Gate& g = c.gates[i];
     const std::string at = " (gate " + std::to_string(i) + ")";
     if (g.q0 < 0 || g.q0 >= c.n) throw std::runtime_error("qubit out of range" + at);
-    if (g.kind == G_CZ) {
-      if (g.q1 < 0 || g.q1 >= c.n || g.q1 == g.q0) throw std::runtime_error("bad CZ target" + at);
+    if (g.kind == G_CZ || g.kind == G_CNOT) {
+      if (g.q1 < 0 || g.q1 >= c.n || g.q1 == g.q0) throw std::runtime_error("bad two-qubit target" + at);
     } else if (is_rot(g.kind)) {
       if (g.param < 0 || g.param >= c.n_params) throw std::runtime_error("param out of range" + at);
     } else {
@@ -453,6 +457,7 @@ int ckpt_interval_gates(const Circuit& c, int ckpt_layers) {
 // 0 and n-1 never share a register group).
 static bool round_eligible(const Circuit& c) {
   for (const Gate& g : c.gates) {
+    if (g.kind == G_CNOT) return false;
     if (g.kind != G_CZ) continue;
     const int dq = std::abs(g.q0 - g.q1);
     if (dq != 1 && !(c.n >= 5 && dq == c.n - 1)) return false;
@@ -875,7 +880,7 @@ FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
             for (size_t i = 0; i < S.size(); ++i) {
               if (fin[i] || lin[i] != 0) continue;
               const Gate& gt = c.gates[S[i]];
-              if (gt.kind != G_CZ && gt.q0 == q) { pick = (int)i; break; }
+              if (is_rot(gt.kind) && gt.q0 == q) { pick = (int)i; break; }
             }
             if (pick < 0) break;
             run.push_back(S[pick]);
@@ -913,6 +918,18 @@ FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
         for (auto& ab : others) {
           fops.push_back({w0(OP_CZ), (uint32_t)ab.first | (uint32_t)ab.second << 8});
           fruns.push_back({});
+        }
+        for (size_t i = 0; i < S.size(); ++i) {
+          if (fin[i] || lin[i] != 0) continue;
+          const Gate& gt = c.gates[S[i]];
+          if (gt.kind != G_CNOT) continue;
+          uint32_t ctl = (uint32_t)gt.q0;
+          for (int r = 0; r < 4; ++r)
+            if (pr.tile.local_to_global[gl[r]] == gt.q0) ctl = (1u << 8) | (uint32_t)r;
+          fops.push_back({w0(OP_CNOT, reg_of(gt.q1) << 4), ctl});
+          fruns.push_back({});
+          finish((int)i);
+          --left;
         }
         if (left == before) throw std::runtime_error("internal: step scheduling stalled");
       }

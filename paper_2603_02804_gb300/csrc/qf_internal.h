@@ -22,7 +22,7 @@ constexpr int kMaxStepSlots = 32;      // gradient slots reduced per step (bwd)
 constexpr int kMaxQubits = 30;
 
 // gate kinds (match the public QF_GATE_* values)
-enum GateKind : int32_t { G_RX = 0, G_RY = 1, G_RZ = 2, G_CZ = 3 };
+enum GateKind : int32_t { G_RX = 0, G_RY = 1, G_RZ = 2, G_CZ = 3, G_CNOT = 4 };
 
 // Op words: every op is a uint2 {w0, w1}; the low 4 bits of w0 are the code.
 enum OpCode : uint32_t {
@@ -33,6 +33,8 @@ enum OpCode : uint32_t {
   OP_CZ = 5,      // CZ(c, t): w1 = c | t << 8
   OP_CKPT = 6,    // fwd: write the tile to checkpoint slot w1
   OP_ANCHOR = 7,  // bwd: reload psi of the tile from checkpoint slot w1
+  OP_CNOT = 8,    // CNOT with target register bit (bits 4-5); w1: control register bit | 1 << 8,
+                  // or the control's global qubit index (a bit of the thread's base index)
 };
 
 // Round programs: a step is OP_STEP {w0: group (bits 4-5) | rounds << 8,

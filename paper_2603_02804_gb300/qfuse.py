@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqfuse.so")
 
 QF_OK, QF_ERR_INVALID_ARG, QF_ERR_UNSUPPORTED, QF_ERR_WORKSPACE, QF_ERR_OOM, QF_ERR_CUDA, QF_ERR_TIMEOUT = range(7)
-QF_GATE_RX, QF_GATE_RY, QF_GATE_RZ, QF_GATE_CZ = range(4)
+QF_GATE_RX, QF_GATE_RY, QF_GATE_RZ, QF_GATE_CZ, QF_GATE_CNOT = range(5)
 QF_ENT_CHAIN, QF_ENT_RING = 0, 1
 QF_ENC_RY_X, QF_ENC_STATE_IN = 0, 1
 QF_PATH_FUSED, QF_PATH_PER_GATE = 0, 1

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-OP_STEP, OP_U, OP_G, OP_CHAIN, OP_CZ, OP_CKPT, OP_ANCHOR = 1, 2, 3, 4, 5, 6, 7
+OP_STEP, OP_U, OP_G, OP_CHAIN, OP_CZ, OP_CKPT, OP_ANCHOR, OP_CNOT = 1, 2, 3, 4, 5, 6, 7, 8
 SRC_GENERATE, BUF_WORK, BUF_NONE = -1, -2, -3
 LAM_SEED, LAM_BUF = -1, -2
 RX, RY, RZ = 0, 1, 2
@@ -98,6 +98,23 @@ def cz_sign(n, c, t):
     return 1 - 2 * (((x >> c) & 1) & ((x >> t) & 1))
 
 
+def cnot(psi, n, c, t):
+    """Swap the amplitude pairs over bit t whose bit c is 1."""
+    x = np.arange(2 ** n, dtype=np.int64)
+    sel = (((x >> c) & 1) == 1) & (((x >> t) & 1) == 0)
+    out = psi.copy()
+    a, b = x[sel], x[sel] | (1 << t)
+    out[a], out[b] = psi[b], psi[a]
+    return out
+
+
+def cnot_op(pd, group, w0, w1):
+    """(control, target) global qubits of an OP_CNOT in pass pd."""
+    t = pd["gmap"][group[(w0 >> 4) & 3]]
+    c = pd["gmap"][group[w1 & 0xFF]] if (w1 >> 8) & 1 else (w1 & 0xFF)
+    return c, t
+
+
 def observable(psi, n, xm, zm):
     x = np.arange(2 ** n, dtype=np.int64)
     xp = x ^ xm
@@ -150,6 +167,8 @@ def fwd_ops(prog, pd, psi, n_eff, theta, slots):
             psi = psi * chain_sign(n_eff, w1)
         elif code == OP_CZ:
             psi = psi * cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
+        elif code == OP_CNOT:
+            psi = cnot(psi, n_eff, *cnot_op(pd, group, w0, w1))
         elif code == OP_CKPT:
             slots[w1] = psi.copy()
         else:
@@ -218,6 +237,9 @@ def bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen):
         elif code == OP_CZ:
             s = cz_sign(n_eff, w1 & 255, (w1 >> 8) & 255)
             psi, lam = psi * s, lam * s
+        elif code == OP_CNOT:
+            ct = cnot_op(pd, group, w0, w1)
+            psi, lam = cnot(psi, n_eff, *ct), cnot(lam, n_eff, *ct)
         elif code == OP_ANCHOR:
             psi = slots[w1].copy()
         else:

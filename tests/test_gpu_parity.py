@@ -285,3 +285,27 @@ def test_workspace_and_batch_errors():
     with pytest.raises(qfuse.QFError) as e:
         qfuse.qf_forward(sim.handle, th, x, 4, qfuse.qf_pauli(0, 1 << 7), E, sim.ws, sim.ws_bytes)
     assert e.value.status == qfuse.QF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_cnot_gate_lists(seed):
+    """CNOTs fused into generic steps (and the per-gate comparator), against the oracle."""
+    rng = np.random.default_rng(80 + seed)
+    n = [6, 11, 15][seed]
+    n_params = 10
+    rows = []
+    for _ in range(70):
+        k = int(rng.choice([orc.RX, orc.RY, orc.RZ, orc.CZ, orc.CNOT]))
+        if k in (orc.CZ, orc.CNOT):
+            a, b = rng.choice(n, 2, replace=False)
+            rows.append((k, int(a), int(b), -1))
+        else:
+            rows.append((k, int(rng.integers(n)), -1, int(rng.integers(n_params))))
+    theta = rng.uniform(0, 2 * np.pi, n_params).astype(np.float32)
+    x = rng.uniform(0, np.pi, (4, n)).astype(np.float32)
+    c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=n_params)
+    gr, Er = orc.gradient(c, f64(theta), f64(x), "ZX", per_sample=True)
+    for path in ("fused", "per_gate"):
+        E, g, _ = gpu_run(n, 0, theta, x, obs="ZX", path=path, gates=rows, n_params=n_params, ckpt=1)
+        assert np.max(np.abs(E - Er)) < TOL, path
+        assert np.max(np.abs(g - gr)) < TOL, path

@@ -381,3 +381,33 @@ def test_consecutive_gates_rows():
     rows = workloads.consecutive_gates(3, 4)
     assert rows[:5] == [(0, 0, -1, 0), (1, 0, -1, 1), (2, 0, -1, 2), (0, 0, -1, 3), (0, 1, -1, 4)]
     assert len(rows) == 12 and sorted(r[3] for r in rows) == list(range(12))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cnot_gate_lists_match_oracle(seed):
+    """Random gate lists with CNOTs (control inside or outside the target's
+    register group, inside or outside the tile) on generic programs."""
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(3, 15))
+    n_params = 9
+    rows = []
+    for _ in range(50):
+        k = int(rng.choice([orc.RX, orc.RY, orc.RZ, orc.CZ, orc.CNOT]))
+        if k in (orc.CZ, orc.CNOT):
+            a, b = rng.choice(n, 2, replace=False)
+            rows.append((k, int(a), int(b), -1))
+        else:
+            rows.append((k, int(rng.integers(n)), -1, int(rng.integers(n_params))))
+    h = qfuse.qf_circuit_create(n, rows, n_params)
+    try:
+        qfuse.qf_plan(h, 2, tile_bits=int(rng.choice([0, 5, 6])), ckpt_layers=1, host_only=True)
+        theta = rng.uniform(0, 2 * np.pi, n_params).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
+        c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=n_params)
+        slot_param = [r[3] for r in rows if r[0] not in (orc.CZ, orc.CNOT)]
+        slot_kind = [r[0] for r in rows if r[0] not in (orc.CZ, orc.CNOT)]
+        obs = "".join(rng.choice(list("IZ"), size=n))
+        info, rounds = interp_check(h, n, theta, x, obs, slot_param, slot_kind, oracle_circ=c)
+        assert not rounds
+    finally:
+        qfuse.qf_circuit_destroy(h)
