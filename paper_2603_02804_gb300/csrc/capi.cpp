@@ -81,6 +81,8 @@ struct qf_circuit {
   void* d_tables = nullptr; // device copy of blob (qf_plan)
   DevTables dt;
   int64_t launches = 0;
+  void* h_stage = nullptr;  // pinned host staging of the host-buffer step (packed copies)
+  size_t h_stage_bytes = 0;
   int64_t call_launches = 0;
   // pass-kernel timing (qf_profile)
   bool profile = false;
@@ -121,6 +123,9 @@ void free_tables(qf_circuit* c) {
   if (c->d_tables) cudaFree(c->d_tables);
   c->d_tables = nullptr;
   c->dt = DevTables();
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  c->h_stage = nullptr;
+  c->h_stage_bytes = 0;
 }
 
 int n_eff_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_eff : c->gp.n_eff; }
@@ -1048,9 +1053,39 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
   float* xd = at<float>(ws_d, L.x);
   float* yd = at<float>(ws_d, L.y);
   const int P = c->circ.n_params;
+  const bool mse = batch > 0 && loss_kind == QF_LOSS_MSE;
+  // Small steps: inputs and outputs each cross the bus as one copy through a
+  // pinned staging buffer laid out like the workspace regions (theta, x, y)
+  // and (E, dL/dE, grad, loss); large inputs are copied directly.
+  const size_t in_span = L.y + (size_t)batch * 4 - L.theta, out_span = L.loss + 8 - L.E;
+  const size_t need = std::max(in_span, out_span);
+  if (need <= ((size_t)1 << 20) && !c->h_stage) {
+    if (cudaHostAlloc(&c->h_stage, need, cudaHostAllocDefault) == cudaSuccess) {
+      c->h_stage_bytes = need;
+    } else {
+      c->h_stage = nullptr;  // fall back to direct copies
+      cudaGetLastError();
+    }
+  }
+  if (c->h_stage && need <= c->h_stage_bytes) {
+    char* h = static_cast<char*>(c->h_stage);
+    if (P) memcpy(h, theta_h, (size_t)P * 4);
+    if (batch) memcpy(h + (L.x - L.theta), x_h, x_bytes(c, batch));
+    if (mse) memcpy(h + (L.y - L.theta), y_h, (size_t)batch * 4);
+    QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, st));
+    s = qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, L.loss), at<double>(ws_d, L.E),
+                      at<double>(ws_d, L.grad), ws_d, ws_bytes, stream);
+    if (s != QF_OK) return s;
+    QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, st));
+    QF_CU(cudaStreamSynchronize(st));
+    memcpy(loss_h, h + (L.loss - L.E), 8);
+    if (E_h && batch) memcpy(E_h, h, (size_t)batch * 8);
+    if (P) memcpy(grad_h, h + (L.grad - L.E), (size_t)P * 8);
+    return QF_OK;
+  }
   if (P) QF_CU(cudaMemcpyAsync(th, theta_h, (size_t)P * 4, cudaMemcpyHostToDevice, st));
   if (batch) QF_CU(cudaMemcpyAsync(xd, x_h, x_bytes(c, batch), cudaMemcpyHostToDevice, st));
-  if (batch && loss_kind == QF_LOSS_MSE) QF_CU(cudaMemcpyAsync(yd, y_h, (size_t)batch * 4, cudaMemcpyHostToDevice, st));
+  if (mse) QF_CU(cudaMemcpyAsync(yd, y_h, (size_t)batch * 4, cudaMemcpyHostToDevice, st));
   s = qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, L.loss), at<double>(ws_d, L.E),
                     at<double>(ws_d, L.grad), ws_d, ws_bytes, stream);
   if (s != QF_OK) return s;
