@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "kernels.h"
 
 namespace qf {
@@ -1454,6 +1456,23 @@ __global__ void batch_loss_kernel(const BatchArgs a) {
   if (threadIdx.x == 0) a.loss[0] = red[0];
 }
 
+// Opt a kernel in to `smem` bytes of dynamic shared memory on the current
+// device, once per device (the call is idempotent, so two threads racing on a
+// first launch only repeat it; devices past the table are opted in every time).
+struct OptIn {
+  std::atomic<bool> done[64] = {};
+};
+static cudaError_t opt_in(const void* fn, size_t smem, OptIn& o) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tab = dev >= 0 && dev < 64;
+  if (tab && o.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && tab) o.done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
 int batch_grid() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -1462,16 +1481,10 @@ int batch_grid() {
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64_t n_grad_out, cudaStream_t st) {
-  static bool once[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+  static OptIn once;
   const size_t smem = 2 * (size_t)kTileAmps * sizeof(float2);
-  if (dev >= 0 && dev < 64 && !once[dev]) {
-    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    once[dev] = true;
-  }
+  cudaError_t e = opt_in(reinterpret_cast<const void*>(batch_kernel), smem, once);
+  if (e != cudaSuccess) return e;
   if (prep_total > 0) batch_prep_kernel<<<(unsigned)((prep_total + 63) / 64), 64, 0, st>>>(a, prep_total);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
@@ -1504,18 +1517,11 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
   const size_t smem = (size_t)(bwd ? 2 : 1) * kTileAmps * sizeof(float2);
   const bool rounds = a.rounds != nullptr;
   if (bwd) {
-    // 64 KiB of dynamic shared memory needs the opt-in, once per device
-    static bool once[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    // 64 KiB of dynamic shared memory needs the opt-in
+    static OptIn once_generic, once_rounds;
+    cudaError_t e = rounds ? opt_in(reinterpret_cast<const void*>(pass_kernel<true, true>), smem, once_rounds)
+                           : opt_in(reinterpret_cast<const void*>(pass_kernel<true, false>), smem, once_generic);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && !once[dev]) {
-      e = cudaFuncSetAttribute(pass_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(pass_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      once[dev] = true;
-    }
     if (rounds) pass_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else pass_kernel<true, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   } else {
@@ -1592,15 +1598,9 @@ cudaError_t launch_pass_tc(const PassArgs& a, cudaStream_t st) {
   const int64_t grid = (int64_t)a.B << a.tps_log2;
   if (grid == 0) return cudaSuccess;
   const size_t smem = (size_t)kTileAmps * sizeof(float2) + (size_t)2 * kMaxStepRounds * kTcBFloats * sizeof(float);
-  static bool once[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  static OptIn once;
+  cudaError_t e = opt_in(reinterpret_cast<const void*>(tc_pass_kernel), smem, once);
   if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64 && !once[dev]) {
-    e = cudaFuncSetAttribute(tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    once[dev] = true;
-  }
   tc_pass_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }

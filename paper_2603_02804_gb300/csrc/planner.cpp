@@ -191,7 +191,7 @@ int run_pass(Sim& s, const Tile& t, std::vector<StepRec>* steps) {
     if (best < 0) break;
     std::vector<int> gs;
     total += absorb_step(s, t.group_qmask[best], kMaxStepSlots, steps ? &gs : nullptr);
-    if (steps) steps->push_back({best, std::move(gs)});
+    if (steps) steps->push_back({best, std::move(gs), {}});
   }
   return total;
 }
