@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512", "paper_hea", "fusion_sweep"])
     ap.add_argument("--qubits", type=int, default=29, help="paper_hea: number of qubits")
+    ap.add_argument("--circuits", type=int, default=0, help="mixed512: first N circuits only (profiling cases)")
+    ap.add_argument("--no-autotune", action="store_true", help="mixed512: 12-qubit tiles for every circuit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
@@ -233,11 +235,12 @@ def run_mixed(args):
     qbuild.build()
     peaks, peak_src = load_peaks()
     circs = workloads.mixed_circuits(512, seed=104 + 1000 * rank)
+    if args.circuits:
+        circs = circs[:args.circuits]  # a subset of the same draw (profiling cases)
     specs = [(c.n, c.d, c.B) for c in circs]
-    tuner = Autotuner(path=os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None)
+    tuner = Autotuner(path=os.environ.get("QF_AUTOTUNE_CACHE"))  # JSON cache file, or in memory only
     t0 = time.perf_counter()
-    bt = Batch(specs, loss="sum", tile_bits=tuner)
+    bt = Batch(specs, loss="sum", tile_bits=None if args.no_autotune else tuner)
     tune_s = time.perf_counter() - t0
     cat = lambda arrs: torch.from_numpy(np.concatenate([a.reshape(-1) for a in arrs])).cuda()
     theta, x = cat([c.theta for c in circs]), cat([c.x for c in circs])
@@ -289,7 +292,7 @@ def run_mixed(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": {"workload": "mixed512: 512 HEA circuits n~U{8..18} d~U{10..200} B~U{1..64}, L=sum E, obs=Z0, "
                                "one persistent launch per step", "samples_per_step": bt.n_samples,
-                   "work_items": bt.n_items, "tile_bits": "autotuned", "tune_s": tune_s,
+                   "work_items": bt.n_items, "tile_bits": "12 (fixed)" if args.no_autotune else "autotuned", "tune_s": tune_s,
                    "l2": "inputs larger than L2 (workspace %.1f GB)" % (bt.ws_bytes / 1e9)},
         "graph": {"value": bt.n_samples * world * args.steps / (graph_ms / 1e3), "unit": "samples/s",
                   "ms_per_step": graph_ms / args.steps},
