@@ -73,6 +73,14 @@ typedef int32_t qf_status;
 #define QF_LOSS_SUM 0 /* L = sum_b E_b (the paper's L = E, Sec. 2.1)       */
 #define QF_LOSS_MSE 1 /* L = mean_b (E_b - y_b)^2                          */
 
+/* State precision of a plan (qf_plan_opts.precision). The paper's library
+ * runs complex64 or complex128 states; its measurements use complex64
+ * (Sec. 4). */
+#define QF_PREC_C64 0  /* complex64 states, float32 arithmetic, float32 theta and x:
+                          qf_forward, qf_backward, qf_train_step(_host, _noalloc)    */
+#define QF_PREC_C128 1 /* complex128 states, float64 arithmetic, float64 theta, x and
+                          y: qf_forward64, qf_backward64, qf_train_step64(_host)    */
+
 typedef struct qf_circuit qf_circuit;
 
 /* One gate of a user circuit. q1 is the target of a CZ (-1 otherwise);
@@ -130,7 +138,14 @@ typedef struct {
   int32_t no_host_staging; /* 1: leave out the workspace's host-input staging
                           (x, theta, y and outputs of qf_train_step_host, which
                           then fails); for device-resident inputs of large states */
-  int32_t reserved[7];
+  int32_t precision;   /* QF_PREC_C64 (default) or QF_PREC_C128. complex128 needs
+                          the fused path and runs generic steps (program 1) on the
+                          CUDA cores; tc_path must be 0. With ckpt_mode 1 and
+                          mem_save the stored pass outputs are complex64 (float32
+                          re, im; the paper's memory-saving mode halves the
+                          precision of stored states). Checkpoints, psi_M and
+                          all arithmetic stay float64                           */
+  int32_t reserved[6];
 } qf_plan_opts;
 
 /* Summary of a plan (host-side numbers). */
@@ -155,6 +170,7 @@ typedef struct {
   int32_t mem_save;
   int32_t n_pass_slots;    /* ckpt_mode 1: stored pass outputs of one block     */
   int32_t tc_path;
+  int32_t precision;       /* QF_PREC_C64 or QF_PREC_C128                       */
 } qf_plan_info_t;
 
 /* Create the hardware-efficient ansatz of the paper's benchmarks with the
@@ -266,6 +282,31 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
                              double* loss_h, double* E_h, double* grad_h, void* ws_d,
                              size_t ws_bytes, void* stream);
 
+/* ---- complex128 plans (opts->precision = QF_PREC_C128) ----------------------
+ * The same operations as qf_forward, qf_backward, qf_loss, qf_train_step and
+ * qf_train_step_host with complex128 states and float64 arithmetic
+ * throughout: theta float64 [n_params]; x float64 [batch][n_qubits] angles
+ * (QF_ENC_RY_X) or complex128 [batch][2^n_qubits] initial states as float64
+ * (re, im) pairs (QF_ENC_STATE_IN); y float64 [batch]. Outputs as for the
+ * complex64 calls (float64 E, loss, dL/dE and gradients). Gate tables are
+ * computed in float64 and used unrounded. Calling a complex64 entry point on
+ * a complex128 plan, or the reverse, returns QF_ERR_INVALID_ARG. */
+qf_status qf_forward64(qf_circuit* c, const double* theta_d, const double* x_d, int64_t batch,
+                       qf_pauli obs, double* E_d, void* ws_d, size_t ws_bytes, void* stream);
+qf_status qf_backward64(qf_circuit* c, const double* theta_d, const double* x_d, int64_t batch,
+                        qf_pauli obs, const double* dLdE_d, double* grad_d, int32_t per_sample,
+                        void* ws_d, size_t ws_bytes, void* stream);
+qf_status qf_loss64(int32_t kind, const double* E_d, const double* y_d, int64_t batch,
+                    double* loss_d, double* dLdE_d, void* stream);
+qf_status qf_train_step64(qf_circuit* c, const double* theta_d, const double* x_d,
+                          const double* y_d, int64_t batch, int32_t loss_kind, qf_pauli obs,
+                          double* loss_d, double* E_d, double* grad_d, void* ws_d,
+                          size_t ws_bytes, void* stream);
+qf_status qf_train_step_host64(qf_circuit* c, const double* theta_h, const double* x_h,
+                               const double* y_h, int64_t batch, int32_t loss_kind, qf_pauli obs,
+                               double* loss_h, double* E_h, double* grad_h, void* ws_d,
+                               size_t ws_bytes, void* stream);
+
 /* Size of the fixed device scratch used by qf_train_step_noalloc. */
 #define QF_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
 
@@ -286,6 +327,7 @@ qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x
  * cudaMalloc, cudaFree or other allocating routine.
  *
  * Limits and behaviour:
+ *  - complex64 plans only (a complex128 plan returns QF_ERR_INVALID_ARG).
  *  - plan tables plus the step's buffers for `batch` samples must fit in
  *    QF_NOALLOC_MAX_BYTES; otherwise QF_ERR_WORKSPACE is returned and
  *    qf_last_error() states the bytes needed.

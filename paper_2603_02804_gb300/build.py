@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libqfuse.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["fused.cu", "pergate.cu", "noalloc.cu", "capi.cpp", "planner.cpp"]
+SOURCES = ["fused.cu", "fused64.cu", "pergate.cu", "noalloc.cu", "capi.cpp", "planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

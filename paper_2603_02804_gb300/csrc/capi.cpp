@@ -72,6 +72,7 @@ struct qf_circuit {
   int encoding = QF_ENC_RY_X;
   bool staging = true;      // workspace holds host-input staging (qf_train_step_host)
   bool tc = false;          // forward rounds on the tensor cores
+  bool f64 = false;         // complex128 states (QF_PREC_C128)
   int64_t batch = 0;
   qf::FusedPlan fp;
   qf::PerGatePlan gp;
@@ -129,9 +130,12 @@ void free_tables(qf_circuit* c) {
 }
 
 int n_eff_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_eff : c->gp.n_eff; }
-// Bytes of one batch of inputs: angles [B][n] float32, or states [B][2^n] complex64.
+// Bytes of one batch of inputs: angles [B][n] float32 (float64), or states
+// [B][2^n] complex64 (complex128 plans: complex128).
 size_t x_bytes(const qf_circuit* c, int64_t B) {
-  return c->encoding == QF_ENC_STATE_IN ? (size_t)B * ((size_t)1 << c->circ.n) * 8 : (size_t)B * c->circ.n * 4;
+  const size_t w = c->f64 ? 2 : 1;
+  return c->encoding == QF_ENC_STATE_IN ? (size_t)B * ((size_t)1 << c->circ.n) * 8 * w
+                                        : (size_t)B * c->circ.n * 4 * w;
 }
 
 int n_slots_of(const qf_circuit* c) { return c->path == QF_PATH_FUSED ? c->fp.n_terms : c->gp.n_slots; }
@@ -150,20 +154,23 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     return at;
   };
   const int64_t Bs = c->staging ? B : 0;  // staged inputs of the host-buffer step
-  L.theta = take((size_t)P * 4);
+  const size_t rw = c->f64 ? 8 : 4;        // bytes of a real input (theta, y)
+  const size_t aw = c->f64 ? 16 : 8;       // bytes of an amplitude
+  L.theta = take((size_t)P * rw);
   L.x = take(x_bytes(c, Bs));
-  L.y = take((size_t)B * 4);
+  L.y = take((size_t)B * rw);
   L.E = take((size_t)B * 8);
   L.dLdE = take((size_t)B * 8);
   L.grad = take((size_t)P * 8);
   L.loss = take(8);
-  L.cs = take((size_t)S * 16);  // (cos, sin) or shear parameters per term
-  L.enc = take((size_t)B * n_eff * 8);
-  L.work = take((size_t)L.state_elems * 8);
-  L.lam = take((size_t)L.state_elems * 8);
+  L.cs = take((size_t)S * 16);  // (cos, sin), float32 or float64, or shear parameters per term
+  L.enc = take((size_t)B * n_eff * aw);
+  L.work = take((size_t)L.state_elems * aw);
+  L.lam = take((size_t)L.state_elems * aw);
   if (c->path == QF_PATH_FUSED) {
     const int n_fused = (int)c->fp.fuse_off.size() - 1;
-    L.mats = take((size_t)std::max(n_fused, 0) * 32);
+    if (c->f64) L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
+    else L.mats = take((size_t)std::max(n_fused, 0) * 32);
     if (c->fp.rounds) {
       L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 128);
       L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * 128);
@@ -172,11 +179,12 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
       L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
       L.tcb = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 2048 * 4);
     }
-    // checkpoint mode A: pass-output slots after the checkpoints (float32), or
-    // a bfloat16 array of them (memory-saving mode)
+    // checkpoint mode A: pass-output slots after the checkpoints, or an array
+    // of them at half the state's precision (memory-saving mode: bfloat16
+    // pairs for complex64 states, complex64 for complex128)
     const int extra = c->fp.ckpt_mode == 1 && !c->fp.mem_save ? c->fp.n_aslots : 0;
-    L.slots = take((size_t)(c->fp.n_ckpt + extra) * L.state_elems * 8);
-    if (c->fp.ckpt_mode == 1 && c->fp.mem_save) L.hslots = take((size_t)c->fp.n_aslots * L.state_elems * 4);
+    L.slots = take((size_t)(c->fp.n_ckpt + extra) * L.state_elems * aw);
+    if (c->fp.ckpt_mode == 1 && c->fp.mem_save) L.hslots = take((size_t)c->fp.n_aslots * L.state_elems * aw / 2);
     L.rows = 1ll << (c->fp.n_eff - c->fp.K);
   } else {
     L.slots = take((size_t)c->gp.ckpt_after.size() * L.state_elems * 8);
@@ -276,9 +284,16 @@ qf_status check_obs(const qf_circuit* c, qf_pauli obs, Obs* o) {
   return QF_OK;
 }
 
-qf_status check_call(const qf_circuit* c, int64_t batch, void* ws, size_t ws_bytes) {
+qf_status check_precision(const qf_circuit* c, bool f64) {
+  if (c->f64 == f64) return QF_OK;
+  return fail(QF_ERR_INVALID_ARG, f64 ? "the plan is complex64: use the entry points without the 64 suffix"
+                                      : "the plan is complex128 (QF_PREC_C128): use the *64 entry points");
+}
+
+qf_status check_call(const qf_circuit* c, int64_t batch, void* ws, size_t ws_bytes, bool f64 = false) {
   if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
   if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan (call qf_plan)");
+  if (check_precision(c, f64) != QF_OK) return QF_ERR_INVALID_ARG;
   if (c->host_only || !c->d_tables) return fail(QF_ERR_WORKSPACE, "plan was built host-only");
   if (batch < 0 || batch > c->batch) return fail(QF_ERR_INVALID_ARG, "batch exceeds the planned batch");
   if (!ws) return fail(QF_ERR_INVALID_ARG, "null workspace");
@@ -519,6 +534,149 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   return QF_OK;
 }
 
+// ---- complex128 plans: the same pass sequences on the float64 kernels ----------
+qf::PassArgs64 pass_args64(const qf_circuit* c, const Layout& L, void* ws, int64_t B, const Obs& o) {
+  const qf::FusedPlan& P = c->fp;
+  qf::PassArgs64 a{};
+  a.n_eff = P.n_eff;
+  a.tps_log2 = P.n_eff - P.K;
+  a.B = B;
+  a.mats = at<double2>(ws, L.mats64);
+  a.cs = at<double2>(ws, L.cs);
+  a.enc = at<double2>(ws, L.enc);
+  a.n_in = c->circ.n;
+  a.work = at<double2>(ws, L.work);
+  a.lam = at<double2>(ws, L.lam);
+  a.slots = at<double2>(ws, L.slots);
+  a.fslots = L.hslots ? at<float2>(ws, L.hslots) : nullptr;
+  a.slot_stride = L.state_elems;
+  a.z_mask = o.z;
+  a.y_count = o.y;
+  a.e_part = at<double>(ws, L.epart);
+  a.g_part = at<double>(ws, L.gpart);
+  a.n_slots = P.n_terms;
+  return a;
+}
+
+// Prep arguments of a complex128 plan: fused 2x2s, terms and encodings in float64.
+qf::PrepArgs prep_args64(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, const double* theta) {
+  qf::PrepArgs pa{};
+  pa.theta64 = theta;
+  pa.fuse_off = T.fuse_off;
+  pa.fuse_gates = T.fuse_gates;
+  pa.mats64 = at<double>(ws, L.mats64);
+  pa.term_off = T.term_off;
+  pa.term_params = T.term_params;
+  pa.term_const = T.term_const;
+  pa.cs64 = at<double2>(ws, L.cs);
+  pa.n = c->circ.n;
+  pa.n_eff = c->fp.n_eff;
+  pa.enc64 = at<double2>(ws, L.enc);
+  return pa;
+}
+
+qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, const double* theta, const double* x,
+                          int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false) {
+  const qf::FusedPlan& P = c->fp;
+  qf::PrepArgs pa = prep_args64(c, T, L, ws, theta);
+  pa.n_fused = (int32_t)P.fuse_off.size() - 1;
+  pa.n_terms = with_terms ? P.n_terms : 0;
+  pa.x64 = x;
+  pa.B = c->encoding == QF_ENC_RY_X ? B : 0;
+  QF_CU(qf::launch_prep(pa, st));
+  c->call_launches++;
+  qf::PassArgs64 a = pass_args64(c, L, ws, B, o);
+  a.ops = T.fwd_ops;
+  a.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const double2*>(x) : nullptr;
+  const int prof = prof_begin(c, st);
+  int32_t full_expect = -1;
+  for (size_t pi = 0; pi < P.fwd.size(); ++pi) {
+    a.pd = P.fwd[pi];
+    a.pd.xm_local = 0;
+    if ((a.pd.flags & qf::PF_EXPECT) && !local_xmask(a.pd, o.x, &a.pd.xm_local)) {
+      a.pd.flags &= ~qf::PF_EXPECT;
+      full_expect = a.pd.psi_dst;
+    }
+    QF_CU(qf::launch_pass64(false, a, st));
+    c->call_launches++;
+  }
+  prof_end(c, prof, 0, (int64_t)P.fwd.size(), st);
+  if (full_expect >= 0) {
+    QF_CU(qf::launch_expect_full64(a.slots + (int64_t)full_expect * a.slot_stride, P.n_eff, B, L.rows, o.x, o.z,
+                                   o.y, a.e_part, st));
+    c->call_launches++;
+  }
+  QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+  c->call_launches++;
+  return QF_OK;
+}
+
+qf_status fused_backward64(qf_circuit* c, const DevTables& T, const Layout& L, const double* theta,
+                           const double* x, int64_t B, const Obs& o, const double* dLdE, double* grad,
+                           int per_sample, void* ws, cudaStream_t st, bool with_prep = true) {
+  const qf::FusedPlan& P = c->fp;
+  if (with_prep) {
+    qf::PrepArgs pa = prep_args64(c, T, L, ws, theta);
+    pa.n_terms = P.n_terms;
+    QF_CU(qf::launch_prep(pa, st));
+    c->call_launches++;
+  }
+  qf::PassArgs64 a = pass_args64(c, L, ws, B, o);
+  a.ops = T.bwd_ops;
+  a.dLdE = dLdE;
+  auto seed = [&](const qf::PassArgs64& p) -> cudaError_t {
+    c->call_launches++;
+    return qf::launch_seed_full64(p.slots + (int64_t)p.pd.psi_src * p.slot_stride, p.lam, P.n_eff, B, o.x, o.z,
+                                  o.y, p.dLdE, st);
+  };
+  const int prof = prof_begin(c, st);
+  if (P.ckpt_mode == 1) {
+    // checkpoint mode A: forward re-runs interleaved with adjoint passes
+    qf::PassArgs64 f = a;
+    f.ops = T.fwd_ops;
+    f.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const double2*>(x) : nullptr;
+    for (size_t i = 0; i < P.a_sched.size(); ++i) {
+      const bool bwd = P.a_dir[i] != 0;
+      qf::PassArgs64& p = bwd ? a : f;
+      p.pd = P.a_sched[i];
+      p.pd.xm_local = 0;
+      if (bwd && p.pd.lam_src == qf::LAM_SEED && !local_xmask(p.pd, o.x, &p.pd.xm_local)) {
+        QF_CU(seed(p));
+        p.pd.lam_src = qf::LAM_BUF;
+      }
+      QF_CU(qf::launch_pass64(bwd, p, st));
+      c->call_launches++;
+    }
+    prof_end(c, prof, 1, (int64_t)P.a_sched.size(), st);
+  } else {
+    for (size_t pi = 0; pi < P.bwd.size(); ++pi) {
+      a.pd = P.bwd[pi];
+      a.pd.xm_local = 0;
+      if (a.pd.lam_src == qf::LAM_SEED && !local_xmask(a.pd, o.x, &a.pd.xm_local)) {
+        QF_CU(seed(a));
+        a.pd.lam_src = qf::LAM_BUF;
+      }
+      QF_CU(qf::launch_pass64(true, a, st));
+      c->call_launches++;
+    }
+    prof_end(c, prof, 1, (int64_t)P.bwd.size(), st);
+  }
+  qf::GradReduceArgs g{};
+  g.g_part = a.g_part;
+  g.B = B;
+  g.tps = L.rows;
+  g.slot_stride = P.n_terms;
+  g.slot_step = 1;
+  g.n_params = c->circ.n_params;
+  g.param_off = T.param_off;
+  g.param_slots = T.param_terms;
+  g.per_sample = per_sample;
+  g.grad = grad;
+  QF_CU(qf::launch_g_reduce(g, st));
+  c->call_launches++;
+  return QF_OK;
+}
+
 qf_status pg_forward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, const float* x,
                      int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st) {
   const qf::PerGatePlan& P = c->gp;
@@ -722,6 +880,12 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     return fail(QF_ERR_UNSUPPORTED, "ckpt_mode 1 applies to the fused path");
   if (o.tc_path != 0 && o.tc_path != 1) return fail(QF_ERR_INVALID_ARG, "tc_path must be 0 or 1");
   if (o.tc_path && o.path != QF_PATH_FUSED) return fail(QF_ERR_UNSUPPORTED, "tc_path applies to the fused path");
+  if (o.precision != QF_PREC_C64 && o.precision != QF_PREC_C128)
+    return fail(QF_ERR_INVALID_ARG, "precision must be QF_PREC_C64 or QF_PREC_C128");
+  if (o.precision == QF_PREC_C128 && o.path != QF_PATH_FUSED)
+    return fail(QF_ERR_UNSUPPORTED, "complex128 runs on the fused path");
+  if (o.precision == QF_PREC_C128 && o.tc_path)
+    return fail(QF_ERR_UNSUPPORTED, "the tensor-core path is complex64 (3xTF32)");
   try {
     free_tables(c);
     c->planned = false;
@@ -729,11 +893,12 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     c->ckpt_layers = o.ckpt_layers > 0 ? o.ckpt_layers : 10;
     c->host_only = o.host_only != 0;
     c->staging = o.no_host_staging == 0;
+    c->f64 = o.precision == QF_PREC_C128;
     c->batch = batch;
     qf::PlanRequest req;
     req.tile_bits = o.tile_bits;
     req.ckpt_layers = c->ckpt_layers;
-    req.generic = o.program == 1;
+    req.generic = o.program == 1 || c->f64;  // complex128 passes run generic steps
     req.ckpt_mode = o.ckpt_mode;
     req.mem_save = o.mem_save != 0;
     c->tc = false;
@@ -849,7 +1014,8 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
   info->ckpt_layers = c->ckpt_layers;
   info->batch = c->batch;
   info->workspace_bytes = (int64_t)c->L.total;
-  info->state_bytes = c->L.state_elems * 8;
+  info->state_bytes = c->L.state_elems * (c->f64 ? 16 : 8);
+  info->precision = c->f64 ? QF_PREC_C128 : QF_PREC_C64;
   if (c->path == QF_PATH_FUSED) {
     info->n_eff = c->fp.n_eff;
     info->n_slots = c->fp.n_terms;
@@ -879,6 +1045,78 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// The host-buffer step for real inputs of type R (float: complex64 plans,
+// double: complex128 plans).
+template <class R>
+qf_status train_step_host(qf_circuit* c, const R* theta_h, const R* x_h, const R* y_h, int64_t batch,
+                          int32_t loss_kind, qf_pauli obs, double* loss_h, double* E_h, double* grad_h, void* ws_d,
+                          size_t ws_bytes, void* stream) {
+  constexpr bool F64 = sizeof(R) == 8;
+  auto step = [&](const R* th, const R* xd, const R* yd) -> qf_status {
+    if constexpr (F64)
+      return qf_train_step64(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
+                             at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, stream);
+    else
+      return qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
+                           at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, stream);
+  };
+  qf_status s = check_call(c, batch, ws_d, ws_bytes, F64);
+  if (s != QF_OK) return s;
+  if (!c->staging) return fail(QF_ERR_UNSUPPORTED, "the plan was made with no_host_staging");
+  if ((!theta_h && c->circ.n_params > 0) || (!x_h && batch > 0) || !loss_h || (!grad_h && c->circ.n_params > 0) ||
+      (loss_kind == QF_LOSS_MSE && batch > 0 && !y_h))
+    return fail(QF_ERR_INVALID_ARG, "null host pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout& L = c->L;
+  R* th = at<R>(ws_d, L.theta);
+  R* xd = at<R>(ws_d, L.x);
+  R* yd = at<R>(ws_d, L.y);
+  const int P = c->circ.n_params;
+  const bool mse = batch > 0 && loss_kind == QF_LOSS_MSE;
+  // Small steps: inputs and outputs each cross the bus as one copy through a
+  // pinned staging buffer laid out like the workspace regions (theta, x, y)
+  // and (E, dL/dE, grad, loss); large inputs are copied directly.
+  const size_t in_span = L.y + (size_t)batch * sizeof(R) - L.theta, out_span = L.loss + 8 - L.E;
+  const size_t need = std::max(in_span, out_span);
+  if (need <= ((size_t)1 << 20) && !c->h_stage) {
+    if (cudaHostAlloc(&c->h_stage, need, cudaHostAllocDefault) == cudaSuccess) {
+      c->h_stage_bytes = need;
+    } else {
+      c->h_stage = nullptr;  // fall back to direct copies
+      cudaGetLastError();
+    }
+  }
+  if (c->h_stage && need <= c->h_stage_bytes) {
+    char* h = static_cast<char*>(c->h_stage);
+    if (P) memcpy(h, theta_h, (size_t)P * sizeof(R));
+    if (batch) memcpy(h + (L.x - L.theta), x_h, x_bytes(c, batch));
+    if (mse) memcpy(h + (L.y - L.theta), y_h, (size_t)batch * sizeof(R));
+    QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, st));
+    s = step(th, xd, yd);
+    if (s != QF_OK) return s;
+    QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, st));
+    QF_CU(cudaStreamSynchronize(st));
+    memcpy(loss_h, h + (L.loss - L.E), 8);
+    if (E_h && batch) memcpy(E_h, h, (size_t)batch * 8);
+    if (P) memcpy(grad_h, h + (L.grad - L.E), (size_t)P * 8);
+    return QF_OK;
+  }
+  if (P) QF_CU(cudaMemcpyAsync(th, theta_h, (size_t)P * sizeof(R), cudaMemcpyHostToDevice, st));
+  if (batch) QF_CU(cudaMemcpyAsync(xd, x_h, x_bytes(c, batch), cudaMemcpyHostToDevice, st));
+  if (mse) QF_CU(cudaMemcpyAsync(yd, y_h, (size_t)batch * sizeof(R), cudaMemcpyHostToDevice, st));
+  s = step(th, xd, yd);
+  if (s != QF_OK) return s;
+  QF_CU(cudaMemcpyAsync(loss_h, at<double>(ws_d, L.loss), 8, cudaMemcpyDeviceToHost, st));
+  if (E_h && batch) QF_CU(cudaMemcpyAsync(E_h, at<double>(ws_d, L.E), (size_t)batch * 8, cudaMemcpyDeviceToHost, st));
+  if (P) QF_CU(cudaMemcpyAsync(grad_h, at<double>(ws_d, L.grad), (size_t)P * 8, cudaMemcpyDeviceToHost, st));
+  QF_CU(cudaStreamSynchronize(st));
+  return QF_OK;
+}
+
+}  // namespace
 
 // A double as two int32 words (low, high) of its bit pattern.
 static void push_double(std::vector<int32_t>& w, double v) {
@@ -1041,59 +1279,7 @@ qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d, c
 qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x_h, const float* y_h,
                              int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_h, double* E_h,
                              double* grad_h, void* ws_d, size_t ws_bytes, void* stream) {
-  qf_status s = check_call(c, batch, ws_d, ws_bytes);
-  if (s != QF_OK) return s;
-  if (!c->staging) return fail(QF_ERR_UNSUPPORTED, "the plan was made with no_host_staging");
-  if ((!theta_h && c->circ.n_params > 0) || (!x_h && batch > 0) || !loss_h || (!grad_h && c->circ.n_params > 0) ||
-      (loss_kind == QF_LOSS_MSE && batch > 0 && !y_h))
-    return fail(QF_ERR_INVALID_ARG, "null host pointer");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Layout& L = c->L;
-  float* th = at<float>(ws_d, L.theta);
-  float* xd = at<float>(ws_d, L.x);
-  float* yd = at<float>(ws_d, L.y);
-  const int P = c->circ.n_params;
-  const bool mse = batch > 0 && loss_kind == QF_LOSS_MSE;
-  // Small steps: inputs and outputs each cross the bus as one copy through a
-  // pinned staging buffer laid out like the workspace regions (theta, x, y)
-  // and (E, dL/dE, grad, loss); large inputs are copied directly.
-  const size_t in_span = L.y + (size_t)batch * 4 - L.theta, out_span = L.loss + 8 - L.E;
-  const size_t need = std::max(in_span, out_span);
-  if (need <= ((size_t)1 << 20) && !c->h_stage) {
-    if (cudaHostAlloc(&c->h_stage, need, cudaHostAllocDefault) == cudaSuccess) {
-      c->h_stage_bytes = need;
-    } else {
-      c->h_stage = nullptr;  // fall back to direct copies
-      cudaGetLastError();
-    }
-  }
-  if (c->h_stage && need <= c->h_stage_bytes) {
-    char* h = static_cast<char*>(c->h_stage);
-    if (P) memcpy(h, theta_h, (size_t)P * 4);
-    if (batch) memcpy(h + (L.x - L.theta), x_h, x_bytes(c, batch));
-    if (mse) memcpy(h + (L.y - L.theta), y_h, (size_t)batch * 4);
-    QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, st));
-    s = qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, L.loss), at<double>(ws_d, L.E),
-                      at<double>(ws_d, L.grad), ws_d, ws_bytes, stream);
-    if (s != QF_OK) return s;
-    QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, st));
-    QF_CU(cudaStreamSynchronize(st));
-    memcpy(loss_h, h + (L.loss - L.E), 8);
-    if (E_h && batch) memcpy(E_h, h, (size_t)batch * 8);
-    if (P) memcpy(grad_h, h + (L.grad - L.E), (size_t)P * 8);
-    return QF_OK;
-  }
-  if (P) QF_CU(cudaMemcpyAsync(th, theta_h, (size_t)P * 4, cudaMemcpyHostToDevice, st));
-  if (batch) QF_CU(cudaMemcpyAsync(xd, x_h, x_bytes(c, batch), cudaMemcpyHostToDevice, st));
-  if (mse) QF_CU(cudaMemcpyAsync(yd, y_h, (size_t)batch * 4, cudaMemcpyHostToDevice, st));
-  s = qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, L.loss), at<double>(ws_d, L.E),
-                    at<double>(ws_d, L.grad), ws_d, ws_bytes, stream);
-  if (s != QF_OK) return s;
-  QF_CU(cudaMemcpyAsync(loss_h, at<double>(ws_d, L.loss), 8, cudaMemcpyDeviceToHost, st));
-  if (E_h && batch) QF_CU(cudaMemcpyAsync(E_h, at<double>(ws_d, L.E), (size_t)batch * 8, cudaMemcpyDeviceToHost, st));
-  if (P) QF_CU(cudaMemcpyAsync(grad_h, at<double>(ws_d, L.grad), (size_t)P * 8, cudaMemcpyDeviceToHost, st));
-  QF_CU(cudaStreamSynchronize(st));
-  return QF_OK;
+  return train_step_host(c, theta_h, x_h, y_h, batch, loss_kind, obs, loss_h, E_h, grad_h, ws_d, ws_bytes, stream);
 }
 
 qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float* x_d, const float* y_d,
@@ -1101,6 +1287,7 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
                                 double* grad_d, void* stream) {
   if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
   if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan (call qf_plan, host_only is enough)");
+  if (check_precision(c, false) != QF_OK) return QF_ERR_INVALID_ARG;
   if (batch < 0) return fail(QF_ERR_INVALID_ARG, "negative batch");
   if (loss_kind != QF_LOSS_SUM && loss_kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
   if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
@@ -1138,6 +1325,78 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
                                : pg_backward(c, T, L, theta_d, batch, o, dLdE, grad_d, 0, ws, st);
   c->launches = c->call_launches;
   return s;
+}
+
+// ---- complex128 plans ---------------------------------------------------------------
+qf_status qf_forward64(qf_circuit* c, const double* theta_d, const double* x_d, int64_t batch, qf_pauli obs,
+                       double* E_d, void* ws_d, size_t ws_bytes, void* stream) {
+  qf_status s = check_call(c, batch, ws_d, ws_bytes, true);
+  if (s != QF_OK) return s;
+  if ((!theta_d && c->circ.n_params > 0) || (!x_d && batch > 0) || (!E_d && batch > 0))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  Obs o;
+  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+  c->call_launches = 0;
+  s = fused_forward64(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, static_cast<cudaStream_t>(stream));
+  c->launches = c->call_launches;
+  return s;
+}
+
+qf_status qf_backward64(qf_circuit* c, const double* theta_d, const double* x_d, int64_t batch, qf_pauli obs,
+                        const double* dLdE_d, double* grad_d, int32_t per_sample, void* ws_d, size_t ws_bytes,
+                        void* stream) {
+  qf_status s = check_call(c, batch, ws_d, ws_bytes, true);
+  if (s != QF_OK) return s;
+  if ((!theta_d && c->circ.n_params > 0) || (!dLdE_d && batch > 0) || (!grad_d && c->circ.n_params > 0))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  if (!x_d && batch > 0 && c->encoding == QF_ENC_STATE_IN && c->fp.ckpt_mode == 1)
+    return fail(QF_ERR_INVALID_ARG, "checkpoint mode 1 re-runs the forward from the given states: x_d is needed");
+  Obs o;
+  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+  c->call_launches = 0;
+  s = fused_backward64(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE_d, grad_d, per_sample, ws_d,
+                       static_cast<cudaStream_t>(stream));
+  c->launches += c->call_launches;
+  return s;
+}
+
+qf_status qf_loss64(int32_t kind, const double* E_d, const double* y_d, int64_t batch, double* loss_d,
+                    double* dLdE_d, void* stream) {
+  if (kind != QF_LOSS_SUM && kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
+  if (batch < 0 || (batch > 0 && (!E_d || !dLdE_d)) || !loss_d || (kind == QF_LOSS_MSE && batch > 0 && !y_d))
+    return fail(QF_ERR_INVALID_ARG, "bad loss arguments");
+  QF_CU(qf::launch_loss64(kind, E_d, y_d, batch, loss_d, dLdE_d, static_cast<cudaStream_t>(stream)));
+  return QF_OK;
+}
+
+qf_status qf_train_step64(qf_circuit* c, const double* theta_d, const double* x_d, const double* y_d,
+                          int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d,
+                          double* grad_d, void* ws_d, size_t ws_bytes, void* stream) {
+  qf_status s = check_call(c, batch, ws_d, ws_bytes, true);
+  if (s != QF_OK) return s;
+  if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
+      (!grad_d && c->circ.n_params > 0))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  Obs o;
+  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  c->call_launches = 0;
+  // one prep launch fills the forward's and the backward's tables
+  s = fused_forward64(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
+  if (s != QF_OK) return s;
+  double* dLdE = at<double>(ws_d, c->L.dLdE);
+  s = qf_loss64(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+  if (s != QF_OK) return s;
+  c->call_launches++;
+  s = fused_backward64(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
+  c->launches = c->call_launches;
+  return s;
+}
+
+qf_status qf_train_step_host64(qf_circuit* c, const double* theta_h, const double* x_h, const double* y_h,
+                               int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_h, double* E_h,
+                               double* grad_h, void* ws_d, size_t ws_bytes, void* stream) {
+  return train_step_host(c, theta_h, x_h, y_h, batch, loss_kind, obs, loss_h, E_h, grad_h, ws_d, ws_bytes, stream);
 }
 
 }  // extern "C"
@@ -1205,6 +1464,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       const std::string at = " (circuit " + std::to_string(i) + ")";
       if (!c || !c->planned) throw std::invalid_argument("circuit has no plan" + at);
       if (c->encoding != QF_ENC_RY_X) throw std::invalid_argument("batched launches take RY(x) encodings" + at);
+      if (c->f64) throw std::invalid_argument("batched launches are complex64" + at);
       if (c->path == QF_PATH_FUSED && (c->fp.ckpt_mode != 0 || c->tc))
         throw std::invalid_argument("batched launches use checkpoint mode 0 on the CUDA cores" + at);
       if (c->path != QF_PATH_FUSED || !c->fp.rounds)

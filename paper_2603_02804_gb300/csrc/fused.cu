@@ -1126,13 +1126,18 @@ __global__ void prep_kernel(const PrepArgs a) {
 
 namespace {
 
+// Parameter p as float64 (float32 parameters are promoted exactly).
+__device__ __forceinline__ double theta_at(const PrepArgs& a, int p) {
+  return a.theta64 ? a.theta64[p] : (double)a.theta[p];
+}
+
 // Fused 2x2 product of fused entry m (float64, rounded once to float32).
 __device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1, double* u64 = nullptr) {
   double u[2][2][2] = {{{1, 0}, {0, 0}}, {{0, 0}, {1, 0}}};  // [row][col][re/im]
   for (int j = a.fuse_off[m]; j < a.fuse_off[m + 1]; ++j) {
     const FuseGate fg = a.fuse_gates[j];
     double s, c;
-    sincos(0.5 * (fg.param >= 0 ? (double)a.theta[fg.param] : fg.angle), &s, &c);
+    sincos(0.5 * (fg.param >= 0 ? theta_at(a, fg.param) : fg.angle), &s, &c);
     // g = c I - i s P
     double g[2][2][2];
     if (fg.kind == G_RX) {
@@ -1171,7 +1176,7 @@ __device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1, do
 // A term's angle is the sum of its parameters (a merged run of RZ gates).
 __device__ double term_angle(const PrepArgs& a, int64_t t) {
   double phi = a.term_const ? a.term_const[t] : 0.0;
-  for (int j = a.term_off[t]; j < a.term_off[t + 1]; ++j) phi += (double)a.theta[a.term_params[j]];
+  for (int j = a.term_off[t]; j < a.term_off[t + 1]; ++j) phi += theta_at(a, a.term_params[j]);
   return phi;
 }
 
@@ -1194,13 +1199,22 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
 // programs) the forward and backward round parameters in round order.
 __device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (i < a.n_fused) {
-    fused_u(a, i, a.mats[2 * i], a.mats[2 * i + 1], a.mats64 ? a.mats64 + 8 * i : nullptr);
+    float4 m0, m1;
+    fused_u(a, i, m0, m1, a.mats64 ? a.mats64 + 8 * i : nullptr);
+    if (a.mats) {
+      a.mats[2 * i] = m0;
+      a.mats[2 * i + 1] = m1;
+    }
     return;
   }
   i -= a.n_fused;
   if (i < a.n_terms) {
     if (a.shear) {
       a.shear[i] = term_shear_of(a, (int32_t)i);
+    } else if (a.cs64) {
+      double s, c;
+      sincos(0.5 * term_angle(a, i), &s, &c);
+      a.cs64[i] = make_double2(c, s);
     } else {
       double s, c;
       sincos(0.5 * term_angle(a, i), &s, &c);
@@ -1212,13 +1226,10 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (i < (int64_t)a.B * a.n_eff) {
     const int64_t bb = i / a.n_eff;
     const int q = (int)(i - bb * a.n_eff);
-    if (q < a.n) {
-      double s, c;
-      sincos(0.5 * (double)a.x[bb * a.n + q], &s, &c);
-      a.enc[i] = make_float2((float)c, (float)s);
-    } else {
-      a.enc[i] = make_float2(1.f, 0.f);  // padding qubit stays |0>
-    }
+    double s = 0.0, c = 1.0;  // a padding qubit stays |0>
+    if (q < a.n) sincos(0.5 * (a.x64 ? a.x64[bb * a.n + q] : (double)a.x[bb * a.n + q]), &s, &c);
+    if (a.enc64) a.enc64[i] = make_double2(c, s);
+    else a.enc[i] = make_float2((float)c, (float)s);
     return;
   }
   i -= (int64_t)a.B * a.n_eff;
@@ -1272,9 +1283,10 @@ __global__ void g_reduce_kernel(const GradReduceArgs a) {
   if (lane == 0) a.grad[out] = s;
 }
 
-// Loss and dL/dE in one block, fixed-order tree reduction.
-__global__ void loss_kernel(int kind, const double* E, const float* y, int64_t B, double* loss,
-                            double* dLdE) {
+// Loss and dL/dE in one block, fixed-order tree reduction (labels float32,
+// or float64 for complex128 plans).
+template <class Y>
+__global__ void loss_kernel(int kind, const double* E, const Y* y, int64_t B, double* loss, double* dLdE) {
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
@@ -1456,13 +1468,7 @@ __global__ void batch_loss_kernel(const BatchArgs a) {
   if (threadIdx.x == 0) a.loss[0] = red[0];
 }
 
-// Opt a kernel in to `smem` bytes of dynamic shared memory on the current
-// device, once per device (the call is idempotent, so two threads racing on a
-// first launch only repeat it; devices past the table are opted in every time).
-struct OptIn {
-  std::atomic<bool> done[64] = {};
-};
-static cudaError_t opt_in(const void* fn, size_t smem, OptIn& o) {
+cudaError_t opt_in(const void* fn, size_t smem, OptIn& o) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1667,7 +1673,13 @@ cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st) {
 
 cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
                         cudaStream_t st) {
-  loss_kernel<<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE);
+  loss_kernel<float><<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss64(int kind, const double* E, const double* y, int64_t B, double* loss, double* dLdE,
+                          cudaStream_t st) {
+  loss_kernel<double><<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "qf_internal.h"
 
 namespace qf {
@@ -38,10 +40,11 @@ struct PassArgs {
 
 struct PrepArgs {
   const float* theta;
+  const double* theta64;       // if non-null: float64 parameters (complex128 plans), theta unused
   int32_t n_fused;
   const int32_t* fuse_off;
   const FuseGate* fuse_gates;
-  float4* mats;
+  float4* mats;                // may be null (complex128 plans need only mats64)
   double* mats64;              // if non-null: the fused 2x2s in float64 too, 8 doubles each
   int32_t n_terms;
   const int32_t* term_off;     // CSR term -> parameters (angles summed)
@@ -50,10 +53,13 @@ struct PrepArgs {
   float2* cs;                  // (cos, sin) of phi/2 per term, or
   float4* shear;               // if non-null instead: (tan(w/4), sin(w/2), wrap parity, 0),
                                // w = phi wrapped into (-pi, pi], phi = w + 2 pi k
+  double2* cs64;               // if non-null instead: (cos, sin) of phi/2 in float64
   const float* x;
+  const double* x64;           // if non-null: float64 encoding angles, x unused
   int64_t B;
   int32_t n, n_eff;
   float2* enc;
+  double2* enc64;              // if non-null instead of enc: (cos, sin) of x/2 in float64
   // round programs: the parameters of every round gathered in round order
   int32_t n_rpf;               // forward rounds
   const uint4* rpf_src;        // forward round records (fused index per item)
@@ -97,6 +103,50 @@ cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E,
 cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st);
 cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
                         cudaStream_t st);
+// The same with float64 labels (complex128 plans).
+cudaError_t launch_loss64(int kind, const double* E, const double* y, int64_t B, double* loss, double* dLdE,
+                          cudaStream_t st);
+
+// Opt a kernel in to `smem` bytes of dynamic shared memory on the current
+// device, once per device (idempotent; two threads racing on a first launch
+// only repeat the call; devices past the table are opted in every time).
+struct OptIn {
+  std::atomic<bool> done[64] = {};
+};
+cudaError_t opt_in(const void* fn, size_t smem, OptIn& o);
+
+// ---- complex128 passes --------------------------------------------------------
+// Arguments of a complex128 pass: the generic step programs of PassArgs with
+// float64 tables and states. Round programs and the tensor-core path are
+// complex64 only.
+struct PassArgs64 {
+  PassDesc pd;
+  int32_t n_eff;
+  int32_t tps_log2;       // log2(tiles per sample) = n_eff - K
+  int64_t B;
+  const uint2* ops;       // program of this direction (generic steps)
+  const double2* mats;    // fused 2x2 matrices, 4 double2 each: u00, u01, u10, u11
+  const double2* cs;      // (cos, sin) of phi/2 per gradient term
+  const double2* enc;     // (cos, sin) of x/2, [B][n_eff]
+  const double2* psi_in;  // given initial states [B][2^n_in] (QF_ENC_STATE_IN), else null
+  int32_t n_in;
+  double2* work;          // working state [B][2^n_eff]
+  double2* lam;           // adjoint state [B][2^n_eff]
+  double2* slots;         // checkpoint states [n_ckpt][slot_stride]
+  float2* fslots;         // complex64 pass-output slots (PF_SRC_H / PF_DST_H, memory-saving mode)
+  int64_t slot_stride;
+  uint32_t z_mask;
+  uint32_t y_count;
+  const double* dLdE;
+  double* e_part;         // [B * tiles per sample]
+  double* g_part;         // [B * tiles per sample][n_slots]
+  int32_t n_slots;
+};
+cudaError_t launch_pass64(bool bwd, const PassArgs64& a, cudaStream_t st);
+cudaError_t launch_expect_full64(const double2* psi, int n_eff, int64_t B, int64_t rows, uint32_t xm, uint32_t zm,
+                                 uint32_t yc, double* e_part, cudaStream_t st);
+cudaError_t launch_seed_full64(const double2* psi, double2* lam, int n_eff, int64_t B, uint32_t xm, uint32_t zm,
+                               uint32_t yc, const double* dLdE, cudaStream_t st);
 
 // ---- batched persistent launch ------------------------------------------------
 // Pointers into the workspace are stored as byte offsets from its base and

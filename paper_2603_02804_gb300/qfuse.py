@@ -20,6 +20,7 @@ QF_ENT_CHAIN, QF_ENT_RING = 0, 1
 QF_ENC_RY_X, QF_ENC_STATE_IN = 0, 1
 QF_PATH_FUSED, QF_PATH_PER_GATE = 0, 1
 QF_LOSS_SUM, QF_LOSS_MSE = 0, 1
+QF_PREC_C64, QF_PREC_C128 = 0, 1
 
 STATUS_NAMES = {0: "QF_OK", 1: "QF_ERR_INVALID_ARG", 2: "QF_ERR_UNSUPPORTED", 3: "QF_ERR_WORKSPACE",
                 4: "QF_ERR_OOM", 5: "QF_ERR_CUDA", 6: "QF_ERR_TIMEOUT"}
@@ -44,7 +45,7 @@ class qf_plan_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("ckpt_layers", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("program", ctypes.c_int32), ("ckpt_mode", ctypes.c_int32),
                 ("mem_save", ctypes.c_int32), ("tc_path", ctypes.c_int32), ("no_host_staging", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class qf_plan_info_t(ctypes.Structure):
@@ -52,7 +53,7 @@ class qf_plan_info_t(ctypes.Structure):
         "n_qubits", "n_eff", "n_params", "n_slots", "path", "tile_bits", "n_passes", "n_steps",
         "n_fused_ops", "n_ckpt", "ckpt_layers", "launches_fwd", "launches_bwd")] + [
         ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64)] + [
-        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "tc_path")]
+        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "tc_path", "precision")]
 
 
 _vp = ctypes.c_void_p
@@ -78,6 +79,11 @@ SIGNATURES = {
     "qf_train_step": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
     "qf_train_step_host": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
     "qf_train_step_noalloc": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp], _i32),
+    "qf_forward64": ([_vp, _vp, _vp, _i64, qf_pauli, _vp, _vp, _sz, _vp], _i32),
+    "qf_backward64": ([_vp, _vp, _vp, _i64, qf_pauli, _vp, _vp, _i32, _vp, _sz, _vp], _i32),
+    "qf_loss64": ([_i32, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "qf_train_step64": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
+    "qf_train_step_host64": ([_vp, _vp, _vp, _vp, _i64, _i32, qf_pauli, _vp, _vp, _vp, _vp, _sz, _vp], _i32),
     "qf_batch_create": ([_i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(qf_pauli), _i32,
                          ctypes.POINTER(_sz), ctypes.POINTER(_vp)], _i32),
     "qf_batch_layout": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i32),
@@ -177,9 +183,9 @@ def qf_circuit_destroy(handle: int) -> None:
 
 def qf_plan(handle: int, batch: int, path: int = QF_PATH_FUSED, tile_bits: int = 0, ckpt_layers: int = 0,
             host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False,
-            tc_path: bool = False, host_staging: bool = True) -> int:
+            tc_path: bool = False, host_staging: bool = True, precision: int = QF_PREC_C64) -> int:
     o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program), int(ckpt_mode), int(mem_save),
-                     int(tc_path), int(not host_staging))
+                     int(tc_path), int(not host_staging), int(precision))
     ws = _sz()
     _check(load().qf_plan(handle, ctypes.byref(o), batch, ctypes.byref(ws)))
     return ws.value
@@ -194,11 +200,11 @@ def qf_mem_model(k: float, d: float, b: float):
 
 def qf_plan_fit(handle: int, batch: int, mem_bytes: int, path: int = QF_PATH_FUSED, tile_bits: int = 0,
                 host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False,
-                tc_path: bool = False, host_staging: bool = True):
+                tc_path: bool = False, host_staging: bool = True, precision: int = QF_PREC_C64):
     """Plan with a checkpoint interval that fits mem_bytes (mode 0: the smallest;
     mode 1: the one with the smallest workspace): (c, workspace bytes)."""
     o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program), int(ckpt_mode), int(mem_save),
-                     int(tc_path), int(not host_staging))
+                     int(tc_path), int(not host_staging), int(precision))
     c = _i32()
     ws = _sz()
     _check(load().qf_plan_fit(handle, ctypes.byref(o), batch, mem_bytes, ctypes.byref(c), ctypes.byref(ws)))
@@ -251,6 +257,32 @@ def qf_train_step_noalloc(handle, theta, x, y, batch, loss_kind, obs, loss, E, g
 
 
 QF_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
+
+
+# complex128 plans (precision=QF_PREC_C128): float64 theta, x, y
+def qf_forward64(handle, theta, x, batch, obs: qf_pauli, E, ws, ws_bytes, stream=None) -> None:
+    _check(load().qf_forward64(handle, _ptr(theta), _ptr(x), batch, obs, _ptr(E), _ptr(ws), ws_bytes,
+                               _stream(stream)))
+
+
+def qf_backward64(handle, theta, x, batch, obs: qf_pauli, dLdE, grad, per_sample, ws, ws_bytes,
+                  stream=None) -> None:
+    _check(load().qf_backward64(handle, _ptr(theta), _ptr(x), batch, obs, _ptr(dLdE), _ptr(grad), int(per_sample),
+                                _ptr(ws), ws_bytes, _stream(stream)))
+
+
+def qf_loss64(kind, E, y, batch, loss, dLdE, stream=None) -> None:
+    _check(load().qf_loss64(kind, _ptr(E), _ptr(y), batch, _ptr(loss), _ptr(dLdE), _stream(stream)))
+
+
+def qf_train_step64(handle, theta, x, y, batch, loss_kind, obs, loss, E, grad, ws, ws_bytes, stream=None) -> None:
+    _check(load().qf_train_step64(handle, _ptr(theta), _ptr(x), _ptr(y), batch, loss_kind, obs, _ptr(loss),
+                                  _ptr(E), _ptr(grad), _ptr(ws), ws_bytes, _stream(stream)))
+
+
+def qf_train_step_host64(handle, theta, x, y, batch, loss_kind, obs, loss, E, grad, ws, ws_bytes, stream=None):
+    _check(load().qf_train_step_host64(handle, _ptr(theta), _ptr(x), _ptr(y), batch, loss_kind, obs, _ptr(loss),
+                                       _ptr(E), _ptr(grad), _ptr(ws), ws_bytes, _stream(stream)))
 
 
 def qf_batch_create(circuits, batch, obs, loss_kind=QF_LOSS_SUM):

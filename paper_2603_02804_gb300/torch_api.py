@@ -20,6 +20,7 @@ _PATHS = {"fused": qfuse.QF_PATH_FUSED, "per_gate": qfuse.QF_PATH_PER_GATE}
 _ENT = {"chain": qfuse.QF_ENT_CHAIN, "ring": qfuse.QF_ENT_RING}
 _LOSS = {"sum": qfuse.QF_LOSS_SUM, "mse": qfuse.QF_LOSS_MSE}
 _ENC = {"angles": qfuse.QF_ENC_RY_X, "state": qfuse.QF_ENC_STATE_IN}
+_PREC = {"complex64": qfuse.QF_PREC_C64, "complex128": qfuse.QF_PREC_C128}
 _ids = itertools.count(1)
 
 
@@ -37,16 +38,21 @@ class Simulator:
     1 re-runs each checkpoint block's forward storing the pass outputs
     (bfloat16 with ``mem_save``), as in the paper's checkpointed scheme.
     ``tc_path`` runs the forward rounds as split-precision blocks on the
-    tensor cores (12-qubit tiles, n >= 12).
+    tensor cores (12-qubit tiles, n >= 12). ``precision="complex128"``
+    simulates complex128 states in float64 arithmetic; theta, x (and y) are
+    then float64 (states: complex128) and the *64 entry points run.
     """
 
     def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
                  tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
                  device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False,
-                 encoding: str = "angles", host_staging: bool = True):
+                 encoding: str = "angles", host_staging: bool = True, precision: str = "complex64"):
         _cuda_check()
         self.device = torch.device(device or "cuda")
         self.encoding = encoding
+        self.f64 = _PREC[precision] == qfuse.QF_PREC_C128
+        self.real = torch.float64 if self.f64 else torch.float32
+        self.cplx = torch.complex128 if self.f64 else torch.complex64
         if gates is None:
             self.handle = qfuse.qf_hea_create(n, d, _ENT[entangler], _ENC[encoding])
             self.n_params = 3 * n * d
@@ -59,7 +65,7 @@ class Simulator:
         with torch.cuda.device(self.device):
             self.ws_bytes = qfuse.qf_plan(self.handle, batch, _PATHS[path], tile_bits, ckpt_layers,
                                           ckpt_mode=ckpt_mode, mem_save=mem_save, tc_path=tc_path,
-                                          host_staging=host_staging)
+                                          host_staging=host_staging, precision=_PREC[precision])
             self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
         self.batch = batch
         self._fwd_id = 0
@@ -84,13 +90,13 @@ class Simulator:
 
     def _check(self, theta, x):
         if self.encoding == "state":
-            # initial states: complex64 [B, 2^n] (passed to the library as float32 pairs)
-            if x.dtype != torch.complex64 or x.dim() != 2 or x.shape[1] != 1 << self.n:
-                raise TypeError("x must be complex64 [B, 2^n] initial states")
-        elif x.dtype != torch.float32 or x.dim() != 2 or x.shape[1] != self.n:
-            raise TypeError("x must be float32 [B, n] encoding angles")
-        if theta.dtype != torch.float32:
-            raise TypeError("theta must be float32")
+            # initial states [B, 2^n] (passed to the library as (re, im) pairs)
+            if x.dtype != self.cplx or x.dim() != 2 or x.shape[1] != 1 << self.n:
+                raise TypeError(f"x must be {self.cplx} [B, 2^n] initial states")
+        elif x.dtype != self.real or x.dim() != 2 or x.shape[1] != self.n:
+            raise TypeError(f"x must be {self.real} [B, n] encoding angles")
+        if theta.dtype != self.real:
+            raise TypeError(f"theta must be {self.real}")
         if not (theta.is_cuda and x.is_cuda and theta.is_contiguous() and x.is_contiguous()):
             raise ValueError("theta and x must be contiguous CUDA tensors")
         if theta.numel() != self.n_params or x.shape[0] > self.batch:
@@ -101,7 +107,8 @@ class Simulator:
         self._check(theta, x)
         B = x.shape[0]
         E = torch.empty(B, dtype=torch.float64, device=self.device)
-        qfuse.qf_forward(self.handle, theta, x, B, self.obs, E, self.ws, self.ws_bytes, self._stream())
+        fn = qfuse.qf_forward64 if self.f64 else qfuse.qf_forward
+        fn(self.handle, theta, x, B, self.obs, E, self.ws, self.ws_bytes, self._stream())
         self._fwd_id = next(_ids)
         return E
 
@@ -112,8 +119,8 @@ class Simulator:
         dLdE = dLdE.to(device=self.device, dtype=torch.float64).contiguous()
         shape = (B, self.n_params) if per_sample else (self.n_params,)
         g = torch.empty(shape, dtype=torch.float64, device=self.device)
-        qfuse.qf_backward(self.handle, theta, x, B, self.obs, dLdE, g, per_sample, self.ws, self.ws_bytes,
-                          self._stream())
+        fn = qfuse.qf_backward64 if self.f64 else qfuse.qf_backward
+        fn(self.handle, theta, x, B, self.obs, dLdE, g, per_sample, self.ws, self.ws_bytes, self._stream())
         return g
 
     def train_step(self, theta, x, y=None, loss: str = "sum"):
@@ -123,8 +130,10 @@ class Simulator:
         out_loss = torch.empty(1, dtype=torch.float64, device=self.device)
         E = torch.empty(B, dtype=torch.float64, device=self.device)
         g = torch.empty(self.n_params, dtype=torch.float64, device=self.device)
-        qfuse.qf_train_step(self.handle, theta, x, y, B, _LOSS[loss], self.obs, out_loss, E, g, self.ws,
-                            self.ws_bytes, self._stream())
+        if y is not None and (y.dtype != self.real or not y.is_cuda):
+            raise TypeError(f"y must be a {self.real} CUDA tensor")
+        fn = qfuse.qf_train_step64 if self.f64 else qfuse.qf_train_step
+        fn(self.handle, theta, x, y, B, _LOSS[loss], self.obs, out_loss, E, g, self.ws, self.ws_bytes, self._stream())
         self._fwd_id = next(_ids)
         return out_loss, E, g
 
@@ -134,8 +143,9 @@ class Simulator:
         out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
         E = torch.empty(B, dtype=torch.float64).pin_memory()
         g = torch.empty(self.n_params, dtype=torch.float64).pin_memory()
-        qfuse.qf_train_step_host(self.handle, theta_h, x_h, y_h, B, _LOSS[loss], self.obs, out_loss, E, g,
-                                 self.ws, self.ws_bytes, self._stream())
+        fn = qfuse.qf_train_step_host64 if self.f64 else qfuse.qf_train_step_host
+        fn(self.handle, theta_h, x_h, y_h, B, _LOSS[loss], self.obs, out_loss, E, g, self.ws, self.ws_bytes,
+           self._stream())
         self._fwd_id = next(_ids)
         return out_loss, E, g
 
@@ -168,15 +178,15 @@ class HEA(torch.nn.Module):
     """Hardware-efficient ansatz with RY(x) encoding, returning <O> per sample."""
 
     def __init__(self, n: int, d: int, max_batch: int, *, obs="Z", entangler="chain", path="fused",
-                 ckpt_layers: int = 0, tile_bits: int = 0, device=None, init=None):
+                 ckpt_layers: int = 0, tile_bits: int = 0, device=None, init=None, precision: str = "complex64"):
         super().__init__()
         self.sim = Simulator(n, d, max_batch, entangler=entangler, path=path, tile_bits=tile_bits,
-                             ckpt_layers=ckpt_layers, obs=obs, device=device)
-        theta = init if init is not None else torch.rand(3 * n * d) * (2 * torch.pi)
-        self.theta = torch.nn.Parameter(theta.to(device=self.sim.device, dtype=torch.float32))
+                             ckpt_layers=ckpt_layers, obs=obs, device=device, precision=precision)
+        theta = init if init is not None else torch.rand(3 * n * d, dtype=self.sim.real) * (2 * torch.pi)
+        self.theta = torch.nn.Parameter(theta.to(device=self.sim.device, dtype=self.sim.real))
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        return QFuseFn.apply(self.theta, x.to(device=self.sim.device, dtype=torch.float32), self.sim)
+        return QFuseFn.apply(self.theta, x.to(device=self.sim.device, dtype=self.sim.real), self.sim)
 
 
 class Batch:

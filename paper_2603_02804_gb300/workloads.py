@@ -74,12 +74,13 @@ def draw_labels(B: int, seed: int) -> np.ndarray:
     return (2 * rng.integers(0, 2, size=B) - 1).astype(np.float32)
 
 
-def draw_state(B: int, n: int, seed: int) -> np.ndarray:
-    """Random normalised initial states (complex Gaussian), complex64 [B, 2^n]."""
+def draw_state(B: int, n: int, seed: int, dtype=np.complex64) -> np.ndarray:
+    """Random normalised initial states (complex Gaussian), [B, 2^n] of
+    `dtype` (complex64, or complex128 for complex128 plans)."""
     rng = np.random.default_rng(seed)
     z = rng.standard_normal((B, 1 << n)) + 1j * rng.standard_normal((B, 1 << n))
     z /= np.linalg.norm(z, axis=1, keepdims=True)
-    return z.astype(np.complex64)
+    return z.astype(dtype)
 
 
 def make_inputs(w: Workload, B: int | None = None):
