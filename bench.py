@@ -35,6 +35,8 @@ from paper_2603_02804_gb300 import workloads  # noqa: E402
 WORKLOAD = "hea12"
 FP32_LANES_PER_SM = 128
 N_SM = 152
+# GB300's dense FP64 rate (the complex128 path's denominator), TFLOP/s nominal
+FP64_TFLOPS_NOMINAL = 1.25
 # DRAM bytes (read + write) of one adjoint pass launch from an ncu capture of the current kernel build
 # (profiles/pass_kernels_hea12.md); None where no capture of the current build exists.
 ADJOINT_TRAFFIC_BYTES = {"hea12": 16_860_160}
@@ -58,6 +60,8 @@ def parse():
     ap.add_argument("--ckpt-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--mem-save", action="store_true", help="checkpoint mode 1 with bfloat16 pass outputs")
     ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core / mode-1 variant timings")
+    ap.add_argument("--precision", default="complex64", choices=["complex64", "complex128"],
+                    help="state precision of the timed step (complex128: float64 inputs and arithmetic)")
     return ap.parse_args()
 
 
@@ -103,6 +107,15 @@ def algorithmic_flops(n, d, B):
     fwd = n * d * pairs * 28
     bwd = (2 * n * d + n) * pairs * 32
     return fwd, bwd
+
+
+def generic_flops(info, n, B):
+    """(forward, adjoint) flops per step of generic step programs (the complex128
+    passes): one fused complex 2x2 per fused entry (28 flops per pair of
+    amplitudes) and one gradient term per rotation (un-apply psi and lambda and
+    Im<lambda|P|psi>: 32 flops per pair)."""
+    pairs = B * (1 << (max(n, 4) - 1))
+    return info["n_fused_ops"] * pairs * 28, info["n_slots"] * pairs * 32
 
 
 class ClockSampler:
@@ -574,31 +587,38 @@ def main():
     if rank > 0:
         x_np = workloads.draw_x(w.B, w.n, w.seeds[1] + 1000 * rank)
     dev = torch.device("cuda", local)
+    c128 = args.precision == "complex128"
+    if c128:  # float64 inputs (the float32 draws, promoted exactly)
+        theta_np, x_np = theta_np.astype(np.float64), x_np.astype(np.float64)
+        y_np = None if y_np is None else y_np.astype(np.float64)
     theta = torch.from_numpy(theta_np).to(dev)
     x = torch.from_numpy(x_np).to(dev)
     y = torch.from_numpy(y_np).to(dev) if y_np is not None else None
     ckpt = w.ckpt_layers or 0
     opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
+    if c128:
+        opts["precision"] = "complex128"
     sim = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs, **opts)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     from paper_2603_02804_gb300 import dp
 
-    def step(s):
-        loss, E, g = s.train_step(theta, x, y, loss=w.loss)
+    def step(s, inp=None):
+        th_, x_, y_ = inp if inp is not None else (theta, x, y)
+        loss, E, g = s.train_step(th_, x_, y_, loss=w.loss)
         if world > 1:
             dp.allreduce_sum(g)  # data-parallel gradient sum over ranks (NCCL)
         return g
 
-    def timed(s, K):
+    def timed(s, K, inp=None):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         launches = 0
         for k in range(K):
             flush.fill_(k & 255)  # evict the state from L2 between timed steps
             starts[k].record(stream)
-            step(s)
+            step(s, inp)
             ends[k].record(stream)
             launches += s.launches()
         torch.cuda.synchronize()
@@ -629,21 +649,26 @@ def main():
     # ---- roofline of the dominant kernel: the fused adjoint pass kernel
     fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, w.B)
     info = sim.info()
+    if c128:
+        fwd_fl, bwd_fl = generic_flops(info, w.n, w.B)
     bwd_launch_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
     fwd_launch_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
     bwd_per_launch = bwd_fl / info["n_passes"]
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    alu_peak = FP64_TFLOPS_NOMINAL if c128 else fp32_peak
     achieved = bwd_per_launch / (bwd_launch_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak,
-                "traffic": ADJOINT_TRAFFIC_BYTES.get(w.name) if not (args.tc or args.ckpt_mode) else None,
-                "kernel": "pass_kernel<true> (fused adjoint)",
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak,
+                "traffic": ADJOINT_TRAFFIC_BYTES.get(w.name) if not (args.tc or args.ckpt_mode or c128) else None,
+                "kernel": ("pass64_kernel<true> (fused adjoint, complex128)" if c128
+                           else "pass_kernel<true> (fused adjoint)"),
+                "peak_source": ("GB300 dense FP64, nominal" if c128 else
+                                f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz"),
                 "fwd_kernel": {"achieved": (fwd_fl / info["n_passes"]) / (fwd_launch_ms / 1e3) / 1e12,
                                "ms": fwd_launch_ms},
                 "bwd_kernel_ms": bwd_launch_ms}
-    state_bytes = w.B * (1 << w.n) * 8
+    state_bytes = w.B * (1 << w.n) * (16 if c128 else 8)
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     hbm = {"algorithmic_bytes_per_step": 4 * state_bytes,
            "achieved_gbs": 4 * state_bytes / (ms_per_step / 1e3) / 1e9,
@@ -651,35 +676,53 @@ def main():
            "frac": 4 * state_bytes / (ms_per_step / 1e3) / 1e9 / hbm_gbs,
            "note": "state of this workload fits in L2; the path is ALU-bound, see roofline"}
 
-    # ---- the same step with the tensor-core forward and with checkpoint mode 1
+    # ---- the same step with the tensor-core forward, with checkpoint mode 1 and
+    # in complex128 (float64 inputs, its own FP64 roofline)
     variants = None
     if not args.no_variants and world == 1:
         variants = {}
+        inp64 = tuple(None if v is None else v.double() for v in (theta, x, y))
         for name, kw in (("tc_path", dict(tc_path=True)), ("ckpt_mode_1", dict(ckpt_mode=1)),
-                         ("ckpt_mode_1_mem_save", dict(ckpt_mode=1, mem_save=True))):
+                         ("ckpt_mode_1_mem_save", dict(ckpt_mode=1, mem_save=True)),
+                         ("complex128", dict(precision="complex128"))):
             if kw == opts:
                 continue
+            c128 = kw.get("precision") == "complex128"
+            inp = inp64 if c128 else None
             try:
                 vs = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs, **kw)
             except qfuse.QFError as err:
                 variants[name] = {"unavailable": str(err)}
                 continue
             for _ in range(args.warmup):
-                step(vs)
+                step(vs, inp)
             torch.cuda.synchronize()
             qfuse.qf_profile(vs.handle, True)
             qfuse.qf_profile_read(vs.handle)
-            K = min(args.steps, 200)
-            v_ms, _ = timed(vs, K)
+            K = min(args.steps, 50 if c128 else 200)
+            v_ms, _ = timed(vs, K, inp)
             vp = qfuse.qf_profile_read(vs.handle)
             variants[name] = {"value": w.B * K / (v_ms / 1e3), "unit": "samples/s", "ms_per_step": v_ms / K,
                               "fwd_ms_per_step": vp["fwd_ms"] / K, "bwd_ms_per_step": vp["bwd_ms"] / K,
                               "device_status": qfuse.qf_device_status(stream)}
+            if c128:
+                vi = vs.info()
+                f_fl, b_fl = generic_flops(vi, w.n, w.B)
+                b_ms = vp["bwd_ms"] / max(vp["bwd_launches"], 1)
+                f_ms = vp["fwd_ms"] / max(vp["fwd_launches"], 1)
+                ach = b_fl / vi["n_passes"] / (b_ms / 1e3) / 1e12
+                variants[name]["dtype"] = "f64"
+                variants[name]["roofline"] = {
+                    "bound": "alu", "kernel": "pass64_kernel<true> (fused adjoint, complex128)",
+                    "achieved": ach, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                    "frac": ach / FP64_TFLOPS_NOMINAL, "peak_source": "GB300 dense FP64, nominal",
+                    "fwd_kernel": {"achieved": f_fl / vi["n_passes"] / (f_ms / 1e3) / 1e12, "ms": f_ms},
+                    "bwd_kernel_ms": b_ms}
             del vs
 
-    # ---- unfused per-gate comparator on the same GPU
+    # ---- unfused per-gate comparator on the same GPU (complex64 only)
     per_gate = None
-    if not args.no_per_gate:
+    if not args.no_per_gate and not c128:
         pg = Simulator(w.n, w.d, w.B, path="per_gate", ckpt_layers=ckpt, obs=w.obs)
         for _ in range(args.warmup):
             step(pg)
@@ -713,12 +756,13 @@ def main():
         line = {
             "metric": "fwd+grad samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if c128 else "f32",
             "data": "synthetic (seeded): theta~U[0,2pi), x~U[0,pi]^n, y~{-1,+1}",
             "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} [RZ,RY,RZ + CZ chain], RY(x) encoding, "
                                    f"batch={w.B}/GPU, loss={w.loss}, obs=Z0",
                        "path": "fused", "tile_bits": info["tile_bits"], "passes": info["n_passes"],
                        "tc_path": bool(args.tc), "ckpt_mode": args.ckpt_mode, "mem_save": bool(args.mem_save),
+                       "precision": args.precision,
                        "ckpt_layers": info["ckpt_layers"], "parallelism": f"dp{world}",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "per_gate": per_gate,

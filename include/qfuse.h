@@ -139,8 +139,9 @@ typedef struct {
                           (x, theta, y and outputs of qf_train_step_host, which
                           then fails); for device-resident inputs of large states */
   int32_t precision;   /* QF_PREC_C64 (default) or QF_PREC_C128. complex128 needs
-                          the fused path and runs generic steps (program 1) on the
-                          CUDA cores; tc_path must be 0. With ckpt_mode 1 and
+                          the fused path and runs the same programs (round or
+                          generic steps) in float64 on the CUDA cores; tc_path
+                          must be 0. With ckpt_mode 1 and
                           mem_save the stored pass outputs are complex64 (float32
                           re, im; the paper's memory-saving mode halves the
                           precision of stored states). Checkpoints, psi_M and

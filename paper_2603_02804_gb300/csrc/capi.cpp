@@ -172,8 +172,10 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     if (c->f64) L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
     else L.mats = take((size_t)std::max(n_fused, 0) * 32);
     if (c->fp.rounds) {
-      L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * 128);
-      L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * 128);
+      // 8 shear parameters per round: float4 (complex64) or Shear64 (complex128)
+      const size_t per = 8 * (c->f64 ? sizeof(qf::Shear64) : 16);
+      L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * per);
+      L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * per);
     }
     if (c->tc) {
       L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
@@ -543,6 +545,8 @@ qf::PassArgs64 pass_args64(const qf_circuit* c, const Layout& L, void* ws, int64
   a.B = B;
   a.mats = at<double2>(ws, L.mats64);
   a.cs = at<double2>(ws, L.cs);
+  a.rounds = nullptr;
+  a.rpar = nullptr;
   a.enc = at<double2>(ws, L.enc);
   a.n_in = c->circ.n;
   a.work = at<double2>(ws, L.work);
@@ -575,18 +579,38 @@ qf::PrepArgs prep_args64(const qf_circuit* c, const DevTables& T, const Layout& 
   return pa;
 }
 
+// The backward round parameters of a complex128 round program.
+void set_rounds64(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, qf::PrepArgs& pa) {
+  pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
+  pa.rpb_src = T.bwd_rounds;
+  pa.rpb64 = at<qf::Shear64>(ws, L.rpb);
+}
+
 qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, const double* theta, const double* x,
                           int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false) {
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa = prep_args64(c, T, L, ws, theta);
-  pa.n_fused = (int32_t)P.fuse_off.size() - 1;
-  pa.n_terms = with_terms ? P.n_terms : 0;
+  if (P.rounds) {
+    // round programs: the forward's and (with_terms) the backward's round parameters
+    pa.n_fused = 0;
+    pa.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
+    pa.rpf_src = T.fwd_rounds;
+    pa.rpf64 = at<qf::Shear64>(ws, L.rpf);
+    if (with_terms) set_rounds64(c, T, L, ws, pa);
+  } else {
+    pa.n_fused = (int32_t)P.fuse_off.size() - 1;
+    pa.n_terms = with_terms ? P.n_terms : 0;
+  }
   pa.x64 = x;
   pa.B = c->encoding == QF_ENC_RY_X ? B : 0;
   QF_CU(qf::launch_prep(pa, st));
   c->call_launches++;
   qf::PassArgs64 a = pass_args64(c, L, ws, B, o);
   a.ops = T.fwd_ops;
+  if (P.rounds) {
+    a.rounds = T.fwd_rounds;
+    a.rpar = at<qf::Shear64>(ws, L.rpf);
+  }
   a.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const double2*>(x) : nullptr;
   const int prof = prof_begin(c, st);
   int32_t full_expect = -1;
@@ -617,13 +641,18 @@ qf_status fused_backward64(qf_circuit* c, const DevTables& T, const Layout& L, c
   const qf::FusedPlan& P = c->fp;
   if (with_prep) {
     qf::PrepArgs pa = prep_args64(c, T, L, ws, theta);
-    pa.n_terms = P.n_terms;
+    if (P.rounds) set_rounds64(c, T, L, ws, pa);
+    else pa.n_terms = P.n_terms;
     QF_CU(qf::launch_prep(pa, st));
     c->call_launches++;
   }
   qf::PassArgs64 a = pass_args64(c, L, ws, B, o);
   a.ops = T.bwd_ops;
   a.dLdE = dLdE;
+  if (P.rounds) {
+    a.rounds = T.bwd_rounds;
+    a.rpar = at<qf::Shear64>(ws, L.rpb);
+  }
   auto seed = [&](const qf::PassArgs64& p) -> cudaError_t {
     c->call_launches++;
     return qf::launch_seed_full64(p.slots + (int64_t)p.pd.psi_src * p.slot_stride, p.lam, P.n_eff, B, o.x, o.z,
@@ -634,6 +663,10 @@ qf_status fused_backward64(qf_circuit* c, const DevTables& T, const Layout& L, c
     // checkpoint mode A: forward re-runs interleaved with adjoint passes
     qf::PassArgs64 f = a;
     f.ops = T.fwd_ops;
+    if (P.rounds) {
+      f.rounds = T.fwd_rounds;
+      f.rpar = at<qf::Shear64>(ws, L.rpf);
+    }
     f.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const double2*>(x) : nullptr;
     for (size_t i = 0; i < P.a_sched.size(); ++i) {
       const bool bwd = P.a_dir[i] != 0;
@@ -898,7 +931,7 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     qf::PlanRequest req;
     req.tile_bits = o.tile_bits;
     req.ckpt_layers = c->ckpt_layers;
-    req.generic = o.program == 1 || c->f64;  // complex128 passes run generic steps
+    req.generic = o.program == 1;
     req.ckpt_mode = o.ckpt_mode;
     req.mem_save = o.mem_save != 0;
     c->tc = false;

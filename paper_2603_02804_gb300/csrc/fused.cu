@@ -1193,6 +1193,20 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
   return make_float4((float)tan(0.25 * w), (float)sin(0.5 * w), __int_as_float(parity), 0.f);
 }
 
+// The same in float64 (complex128 round programs).
+__device__ Shear64 term_shear64(const PrepArgs& a, int32_t t) {
+  Shear64 r{0.0, 0.0, 0, 0};
+  if (t < 0) return r;
+  const double phi = term_angle(a, t);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double k = rint(phi / two_pi);
+  const double w = phi - two_pi * k;
+  r.t = tan(0.25 * w);
+  r.s = sin(0.5 * w);
+  r.wrap = ((long long)k) & 1;
+  return r;
+}
+
 }  // namespace
 
 // Element i of the tables: fused matrices, terms, encodings, then (round
@@ -1238,8 +1252,13 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     const int64_t r = i >> 2;
     const int k = (int)(i & 3);
     const int32_t* rec = reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords;
-    a.rpf[r * 8 + 2 * k] = term_shear_of(a, rec[12 + k]);
-    a.rpf[r * 8 + 2 * k + 1] = term_shear_of(a, rec[8 + k]);
+    if (a.rpf64) {
+      a.rpf64[r * 8 + 2 * k] = term_shear64(a, rec[12 + k]);
+      a.rpf64[r * 8 + 2 * k + 1] = term_shear64(a, rec[8 + k]);
+    } else {
+      a.rpf[r * 8 + 2 * k] = term_shear_of(a, rec[12 + k]);
+      a.rpf[r * 8 + 2 * k + 1] = term_shear_of(a, rec[8 + k]);
+    }
     return;
   }
   i -= 4ll * a.n_rpf;
@@ -1248,7 +1267,8 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     const int64_t r = i >> 3;
     const int k = (int)(i & 7);
     const int32_t t = reinterpret_cast<const int32_t*>(a.rpb_src)[r * kBwdRoundWords + k];
-    a.rpb[i] = term_shear_of(a, t);
+    if (a.rpb64) a.rpb64[i] = term_shear64(a, t);
+    else a.rpb[i] = term_shear_of(a, t);
   }
 }
 

@@ -1,13 +1,16 @@
 // Complex128 fused forward / adjoint passes for sm_103a.
 //
-// The same plans and generic step programs as the complex64 passes (a fused
-// 2x2 per register bit in the forward, CZ signs and CNOT swaps, one rotation
-// at a time un-applied to psi and lambda in the adjoint with its gradient
-// term; Secs. 3.2-3.3), with every amplitude, table entry and partial in
-// float64: the double-precision state type the paper's library supports
-// next to complex64. GB300's FP64 pipe runs at 1/64 of its FP32 rate, so these
-// passes are bound by FP64 arithmetic, never by memory, and need no round
-// programs or packed arithmetic: the generic steps are the whole design.
+// The same plans and step programs as the complex64 passes (Secs. 3.2-3.3),
+// with every amplitude, table entry and partial in float64: the
+// double-precision state type the paper's library supports next to
+// complex64. Generic steps apply a fused 2x2 per register bit in the forward,
+// CZ signs and CNOT swaps, and un-apply one rotation at a time in the
+// adjoint. Round programs apply per register bit an RY and a merged RZ run as
+// three-shear rotations with pending CZ signs, so a qubit-layer of the
+// hardware-efficient ansatz costs 12 FP64 instructions per amplitude pair
+// forward (16 as a fused 2x2) and two gradient terms of 16 backward (three of
+// 20 one rotation at a time). GB300's FP64 pipe runs at 1/61 of its FP32
+// rate, so these passes are bound by FP64 instruction issue, never by memory.
 //
 // A CTA (256 threads) owns 4096 amplitudes per state, as in the complex64
 // passes; the tile is 64 KiB per state here (16-byte amplitudes), so the
@@ -148,6 +151,168 @@ __device__ __forceinline__ void cnot64(double2 (&r)[16], double2 (&l)[16], bool 
   }
 }
 
+// ---- round programs (the complex64 round programs' items in float64) -----------
+// A round applies one item per register bit r (the RY, then the merged RZ
+// run; the adjoint runs the exact reverse) and then the round's CZ links.
+// Rotations run as three shears: a plane rotation by phi is x += a y;
+// y += b x; x += a y with a = -tan(phi/2), b = sin(phi), |a| <= 1 for
+// |phi| <= pi/2 (term angles are wrapped into (-pi, pi], the wrap parity
+// kept as a sign). Pending CZ signs D: the registers hold psi~ with
+// psi = D psi~, D = (-1)^(c0 + sum_r A_r j_r) (bit 4: c0, bits 0..3: A);
+// a gate on register bit r sees only Z_r^(A_r), folded into it; CZs between
+// two register bits flip the registers directly.
+
+// Link q couples qubit q with q + 1 mod n: the constant (t2 & gb) and linear
+// (u) parts of the links L for thread base index gb.
+__device__ __forceinline__ void link_terms64(uint32_t L, uint32_t gb, int n, uint32_t& t2, uint32_t& u) {
+  const uint32_t nmask = n >= 32 ? ~0u : ((1u << n) - 1u);
+  const uint32_t t1 = L & gb;
+  t2 = L & (((gb >> 1) | ((gb & 1u) << (n - 1))) & nmask);
+  u = (((t1 << 1) | (t1 >> (n - 1))) & nmask) ^ t2;
+}
+
+template <bool BWD>
+__device__ __forceinline__ void chain64(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4], int n,
+                                        uint32_t& D, double2 (&r)[16], double2 (&l)[16]) {
+  uint32_t t2, u;
+  link_terms64(L, gb, n, t2, u);
+  D ^= (((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) | (((u >> p[3]) & 1u) << 3)) |
+       ((__popc(t2 & gb) & 1u) << 4);
+#pragma unroll
+  for (int rb = 0; rb < 3; ++rb) {
+    const uint32_t f = (bbits >> rb) & 1u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (((j >> rb) & 3) != 3) continue;
+      r[j] = make_double2(flipd(r[j].x, f), flipd(r[j].y, f));
+      if (BWD) l[j] = make_double2(flipd(l[j].x, f), flipd(l[j].y, f));
+    }
+  }
+}
+
+// Multiply the registers by D (end of a step).
+template <bool BWD>
+__device__ __forceinline__ void pending64(uint32_t D, double2 (&r)[16], double2 (&l)[16]) {
+  uint32_t S = (D & 16u) ? 0xFFFFu : 0u;
+  S ^= (D & 1u) ? 0xAAAAu : 0u;
+  S ^= (D & 2u) ? 0xCCCCu : 0u;
+  S ^= (D & 4u) ? 0xF0F0u : 0u;
+  S ^= (D & 8u) ? 0xFF00u : 0u;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const uint32_t f = (S >> j) & 1u;
+    r[j] = make_double2(flipd(r[j].x, f), flipd(r[j].y, f));
+    if (BWD) l[j] = make_double2(flipd(l[j].x, f), flipd(l[j].y, f));
+  }
+}
+
+// Forward item on register bit R: the RY, then the RZ run. y, z: the terms'
+// shear parameters of the un-apply direction; applying rotates the other
+// way. A pending Z_R turns RY(w) into RY(-w); the wrap parities go to the
+// pending constant sign.
+template <int R>
+__device__ __forceinline__ void item_fwd64(double2 (&r)[16], const Shear64& y, const Shear64& z, uint32_t a,
+                                           uint32_t& D) {
+  const double ty = a ? y.t : -y.t, sy = a ? -y.s : y.s;
+  const double t = z.t, s = z.s;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    double2 p0 = r[j], p1 = r[j1];
+    // RY(w) on (p0, p1): rotation by +w/2, the same shears on re and im
+    p0.x = fma(ty, p1.x, p0.x); p0.y = fma(ty, p1.y, p0.y);
+    p1.x = fma(sy, p0.x, p1.x); p1.y = fma(sy, p0.y, p1.y);
+    p0.x = fma(ty, p1.x, p0.x); p0.y = fma(ty, p1.y, p0.y);
+    // RZ run: bit-R-clear amplitude times e^{-iw/2}, set one times e^{+iw/2}
+    p0.x = fma(t, p0.y, p0.x); p0.y = fma(-s, p0.x, p0.y); p0.x = fma(t, p0.y, p0.x);
+    p1.x = fma(-t, p1.y, p1.x); p1.y = fma(s, p1.x, p1.y); p1.x = fma(-t, p1.y, p1.x);
+    r[j] = p0;
+    r[j1] = p1;
+  }
+  D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
+}
+
+// Un-apply one rotation on register bit R by three shears; returns the
+// thread's sum of Im<lambda|P|psi> taken before it.
+//   RZ: bit-R-clear amplitudes times e^{+iw/2}, set ones times e^{-iw/2}.
+//   RY: (x, y) <- RY(w)^dagger (x, y), a rotation by -w/2: a = t, b = -s.
+template <int R, int KIND>
+__device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16], const double t, const double s) {
+  double acc = 0.0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    double2 p0 = p[j], p1 = p[j1], l0 = l[j], l1 = l[j1];
+    if (KIND == G_RZ) {
+      acc += l0.x * p0.y - l0.y * p0.x - l1.x * p1.y + l1.y * p1.x;
+      p0.x = fma(-t, p0.y, p0.x); p0.y = fma(s, p0.x, p0.y); p0.x = fma(-t, p0.y, p0.x);
+      l0.x = fma(-t, l0.y, l0.x); l0.y = fma(s, l0.x, l0.y); l0.x = fma(-t, l0.y, l0.x);
+      p1.x = fma(t, p1.y, p1.x); p1.y = fma(-s, p1.x, p1.y); p1.x = fma(t, p1.y, p1.x);
+      l1.x = fma(t, l1.y, l1.x); l1.y = fma(-s, l1.x, l1.y); l1.x = fma(t, l1.y, l1.x);
+    } else {
+      acc += l1.x * p0.x + l1.y * p0.y - l0.x * p1.x - l0.y * p1.y;
+      p0.x = fma(t, p1.x, p0.x); p0.y = fma(t, p1.y, p0.y);
+      p1.x = fma(-s, p0.x, p1.x); p1.y = fma(-s, p0.y, p1.y);
+      p0.x = fma(t, p1.x, p0.x); p0.y = fma(t, p1.y, p0.y);
+      l0.x = fma(t, l1.x, l0.x); l0.y = fma(t, l1.y, l0.y);
+      l1.x = fma(-s, l0.x, l1.x); l1.y = fma(-s, l0.y, l1.y);
+      l0.x = fma(t, l1.x, l0.x); l0.y = fma(t, l1.y, l0.y);
+    }
+    p[j] = p0;
+    p[j1] = p1;
+    l[j] = l0;
+    l[j1] = l1;
+  }
+  return acc;
+}
+
+// Backward item on register bit R: the merged RZ run, then the RY. With a
+// pending Z_R the RY un-applies as RY(+w) and its Im<lambda|Y|psi> changes sign.
+template <int R>
+__device__ __forceinline__ void item_bwd64(double2 (&p)[16], double2 (&l)[16], const Shear64& z, const Shear64& y,
+                                           uint32_t a, uint32_t& D, double& gz, double& gy) {
+  gz = shear_bwd64<R, G_RZ>(p, l, z.t, z.s);
+  const double g = shear_bwd64<R, G_RY>(p, l, a ? -y.t : y.t, a ? -y.s : y.s);
+  gy = a ? -g : g;
+  D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
+}
+
+// Reduce 8 per-thread values over `lanes` lanes (8, 16 or 32; whole-warp
+// call): afterwards the lanes with (lane & (lanes/8 - 1)) == 0 hold the 8
+// lanes-sums, lane's being that of value *idx.
+__device__ __forceinline__ double butterfly8_64(double (&v)[8], int lanes, int lane, int& idx) {
+  int o = lanes >> 1;
+  bool up = (lane & o) != 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double send = up ? v[i] : v[i + 4];
+    const double keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+  idx = up ? 4 : 0;
+  o >>= 1;
+  up = (lane & o) != 0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double send = up ? v[i] : v[i + 2];
+    const double keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+  idx += up ? 2 : 0;
+  o >>= 1;
+  up = (lane & o) != 0;
+  {
+    const double send = up ? v[0] : v[1];
+    const double keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+  idx += up ? 1 : 0;
+  for (o >>= 1; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
+
 struct Shared64 {
   uint32_t lg[256];                              // thread-part of the local index -> global bits
   double red[2][kThreads / 32][kMaxStepSlots];   // per-warp gradient sums of a step (double-buffered)
@@ -162,7 +327,7 @@ struct Shared64 {
 // One complex128 pass: CTA c owns tiles c * tiles_per_cta .. (tile = sample *
 // tiles_per_sample + tile within the sample); 2^(K-4) threads per tile, 16
 // amplitudes per thread per step.
-template <bool BWD>
+template <bool BWD, bool ROUNDS>
 __global__ void __launch_bounds__(kThreads, 1) pass64_kernel(const PassArgs64 a) {
   extern __shared__ __align__(16) double2 smem64[];
   __shared__ Shared64 sh;
@@ -294,7 +459,80 @@ __global__ void __launch_bounds__(kThreads, 1) pass64_kernel(const PassArgs64 a)
   while (pc < pd.op_end) {
     const uint2 op = __ldg(ops + pc++);
     const uint32_t code = op.x & 15u;
-    if (code == OP_STEP) {
+    if (ROUNDS && code == OP_STEP) {
+      // ---- round step: rounds op.y .. op.y + nr - 1 on register group g
+      const int g = (op.x >> 4) & 3;
+      const int nr = (op.x >> 8) & 0xffff;
+      const uint32_t lb0 = sh.grp[g][0], lb1 = sh.grp[g][1], lb2 = sh.grp[g][2], lb3 = sh.grp[g][3];
+      const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
+      const uint32_t base = pdep(tau, ((1u << K) - 1u) & ~gm);
+      const uint32_t pb = swz64(base);
+      const uint32_t so[4] = {swz64(1u << lb0), swz64(1u << lb1), swz64(1u << lb2), swz64(1u << lb3)};
+      const uint32_t gb = gidx(base);
+      const uint32_t pos[4] = {sh.gmap[lb0], sh.gmap[lb1], sh.gmap[lb2], sh.gmap[lb3]};
+      double2 r[16];
+      double2 l[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        r[j] = tp[pb ^ reg_offset(j, so)];
+        if (BWD) l[j] = tl[pb ^ reg_offset(j, so)];
+      }
+      uint32_t D = 0;
+#pragma unroll 1
+      for (int k = 0; k < nr; ++k) {
+        const size_t rr = (size_t)op.y + k;
+        const Shear64* v = a.rpar + 8 * rr;
+        if (!BWD) {
+          const uint4 lk = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 1);
+          item_fwd64<0>(r, v[0], v[1], D & 1u, D);
+          item_fwd64<1>(r, v[2], v[3], (D >> 1) & 1u, D);
+          item_fwd64<2>(r, v[4], v[5], (D >> 2) & 1u, D);
+          item_fwd64<3>(r, v[6], v[7], (D >> 3) & 1u, D);
+          chain64<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
+        } else {
+          const uint4 lk = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 2);
+          chain64<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
+          double gv[8];
+          item_bwd64<0>(r, l, v[0], v[4], D & 1u, D, gv[0], gv[4]);
+          item_bwd64<1>(r, l, v[1], v[5], (D >> 1) & 1u, D, gv[1], gv[5]);
+          item_bwd64<2>(r, l, v[2], v[6], (D >> 2) & 1u, D, gv[2], gv[6]);
+          item_bwd64<3>(r, l, v[3], v[7], (D >> 3) & 1u, D, gv[3], gv[7]);
+          int idx;
+          const double sum = butterfly8_64(gv, lanes, lane, idx);
+          const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
+          const int32_t term = __ldg(reinterpret_cast<const int32_t*>(a.rounds + rr * (kBwdRoundWords / 4)) + idx);
+          if (Tt >= 32) {
+            if (owner) {
+              sh.red[buf][warp][k * 8 + idx] = sum;
+              if (warp == 0) sh.slot[buf][k * 8 + idx] = term;
+            }
+          } else if (owner && active && term >= 0) {
+            a.g_part[tile * a.n_slots + term] = 0.5 * sum;
+          }
+        }
+      }
+      pending64<BWD>(D, r, l);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        tp[pb ^ reg_offset(j, so)] = r[j];
+        if (BWD) tl[pb ^ reg_offset(j, so)] = l[j];
+      }
+      __syncthreads();
+      if (BWD && Tt >= 32) {
+        const int nk = nr * 8;
+        for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
+          const int tc = e / nk, kk = e - tc * nk;
+          const int64_t t2 = first_tile + tc;
+          const int32_t term = sh.slot[buf][kk];
+          if (t2 < total_tiles && term >= 0) {
+            double sum = 0.0;
+            for (int w = 0; w < wpt; ++w) sum += sh.red[buf][tc * wpt + w][kk];
+            a.g_part[t2 * a.n_slots + term] = 0.5 * sum;
+          }
+        }
+        buf ^= 1;
+      }
+    } else if (!ROUNDS && code == OP_STEP) {
       const int g = (op.x >> 4) & 3;
       const int nops = (op.x >> 8) & 0xffff;
       const int nk = (int)op.y;
@@ -502,12 +740,19 @@ cudaError_t launch_pass64(bool bwd, const PassArgs64& a, cudaStream_t st) {
   const int64_t grid = (total_tiles + tiles_per_cta - 1) / tiles_per_cta;
   if (grid == 0) return cudaSuccess;
   const size_t smem = (size_t)(bwd ? 2 : 1) * kTileAmps * sizeof(double2);
-  static OptIn once_f, once_b;
-  cudaError_t e = bwd ? opt_in(reinterpret_cast<const void*>(pass64_kernel<true>), smem, once_b)
-                      : opt_in(reinterpret_cast<const void*>(pass64_kernel<false>), smem, once_f);
+  const bool rounds = a.rounds != nullptr;
+  if (rounds && (a.rpar == nullptr || a.pd.K < 7)) return cudaErrorInvalidValue;  // 8 lanes per tile at least
+  static OptIn once[4];
+  const void* fn = bwd ? (rounds ? reinterpret_cast<const void*>(pass64_kernel<true, true>)
+                                 : reinterpret_cast<const void*>(pass64_kernel<true, false>))
+                       : (rounds ? reinterpret_cast<const void*>(pass64_kernel<false, true>)
+                                 : reinterpret_cast<const void*>(pass64_kernel<false, false>));
+  cudaError_t e = opt_in(fn, smem, once[(bwd ? 2 : 0) + (rounds ? 1 : 0)]);
   if (e != cudaSuccess) return e;
-  if (bwd) pass64_kernel<true><<<(unsigned)grid, kThreads, smem, st>>>(a);
-  else pass64_kernel<false><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  if (bwd && rounds) pass64_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  else if (bwd) pass64_kernel<true, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  else if (rounds) pass64_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  else pass64_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,14 @@ struct PassArgs {
   int32_t g_accum;        // round programs: add the partials of a sample's tiles into one row
 };
 
+// Float64 three-shear parameters of a gradient term (complex128 round
+// programs): t = tan(w/4), s = sin(w/2) with w = phi - 2 pi k in (-pi, pi],
+// wrap = k & 1 (u(phi) = (-1)^k u(w)).
+struct alignas(16) Shear64 {
+  double t, s;
+  int64_t wrap, pad;
+};
+
 struct PrepArgs {
   const float* theta;
   const double* theta64;       // if non-null: float64 parameters (complex128 plans), theta unused
@@ -67,6 +75,8 @@ struct PrepArgs {
   int32_t n_rpb;               // backward rounds
   const uint4* rpb_src;        // backward round records (tz[4], ty[4] terms)
   float4* rpb;                 // [n_rpb][8]: shear parameters of tz[0..3], ty[0..3]
+  Shear64* rpf64;              // if non-null instead of rpf / rpb: the same in float64
+  Shear64* rpb64;              //   (complex128 round programs)
 };
 
 struct GradReduceArgs {
@@ -116,16 +126,18 @@ struct OptIn {
 cudaError_t opt_in(const void* fn, size_t smem, OptIn& o);
 
 // ---- complex128 passes --------------------------------------------------------
-// Arguments of a complex128 pass: the generic step programs of PassArgs with
-// float64 tables and states. Round programs and the tensor-core path are
+// Arguments of a complex128 pass: the step programs of PassArgs (generic or
+// round programs) with float64 tables and states. The tensor-core path is
 // complex64 only.
 struct PassArgs64 {
   PassDesc pd;
   int32_t n_eff;
   int32_t tps_log2;       // log2(tiles per sample) = n_eff - K
   int64_t B;
-  const uint2* ops;       // program of this direction (generic steps)
-  const double2* mats;    // fused 2x2 matrices, 4 double2 each: u00, u01, u10, u11
+  const uint2* ops;       // program of this direction
+  const uint4* rounds;    // round records of this direction (round programs), else null
+  const Shear64* rpar;    // per-round item parameters, 8 per round (round programs)
+  const double2* mats;    // fused 2x2 matrices, 4 double2 each: u00, u01, u10, u11 (generic)
   const double2* cs;      // (cos, sin) of phi/2 per gradient term
   const double2* enc;     // (cos, sin) of x/2, [B][n_eff]
   const double2* psi_in;  // given initial states [B][2^n_in] (QF_ENC_STATE_IN), else null

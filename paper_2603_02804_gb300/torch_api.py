@@ -41,12 +41,14 @@ class Simulator:
     tensor cores (12-qubit tiles, n >= 12). ``precision="complex128"``
     simulates complex128 states in float64 arithmetic; theta, x (and y) are
     then float64 (states: complex128) and the *64 entry points run.
+    ``program=1`` forces generic steps where round programs would be used.
     """
 
     def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
                  tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
                  device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False,
-                 encoding: str = "angles", host_staging: bool = True, precision: str = "complex64"):
+                 encoding: str = "angles", host_staging: bool = True, precision: str = "complex64",
+                 program: int = 0):
         _cuda_check()
         self.device = torch.device(device or "cuda")
         self.encoding = encoding
@@ -65,7 +67,7 @@ class Simulator:
         with torch.cuda.device(self.device):
             self.ws_bytes = qfuse.qf_plan(self.handle, batch, _PATHS[path], tile_bits, ckpt_layers,
                                           ckpt_mode=ckpt_mode, mem_save=mem_save, tc_path=tc_path,
-                                          host_staging=host_staging, precision=_PREC[precision])
+                                          host_staging=host_staging, precision=_PREC[precision], program=program)
             self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
         self.batch = batch
         self._fwd_id = 0

@@ -38,12 +38,15 @@ def test_plan_info_and_workspace(hea12):
     assert ws64 < 2 * ws32 + (1 << 20)
 
 
-def test_complex128_plans_run_generic_steps(hea12):
-    """The RZ,RY,RZ + chain circuit gets round programs in complex64 and
-    generic steps in complex128 (the round programs are float32 shears)."""
+def test_complex128_plans_share_the_programs(hea12):
+    """complex128 plans get the same programs as complex64 ones: round
+    programs for the RZ,RY,RZ + chain circuit, generic steps on request."""
     qfuse.qf_plan(hea12, 2, host_only=True)
-    assert qfuse.qf_plan_export(hea12, 0)[0] == 1
+    p32 = qfuse.qf_plan_export(hea12, 0)
     qfuse.qf_plan(hea12, 2, host_only=True, precision=qfuse.QF_PREC_C128)
+    p64 = qfuse.qf_plan_export(hea12, 0)
+    assert p64[0] == 1 and np.array_equal(p32, p64)
+    qfuse.qf_plan(hea12, 2, host_only=True, precision=qfuse.QF_PREC_C128, program=1)
     assert qfuse.qf_plan_export(hea12, 0)[0] == 0
 
 
@@ -79,20 +82,22 @@ def test_mode_a_mem_save_stores_complex64():
     assert abs(saved - slots * B * (1 << n) * 8) < 4096
 
 
+@pytest.mark.parametrize("program", [0, 1])
 @pytest.mark.parametrize("n,d,K,ck", [(5, 3, 0, 1), (9, 3, 6, 1), (13, 2, 0, 1)])
-def test_exported_program_matches_oracle(n, d, K, ck):
+def test_exported_program_matches_oracle(n, d, K, ck, program):
     """The complex128 plan's forward and backward programs, interpreted in
     complex128 on the host, give the oracle's E and gradients."""
     rng = np.random.default_rng(4000 + n)
     h = qfuse.qf_hea_create(n, d)
     try:
-        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, precision=qfuse.QF_PREC_C128)
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, precision=qfuse.QF_PREC_C128,
+                      program=program)
         info = qfuse.qf_plan_info(h)
         theta = rng.uniform(0, 2 * np.pi, 3 * n * d)
         x = rng.uniform(0, np.pi, (2, n))
         fwd = pi.parse(qfuse.qf_plan_export(h, 0))
         bwd = pi.parse(qfuse.qf_plan_export(h, 1))
-        assert not fwd.rounds_mode
+        assert fwd.rounds_mode == (program == 0 and info["tile_bits"] >= 7)
         pq = qfuse.pauli("XZ", n)
         gr, Er = orc.gradient(orc.hea(n, d), theta, x, "XZ", per_sample=True)
         for b in range(2):

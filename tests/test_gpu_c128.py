@@ -47,17 +47,19 @@ def draw(n_params, B, n, seed):
     return rng.uniform(0, 2 * np.pi, n_params), rng.uniform(0, np.pi, (B, n))
 
 
+@pytest.mark.parametrize("program", [0, 1])
 @pytest.mark.parametrize("n,d,K,ck,obs", [
     (1, 2, 0, 0, "X"), (3, 3, 0, 0, "XZ"), (4, 3, 0, 0, "ZX"), (6, 4, 0, 1, "XZ"), (9, 4, 6, 2, "ZZ"),
     (12, 6, 0, 2, "XYZ"), (13, 3, 5, 1, "Z"), (14, 4, 0, 1, "XZ"),
 ])
-def test_hea_angles(n, d, K, ck, obs):
+def test_hea_angles(n, d, K, ck, obs, program):
     """RY(x) encoding, RZ,RY,RZ + CZ chain: single tiles (n <= 12, including
     padded n < 4 and the one-thread tile n = 4), several passes per layer
-    (tile_bits 5 and 6), checkpoints and re-anchoring, X/Y observables."""
+    (tile_bits 5 and 6), checkpoints and re-anchoring, X/Y observables; round
+    programs (program 0, tiles of >= 7 qubits) and generic steps."""
     B = 5
     theta, x = draw(3 * n * d, B, n, 500 + 31 * n + d)
-    E, g, sim = run64(n, d, theta, x, obs=obs, tile_bits=K, ckpt_layers=ck)
+    E, g, sim = run64(n, d, theta, x, obs=obs, tile_bits=K, ckpt_layers=ck, program=program)
     info = sim.info()
     assert info["precision"] == qfuse.QF_PREC_C128
     assert info["state_bytes"] == 16 * B * (1 << info["n_eff"])
@@ -122,13 +124,14 @@ def test_given_states_ixyz(n, d, ck, mode):
     assert np.max(np.abs(g - gr)) < TOL64
 
 
+@pytest.mark.parametrize("program", [0, 1])
 @pytest.mark.parametrize("mem_save", [False, True])
-def test_mode_a_block_recompute(mem_save):
+def test_mode_a_block_recompute(mem_save, program):
     """Checkpoint mode 1 (per-block forward re-run storing pass outputs); with
     mem_save the stored pass outputs are complex64."""
     n, d, B = 14, 6, 3
     theta, x = draw(3 * n * d, B, n, 1414)
-    E, g, sim = run64(n, d, theta, x, obs="XZ", ckpt_layers=2, ckpt_mode=1, mem_save=mem_save)
+    E, g, sim = run64(n, d, theta, x, obs="XZ", ckpt_layers=2, ckpt_mode=1, mem_save=mem_save, program=program)
     info = sim.info()
     assert info["ckpt_mode"] == 1 and info["n_pass_slots"] > 0 and info["mem_save"] == int(mem_save)
     gr, Er = orc.gradient(orc.hea(n, d), theta, x, "XZ", per_sample=True)
