@@ -736,12 +736,13 @@ def main():
     th_h = torch.from_numpy(theta_np).pin_memory()
     x_h = torch.from_numpy(x_np).pin_memory()
     y_h = torch.from_numpy(y_np).pin_memory() if y_np is not None else None
+    outs_h = sim.host_outputs()  # pinned once, written by every step
     for _ in range(2):
-        sim.train_step_host(th_h, x_h, y_h, loss=w.loss)
+        sim.train_step_host(th_h, x_h, y_h, loss=w.loss, out=outs_h)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for _ in range(args.steps):
-        loss_h, E_h, g_h = sim.train_step_host(th_h, x_h, y_h, loss=w.loss)
+        loss_h, E_h, g_h = sim.train_step_host(th_h, x_h, y_h, loss=w.loss, out=outs_h)
     e_dt = time.perf_counter() - e0
     h2d = theta_np.nbytes + x_np.nbytes + (y_np.nbytes if y_np is not None else 0)
     d2h = 8 + 8 * w.B + 8 * w.n_params

@@ -139,12 +139,21 @@ class Simulator:
         self._fwd_id = next(_ids)
         return out_loss, E, g
 
-    def train_step_host(self, theta_h, x_h, y_h=None, loss: str = "sum"):
-        """The same step from host (ideally pinned) tensors; returns host results."""
+    def host_outputs(self, batch: int | None = None):
+        """Pinned host buffers (loss [1], E [B], grad [P]) for ``train_step_host(out=...)``."""
+        B = self.batch if batch is None else batch
+        z = lambda k: torch.empty(k, dtype=torch.float64).pin_memory()
+        return z(1), z(B), z(self.n_params)
+
+    def train_step_host(self, theta_h, x_h, y_h=None, loss: str = "sum", out=None):
+        """The same step from host (ideally pinned) tensors; returns host results.
+        ``out``: (loss [1], E [B], grad [P]) float64 host tensors to write
+        (e.g. from ``host_outputs()``); pinning them once instead of per call
+        saves a host allocation per step."""
         B = x_h.shape[0]
-        out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
-        E = torch.empty(B, dtype=torch.float64).pin_memory()
-        g = torch.empty(self.n_params, dtype=torch.float64).pin_memory()
+        out_loss, E, g = out if out is not None else self.host_outputs(B)
+        if E.numel() < B or g.numel() != self.n_params or E.dtype != torch.float64:
+            raise ValueError("out buffers must be float64 (loss [1], E [>= B], grad [P])")
         fn = qfuse.qf_train_step_host64 if self.f64 else qfuse.qf_train_step_host
         fn(self.handle, theta_h, x_h, y_h, B, _LOSS[loss], self.obs, out_loss, E, g, self.ws, self.ws_bytes,
            self._stream())
