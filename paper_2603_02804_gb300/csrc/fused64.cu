@@ -209,26 +209,38 @@ __device__ __forceinline__ void pending64(uint32_t D, double2 (&r)[16], double2 
 // Forward item on register bit R: the RY, then the RZ run. y, z: the terms'
 // shear parameters of the un-apply direction; applying rotates the other
 // way. A pending Z_R turns RY(w) into RY(-w); the wrap parities go to the
-// pending constant sign.
+// pending constant sign. An absent part (no term) is the identity: skipped.
 template <int R>
 __device__ __forceinline__ void item_fwd64(double2 (&r)[16], const Shear64& y, const Shear64& z, uint32_t a,
-                                           uint32_t& D) {
+                                           uint32_t& D, bool has_y, bool has_z) {
   const double ty = a ? y.t : -y.t, sy = a ? -y.s : y.s;
   const double t = z.t, s = z.s;
+  if (has_y) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (j & (1 << R)) continue;
-    const int j1 = j | (1 << R);
-    double2 p0 = r[j], p1 = r[j1];
-    // RY(w) on (p0, p1): rotation by +w/2, the same shears on re and im
-    p0.x = fma(ty, p1.x, p0.x); p0.y = fma(ty, p1.y, p0.y);
-    p1.x = fma(sy, p0.x, p1.x); p1.y = fma(sy, p0.y, p1.y);
-    p0.x = fma(ty, p1.x, p0.x); p0.y = fma(ty, p1.y, p0.y);
-    // RZ run: bit-R-clear amplitude times e^{-iw/2}, set one times e^{+iw/2}
-    p0.x = fma(t, p0.y, p0.x); p0.y = fma(-s, p0.x, p0.y); p0.x = fma(t, p0.y, p0.x);
-    p1.x = fma(-t, p1.y, p1.x); p1.y = fma(s, p1.x, p1.y); p1.x = fma(-t, p1.y, p1.x);
-    r[j] = p0;
-    r[j1] = p1;
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << R)) continue;
+      const int j1 = j | (1 << R);
+      double2 p0 = r[j], p1 = r[j1];
+      // RY(w) on (p0, p1): rotation by +w/2, the same shears on re and im
+      p0.x = fma(ty, p1.x, p0.x); p0.y = fma(ty, p1.y, p0.y);
+      p1.x = fma(sy, p0.x, p1.x); p1.y = fma(sy, p0.y, p1.y);
+      p0.x = fma(ty, p1.x, p0.x); p0.y = fma(ty, p1.y, p0.y);
+      r[j] = p0;
+      r[j1] = p1;
+    }
+  }
+  if (has_z) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << R)) continue;
+      const int j1 = j | (1 << R);
+      double2 p0 = r[j], p1 = r[j1];
+      // RZ run: bit-R-clear amplitude times e^{-iw/2}, set one times e^{+iw/2}
+      p0.x = fma(t, p0.y, p0.x); p0.y = fma(-s, p0.x, p0.y); p0.x = fma(t, p0.y, p0.x);
+      p1.x = fma(-t, p1.y, p1.x); p1.y = fma(s, p1.x, p1.y); p1.x = fma(-t, p1.y, p1.x);
+      r[j] = p0;
+      r[j1] = p1;
+    }
   }
   D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
 }
@@ -269,13 +281,17 @@ __device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16]
 }
 
 // Backward item on register bit R: the merged RZ run, then the RY. With a
-// pending Z_R the RY un-applies as RY(+w) and its Im<lambda|Y|psi> changes sign.
+// pending Z_R the RY un-applies as RY(+w) and its Im<lambda|Y|psi> changes
+// sign. An absent part (no term) is skipped; its value is 0.
 template <int R>
 __device__ __forceinline__ void item_bwd64(double2 (&p)[16], double2 (&l)[16], const Shear64& z, const Shear64& y,
-                                           uint32_t a, uint32_t& D, double& gz, double& gy) {
-  gz = shear_bwd64<R, G_RZ>(p, l, z.t, z.s);
-  const double g = shear_bwd64<R, G_RY>(p, l, a ? -y.t : y.t, a ? -y.s : y.s);
-  gy = a ? -g : g;
+                                           uint32_t a, uint32_t& D, double& gz, double& gy, bool has_z, bool has_y) {
+  gz = has_z ? shear_bwd64<R, G_RZ>(p, l, z.t, z.s) : 0.0;
+  gy = 0.0;
+  if (has_y) {
+    const double g = shear_bwd64<R, G_RY>(p, l, a ? -y.t : y.t, a ? -y.s : y.s);
+    gy = a ? -g : g;
+  }
   D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
 }
 
@@ -484,19 +500,23 @@ __global__ void __launch_bounds__(kThreads, 1) pass64_kernel(const PassArgs64 a)
         const Shear64* v = a.rpar + 8 * rr;
         if (!BWD) {
           const uint4 lk = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 1);
-          item_fwd64<0>(r, v[0], v[1], D & 1u, D);
-          item_fwd64<1>(r, v[2], v[3], (D >> 1) & 1u, D);
-          item_fwd64<2>(r, v[4], v[5], (D >> 2) & 1u, D);
-          item_fwd64<3>(r, v[6], v[7], (D >> 3) & 1u, D);
+          // the items' terms (-1: the part is absent): tz in words 8..11, ty in 12..15
+          const uint4 tz = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 2);
+          const uint4 ty = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 3);
+          item_fwd64<0>(r, v[0], v[1], D & 1u, D, (int)ty.x >= 0, (int)tz.x >= 0);
+          item_fwd64<1>(r, v[2], v[3], (D >> 1) & 1u, D, (int)ty.y >= 0, (int)tz.y >= 0);
+          item_fwd64<2>(r, v[4], v[5], (D >> 2) & 1u, D, (int)ty.z >= 0, (int)tz.z >= 0);
+          item_fwd64<3>(r, v[6], v[7], (D >> 3) & 1u, D, (int)ty.w >= 0, (int)tz.w >= 0);
           chain64<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
         } else {
           const uint4 lk = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 2);
+          const uint4 tz = __ldg(a.rounds + rr * (kBwdRoundWords / 4)), ty = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 1);
           chain64<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
           double gv[8];
-          item_bwd64<0>(r, l, v[0], v[4], D & 1u, D, gv[0], gv[4]);
-          item_bwd64<1>(r, l, v[1], v[5], (D >> 1) & 1u, D, gv[1], gv[5]);
-          item_bwd64<2>(r, l, v[2], v[6], (D >> 2) & 1u, D, gv[2], gv[6]);
-          item_bwd64<3>(r, l, v[3], v[7], (D >> 3) & 1u, D, gv[3], gv[7]);
+          item_bwd64<0>(r, l, v[0], v[4], D & 1u, D, gv[0], gv[4], (int)tz.x >= 0, (int)ty.x >= 0);
+          item_bwd64<1>(r, l, v[1], v[5], (D >> 1) & 1u, D, gv[1], gv[5], (int)tz.y >= 0, (int)ty.y >= 0);
+          item_bwd64<2>(r, l, v[2], v[6], (D >> 2) & 1u, D, gv[2], gv[6], (int)tz.z >= 0, (int)ty.z >= 0);
+          item_bwd64<3>(r, l, v[3], v[7], (D >> 3) & 1u, D, gv[3], gv[7], (int)tz.w >= 0, (int)ty.w >= 0);
           int idx;
           const double sum = butterfly8_64(gv, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;

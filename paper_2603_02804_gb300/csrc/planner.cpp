@@ -208,11 +208,43 @@ struct QubitRots {
     while (i < l.size() && s.done[l[i]]) ++i;
     return i < l.size() ? l[i] : -1;
   }
+  // rotations of qubit q absorbed so far (its progress)
+  int pos(const Sim& s, int q) const {
+    const auto& l = rots[q];
+    size_t i = cursor[q];
+    while (i < l.size() && s.done[l[i]]) ++i;
+    return (int)i;
+  }
   void commit(const Sim& s) {
     for (size_t q = 0; q < rots.size(); ++q)
       while (cursor[q] < rots[q].size() && s.done[rots[q][cursor[q]]]) ++cursor[q];
   }
 };
+
+// The same tile with its free qubits (local bits 4..K-1) grouped by progress:
+// sorted by their next pending rotation, then cut into groups of 4, each
+// sorted ascending so that chain neighbours inside a group sit on adjacent
+// register bits (the round programs apply register-register CZs between
+// adjacent register bits only). Local bits 0..3 stay global qubits 0..3.
+// Qubits at the same depth of the frontier then share a group, so round
+// steps on them stay full where a staircase frontier crosses the nibbles.
+Tile make_tile_by_progress(const std::vector<int>& globals_sorted, int K, const Sim& s, const QubitRots& qr) {
+  std::vector<std::pair<long, int>> fr;
+  for (int i = 4; i < K; ++i) {
+    const int q = globals_sorted[i];
+    const int g = qr.next(s, q);
+    fr.push_back({g < 0 ? (1l << 40) : (long)g, q});
+  }
+  std::stable_sort(fr.begin(), fr.end());
+  std::vector<int> order(globals_sorted.begin(), globals_sorted.begin() + 4);
+  for (size_t c = 0; c < fr.size(); c += 4) {
+    std::vector<int> grp;
+    for (size_t k = c; k < std::min(fr.size(), c + 4); ++k) grp.push_back(fr[k].second);
+    std::sort(grp.begin(), grp.end());
+    order.insert(order.end(), grp.begin(), grp.end());
+  }
+  return make_tile(order, K);
+}
 
 bool ready(const Sim& s, int g) { return g >= 0 && !s.done[g] && s.indeg[g] == 0; }
 
@@ -243,23 +275,35 @@ bool take_item(Sim& s, const QubitRots& qr, int q, ItemRec* it) {
 bool has_rotations_left(const Sim& s, const QubitRots& qr, int q) { return qr.next(s, q) >= 0; }
 
 // One round on the group's qubits. full: every qubit of the group that still
-// has rotations must contribute an item. Ready CZs are absorbed at its end.
-bool form_round(Sim& s, const QubitRots& qr, const int (&qs)[4], bool full, RoundRec* rr, int* n_rot) {
+// has rotations must contribute an item, except a qubit shared with an
+// earlier, overlapping group (not in `home`) that is already ahead of the
+// group's own qubits (its next rotation comes later in the circuit than
+// theirs). cap_pos >= 0 (a catch-up round, partial): only qubits with at
+// most cap_pos rotations done contribute, so that lagging qubits catch up and
+// full rounds resume. Ready CZs are absorbed at its end.
+bool form_round(Sim& s, const QubitRots& qr, const int (&qs)[4], bool full, RoundRec* rr, int* n_rot,
+                uint32_t home = 0xFu, int cap_pos = -1) {
   const size_t mark = s.log.size();
+  long home_next = -1;
+  for (int k = 0; k < 4; ++k)
+    if ((home >> k) & 1u) home_next = std::max(home_next, (long)qr.next(s, qs[k]));
   RoundRec r;
-  int items = 0, want = 0, rot = 0;
+  int items = 0, want = 0, got = 0, rot = 0;
   for (int k = 0; k < 4; ++k) {
     bool dup = false;
     for (int j = 0; j < k; ++j) dup |= qs[j] == qs[k];
     if (dup || qs[k] >= s.c->n) continue;
     if (!has_rotations_left(s, qr, qs[k])) continue;
-    ++want;
+    if (cap_pos >= 0 && qr.pos(s, qs[k]) > cap_pos) continue;
+    const bool need = ((home >> k) & 1u) || (long)qr.next(s, qs[k]) <= home_next;
+    want += need;
     if (take_item(s, qr, qs[k], &r.it[k])) {
       ++items;
+      got += need;
       rot += (int)r.it[k].pre.size() + (r.it[k].y >= 0) + (int)r.it[k].post.size();
     }
   }
-  if (full && (items < want || items == 0)) {
+  if (full && (got < want || items == 0)) {
     s.undo_to(mark);
     return false;
   }
@@ -283,6 +327,15 @@ int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<Step
   auto group_qubits = [&](int gi, int (&qs)[4]) {
     for (int k = 0; k < 4; ++k) qs[k] = t.local_to_global[t.groups[gi][k]];
   };
+  // home qubits of each group: those not in an earlier group
+  std::vector<uint32_t> home(t.groups.size(), 0u);
+  for (int gi = 0; gi < (int)t.groups.size(); ++gi)
+    for (int k = 0; k < 4; ++k) {
+      bool earlier = false;
+      for (int gj = 0; gj < gi; ++gj)
+        for (int b : t.groups[gj]) earlier |= b == t.groups[gi][k];
+      if (!earlier) home[gi] |= 1u << k;
+    }
   for (;;) {
     // prefer the group that absorbs the most full rounds (then the most rotations)
     int best = -1, best_rounds = 0, best_rot = 0;
@@ -291,7 +344,7 @@ int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<Step
       group_qubits(gi, qs);
       const size_t mark = s.log.size();
       int nr = 0, rot = 0, r1;
-      while (nr < kMaxStepRounds && form_round(s, qr, qs, true, nullptr, &r1)) {
+      while (nr < kMaxStepRounds && form_round(s, qr, qs, true, nullptr, &r1, home[gi])) {
         ++nr;
         rot += r1;
       }
@@ -303,21 +356,33 @@ int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<Step
       }
     }
     bool partial = false;
+    int cap = -1;
     if (best_rounds == 0) {
       if (!allow_partial) break;
-      // no full round anywhere: one partial round in the group that absorbs most
-      best = -1;
-      best_rot = -1;
-      for (int gi = 0; gi < (int)t.groups.size(); ++gi) {
-        int qs[4];
-        group_qubits(gi, qs);
-        const size_t mark = s.log.size();
-        int r1 = 0;
-        if (form_round(s, qr, qs, false, nullptr, &r1) && r1 > best_rot) {
-          best = gi;
-          best_rot = r1;
+      // no full round anywhere: one partial round of the tile's least
+      // advanced qubits (the cap rises until some group can take one), in
+      // the group that absorbs most
+      int tile_min = 1 << 30, tile_max = 0;
+      for (int q : t.local_to_global)
+        if (q < s.c->n && has_rotations_left(s, qr, q)) {
+          tile_min = std::min(tile_min, qr.pos(s, q));
+          tile_max = std::max(tile_max, qr.pos(s, q));
         }
-        s.undo_to(mark);
+      best = -1;
+      for (int c = tile_min; c <= tile_max && best < 0; ++c) {
+        best_rot = -1;
+        for (int gi = 0; gi < (int)t.groups.size(); ++gi) {
+          int qs[4];
+          group_qubits(gi, qs);
+          const size_t mark = s.log.size();
+          int r1 = 0;
+          if (form_round(s, qr, qs, false, nullptr, &r1, home[gi], c) && r1 > best_rot) {
+            best = gi;
+            best_rot = r1;
+            cap = c;
+          }
+          s.undo_to(mark);
+        }
       }
       if (best < 0) break;
       partial = true;
@@ -330,7 +395,7 @@ int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<Step
     for (int nr = 0; nr < (partial ? 1 : kMaxStepRounds); ++nr) {
       RoundRec rr;
       int r1 = 0;
-      if (!form_round(s, qr, qs, !partial, &rr, &r1)) break;
+      if (!form_round(s, qr, qs, !partial, &rr, &r1, home[best], cap)) break;
       int pads = 0;
       for (int k = 0; k < 4; ++k) pads += rr.it[k].empty();
       total += 4 * r1 - pads;  // useful rotations, minus identity items
@@ -377,11 +442,16 @@ std::vector<std::vector<int>> tile_candidates(const Sim& s, int n_eff, int K) {
         cands.push_back(c);
       }
   }
-  // unions of aligned 4-qubit chunks {4k..4k+3} (qubits of one chunk tend to
-  // advance together, so round steps on them stay full)
+  // unions of disjoint 4-qubit chunks, aligned from qubit 4 up ({4k..4k+3})
+  // or from the top qubit down ({n-4k..n-4k+3}), so every qubit belongs to
+  // some aligned chunk when n is not a multiple of 4 (qubits of one chunk tend
+  // to advance together, so round steps on them stay full)
   if (extra % 4 == 0 && extra > 0) {
     std::vector<int> chunks;
     for (int b = 4; b + 4 <= n_eff; b += 4) chunks.push_back(b);
+    for (int b = n_eff - 4; b >= 4; b -= 4) chunks.push_back(b);
+    std::sort(chunks.begin(), chunks.end());
+    chunks.erase(std::unique(chunks.begin(), chunks.end()), chunks.end());
     const int need = extra / 4;
     std::vector<int> pick(need);
     std::function<void(int, int)> rec = [&](int at, int from) {
@@ -393,6 +463,7 @@ std::vector<std::vector<int>> tile_candidates(const Sim& s, int n_eff, int K) {
         return;
       }
       for (int i = from; i < (int)chunks.size(); ++i) {
+        if (at > 0 && chunks[i] < pick[at - 1] + 4) continue;  // disjoint
         pick[at] = chunks[i];
         rec(at + 1, i + 1);
       }
@@ -691,19 +762,20 @@ FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
         sim.undo_to(mark);
       } else {
         auto cands = tile_candidates(sim, P.n_eff, K);
-        int best = -1;
         best_score = -1;
-        for (int i = 0; i < (int)cands.size(); ++i) {
-          Tile t = make_tile(cands[i], K);
-          size_t mark = sim.log.size();
-          int sc = pass_run(t, nullptr);
-          sim.undo_to(mark);
-          if (sc > best_score) {
-            best_score = sc;
-            best = i;
+        // round programs also try each tile with its qubits grouped by progress
+        const int layouts = P.rounds && K % 4 == 0 ? 2 : 1;
+        for (int i = 0; i < (int)cands.size(); ++i)
+          for (int lay = 0; lay < layouts; ++lay) {
+            Tile t = lay == 0 ? make_tile(cands[i], K) : make_tile_by_progress(cands[i], K, sim, qr);
+            size_t mark = sim.log.size();
+            int sc = pass_run(t, nullptr);
+            sim.undo_to(mark);
+            if (sc > best_score) {
+              best_score = sc;
+              tile = t;
+            }
           }
-        }
-        tile = make_tile(cands[best], K);
       }
       if (best_score > 0 || allow_partial) break;
       allow_partial = true;
