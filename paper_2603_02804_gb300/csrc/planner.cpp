@@ -322,7 +322,12 @@ bool form_round(Sim& s, const QubitRots& qr, const int (&qs)[4], bool full, Roun
   return true;
 }
 
-int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<StepRec>* steps, bool allow_partial) {
+// strict_catch_up: partial rounds of a multi-tile pass take only qubits at
+// the tile's least advanced level (when none of them is ready the pass ends);
+// otherwise the level cap rises until some group can take a round.
+int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<StepRec>* steps, bool allow_partial,
+                    bool strict_catch_up) {
+  const bool rising = !strict_catch_up || (int)t.local_to_global.size() >= s.c->n;
   int total = 0;
   auto group_qubits = [&](int gi, int (&qs)[4]) {
     for (int k = 0; k < 4; ++k) qs[k] = t.local_to_global[t.groups[gi][k]];
@@ -357,19 +362,25 @@ int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<Step
     }
     bool partial = false;
     int cap = -1;
-    if (best_rounds == 0) {
-      if (!allow_partial) break;
-      // no full round anywhere: one partial round of the tile's least
-      // advanced qubits (the cap rises until some group can take one), in
-      // the group that absorbs most
-      int tile_min = 1 << 30, tile_max = 0;
+    // least and most advanced levels (rotations done) of the tile's qubits
+    auto tile_levels = [&](int& lo, int& hi) {
+      lo = 1 << 30;
+      hi = 0;
       for (int q : t.local_to_global)
         if (q < s.c->n && has_rotations_left(s, qr, q)) {
-          tile_min = std::min(tile_min, qr.pos(s, q));
-          tile_max = std::max(tile_max, qr.pos(s, q));
+          lo = std::min(lo, qr.pos(s, q));
+          hi = std::max(hi, qr.pos(s, q));
         }
+    };
+    if (best_rounds == 0) {
+      if (!allow_partial) break;
+      // no full round anywhere: a partial round of the tile's least
+      // advanced qubits (the cap rises until some group can take one), in
+      // the group that absorbs most
+      int tile_min, tile_max;
+      tile_levels(tile_min, tile_max);
       best = -1;
-      for (int c = tile_min; c <= tile_max && best < 0; ++c) {
+      for (int c = tile_min; c <= (rising ? tile_max : tile_min) && best < 0; ++c) {
         best_rot = -1;
         for (int gi = 0; gi < (int)t.groups.size(); ++gi) {
           int qs[4];
@@ -392,10 +403,18 @@ int run_pass_rounds(Sim& s, const QubitRots& qr, const Tile& t, std::vector<Step
     StepRec st;
     st.group = best;
     const size_t mark = s.log.size();
-    for (int nr = 0; nr < (partial ? 1 : kMaxStepRounds); ++nr) {
+    for (int nr = 0; nr < kMaxStepRounds; ++nr) {
       RoundRec rr;
       int r1 = 0;
-      if (!form_round(s, qr, qs, !partial, &rr, &r1, home[best], cap)) break;
+      bool ok = form_round(s, qr, qs, true, &rr, &r1, home[best]);
+      if (!ok && partial) {
+        // a catch-up round: the first at the cap found above, later ones of
+        // qubits at the tile's current least advanced level
+        int lo = cap, hi;
+        if (nr > 0) tile_levels(lo, hi);
+        ok = form_round(s, qr, qs, false, &rr, &r1, home[best], lo);
+      }
+      if (!ok) break;
       int pads = 0;
       for (int k = 0; k < 4; ++k) pads += rr.it[k].empty();
       total += 4 * r1 - pads;  // useful rotations, minus identity items
@@ -691,7 +710,32 @@ static void build_mode_a(FusedPlan& P, bool mem_save) {
   }
 }
 
+namespace {
+FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool strict_catch_up);
+}
+
+// Relative cost of a plan in round units: a round (one item per register bit
+// of a 4096-amplitude tile, forward and adjoint), a step boundary (the
+// shared-memory transpose and barrier, about a quarter of a round) and, when
+// the state spans several tiles, a pass (streaming the state through the
+// SMs once per direction, about two rounds; fitted to GB300 timings of the
+// hardware-efficient ansatz at n = 18).
+static double plan_cost(const FusedPlan& P) {
+  const double passes = P.n_eff > P.K ? (double)P.fwd.size() : 0.0;
+  return (double)P.n_rounds + 0.25 * P.n_steps + 2.0 * passes;
+}
+
+// Multi-tile round programs are planned with both catch-up rules and the
+// cheaper plan is kept.
 FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
+  FusedPlan a = plan_fused_with(c_in, req, false);
+  if (!a.rounds || a.n_eff <= a.K) return a;
+  FusedPlan b = plan_fused_with(c_in, req, true);
+  return plan_cost(b) < plan_cost(a) ? b : a;
+}
+
+namespace {
+FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool strict_catch_up) {
   validate_circuit(c_in);
   FusedPlan P;
   P.n_eff = std::max(c_in.n, kRegBits);
@@ -731,7 +775,7 @@ FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
   // otherwise.
   bool allow_partial = false;
   auto pass_run = [&](const Tile& t, std::vector<StepRec>* steps) {
-    return P.rounds ? run_pass_rounds(sim, qr, t, steps, allow_partial) : run_pass(sim, t, steps);
+    return P.rounds ? run_pass_rounds(sim, qr, t, steps, allow_partial, strict_catch_up) : run_pass(sim, t, steps);
   };
 
   // checkpoint boundaries in gate-sequence positions
@@ -1099,6 +1143,7 @@ FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
   else if (req.mem_save) throw std::runtime_error("mem_save needs ckpt_mode 1");
   return P;
 }
+}  // namespace
 
 PerGatePlan plan_per_gate(const Circuit& c, const PlanRequest& req) {
   validate_circuit(c);
