@@ -309,3 +309,22 @@ def test_cnot_gate_lists(seed):
         E, g, _ = gpu_run(n, 0, theta, x, obs="ZX", path=path, gates=rows, n_params=n_params, ckpt=1)
         assert np.max(np.abs(E - Er)) < TOL, path
         assert np.max(np.abs(g - gr)) < TOL, path
+
+
+@pytest.mark.parametrize("n", range(9, 20))
+def test_round_programs_every_width(n):
+    """Round programs at every width 9..19: single tiles with an overlapping
+    group (9-11), and multi-tile plans whose 4-qubit groups straddle the
+    progress frontier (13-15, 17-19), where the planner mixes full rounds with
+    catch-up rounds of the least advanced qubits."""
+    d, B = 9, 3
+    rng = np.random.default_rng(9000 + n)
+    theta = rng.uniform(0, 2 * np.pi, 3 * n * d).astype(np.float32)
+    x = rng.uniform(0, np.pi, (B, n)).astype(np.float32)
+    obs = "ZZ" + "I" * (n - 3) + "Z"
+    E, g, sim = gpu_run(n, d, theta, x, obs=obs, ckpt=3)
+    info = sim.info()
+    assert info["n_eff"] == n and (n <= 12) == (info["n_passes"] == 1)
+    gr, Er = orc.gradient(orc.hea(n, d), f64(theta), f64(x), obs, per_sample=True)
+    assert np.max(np.abs(E - Er)) < TOL
+    assert np.max(np.abs(g - gr)) < TOL
