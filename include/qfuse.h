@@ -172,6 +172,11 @@ typedef struct {
   int32_t n_pass_slots;    /* ckpt_mode 1: stored pass outputs of one block     */
   int32_t tc_path;
   int32_t precision;       /* QF_PREC_C64 or QF_PREC_C128                       */
+  int32_t qubit_shift;     /* fused plans: circuit qubit q is simulated as bit
+                              (q + qubit_shift) mod n of the state index (the
+                              planner's layout; 0 for QF_ENC_STATE_IN circuits).
+                              Inputs, observables and results use circuit
+                              qubits; only exported programs show the layout  */
 } qf_plan_info_t;
 
 /* Create the hardware-efficient ansatz of the paper's benchmarks with the
@@ -229,14 +234,16 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info);
 /* Export the forward (direction 0) or backward (1) program for inspection,
  * or (direction 2, ckpt_mode 1 plans) the adjoint's launch list:
  * writes up to cap int32 words to buf (may be NULL) and the full length to
- * *len. Layout: [program kind (0 generic steps, 1 round steps), n_passes,
+ * *len. Layout: [program kind (0 generic steps, 1 round steps), qubit shift
+ * (qf_plan_info_t.qubit_shift: every qubit index and mask below is a
+ * simulated bit), n_passes,
  * then per pass: 11 header words (op_begin, op_end, psi_src, psi_dst,
  * lam_src, lam_dst, flags, K, n_groups, outer_mask, xm_local), 16 gmap
  * words, 16 group words], then [n_ops, 2 words per op], then [n_fused, per
  * fused op: count, then count (kind, param, angle as 2 words) gates, param -1
  * for a constant angle], then [n round words of this direction, the words],
  * then [n_terms, per gradient term: kind, count, count parameters, constant
- * angle as 2 words]. Doubles are exported as (low, high) words of their bits. Direction 2: [program kind, n_launches, then per
+ * angle as 2 words]. Doubles are exported as (low, high) words of their bits. Direction 2: [program kind, qubit shift, n_launches, then per
  * launch: program (0 forward, 1 backward; op ranges index that direction's
  * ops), the 11 header words, 16 gmap words, 16 group words]. Host only. */
 qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf,

@@ -73,6 +73,10 @@ struct qf_circuit {
   bool staging = true;      // workspace holds host-input staging (qf_train_step_host)
   bool tc = false;          // forward rounds on the tensor cores
   bool f64 = false;         // complex128 states (QF_PREC_C128)
+  // layout chosen by the planner for (tile_bits option, program option); kept
+  // so that re-planning (e.g. qf_plan_fit's search) does not search again
+  bool lay_valid = false;
+  int lay_tile_bits = 0, lay_generic = 0, lay_shift = 0, lay_strict = 0;
   int64_t batch = 0;
   qf::FusedPlan fp;
   qf::PerGatePlan gp;
@@ -276,13 +280,22 @@ struct Obs {
   uint32_t x = 0, z = 0, y = 0;
 };
 
+// Circuit qubit q to simulated bit (q + s) mod n, for a mask of qubits.
+uint32_t rotate_mask(uint32_t m, int s, int n) {
+  if (s == 0 || n <= 0) return m;
+  const uint32_t all = n >= 32 ? ~0u : ((1u << n) - 1u);
+  return ((m << s) | (m >> (n - s))) & all;
+}
+
 qf_status check_obs(const qf_circuit* c, qf_pauli obs, Obs* o) {
   const uint64_t valid = (c->circ.n >= 64) ? ~0ull : ((1ull << c->circ.n) - 1);
   if ((obs.x_mask | obs.z_mask) & ~valid)
     return fail(QF_ERR_INVALID_ARG, "observable acts on a qubit outside the circuit");
-  o->x = (uint32_t)obs.x_mask;
-  o->z = (uint32_t)obs.z_mask;
   o->y = (uint32_t)__builtin_popcountll(obs.x_mask & obs.z_mask) & 3u;
+  // fused plans simulate the qubits in the plan's layout
+  const int s = c->path == QF_PATH_FUSED ? c->fp.qshift : 0;
+  o->x = rotate_mask((uint32_t)obs.x_mask, s, c->circ.n);
+  o->z = rotate_mask((uint32_t)obs.z_mask, s, c->circ.n);
   return QF_OK;
 }
 
@@ -382,6 +395,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.B = c->encoding == QF_ENC_RY_X ? B : 0;  // given states need no encoding table
   pa.n = c->circ.n;
   pa.n_eff = P.n_eff;
+  pa.qshift = P.qshift;
   pa.enc = at<float2>(ws, L.enc);
   QF_CU(qf::launch_prep(pa, st));
   c->call_launches++;
@@ -575,6 +589,7 @@ qf::PrepArgs prep_args64(const qf_circuit* c, const DevTables& T, const Layout& 
   pa.cs64 = at<double2>(ws, L.cs);
   pa.n = c->circ.n;
   pa.n_eff = c->fp.n_eff;
+  pa.qshift = c->fp.qshift;
   pa.enc64 = at<double2>(ws, L.enc);
   return pa;
 }
@@ -934,9 +949,20 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     req.generic = o.program == 1;
     req.ckpt_mode = o.ckpt_mode;
     req.mem_save = o.mem_save != 0;
+    // given states arrive in circuit order: their plans keep the identity layout
+    req.relabel = c->encoding == QF_ENC_RY_X;
+    if (c->lay_valid && c->lay_tile_bits == o.tile_bits && c->lay_generic == (int)req.generic) {
+      req.qshift = c->lay_shift;
+      req.strict = c->lay_strict;
+    }
     c->tc = false;
     if (c->path == QF_PATH_FUSED) {
       c->fp = qf::plan_fused(c->circ, req);
+      c->lay_valid = true;
+      c->lay_tile_bits = o.tile_bits;
+      c->lay_generic = (int)req.generic;
+      c->lay_shift = c->fp.qshift;
+      c->lay_strict = c->fp.strict;
       c->gp = qf::PerGatePlan();
       if (o.tc_path) {
         if (!c->fp.rounds || c->fp.K != qf::kMaxTileBits)
@@ -1063,6 +1089,7 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
     info->mem_save = c->fp.mem_save ? 1 : 0;
     info->n_pass_slots = c->fp.n_aslots;
     info->tc_path = c->tc ? 1 : 0;
+    info->qubit_shift = c->fp.qshift;
     if (c->tc) info->launches_fwd += 1;  // the B-block table
     if (c->fp.ckpt_mode == 1) info->launches_bwd = (int32_t)c->fp.a_sched.size() + 2;
   } else {
@@ -1170,6 +1197,7 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, i
     if (P.ckpt_mode != 1) return fail(QF_ERR_INVALID_ARG, "direction 2 needs a ckpt_mode 1 plan");
     std::vector<int32_t> w;
     w.push_back(P.rounds ? 1 : 0);
+    w.push_back(P.qshift);
     w.push_back((int32_t)P.a_sched.size());
     for (size_t i = 0; i < P.a_sched.size(); ++i) {
       const qf::PassDesc& pd = P.a_sched[i];
@@ -1189,6 +1217,7 @@ qf_status qf_plan_export(const qf_circuit* c, int32_t direction, int32_t* buf, i
   const auto& ops = direction == 0 ? P.fwd_ops : P.bwd_ops;
   std::vector<int32_t> w;
   w.push_back(P.rounds ? 1 : 0);
+  w.push_back(P.qshift);
   w.push_back((int32_t)passes.size());
   for (const qf::PassDesc& pd : passes) {
     const int32_t hdr[11] = {pd.op_begin, pd.op_end, pd.psi_src, pd.psi_dst, pd.lam_src, pd.lam_dst,
@@ -1645,6 +1674,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       p.B = b->B[i];
       p.n = c->circ.n;
       p.n_eff = P.n_eff;
+      p.qshift = P.qshift;
       p.enc = rel<float2>(w0 + L.enc);
       p.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
       p.rpf_src = T.fwd_rounds;

@@ -1241,7 +1241,11 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     const int64_t bb = i / a.n_eff;
     const int q = (int)(i - bb * a.n_eff);
     double s = 0.0, c = 1.0;  // a padding qubit stays |0>
-    if (q < a.n) sincos(0.5 * (a.x64 ? a.x64[bb * a.n + q] : (double)a.x[bb * a.n + q]), &s, &c);
+    if (q < a.n) {
+      // simulated bit q holds circuit qubit (q - qshift) mod n
+      const int qc = a.qshift ? (q + a.n - a.qshift) % a.n : q;
+      sincos(0.5 * (a.x64 ? a.x64[bb * a.n + qc] : (double)a.x[bb * a.n + qc]), &s, &c);
+    }
     if (a.enc64) a.enc64[i] = make_double2(c, s);
     else a.enc[i] = make_float2((float)c, (float)s);
     return;

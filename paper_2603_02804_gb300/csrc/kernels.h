@@ -66,6 +66,7 @@ struct PrepArgs {
   const double* x64;           // if non-null: float64 encoding angles, x unused
   int64_t B;
   int32_t n, n_eff;
+  int32_t qshift;              // simulated bit of circuit qubit q: (q + qshift) mod n
   float2* enc;
   double2* enc64;              // if non-null instead of enc: (cos, sin) of x/2 in float64
   // round programs: the parameters of every round gathered in round order

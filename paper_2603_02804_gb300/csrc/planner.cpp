@@ -725,13 +725,64 @@ static double plan_cost(const FusedPlan& P) {
   return (double)P.n_rounds + 0.25 * P.n_steps + 2.0 * passes;
 }
 
-// Multi-tile round programs are planned with both catch-up rules and the
-// cheaper plan is kept.
+namespace {
+// The circuit with qubit q relabelled (q + s) mod n. Round programs stay
+// eligible: a CZ between neighbours q, q+1 (or the ring's n-1, 0) joins
+// neighbours again, or the pair n-1, 0.
+Circuit shifted(const Circuit& c, int s) {
+  if (s == 0) return c;
+  Circuit r = c;
+  for (Gate& g : r.gates) {
+    g.q0 = (g.q0 + s) % c.n;
+    if (g.q1 >= 0) g.q1 = (g.q1 + s) % c.n;
+  }
+  return r;
+}
+}  // namespace
+
+// Layout and catch-up rule. Every tile holds simulated qubits 0..3 (whole
+// 128-byte runs of the state), so a chain whose end sits there is cut into two
+// segments by most tiles, and each pass's light cone is shallower. For
+// multi-tile round programs the planner therefore tries every cyclic shift
+// of the qubits and both catch-up rules on a prefix of the circuit (about
+// 16 layers of the ansatz; the plan's structure repeats) and keeps the
+// cheapest.
+void choose_layout(const Circuit& c, const PlanRequest& req, int* qshift, int* strict) {
+  *qshift = 0;
+  *strict = 0;
+  Circuit pre = c;
+  pre.layers = -1;
+  pre.gates.resize(std::min<size_t>(c.gates.size(), (size_t)64 * std::max(c.n, 1)));
+  PlanRequest rq = req;
+  rq.ckpt_layers = 1 << 30;
+  rq.ckpt_mode = 0;
+  rq.mem_save = false;
+  const FusedPlan probe = plan_fused_with(pre, rq, false);
+  if (!probe.rounds || probe.n_eff <= probe.K) return;
+  double best = plan_cost(probe);
+  const int shifts = req.relabel && c.n >= 5 ? c.n : 1;
+  for (int s = 0; s < shifts; ++s) {
+    const Circuit cs = shifted(pre, s);
+    for (int st = 0; st < 2; ++st) {
+      if (s == 0 && st == 0) continue;  // the probe
+      const double cost = plan_cost(plan_fused_with(cs, rq, st != 0));
+      if (cost < best) {
+        best = cost;
+        *qshift = s;
+        *strict = st;
+      }
+    }
+  }
+}
+
 FusedPlan plan_fused(const Circuit& c_in, const PlanRequest& req) {
-  FusedPlan a = plan_fused_with(c_in, req, false);
-  if (!a.rounds || a.n_eff <= a.K) return a;
-  FusedPlan b = plan_fused_with(c_in, req, true);
-  return plan_cost(b) < plan_cost(a) ? b : a;
+  int s = req.qshift, st = req.strict;
+  if (s < 0 || st < 0) choose_layout(c_in, req, &s, &st);
+  if (!req.relabel || c_in.n < 5) s = 0;
+  FusedPlan P = plan_fused_with(shifted(c_in, s), req, st != 0);
+  P.qshift = s;
+  P.strict = st;
+  return P;
 }
 
 namespace {

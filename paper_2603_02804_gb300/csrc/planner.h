@@ -56,6 +56,11 @@ struct FusedPlan {
   int n_aslots = 0;          // A: pass-output slots (one block's worth)
   std::vector<PassDesc> a_sched;
   std::vector<uint8_t> a_dir;  // 0: forward program pass, 1: adjoint program pass
+  // Layout: circuit qubit q is simulated as bit (q + qshift) mod n of the
+  // state index (0 for n < 5). Every table, mask and index of the plan is in
+  // simulated bits; observables and encodings are mapped at the boundary.
+  int qshift = 0;
+  int strict = 0;  // catch-up rule the plan was made with (multi-tile round programs)
 };
 
 // Per-gate schedule (the unfused comparator path).
@@ -74,12 +79,17 @@ struct PlanRequest {
   bool generic = false;  // force the generic step program
   int ckpt_mode = 0;     // 0 = B (reverse in-kernel), 1 = A (per-block recompute)
   bool mem_save = false; // A only: bfloat16 pass outputs
+  bool relabel = true;   // the planner may simulate the qubits in a cyclically shifted order
+  int qshift = -1;       // layout to use (-1: choose), as FusedPlan::qshift
+  int strict = -1;       // catch-up rule to use (-1: choose), as FusedPlan::strict
 };
 
 // Throws std::runtime_error with a message on invalid input.
 void build_hea(Circuit& c, int n, int d, int entangler);
 void validate_circuit(const Circuit& c);
 FusedPlan plan_fused(const Circuit& c, const PlanRequest& req);
+// The layout (qubit shift) and catch-up rule plan_fused would choose.
+void choose_layout(const Circuit& c, const PlanRequest& req, int* qshift, int* strict);
 PerGatePlan plan_per_gate(const Circuit& c, const PlanRequest& req);
 int ckpt_interval_gates(const Circuit& c, int ckpt_layers);
 

@@ -53,7 +53,8 @@ class qf_plan_info_t(ctypes.Structure):
         "n_qubits", "n_eff", "n_params", "n_slots", "path", "tile_bits", "n_passes", "n_steps",
         "n_fused_ops", "n_ckpt", "ckpt_layers", "launches_fwd", "launches_bwd")] + [
         ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64)] + [
-        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "tc_path", "precision")]
+        (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "tc_path", "precision",
+                                            "qubit_shift")]
 
 
 _vp = ctypes.c_void_p

@@ -30,6 +30,7 @@ def parse(words):
     prog = Program()
     prog.rounds_mode = w[i] == 1
     i += 1
+    prog.qshift = w[i]; i += 1  # circuit qubit q is simulated bit (q + qshift) mod n
     n_pass = w[i]; i += 1
     passes = []
     keys = ["op_begin", "op_end", "psi_src", "psi_dst", "lam_src", "lam_dst", "flags", "K", "n_groups",
@@ -176,7 +177,22 @@ def fwd_ops(prog, pd, psi, n_eff, theta, slots):
     return psi
 
 
+def layout_mask(prog, m, n):
+    """A mask of circuit qubits as simulated bits of the plan's layout."""
+    s = getattr(prog, "qshift", 0)
+    if s == 0:
+        return m
+    return ((m << s) | (m >> (n - s))) & ((1 << n) - 1)
+
+
+def layout_x(prog, xrow, n):
+    """Encoding angles per simulated bit: bit p holds circuit qubit (p - s) mod n."""
+    s = getattr(prog, "qshift", 0)
+    return np.asarray([xrow[(p - s) % n] for p in range(n)]) if s else xrow
+
+
 def run_forward(prog, n, n_eff, theta, xrow, xm, zm):
+    xrow, xm, zm = layout_x(prog, xrow, n), layout_mask(prog, xm, n), layout_mask(prog, zm, n)
     slots = {}
     work = None
     E = None
@@ -258,6 +274,7 @@ def _term_grad(prog, grad_term, seen, n_params):
 
 def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params):
     """Per-parameter gradient; every gradient term must be visited once."""
+    xm, zm = layout_mask(prog, xm, n_eff), layout_mask(prog, zm, n_eff)  # a shift implies n = n_eff
     grad_term = np.zeros(len(prog.terms))
     seen = np.zeros(len(prog.terms), int)
     work = lam_buf = None
@@ -279,10 +296,10 @@ PF_SRC_H, PF_DST_H = 2, 4
 def parse_schedule(words):
     """Mode A adjoint launch list (qf_plan_export direction 2)."""
     w = [int(v) for v in words]
-    n = w[1]
+    n = w[2]  # w[1]: the layout's qubit shift (as in the programs)
     keys = ["op_begin", "op_end", "psi_src", "psi_dst", "lam_src", "lam_dst", "flags", "K", "n_groups",
             "outer_mask", "xm_local"]
-    out, i = [], 2
+    out, i = [], 3
     for _ in range(n):
         d = dict(zip(keys, w[i + 1:i + 12]))
         d["dir"] = w[i]
@@ -311,6 +328,7 @@ def run_backward_mode_a(fprog, bprog, sched, n, n_eff, theta, xrow, slots, xm, z
     seen = np.zeros(len(bprog.terms), int)
     aslots = {}
     lam_buf = None
+    xrow, xm, zm = layout_x(bprog, xrow, n), layout_mask(bprog, xm, n), layout_mask(bprog, zm, n)
 
     def load(src, half):
         if src == SRC_GENERATE:
