@@ -687,8 +687,8 @@ def main():
                          ("complex128", dict(precision="complex128"))):
             if kw == opts:
                 continue
-            c128 = kw.get("precision") == "complex128"
-            inp = inp64 if c128 else None
+            v128 = kw.get("precision") == "complex128"
+            inp = inp64 if v128 else None
             try:
                 vs = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs, **kw)
             except qfuse.QFError as err:
@@ -699,13 +699,13 @@ def main():
             torch.cuda.synchronize()
             qfuse.qf_profile(vs.handle, True)
             qfuse.qf_profile_read(vs.handle)
-            K = min(args.steps, 50 if c128 else 200)
+            K = min(args.steps, 50 if v128 else 200)
             v_ms, _ = timed(vs, K, inp)
             vp = qfuse.qf_profile_read(vs.handle)
             variants[name] = {"value": w.B * K / (v_ms / 1e3), "unit": "samples/s", "ms_per_step": v_ms / K,
                               "fwd_ms_per_step": vp["fwd_ms"] / K, "bwd_ms_per_step": vp["bwd_ms"] / K,
                               "device_status": qfuse.qf_device_status(stream)}
-            if c128:
+            if v128:
                 vi = vs.info()
                 f_fl, b_fl = generic_flops(vi, w.n, w.B)
                 b_ms = vp["bwd_ms"] / max(vp["bwd_launches"], 1)

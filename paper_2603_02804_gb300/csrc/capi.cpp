@@ -1685,7 +1685,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       r.n_params = c->circ.n_params;
       r.param_off = T.param_off;
       r.param_terms = T.param_terms;
-      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff + 4ll * p.n_rpf + 8ll * p.n_rpb;
+      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff + 8ll * p.n_rpf + 8ll * p.n_rpb;
       gout_pref[i + 1] = gout_pref[i] + c->circ.n_params;
     }
     memcpy(img.data() + circ_off, recs.data(), recs.size() * sizeof(qf::BatchCircuit));

@@ -1182,28 +1182,35 @@ __device__ double term_angle(const PrepArgs& a, int64_t t) {
 
 // u(phi) = (-1)^k u(w) with w = phi - 2 pi k in (-pi, pi]: the rotation by w/2
 // as three shears needs tan(w/4) (|.| <= 1) and sin(w/2); a missing term (-1)
-// is the identity (all zero).
-__device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
-  if (t < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+// is the identity (all zero). tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the
+// half-angle identity; the denominator lies in [1, 2] for |w/2| <= pi/2), so
+// one float64 sincos gives both.
+__device__ void shear_params(const PrepArgs& a, int32_t t, double& tq, double& sh, int& parity) {
   const double phi = term_angle(a, t);
   const double two_pi = 6.283185307179586476925286766559;
   const double k = rint(phi / two_pi);
   const double w = phi - two_pi * k;
-  const int parity = ((long long)k) & 1;
-  return make_float4((float)tan(0.25 * w), (float)sin(0.5 * w), __int_as_float(parity), 0.f);
+  double c;
+  sincos(0.5 * w, &sh, &c);
+  tq = sh / (1.0 + c);
+  parity = ((long long)k) & 1;
+}
+
+__device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
+  if (t < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  double tq, sh;
+  int parity;
+  shear_params(a, t, tq, sh, parity);
+  return make_float4((float)tq, (float)sh, __int_as_float(parity), 0.f);
 }
 
 // The same in float64 (complex128 round programs).
 __device__ Shear64 term_shear64(const PrepArgs& a, int32_t t) {
   Shear64 r{0.0, 0.0, 0, 0};
   if (t < 0) return r;
-  const double phi = term_angle(a, t);
-  const double two_pi = 6.283185307179586476925286766559;
-  const double k = rint(phi / two_pi);
-  const double w = phi - two_pi * k;
-  r.t = tan(0.25 * w);
-  r.s = sin(0.5 * w);
-  r.wrap = ((long long)k) & 1;
+  int parity;
+  shear_params(a, t, r.t, r.s, parity);
+  r.wrap = parity;
   return r;
 }
 
@@ -1251,21 +1258,18 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     return;
   }
   i -= (int64_t)a.B * a.n_eff;
-  if (i < 4ll * a.n_rpf) {
-    // forward round r, item k: shear parameters of its RY term and RZ-run term
-    const int64_t r = i >> 2;
-    const int k = (int)(i & 3);
+  if (i < 8ll * a.n_rpf) {
+    // forward round r, item k: shear parameters of its RY term (j = 0) or of
+    // its RZ-run term (j = 1), at 2k + j
+    const int64_t r = i >> 3;
+    const int k = (int)((i >> 1) & 3), j = (int)(i & 1);
     const int32_t* rec = reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords;
-    if (a.rpf64) {
-      a.rpf64[r * 8 + 2 * k] = term_shear64(a, rec[12 + k]);
-      a.rpf64[r * 8 + 2 * k + 1] = term_shear64(a, rec[8 + k]);
-    } else {
-      a.rpf[r * 8 + 2 * k] = term_shear_of(a, rec[12 + k]);
-      a.rpf[r * 8 + 2 * k + 1] = term_shear_of(a, rec[8 + k]);
-    }
+    const int32_t t = rec[j ? 8 + k : 12 + k];
+    if (a.rpf64) a.rpf64[r * 8 + 2 * k + j] = term_shear64(a, t);
+    else a.rpf[r * 8 + 2 * k + j] = term_shear_of(a, t);
     return;
   }
-  i -= 4ll * a.n_rpf;
+  i -= 8ll * a.n_rpf;
   if (i < 8ll * a.n_rpb) {
     // backward round r, slot k: tz[0..3] then ty[0..3]
     const int64_t r = i >> 3;
@@ -1531,7 +1535,7 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + 4ll * a.n_rpf + 8ll * a.n_rpb;
+  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + 8ll * a.n_rpf + 8ll * a.n_rpb;
   if (total == 0) return cudaSuccess;
   // float64 work per element: small blocks spread it over more SMs
   const int blk = 64;

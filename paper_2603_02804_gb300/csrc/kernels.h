@@ -72,7 +72,7 @@ struct PrepArgs {
   // round programs: the parameters of every round gathered in round order
   int32_t n_rpf;               // forward rounds
   const uint4* rpf_src;        // forward round records (fused index per item)
-  float4* rpf;                 // [n_rpf][8]: item k's fused 2x2 at 2k, 2k+1
+  float4* rpf;                 // [n_rpf][8]: item k's RY-term shear at 2k, its RZ-run-term shear at 2k+1
   int32_t n_rpb;               // backward rounds
   const uint4* rpb_src;        // backward round records (tz[4], ty[4] terms)
   float4* rpb;                 // [n_rpb][8]: shear parameters of tz[0..3], ty[0..3]
