@@ -35,7 +35,7 @@ struct Layout {
   size_t rpf = 0, rpb = 0;  // round-ordered item parameters (round programs)
   size_t mats64 = 0, tcb = 0;  // tensor-core path: float64 fused 2x2s, per-round B blocks
   size_t work = 0, lam = 0, slots = 0, hslots = 0;
-  size_t epart = 0, gpart = 0;
+  size_t epart = 0, gpart = 0, gred = 0;  // gred: stage-1 scratch of a two-stage gradient reduction
   size_t total = 0;
   int64_t state_elems = 0;  // batch * 2^n_eff
   int64_t rows = 0;         // partial rows per sample (tiles or chunks)
@@ -198,6 +198,8 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
   }
   L.epart = take((size_t)B * L.rows * 8);
   L.gpart = take((size_t)B * L.rows * S * 8);
+  if (c->path == QF_PATH_FUSED && qf::g_reduce_stages(L.rows, 1) == 2)
+    L.gred = take((size_t)qf::g_reduce_scratch(B, L.rows, S) * 8);
   L.total = o;
   return L;
 }
@@ -545,8 +547,9 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   g.param_slots = T.param_terms;
   g.per_sample = per_sample;
   g.grad = grad;
+  g.scratch = L.gred ? at<double>(ws, L.gred) : nullptr;
   QF_CU(qf::launch_g_reduce(g, st));
-  c->call_launches++;
+  c->call_launches += qf::g_reduce_stages(g.tps, g.slot_step);
   return QF_OK;
 }
 
@@ -720,8 +723,9 @@ qf_status fused_backward64(qf_circuit* c, const DevTables& T, const Layout& L, c
   g.param_slots = T.param_terms;
   g.per_sample = per_sample;
   g.grad = grad;
+  g.scratch = L.gred ? at<double>(ws, L.gred) : nullptr;
   QF_CU(qf::launch_g_reduce(g, st));
-  c->call_launches++;
+  c->call_launches += qf::g_reduce_stages(g.tps, g.slot_step);
   return QF_OK;
 }
 
@@ -822,8 +826,9 @@ qf_status pg_backward(qf_circuit* c, const DevTables& T, const Layout& L, const 
   g.param_slots = T.param_terms;
   g.per_sample = per_sample;
   g.grad = grad;
+  g.scratch = L.gred ? at<double>(ws, L.gred) : nullptr;
   QF_CU(qf::launch_g_reduce(g, st));
-  c->call_launches++;
+  c->call_launches += qf::g_reduce_stages(g.tps, g.slot_step);
   return QF_OK;
 }
 
@@ -1084,14 +1089,15 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
     info->n_fused_ops = (int32_t)c->fp.fuse_off.size() - 1;
     info->n_ckpt = c->fp.n_ckpt;
     info->launches_fwd = info->n_passes + 2;
-    info->launches_bwd = info->n_passes + 2;
+    // a two-stage gradient reduction when a sample has many tile rows
+    info->launches_bwd = info->n_passes + 1 + qf::g_reduce_stages(c->L.rows, 1);
     info->ckpt_mode = c->fp.ckpt_mode;
     info->mem_save = c->fp.mem_save ? 1 : 0;
     info->n_pass_slots = c->fp.n_aslots;
     info->tc_path = c->tc ? 1 : 0;
     info->qubit_shift = c->fp.qshift;
     if (c->tc) info->launches_fwd += 1;  // the B-block table
-    if (c->fp.ckpt_mode == 1) info->launches_bwd = (int32_t)c->fp.a_sched.size() + 2;
+    if (c->fp.ckpt_mode == 1) info->launches_bwd = (int32_t)c->fp.a_sched.size() + 1 + qf::g_reduce_stages(c->L.rows, 1);
   } else {
     info->n_eff = c->gp.n_eff;
     info->n_slots = c->gp.n_slots;

@@ -1289,6 +1289,39 @@ __global__ void e_reduce_kernel(const double* e_part, int64_t B, int tps, double
   E[bb] = s;
 }
 
+// The same for many partials per sample: one block per sample, thread k sums
+// partials k, k + 256, ... in order, then a fixed tree (bitwise repeatable).
+__global__ void __launch_bounds__(256) e_reduce_block_kernel(const double* e_part, int tps, double* E) {
+  __shared__ double red[256];
+  const int64_t bb = blockIdx.x;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < tps; t += 256) s += e_part[bb * tps + t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) E[bb] = red[0];
+}
+
+// Stage 1 of a two-stage gradient reduction over partials [row][slot]
+// (slots contiguous): block (group g, chunk c) sums rows
+// g * rows_per_group + c * kGReduceChunk .. (chunk end) of each slot in row
+// order; consecutive threads read consecutive slots of a row.
+__global__ void g_partial_kernel(const double* g_part, int64_t rows_per_group, int64_t chunks, int64_t slot_stride,
+                                 int S, double* out) {
+  const int64_t gc = blockIdx.x;
+  const int64_t g = gc / chunks, c = gc - g * chunks;
+  const int s = blockIdx.y * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const int64_t r0 = g * rows_per_group + c * kGReduceChunk;
+  const int64_t r1 = g * rows_per_group + min(rows_per_group, (c + 1) * (int64_t)kGReduceChunk);
+  double acc = 0.0;
+  for (int64_t r = r0; r < r1; ++r) acc += g_part[r * slot_stride + s];
+  out[gc * S + s] = acc;
+}
+
 // grad[p] (or grad[b][p]) = sum over tiles, then over the slots of p, in a
 // fixed order.
 __global__ void g_reduce_kernel(const GradReduceArgs a) {
@@ -1687,15 +1720,34 @@ cudaError_t device_status(int32_t* code, cudaStream_t st) {
 
 cudaError_t launch_e_reduce(const double* e_part, int64_t B, int tps, double* E, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  e_reduce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(e_part, B, tps, E);
+  if (tps >= 256) e_reduce_block_kernel<<<(unsigned)B, 256, 0, st>>>(e_part, tps, E);
+  else e_reduce_kernel<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(e_part, B, tps, E);
   return cudaGetLastError();
 }
 
 cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st) {
   const int64_t n = a.per_sample ? (int64_t)a.B * a.n_params : a.n_params;
   if (n == 0) return cudaSuccess;
+  GradReduceArgs r = a;
+  if (g_reduce_stages(a.tps, a.slot_step) == 2) {
+    // many rows per output: coalesced chunk sums first (groups: the samples
+    // in per-sample mode, else all rows), then the fixed-order sum over chunks
+    if (a.scratch == nullptr || a.B == 0) return cudaErrorInvalidValue;
+    const int64_t groups = a.per_sample ? a.B : 1;
+    const int64_t rows = a.per_sample ? a.tps : a.B * a.tps;
+    const int64_t chunks = (rows + kGReduceChunk - 1) / kGReduceChunk;
+    const int S = (int)a.slot_stride;
+    const dim3 grid((unsigned)(groups * chunks), (unsigned)((S + 255) / 256));
+    g_partial_kernel<<<grid, 256, 0, st>>>(a.g_part, rows, chunks, a.slot_stride, S, a.scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    r.g_part = a.scratch;
+    r.B = groups;
+    r.tps = chunks;
+    r.per_sample = a.per_sample;
+  }
   const int64_t threads = n * 32;
-  g_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
+  g_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(r);
   return cudaGetLastError();
 }
 

@@ -91,7 +91,18 @@ struct GradReduceArgs {
   const int32_t* param_slots;
   int32_t per_sample;
   double* grad;
+  double* scratch;      // stage-1 partials of a two-stage reduction (g_reduce_stages() == 2)
 };
+
+// Launches of launch_g_reduce for partial rows per sample `tps` and slot
+// step: two (a coalesced stage over row chunks, then the fixed-order sum)
+// when a sample has at least kGReduceChunk rows of contiguous slots.
+constexpr int kGReduceChunk = 256;
+inline int g_reduce_stages(int64_t tps, int64_t slot_step) { return slot_step == 1 && tps >= kGReduceChunk ? 2 : 1; }
+// Elements of the stage-1 scratch for B samples.
+inline int64_t g_reduce_scratch(int64_t B, int64_t tps, int64_t n_slots) {
+  return B * ((tps + kGReduceChunk - 1) / kGReduceChunk) * n_slots;
+}
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
 cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st);
