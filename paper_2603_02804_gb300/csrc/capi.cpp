@@ -414,6 +414,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.tcb = c->tc ? at<float>(ws, L.tcb) : nullptr;
   set_input(c, x, a);
   a.rounds = P.rounds ? T.fwd_rounds : nullptr;
+  a.rx_items = P.has_rx ? 1 : 0;
   a.rpar = P.rounds ? at<float4>(ws, L.rpf) : nullptr;
   a.mats = pa.mats;
   a.cs = pa.cs;
@@ -483,6 +484,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.B = B;
   a.ops = T.bwd_ops;
   a.rounds = P.rounds ? T.bwd_rounds : nullptr;
+  a.rx_items = P.has_rx ? 1 : 0;
   a.rpar = P.rounds ? at<float4>(ws, L.rpb) : nullptr;
   a.cs = pa.cs;
   a.shear = pa.shear;
@@ -564,6 +566,7 @@ qf::PassArgs64 pass_args64(const qf_circuit* c, const Layout& L, void* ws, int64
   a.cs = at<double2>(ws, L.cs);
   a.rounds = nullptr;
   a.rpar = nullptr;
+  a.rx_items = P.has_rx ? 1 : 0;
   a.enc = at<double2>(ws, L.enc);
   a.n_in = c->circ.n;
   a.work = at<double2>(ws, L.work);
@@ -1533,6 +1536,8 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       if (!c || !c->planned) throw std::invalid_argument("circuit has no plan" + at);
       if (c->encoding != QF_ENC_RY_X) throw std::invalid_argument("batched launches take RY(x) encodings" + at);
       if (c->f64) throw std::invalid_argument("batched launches are complex64" + at);
+      if (c->path == QF_PATH_FUSED && c->fp.has_rx)
+        throw std::invalid_argument("batched launches take RZ/RY round programs (no RX)" + at);
       if (c->path == QF_PATH_FUSED && (c->fp.ckpt_mode != 0 || c->tc))
         throw std::invalid_argument("batched launches use checkpoint mode 0 on the CUDA cores" + at);
       if (c->path != QF_PATH_FUSED || !c->fp.rounds)

@@ -230,6 +230,55 @@ __device__ __forceinline__ void apply_pending(uint32_t D, float2 (&r)[16], float
 // (-t, -s). A pending Z_R turns RY(w) into RY(-w); the wrap parities go to
 // the pending constant sign.
 template <int R>
+__device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D);
+
+// RX(w) applied on register bit R: a rotation by -w/2 of the real pairs
+// (re p0, im p1) and (re p1, im p0), three shears each (x += t y; y -= s x;
+// x += t y). A pending Z_R turns RX(w) into RX(-w).
+template <int R>
+__device__ __forceinline__ void rx_fwd(float2 (&r)[16], float4 yq, uint32_t a) {
+  const int f = (int)(a << 31);
+  const float t = __int_as_float(__float_as_int(yq.x) ^ f), s = __int_as_float(__float_as_int(yq.y) ^ f);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    float2 p0 = r[j], p1 = r[j1];
+    p0.x = fmaf(t, p1.y, p0.x); p1.y = fmaf(-s, p0.x, p1.y); p0.x = fmaf(t, p1.y, p0.x);
+    p1.x = fmaf(t, p0.y, p1.x); p0.y = fmaf(-s, p1.x, p0.y); p1.x = fmaf(t, p0.y, p1.x);
+    r[j] = p0; r[j1] = p1;
+  }
+}
+
+// The RZ run of an item on register bit R, applied.
+template <int R>
+__device__ __forceinline__ void rz_fwd(float2 (&r)[16], float4 zq) {
+  const float t = zq.x, s = zq.y;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << R)) continue;
+    const int j1 = j | (1 << R);
+    float2 p0 = r[j], p1 = r[j1];
+    p0.x = fmaf(t, p0.y, p0.x); p0.y = fmaf(-s, p0.x, p0.y); p0.x = fmaf(t, p0.y, p0.x);
+    p1.x = fmaf(-t, p1.y, p1.x); p1.y = fmaf(s, p1.x, p1.y); p1.x = fmaf(-t, p1.y, p1.x);
+    r[j] = p0; r[j1] = p1;
+  }
+}
+
+// Forward item of a round program that may hold RX items (rx: this item's
+// rotation is an RX; uniform over the CTA).
+template <int R, bool RX>
+__device__ __forceinline__ void item_fwd_x(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D, bool rx) {
+  if (RX && rx) {
+    rx_fwd<R>(r, yq, a);
+    rz_fwd<R>(r, zq);
+    D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
+  } else {
+    item_fwd<R>(r, yq, zq, a, D);
+  }
+}
+
+template <int R>
 __device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D) {
   const int f = (int)(a << 31);
   const float2 T = make_float2(-__int_as_float(__float_as_int(yq.x) ^ f), 0.f);
@@ -276,6 +325,14 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
       l0.x = fmaf(-t, l0.y, l0.x); l0.y = fmaf(s, l0.x, l0.y); l0.x = fmaf(-t, l0.y, l0.x);
       p1.x = fmaf(t, p1.y, p1.x); p1.y = fmaf(-s, p1.x, p1.y); p1.x = fmaf(t, p1.y, p1.x);
       l1.x = fmaf(t, l1.y, l1.x); l1.y = fmaf(-s, l1.x, l1.y); l1.x = fmaf(t, l1.y, l1.x);
+    } else if (KIND == G_RX) {
+      // Im<lambda|X|psi> per pair; RX(w)^dagger rotates (re p0, im p1) and
+      // (re p1, im p0) by +w/2: x -= t y; y += s x; x -= t y
+      acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
+      p0.x = fmaf(-t, p1.y, p0.x); p1.y = fmaf(s, p0.x, p1.y); p0.x = fmaf(-t, p1.y, p0.x);
+      p1.x = fmaf(-t, p0.y, p1.x); p0.y = fmaf(s, p1.x, p0.y); p1.x = fmaf(-t, p0.y, p1.x);
+      l0.x = fmaf(-t, l1.y, l0.x); l1.y = fmaf(s, l0.x, l1.y); l0.x = fmaf(-t, l1.y, l0.x);
+      l1.x = fmaf(-t, l0.y, l1.x); l0.y = fmaf(s, l1.x, l0.y); l1.x = fmaf(-t, l0.y, l1.x);
     } else {
       // RY is real: the same shear acts on re and im, so each step is one
       // packed FFMA2 on the (re, im) pair; Im<lambda|Y|psi> per pair is
@@ -291,7 +348,7 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
     }
     p[j] = p0; p[j1] = p1; l[j] = l0; l[j1] = l1;
   }
-  if (KIND != G_RZ) acc = (accp.x + accp.y) - (accm.x + accm.y);
+  if (KIND == G_RY) acc = (accp.x + accp.y) - (accm.x + accm.y);
   return acc;
 }
 
@@ -299,14 +356,17 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
 // parameters (t, s, wrap parity)). With a pending Z_R the RY un-applies as
 // RY(+w) (t, s negated) and its Im<lambda|Y|psi> changes sign. The wrap
 // parities (u(phi) = -u(w) for odd k) go to the pending constant sign.
-template <int R>
+// rx: the item's rotation is an RX (RX: the program holds RX items); a
+// pending Z_R acts on it as on an RY.
+template <int R, bool RX = false>
 __device__ __forceinline__ void item_bwd(float2 (&p)[16], float2 (&l)[16], float4 zq, float4 yq, uint32_t a,
-                                         uint32_t& D, float& gz, float& gy) {
+                                         uint32_t& D, float& gz, float& gy, bool rx = false) {
   gz = bwd_shear<R, G_RZ>(p, l, zq.x, zq.y);
   const int f = (int)(a << 31);
   const float t = __int_as_float(__float_as_int(yq.x) ^ f);
   const float s = __int_as_float(__float_as_int(yq.y) ^ f);
-  gy = __int_as_float(__float_as_int(bwd_shear<R, G_RY>(p, l, t, s)) ^ f);
+  const float g = RX && rx ? bwd_shear<R, G_RX>(p, l, t, s) : bwd_shear<R, G_RY>(p, l, t, s);
+  gy = __int_as_float(__float_as_int(g) ^ f);
   D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
 }
 
@@ -580,7 +640,7 @@ struct PassShared {
 // (tile = sample * tiles_per_sample + tile within the sample). Ends with a
 // barrier, so a CTA may call it again for another pass or tile range. LOADS:
 // tile loads in flight per thread and state (8 = the whole tile at once).
-template <bool BWD, bool ROUNDS, int LOADS = 8, bool TC = false>
+template <bool BWD, bool ROUNDS, int LOADS = 8, bool TC = false, bool RX = false>
 __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_tile, float2* smem, PassShared& sh,
                                          const TcCtx* tc = nullptr) {
   uint32_t (&s_lg)[256] = sh.lg;
@@ -808,20 +868,20 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
 #pragma unroll 1
       for (int k = 0; k < nr; ++k) {
         if (!BWD) {
-          const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];
-          item_fwd<0>(r, P.v[k][0], P.v[k][1], D & 1u, D);
-          item_fwd<1>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u, D);
-          item_fwd<2>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u, D);
-          item_fwd<3>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u, D);
+          const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];  // links, bbits, rx mask
+          item_fwd_x<0, RX>(r, P.v[k][0], P.v[k][1], D & 1u, D, lk.z & 1u);
+          item_fwd_x<1, RX>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u, D, (lk.z >> 1) & 1u);
+          item_fwd_x<2, RX>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u, D, (lk.z >> 2) & 1u);
+          item_fwd_x<3, RX>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u, D, (lk.z >> 3) & 1u);
           chain_pending<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
         } else {
-          const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];
+          const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];  // links, bbits, rx mask
           chain_pending<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
           float v[8];
-          item_bwd<0>(r, l, P.v[k][0], P.v[k][4], D & 1u, D, v[0], v[4]);
-          item_bwd<1>(r, l, P.v[k][1], P.v[k][5], (D >> 1) & 1u, D, v[1], v[5]);
-          item_bwd<2>(r, l, P.v[k][2], P.v[k][6], (D >> 2) & 1u, D, v[2], v[6]);
-          item_bwd<3>(r, l, P.v[k][3], P.v[k][7], (D >> 3) & 1u, D, v[3], v[7]);
+          item_bwd<0, RX>(r, l, P.v[k][0], P.v[k][4], D & 1u, D, v[0], v[4], lk.z & 1u);
+          item_bwd<1, RX>(r, l, P.v[k][1], P.v[k][5], (D >> 1) & 1u, D, v[1], v[5], (lk.z >> 1) & 1u);
+          item_bwd<2, RX>(r, l, P.v[k][2], P.v[k][6], (D >> 2) & 1u, D, v[2], v[6], (lk.z >> 2) & 1u);
+          item_bwd<3, RX>(r, l, P.v[k][3], P.v[k][7], (D >> 3) & 1u, D, v[3], v[7], (lk.z >> 3) & 1u);
           int idx;
           const float sum = butterfly8(v, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
@@ -1042,11 +1102,13 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
   __syncthreads();
 }
 
-template <bool BWD, bool ROUNDS>
+// RX: round programs holding RX items (their own instance, so that programs
+// of RZ / RY items keep the plain code).
+template <bool BWD, bool ROUNDS, bool RX = false>
 __global__ void __launch_bounds__(kThreads, 2) pass_kernel(const PassArgs a) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ PassShared sh;
-  pass_cta<BWD, ROUNDS>(a, (int64_t)blockIdx.x * (kThreads >> (a.pd.K - kRegBits)), smem, sh);
+  pass_cta<BWD, ROUNDS, 8, false, RX>(a, (int64_t)blockIdx.x * (kThreads >> (a.pd.K - kRegBits)), smem, sh);
 }
 
 // Forward pass with the rounds on the tensor cores: one 12-qubit tile per
@@ -1582,17 +1644,20 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
   const int64_t grid = (total_tiles + tiles_per_cta - 1) / tiles_per_cta;
   if (grid == 0) return cudaSuccess;
   const size_t smem = (size_t)(bwd ? 2 : 1) * kTileAmps * sizeof(float2);
-  const bool rounds = a.rounds != nullptr;
+  const bool rounds = a.rounds != nullptr, rx = rounds && a.rx_items;
   if (bwd) {
     // 64 KiB of dynamic shared memory needs the opt-in
-    static OptIn once_generic, once_rounds;
-    cudaError_t e = rounds ? opt_in(reinterpret_cast<const void*>(pass_kernel<true, true>), smem, once_rounds)
-                           : opt_in(reinterpret_cast<const void*>(pass_kernel<true, false>), smem, once_generic);
+    static OptIn once_generic, once_rounds, once_rx;
+    cudaError_t e = rx       ? opt_in(reinterpret_cast<const void*>(pass_kernel<true, true, true>), smem, once_rx)
+                    : rounds ? opt_in(reinterpret_cast<const void*>(pass_kernel<true, true>), smem, once_rounds)
+                             : opt_in(reinterpret_cast<const void*>(pass_kernel<true, false>), smem, once_generic);
     if (e != cudaSuccess) return e;
-    if (rounds) pass_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    if (rx) pass_kernel<true, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    else if (rounds) pass_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else pass_kernel<true, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   } else {
-    if (rounds) pass_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    if (rx) pass_kernel<false, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    else if (rounds) pass_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else pass_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   }
   return cudaGetLastError();

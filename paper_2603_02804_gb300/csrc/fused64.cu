@@ -212,10 +212,24 @@ __device__ __forceinline__ void pending64(uint32_t D, double2 (&r)[16], double2 
 // pending constant sign. An absent part (no term) is the identity: skipped.
 template <int R>
 __device__ __forceinline__ void item_fwd64(double2 (&r)[16], const Shear64& y, const Shear64& z, uint32_t a,
-                                           uint32_t& D, bool has_y, bool has_z) {
+                                           uint32_t& D, bool has_y, bool has_z, bool rx = false) {
   const double ty = a ? y.t : -y.t, sy = a ? -y.s : y.s;
   const double t = z.t, s = z.s;
-  if (has_y) {
+  if (has_y && rx) {
+    // RX(w): a rotation by -w/2 of (re p0, im p1) and (re p1, im p0):
+    // x += t y; y -= s x; x += t y (t, s negated under a pending Z_R)
+    const double tx = -ty, sx = sy;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << R)) continue;
+      const int j1 = j | (1 << R);
+      double2 p0 = r[j], p1 = r[j1];
+      p0.x = fma(tx, p1.y, p0.x); p1.y = fma(-sx, p0.x, p1.y); p0.x = fma(tx, p1.y, p0.x);
+      p1.x = fma(tx, p0.y, p1.x); p0.y = fma(-sx, p1.x, p0.y); p1.x = fma(tx, p0.y, p1.x);
+      r[j] = p0;
+      r[j1] = p1;
+    }
+  } else if (has_y) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       if (j & (1 << R)) continue;
@@ -263,6 +277,13 @@ __device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16]
       l0.x = fma(-t, l0.y, l0.x); l0.y = fma(s, l0.x, l0.y); l0.x = fma(-t, l0.y, l0.x);
       p1.x = fma(t, p1.y, p1.x); p1.y = fma(-s, p1.x, p1.y); p1.x = fma(t, p1.y, p1.x);
       l1.x = fma(t, l1.y, l1.x); l1.y = fma(-s, l1.x, l1.y); l1.x = fma(t, l1.y, l1.x);
+    } else if (KIND == G_RX) {
+      // Im<lambda|X|psi>; RX(w)^dagger rotates (re p0, im p1) and (re p1, im p0) by +w/2
+      acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
+      p0.x = fma(-t, p1.y, p0.x); p1.y = fma(s, p0.x, p1.y); p0.x = fma(-t, p1.y, p0.x);
+      p1.x = fma(-t, p0.y, p1.x); p0.y = fma(s, p1.x, p0.y); p1.x = fma(-t, p0.y, p1.x);
+      l0.x = fma(-t, l1.y, l0.x); l1.y = fma(s, l0.x, l1.y); l0.x = fma(-t, l1.y, l0.x);
+      l1.x = fma(-t, l0.y, l1.x); l0.y = fma(s, l1.x, l0.y); l1.x = fma(-t, l0.y, l1.x);
     } else {
       acc += l1.x * p0.x + l1.y * p0.y - l0.x * p1.x - l0.y * p1.y;
       p0.x = fma(t, p1.x, p0.x); p0.y = fma(t, p1.y, p0.y);
@@ -285,11 +306,13 @@ __device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16]
 // sign. An absent part (no term) is skipped; its value is 0.
 template <int R>
 __device__ __forceinline__ void item_bwd64(double2 (&p)[16], double2 (&l)[16], const Shear64& z, const Shear64& y,
-                                           uint32_t a, uint32_t& D, double& gz, double& gy, bool has_z, bool has_y) {
+                                           uint32_t a, uint32_t& D, double& gz, double& gy, bool has_z, bool has_y,
+                                           bool rx = false) {
   gz = has_z ? shear_bwd64<R, G_RZ>(p, l, z.t, z.s) : 0.0;
   gy = 0.0;
   if (has_y) {
-    const double g = shear_bwd64<R, G_RY>(p, l, a ? -y.t : y.t, a ? -y.s : y.s);
+    const double t = a ? -y.t : y.t, s = a ? -y.s : y.s;
+    const double g = rx ? shear_bwd64<R, G_RX>(p, l, t, s) : shear_bwd64<R, G_RY>(p, l, t, s);
     gy = a ? -g : g;
   }
   D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
@@ -343,7 +366,7 @@ struct Shared64 {
 // One complex128 pass: CTA c owns tiles c * tiles_per_cta .. (tile = sample *
 // tiles_per_sample + tile within the sample); 2^(K-4) threads per tile, 16
 // amplitudes per thread per step.
-template <bool BWD, bool ROUNDS>
+template <bool BWD, bool ROUNDS, bool RX = false>
 __global__ void __launch_bounds__(kThreads, 1) pass64_kernel(const PassArgs64 a) {
   extern __shared__ __align__(16) double2 smem64[];
   __shared__ Shared64 sh;
@@ -503,20 +526,23 @@ __global__ void __launch_bounds__(kThreads, 1) pass64_kernel(const PassArgs64 a)
           // the items' terms (-1: the part is absent): tz in words 8..11, ty in 12..15
           const uint4 tz = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 2);
           const uint4 ty = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 3);
-          item_fwd64<0>(r, v[0], v[1], D & 1u, D, (int)ty.x >= 0, (int)tz.x >= 0);
-          item_fwd64<1>(r, v[2], v[3], (D >> 1) & 1u, D, (int)ty.y >= 0, (int)tz.y >= 0);
-          item_fwd64<2>(r, v[4], v[5], (D >> 2) & 1u, D, (int)ty.z >= 0, (int)tz.z >= 0);
-          item_fwd64<3>(r, v[6], v[7], (D >> 3) & 1u, D, (int)ty.w >= 0, (int)tz.w >= 0);
+          item_fwd64<0>(r, v[0], v[1], D & 1u, D, (int)ty.x >= 0, (int)tz.x >= 0, RX && (lk.z & 1u));
+          item_fwd64<1>(r, v[2], v[3], (D >> 1) & 1u, D, (int)ty.y >= 0, (int)tz.y >= 0, RX && ((lk.z >> 1) & 1u));
+          item_fwd64<2>(r, v[4], v[5], (D >> 2) & 1u, D, (int)ty.z >= 0, (int)tz.z >= 0, RX && ((lk.z >> 2) & 1u));
+          item_fwd64<3>(r, v[6], v[7], (D >> 3) & 1u, D, (int)ty.w >= 0, (int)tz.w >= 0, RX && ((lk.z >> 3) & 1u));
           chain64<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
         } else {
           const uint4 lk = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 2);
           const uint4 tz = __ldg(a.rounds + rr * (kBwdRoundWords / 4)), ty = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 1);
           chain64<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
           double gv[8];
-          item_bwd64<0>(r, l, v[0], v[4], D & 1u, D, gv[0], gv[4], (int)tz.x >= 0, (int)ty.x >= 0);
-          item_bwd64<1>(r, l, v[1], v[5], (D >> 1) & 1u, D, gv[1], gv[5], (int)tz.y >= 0, (int)ty.y >= 0);
-          item_bwd64<2>(r, l, v[2], v[6], (D >> 2) & 1u, D, gv[2], gv[6], (int)tz.z >= 0, (int)ty.z >= 0);
-          item_bwd64<3>(r, l, v[3], v[7], (D >> 3) & 1u, D, gv[3], gv[7], (int)tz.w >= 0, (int)ty.w >= 0);
+          item_bwd64<0>(r, l, v[0], v[4], D & 1u, D, gv[0], gv[4], (int)tz.x >= 0, (int)ty.x >= 0, RX && (lk.z & 1u));
+          item_bwd64<1>(r, l, v[1], v[5], (D >> 1) & 1u, D, gv[1], gv[5], (int)tz.y >= 0, (int)ty.y >= 0,
+                        RX && ((lk.z >> 1) & 1u));
+          item_bwd64<2>(r, l, v[2], v[6], (D >> 2) & 1u, D, gv[2], gv[6], (int)tz.z >= 0, (int)ty.z >= 0,
+                        RX && ((lk.z >> 2) & 1u));
+          item_bwd64<3>(r, l, v[3], v[7], (D >> 3) & 1u, D, gv[3], gv[7], (int)tz.w >= 0, (int)ty.w >= 0,
+                        RX && ((lk.z >> 3) & 1u));
           int idx;
           const double sum = butterfly8_64(gv, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
@@ -760,17 +786,21 @@ cudaError_t launch_pass64(bool bwd, const PassArgs64& a, cudaStream_t st) {
   const int64_t grid = (total_tiles + tiles_per_cta - 1) / tiles_per_cta;
   if (grid == 0) return cudaSuccess;
   const size_t smem = (size_t)(bwd ? 2 : 1) * kTileAmps * sizeof(double2);
-  const bool rounds = a.rounds != nullptr;
+  const bool rounds = a.rounds != nullptr, rx = rounds && a.rx_items;
   if (rounds && (a.rpar == nullptr || a.pd.K < 7)) return cudaErrorInvalidValue;  // 8 lanes per tile at least
-  static OptIn once[4];
-  const void* fn = bwd ? (rounds ? reinterpret_cast<const void*>(pass64_kernel<true, true>)
-                                 : reinterpret_cast<const void*>(pass64_kernel<true, false>))
-                       : (rounds ? reinterpret_cast<const void*>(pass64_kernel<false, true>)
-                                 : reinterpret_cast<const void*>(pass64_kernel<false, false>));
-  cudaError_t e = opt_in(fn, smem, once[(bwd ? 2 : 0) + (rounds ? 1 : 0)]);
+  static OptIn once[6];
+  const void* fn = bwd ? (rx       ? reinterpret_cast<const void*>(pass64_kernel<true, true, true>)
+                          : rounds ? reinterpret_cast<const void*>(pass64_kernel<true, true>)
+                                   : reinterpret_cast<const void*>(pass64_kernel<true, false>))
+                       : (rx       ? reinterpret_cast<const void*>(pass64_kernel<false, true, true>)
+                          : rounds ? reinterpret_cast<const void*>(pass64_kernel<false, true>)
+                                   : reinterpret_cast<const void*>(pass64_kernel<false, false>));
+  cudaError_t e = opt_in(fn, smem, once[(bwd ? 3 : 0) + (rx ? 2 : rounds ? 1 : 0)]);
   if (e != cudaSuccess) return e;
-  if (bwd && rounds) pass64_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  if (bwd && rx) pass64_kernel<true, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  else if (bwd && rounds) pass64_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
   else if (bwd) pass64_kernel<true, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
+  else if (rx) pass64_kernel<false, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
   else if (rounds) pass64_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
   else pass64_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();

@@ -36,6 +36,7 @@ struct PassArgs {
   double* g_part;         // [B * tiles per sample][n_slots], or [B][n_slots] when g_accum
   int32_t n_slots;
   int32_t g_accum;        // round programs: add the partials of a sample's tiles into one row
+  int32_t rx_items;       // round programs with RX items (the RX-capable kernels run them)
 };
 
 // Float64 three-shear parameters of a gradient term (complex128 round
@@ -149,6 +150,7 @@ struct PassArgs64 {
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs), else null
   const Shear64* rpar;    // per-round item parameters, 8 per round (round programs)
+  int32_t rx_items;       // round programs with RX items
   const double2* mats;    // fused 2x2 matrices, 4 double2 each: u00, u01, u10, u11 (generic)
   const double2* cs;      // (cos, sin) of phi/2 per gradient term
   const double2* enc;     // (cos, sin) of x/2, [B][n_eff]

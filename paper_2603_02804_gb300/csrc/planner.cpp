@@ -541,10 +541,9 @@ int ckpt_interval_gates(const Circuit& c, int ckpt_layers) {
   return (int)std::min<long>(g, 1L << 30);
 }
 
-// Round programs handle RZ / RY rotations and CZs on neighbouring qubits.
-// Round programs take RZ / RY rotations (RX is rewritten, below) and CZs on
-// neighbouring qubits, plus the ring's CZ(n-1, 0) when n >= 5 (then qubits
-// 0 and n-1 never share a register group).
+// Round programs take RZ, RY and RX rotations and CZs on neighbouring
+// qubits, plus the ring's CZ(n-1, 0) when n >= 5 (then qubits 0 and n-1
+// never share a register group).
 static bool round_eligible(const Circuit& c) {
   for (const Gate& g : c.gates) {
     if (g.kind == G_CNOT) return false;
@@ -553,26 +552,6 @@ static bool round_eligible(const Circuit& c) {
     if (dq != 1 && !(c.n >= 5 && dq == c.n - 1)) return false;
   }
   return true;
-}
-
-// RX(t) = RZ(-pi/2) RY(t) RZ(pi/2) (RZ(pi/2) acts first): exact, and the
-// gradient with respect to t is that of the RY. The constant RZs carry no
-// parameter (param -1) and merge into the RZ runs around them.
-static Circuit rewrite_rx(const Circuit& c) {
-  Circuit r = c;
-  r.gates.clear();
-  const double half_pi = 1.5707963267948966192313216916398;
-  for (const Gate& g : c.gates) {
-    if (g.kind != G_RX) {
-      r.gates.push_back(g);
-      continue;
-    }
-    r.gates.push_back({G_RZ, g.q0, -1, -1, half_pi});
-    r.gates.push_back({G_RY, g.q0, -1, g.param, 0.0});
-    r.gates.push_back({G_RZ, g.q0, -1, -1, -half_pi});
-  }
-  if (c.layers > 0 && !c.gates.empty()) r.gates_per_layer = (int)r.gates.size() / c.layers;
-  return r;
 }
 
 static void fill_slots(const Circuit& c, std::vector<int32_t>& slot_param, std::vector<int32_t>& slot_kind,
@@ -797,8 +776,7 @@ FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool stri
   if (P.n_eff > K && K < kRegBits + 1) K = kRegBits + 1;
   P.K = K;
   P.rounds = !req.generic && K >= 7 && round_eligible(c_in);
-  const Circuit rewritten = P.rounds ? rewrite_rx(c_in) : Circuit();
-  const Circuit& c = P.rounds ? rewritten : c_in;
+  const Circuit& c = c_in;
   // gradient terms: generic programs have one per rotation, in circuit order
   std::vector<int> term_of_gate(c.gates.size(), -1);
   P.term_off.assign(1, 0);
@@ -946,6 +924,7 @@ FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool stri
         if (gq[r + 1] == gq[r] + 1 && ((links >> gq[r]) & 1u)) bbits |= 1u << r;
       std::vector<uint32_t> fw(kFwdRoundWords, 0u);
       std::vector<int32_t> bw(kBwdRoundWords, -1);
+      uint32_t rx_mask = 0;  // items whose rotation is an RX
       for (int r = 0; r < 4; ++r) {
         const ItemRec& it = rr.it[r];
         std::vector<int> fg = it.pre;
@@ -953,7 +932,8 @@ FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool stri
           fg.push_back(it.y);
           fg.insert(fg.end(), it.post.begin(), it.post.end());
           bw[r] = new_term(it.post, G_RZ);
-          bw[4 + r] = new_term({it.y}, G_RY);
+          bw[4 + r] = new_term({it.y}, c.gates[it.y].kind);  // an RY or an RX
+          if (c.gates[it.y].kind == G_RX) rx_mask |= 1u << r;
         } else {
           bw[r] = new_term(it.pre, G_RZ);
         }
@@ -961,10 +941,13 @@ FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool stri
       }
       fw[4] = links;
       fw[5] = bbits;
+      fw[6] = rx_mask;
       for (int r = 0; r < 8; ++r) fw[8 + r] = (uint32_t)bw[r];  // the items' terms (forward shears)
       bw[8] = (int32_t)links;
       bw[9] = (int32_t)bbits;
-      bw[10] = bw[11] = 0;
+      bw[10] = (int32_t)rx_mask;
+      bw[11] = 0;
+      P.has_rx |= rx_mask != 0;
       P.fwd_rounds.insert(P.fwd_rounds.end(), fw.begin(), fw.end());
       brs.push_back(std::move(bw));
     }

@@ -33,6 +33,7 @@ struct FusedPlan {
   int n_eff = 0;    // simulated qubits (>= 4)
   int K = 0;        // tile bits
   bool rounds = false;  // round program (straight-line steps) instead of generic ops
+  bool has_rx = false;  // round program with RX items (the RX-capable pass kernels run it)
   int n_terms = 0;  // gradient terms
   int n_ckpt = 0;   // checkpoint state slots including the final state
   int n_steps = 0;

@@ -42,13 +42,16 @@ enum OpCode : uint32_t {
 // and then the CZ links of the round.
 //   forward round, kFwdRoundWords words: m[4] (fused 2x2 index per register
 //     bit, 0 = identity), links, bbits (links between register bits r, r+1),
-//     2 pad words, tz[4], ty[4] (the items' gradient terms, as below).
+//     rx (bit r: item r's rotation is an RX), a pad word, tz[4], ty[4] (the
+//     items' gradient terms, as below).
 //   backward round, kBwdRoundWords words: tz[4], ty[4] (term of the merged RZ
-//     run and of the RY of each item, -1 = none), links, bbits, 2 pad words.
-// An item is an RZ run alone or an RY followed by an RZ run. A forward round
-// applies per item the RY and then the RZ run, then the links; a backward step
-// runs its rounds in the order stored, each applying the links first, then per
-// item the RZ run and then the RY (the exact reverse).
+//     run and of the rotation of each item, -1 = none), links, bbits, rx, a
+//     pad word.
+// An item is an RZ run alone or a rotation (RY or RX) followed by an RZ run.
+// A forward round applies per item the rotation and then the RZ run, then the
+// links; a backward step runs its rounds in the order stored, each applying
+// the links first, then per item the RZ run and then the rotation (the exact
+// reverse).
 constexpr int kFwdRoundWords = 16;
 constexpr int kBwdRoundWords = 12;
 constexpr int kMaxStepRounds = 4;   // 8 gradient values per round

@@ -93,13 +93,8 @@ def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, ora
     bwd = pi.parse(qfuse.qf_plan_export(handle, 1))
     # every rotation gate appears exactly once in the fused forward entries
     entries = sorted((k, p) for run in fwd.fused for (k, p, _) in run)
-    expect = []
-    for k, p in zip(slot_kind, slot_param):
-        if fwd.rounds_mode and k == orc.RX:  # round programs run RX(t) as RZ(-pi/2) RY(t) RZ(pi/2)
-            expect += [(orc.RZ, -1), (orc.RY, p), (orc.RZ, -1)]
-        else:
-            expect.append((k, p))
-    assert entries == sorted(expect)
+    expect = sorted(zip(slot_kind, slot_param))
+    assert entries == expect
     # and exactly once in the gradient terms
     assert sorted(p for _, ps in bwd.terms for p in ps) == sorted(slot_param)
     pq = qfuse.pauli(obs, n)
