@@ -720,6 +720,35 @@ def main():
                     "bwd_kernel_ms": b_ms}
             del vs
 
+    # ---- the same step captured once in a CUDA graph and replayed (the C-ABI
+    # allocates and synchronises nothing after qf_plan)
+    if variants is not None and not c128:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            step(sim)
+        stream.wait_stream(gs)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step(sim)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        K = min(args.steps, 200)
+        g_st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        g_en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            flush.fill_(k & 255)
+            g_st[k].record(stream)
+            graph.replay()
+            g_en[k].record(stream)
+        torch.cuda.synchronize()
+        g_ms = sum(a.elapsed_time(b) for a, b in zip(g_st, g_en))
+        variants["cuda_graph"] = {"value": w.B * K / (g_ms / 1e3), "unit": "samples/s", "ms_per_step": g_ms / K,
+                                  "note": "qf_train_step captured once with torch.cuda.graph, replayed per step"}
+        del graph
+
     # ---- unfused per-gate comparator on the same GPU (complex64 only)
     per_gate = None
     if not args.no_per_gate and not c128:

@@ -328,3 +328,25 @@ def test_round_programs_every_width(n):
     gr, Er = orc.gradient(orc.hea(n, d), f64(theta), f64(x), obs, per_sample=True)
     assert np.max(np.abs(E - Er)) < TOL
     assert np.max(np.abs(g - gr)) < TOL
+
+
+def test_train_step_cuda_graph_replay():
+    """One qf_train_step captured in a CUDA graph (the C-ABI allocates and
+    synchronises nothing after qf_plan) replays to the eager result bit for bit."""
+    w = workloads.WORKLOADS["hea12"]
+    theta, x, y = workloads.make_inputs(w, B=64)
+    sim = Simulator(w.n, w.d, 64)
+    th, xd, yd = dev(theta), dev(x), dev(y)
+    loss_e, E_e, g_e = (t.clone() for t in sim.train_step(th, xd, yd, loss="mse"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        sim.train_step(th, xd, yd, loss="mse")  # warm on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        out = sim.train_step(th, xd, yd, loss="mse")
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], loss_e) and torch.equal(out[1], E_e) and torch.equal(out[2], g_e)
