@@ -374,9 +374,10 @@ def run_epoch(args, w):
     info = sim.info()
     fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, mb)
     bwd_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
-    n_bwd = info["n_passes"]
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    ach = (bwd_fl / n_bwd) / (bwd_ms / 1e3) / 1e12
+    # the adjoint phase's flops over its time (checkpoint mode 1: it also re-runs the forward)
+    phase_fl = (bwd_fl + (fwd_fl if args.ckpt_mode == 1 else 0)) * len(xs) * args.steps
+    ach = phase_fl / (prof["bwd_ms"] / 1e3) / 1e12
     bytes_bwd = 32 * mb * (1 << w.n)  # read + write psi and lambda per adjoint pass
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     line = {
@@ -390,7 +391,8 @@ def run_epoch(args, w):
                    "workspace_gb": sim.ws_bytes / 1e9, "passes": info["n_passes"],
                    "l2": "inputs larger than L2"},
         "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                     "traffic": None, "kernel": "pass_kernel<true,true> (fused adjoint)",
+                     "traffic": None, "kernel": ("pass_kernel<true,true> (fused adjoint)" if args.ckpt_mode == 0 else
+                                                 "adjoint phase: pass_kernel<true,true> and forward re-runs"),
                      "bwd_pass_ms": bwd_ms,
                      "hbm": {"achieved_gbs": bytes_bwd / (bwd_ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
                              "frac": bytes_bwd / (bwd_ms / 1e3) / 1e9 / hbm_gbs, "peak_source": peak_src}},
