@@ -88,6 +88,16 @@ struct qf_circuit {
   int64_t launches = 0;
   void* h_stage = nullptr;  // pinned host staging of the host-buffer step (packed copies)
   size_t h_stage_bytes = 0;
+  // the host-buffer step's device part (packed copy in, train step, packed
+  // copy out) recorded once as a CUDA graph for a (workspace, batch, loss,
+  // observable) key seen before, and replayed on the caller's stream
+  cudaStream_t hg_stream = nullptr;
+  cudaGraphExec_t hg_exec = nullptr;
+  bool hg_seen = false;
+  void* hg_ws = nullptr;
+  int64_t hg_batch = -1, hg_launches = 0;
+  int32_t hg_loss = -1;
+  uint64_t hg_x = 0, hg_z = 0;
   int64_t call_launches = 0;
   // pass-kernel timing (qf_profile)
   bool profile = false;
@@ -124,7 +134,16 @@ void prof_end(qf_circuit* c, int k, int dir, int64_t launches, cudaStream_t st) 
   c->ev_launches[k] = launches;
 }
 
+void drop_host_graph(qf_circuit* c) {
+  if (c->hg_exec) cudaGraphExecDestroy(c->hg_exec);
+  c->hg_exec = nullptr;
+  c->hg_seen = false;
+  c->hg_ws = nullptr;
+  c->hg_batch = -1;
+}
+
 void free_tables(qf_circuit* c) {
+  drop_host_graph(c);
   if (c->d_tables) cudaFree(c->d_tables);
   c->d_tables = nullptr;
   c->dt = DevTables();
@@ -915,6 +934,7 @@ qf_status qf_circuit_destroy(qf_circuit* c) {
   if (!c) return QF_OK;
   destroy_events(c);
   free_tables(c);
+  if (c->hg_stream) cudaStreamDestroy(c->hg_stream);
   delete c;
   return QF_OK;
 }
@@ -1124,14 +1144,15 @@ qf_status train_step_host(qf_circuit* c, const R* theta_h, const R* x_h, const R
                           int32_t loss_kind, qf_pauli obs, double* loss_h, double* E_h, double* grad_h, void* ws_d,
                           size_t ws_bytes, void* stream) {
   constexpr bool F64 = sizeof(R) == 8;
-  auto step = [&](const R* th, const R* xd, const R* yd) -> qf_status {
+  auto step_on = [&](const R* th, const R* xd, const R* yd, void* strm) -> qf_status {
     if constexpr (F64)
       return qf_train_step64(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
-                             at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, stream);
+                             at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, strm);
     else
       return qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
-                           at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, stream);
+                           at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, strm);
   };
+  auto step = [&](const R* th, const R* xd, const R* yd) -> qf_status { return step_on(th, xd, yd, stream); };
   qf_status s = check_call(c, batch, ws_d, ws_bytes, F64);
   if (s != QF_OK) return s;
   if (!c->staging) return fail(QF_ERR_UNSUPPORTED, "the plan was made with no_host_staging");
@@ -1163,10 +1184,53 @@ qf_status train_step_host(qf_circuit* c, const R* theta_h, const R* x_h, const R
     if (P) memcpy(h, theta_h, (size_t)P * sizeof(R));
     if (batch) memcpy(h + (L.x - L.theta), x_h, x_bytes(c, batch));
     if (mse) memcpy(h + (L.y - L.theta), y_h, (size_t)batch * sizeof(R));
-    QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, st));
-    s = step(th, xd, yd);
-    if (s != QF_OK) return s;
-    QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, st));
+    const bool same = c->hg_ws == ws_d && c->hg_batch == batch && c->hg_loss == loss_kind &&
+                      c->hg_x == obs.x_mask && c->hg_z == obs.z_mask;
+    if (!same) {
+      drop_host_graph(c);
+      c->hg_ws = ws_d;
+      c->hg_batch = batch;
+      c->hg_loss = loss_kind;
+      c->hg_x = obs.x_mask;
+      c->hg_z = obs.z_mask;
+    }
+    if (same && c->hg_seen && !c->hg_exec && !c->profile && batch > 0) {
+      // second call with this key: record the device part once (a failed
+      // capture leaves the eager path in use)
+      if (!c->hg_stream && cudaStreamCreateWithFlags(&c->hg_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->hg_stream = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      if (c->hg_stream && cudaStreamBeginCapture(c->hg_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        qf_status sc = QF_ERR_CUDA;
+        if (cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, c->hg_stream) == cudaSuccess) {
+          sc = step_on(th, xd, yd, c->hg_stream);
+          if (sc == QF_OK &&
+              cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, c->hg_stream) != cudaSuccess)
+            sc = QF_ERR_CUDA;
+        }
+        const cudaError_t ec = cudaStreamEndCapture(c->hg_stream, &g);
+        if (sc == QF_OK && ec == cudaSuccess && g &&
+            cudaGraphInstantiate(&c->hg_exec, g, 0) == cudaSuccess) {
+          c->hg_launches = c->launches;
+        } else {
+          c->hg_exec = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+      }
+    }
+    if (same && c->hg_exec && !c->profile) {
+      QF_CU(cudaGraphLaunch(c->hg_exec, st));
+      c->launches = c->hg_launches;
+    } else {
+      QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, st));
+      s = step(th, xd, yd);
+      if (s != QF_OK) return s;
+      QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, st));
+      c->hg_seen = true;
+    }
     QF_CU(cudaStreamSynchronize(st));
     memcpy(loss_h, h + (L.loss - L.E), 8);
     if (E_h && batch) memcpy(E_h, h, (size_t)batch * 8);

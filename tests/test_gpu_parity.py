@@ -350,3 +350,25 @@ def test_train_step_cuda_graph_replay():
         graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(out[0], loss_e) and torch.equal(out[1], E_e) and torch.equal(out[2], g_e)
+
+
+def test_host_step_graph_replay_tracks_inputs():
+    """qf_train_step_host records its device part (copies in, step, copies
+    out) as a CUDA graph on the second call with the same workspace, batch,
+    loss and observable, and replays it afterwards: every call must equal the
+    device-buffer step on that call's inputs, bit for bit."""
+    w = workloads.WORKLOADS["hea12"]
+    theta, x, y = workloads.make_inputs(w, B=32)
+    sim = Simulator(w.n, w.d, 32)
+    out = sim.host_outputs(32)
+    rng = np.random.default_rng(7)
+    for call in range(4):
+        th = (theta + np.float32(0.1 * call)).astype(np.float32)
+        xs = rng.uniform(0, np.pi, x.shape).astype(np.float32)
+        lh, Eh, gh = sim.train_step_host(torch.from_numpy(th).pin_memory(), torch.from_numpy(xs).pin_memory(),
+                                         torch.from_numpy(y).pin_memory(), loss="mse", out=out)
+        lh, Eh, gh = lh.clone(), Eh.clone(), gh.clone()
+        ld, Ed, gd = sim.train_step(dev(th), dev(xs), dev(y), loss="mse")
+        torch.cuda.synchronize()
+        assert lh.item() == ld.item(), call
+        assert torch.equal(Eh, Ed.cpu()) and torch.equal(gh, gd.cpu()), call
