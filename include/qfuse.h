@@ -284,7 +284,13 @@ qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d,
 /* The same step from HOST buffers: copies theta_h, x_h (and y_h) into the
  * workspace's staging area, runs qf_train_step, copies loss, E (may be NULL)
  * and grad back, and synchronises `stream` before returning. Pinned host
- * memory gives asynchronous copies; pageable memory works but is slower. */
+ * memory gives asynchronous copies; pageable memory works but is slower.
+ * Small steps cross the bus as one packed copy each way through a pinned
+ * buffer the handle owns. From the second call with the same workspace,
+ * batch, loss and observable, that copy-in, the step's kernels and the
+ * copy-out are replayed from a CUDA graph the handle recorded (on a stream of
+ * its own) instead of being launched one by one; re-planning drops it. The
+ * call synchronises, so it cannot itself be captured into a caller's graph. */
 qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x_h,
                              const float* y_h, int64_t batch, int32_t loss_kind, qf_pauli obs,
                              double* loss_h, double* E_h, double* grad_h, void* ws_d,
