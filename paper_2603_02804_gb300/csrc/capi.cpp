@@ -195,8 +195,8 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     if (c->f64) L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
     else L.mats = take((size_t)std::max(n_fused, 0) * 32);
     if (c->fp.rounds) {
-      // 8 shear parameters per round: float4 (complex64) or Shear64 (complex128)
-      const size_t per = 8 * (c->f64 ? sizeof(qf::Shear64) : 16);
+      // per round: kRoundPar float4 (complex64) or kRoundPar64 Shear64 (complex128)
+      const size_t per = c->f64 ? qf::kRoundPar64 * sizeof(qf::Shear64) : qf::kRoundPar * 16;
       L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * per);
       L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * per);
     }
@@ -1760,7 +1760,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       r.n_params = c->circ.n_params;
       r.param_off = T.param_off;
       r.param_terms = T.param_terms;
-      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff + 8ll * p.n_rpf + 8ll * p.n_rpb;
+      prep_pref[i + 1] = prep_pref[i] + p.n_fused + p.n_terms + p.B * p.n_eff + qf::round_par_elems(p);
       gout_pref[i + 1] = gout_pref[i] + c->circ.n_params;
     }
     memcpy(img.data() + circ_off, recs.data(), recs.size() * sizeof(qf::BatchCircuit));

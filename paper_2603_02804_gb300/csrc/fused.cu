@@ -224,17 +224,10 @@ __device__ __forceinline__ void apply_pending(uint32_t D, float2 (&r)[16], float
   }
 }
 
-// Forward item on register bit R: the RY, then the RZ run (the adjoint item
-// run forward). yq, zq: the terms' shear parameters (t, s, wrap parity) of the
-// un-apply direction; applying is the rotation the other way, (t, s) ->
-// (-t, -s). A pending Z_R turns RY(w) into RY(-w); the wrap parities go to
-// the pending constant sign.
-template <int R>
-__device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D);
-
 // RX(w) applied on register bit R: a rotation by -w/2 of the real pairs
 // (re p0, im p1) and (re p1, im p0), three shears each (x += t y; y -= s x;
-// x += t y). A pending Z_R turns RX(w) into RX(-w).
+// x += t y). yq: the term's shear parameters (t, s, wrap parity) of the
+// un-apply direction. A pending Z_R turns RX(w) into RX(-w).
 template <int R>
 __device__ __forceinline__ void rx_fwd(float2 (&r)[16], float4 yq, uint32_t a) {
   const int f = (int)(a << 31);
@@ -250,64 +243,98 @@ __device__ __forceinline__ void rx_fwd(float2 (&r)[16], float4 yq, uint32_t a) {
   }
 }
 
-// The RZ run of an item on register bit R, applied.
-template <int R>
-__device__ __forceinline__ void rz_fwd(float2 (&r)[16], float4 zq) {
-  const float t = zq.x, s = zq.y;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (j & (1 << R)) continue;
-    const int j1 = j | (1 << R);
-    float2 p0 = r[j], p1 = r[j1];
-    p0.x = fmaf(t, p0.y, p0.x); p0.y = fmaf(-s, p0.x, p0.y); p0.x = fmaf(t, p0.y, p0.x);
-    p1.x = fmaf(-t, p1.y, p1.x); p1.y = fmaf(s, p1.x, p1.y); p1.x = fmaf(-t, p1.y, p1.x);
-    r[j] = p0; r[j1] = p1;
-  }
-}
-
-// Forward item of a round program that may hold RX items (rx: this item's
-// rotation is an RX; uniform over the CTA).
+// The rotation of a forward item on register bit R (RY, or RX where rx; rx is
+// uniform over the CTA): applying is the un-apply rotation the other way,
+// (t, s) -> (-t, -s). A pending Z_R turns the rotation by w into one by -w;
+// the wrap parity goes to the pending constant sign.
 template <int R, bool RX>
-__device__ __forceinline__ void item_fwd_x(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D, bool rx) {
+__device__ __forceinline__ void rot_fwd(float2 (&r)[16], float4 yq, uint32_t a, uint32_t& D, bool rx) {
   if (RX && rx) {
     rx_fwd<R>(r, yq, a);
-    rz_fwd<R>(r, zq);
-    D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
   } else {
-    item_fwd<R>(r, yq, zq, a, D);
+    const int f = (int)(a << 31);
+    const float tn = -__int_as_float(__float_as_int(yq.x) ^ f), sp = __int_as_float(__float_as_int(yq.y) ^ f);
+    const float2 t2 = make_float2(tn, tn), ms2 = make_float2(sp, sp);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << R)) continue;
+      const int j1 = j | (1 << R);
+      float2 p0 = r[j], p1 = r[j1];
+      // RY(w) on (p0, p1): rotation by +w/2 as three packed shears
+      p0 = __ffma2_rn(t2, p1, p0);
+      p1 = __ffma2_rn(ms2, p0, p1);
+      p0 = __ffma2_rn(t2, p1, p0);
+      r[j] = p0; r[j1] = p1;
+    }
+  }
+  D ^= ((uint32_t)__float_as_int(yq.z) & 1u) << 4;
+}
+
+// v *= (c + i s)
+__device__ __forceinline__ void cmul(float2& v, float c, float s) {
+  const float x = v.x;
+  v.x = fmaf(c, x, -s * v.y);
+  v.y = fmaf(s, x, c * v.y);
+}
+
+// The round's diagonal (its 4 RZ runs merged), applied: register amplitude j
+// times the phase (cos, sin) held in ph[j / 2] (x, y for even j; z, w for odd
+// j). An RZ run commutes with the rotations on the other register bits and
+// with the pending signs, so the four run together, once per round, after the
+// rotations (the adjoint un-applies them before its rotations, diag_bwd).
+__device__ __forceinline__ void apply_diag(float2 (&r)[16], const float4* ph) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const float4 e = ph[m];
+    cmul(r[2 * m], e.x, e.y);
+    cmul(r[2 * m + 1], e.z, e.w);
   }
 }
 
-template <int R>
-__device__ __forceinline__ void item_fwd(float2 (&r)[16], float4 yq, float4 zq, uint32_t a, uint32_t& D) {
-  const int f = (int)(a << 31);
-  const float2 T = make_float2(-__int_as_float(__float_as_int(yq.x) ^ f), 0.f);
-  const float2 t2 = make_float2(T.x, T.x), ms2 = make_float2(__int_as_float(__float_as_int(yq.y) ^ f),
-                                                               __int_as_float(__float_as_int(yq.y) ^ f));
-  const float t = zq.x, s = zq.y;
+// Adjoint side of the round's diagonal: its RZ-run gradient terms, then the
+// un-apply. g[r] = sum_j sigma_r(j) w_j with w_j = Im(conj(lambda_j) psi_j)
+// and sigma_r(j) = +1 where bit r of j is clear, else -1 (the thread's share
+// of Im<lambda|Z_r|psi>). w_j is unchanged by a diagonal acting on both states
+// and Z_r commutes with the rotations on the other bits, so the four terms
+// are taken together at the diagonal; the signed sums share partial sums (a
+// Walsh transform along each register bit), and each pair of amplitudes is
+// multiplied by its phases as it is read.
+__device__ __forceinline__ void diag_bwd(float2 (&p)[16], float2 (&l)[16], const float4* ph, float (&g)[8]) {
+  float s2[4];
+  float d0 = 0.f, d1 = 0.f, se = 0.f;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (j & (1 << R)) continue;
-    const int j1 = j | (1 << R);
-    float2 p0 = r[j], p1 = r[j1];
-    // RY(w) on (p0, p1): rotation by +w/2 as three packed shears
-    p0 = __ffma2_rn(t2, p1, p0);
-    p1 = __ffma2_rn(ms2, p0, p1);
-    p0 = __ffma2_rn(t2, p1, p0);
-    // RZ run: bit-R-clear amplitude times e^{-iw/2}, set one times e^{+iw/2}
-    p0.x = fmaf(t, p0.y, p0.x); p0.y = fmaf(-s, p0.x, p0.y); p0.x = fmaf(t, p0.y, p0.x);
-    p1.x = fmaf(-t, p1.y, p1.x); p1.y = fmaf(s, p1.x, p1.y); p1.x = fmaf(-t, p1.y, p1.x);
-    r[j] = p0; r[j1] = p1;
+  for (int m = 0; m < 8; ++m) {
+    const float4 e = ph[m];
+    float2& p0 = p[2 * m];
+    float2& p1 = p[2 * m + 1];
+    float2& l0 = l[2 * m];
+    float2& l1 = l[2 * m + 1];
+    const float w0 = fmaf(l0.x, p0.y, -l0.y * p0.x);
+    const float w1 = fmaf(l1.x, p1.y, -l1.y * p1.x);
+    cmul(p0, e.x, e.y);
+    cmul(l0, e.x, e.y);
+    cmul(p1, e.z, e.w);
+    cmul(l1, e.z, e.w);
+    const float sm = w0 + w1;  // bit 0 summed out
+    d0 += w0 - w1;
+    if (m & 1) {
+      s2[m >> 1] = se + sm;  // bits 0, 1 summed out
+      d1 += se - sm;
+    } else {
+      se = sm;
+    }
   }
-  D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
+  g[0] = d0;
+  g[1] = d1;
+  g[2] = (s2[0] - s2[1]) + (s2[2] - s2[3]);
+  g[3] = (s2[0] + s2[1]) - (s2[2] + s2[3]);
 }
 
 // Un-apply one rotation on register bit R by three shears and return the
 // thread's sum of Im<lambda|P|psi> taken before it. A plane rotation by phi
 // equals x += a y; y += b x; x += a y with a = -tan(phi/2), b = sin(phi)
-// (exact; |a| <= 1 for |phi| <= pi/2), three FMAs per component.
-//   RZ: amplitudes with bit R = 0 are multiplied by e^{+iw/2} (a rotation of
-//   (re, im) by w/2), those with bit R = 1 by e^{-iw/2}; t = tan(w/4), s = sin(w/2).
+// (exact; |a| <= 1 for |phi| <= pi/2), three FMAs per component; t =
+// tan(w/4), s = sin(w/2).
 //   RY: (x, y) <- RY(w)^dagger (x, y) = rotation by -w/2: a = t, b = -s.
 template <int R, int KIND>
 __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], const float t, const float s) {
@@ -319,13 +346,7 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
     if (j & (1 << R)) continue;
     const int j1 = j | (1 << R);
     float2 p0 = p[j], p1 = p[j1], l0 = l[j], l1 = l[j1];
-    if (KIND == G_RZ) {
-      acc += l0.x * p0.y - l0.y * p0.x - l1.x * p1.y + l1.y * p1.x;
-      p0.x = fmaf(-t, p0.y, p0.x); p0.y = fmaf(s, p0.x, p0.y); p0.x = fmaf(-t, p0.y, p0.x);
-      l0.x = fmaf(-t, l0.y, l0.x); l0.y = fmaf(s, l0.x, l0.y); l0.x = fmaf(-t, l0.y, l0.x);
-      p1.x = fmaf(t, p1.y, p1.x); p1.y = fmaf(-s, p1.x, p1.y); p1.x = fmaf(t, p1.y, p1.x);
-      l1.x = fmaf(t, l1.y, l1.x); l1.y = fmaf(-s, l1.x, l1.y); l1.x = fmaf(t, l1.y, l1.x);
-    } else if (KIND == G_RX) {
+    if (KIND == G_RX) {
       // Im<lambda|X|psi> per pair; RX(w)^dagger rotates (re p0, im p1) and
       // (re p1, im p0) by +w/2: x -= t y; y += s x; x -= t y
       acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
@@ -352,22 +373,20 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
   return acc;
 }
 
-// Backward item on register bit R: the merged RZ run, then the RY (shear
-// parameters (t, s, wrap parity)). With a pending Z_R the RY un-applies as
-// RY(+w) (t, s negated) and its Im<lambda|Y|psi> changes sign. The wrap
-// parities (u(phi) = -u(w) for odd k) go to the pending constant sign.
-// rx: the item's rotation is an RX (RX: the program holds RX items); a
-// pending Z_R acts on it as on an RY.
+// The rotation of an adjoint item on register bit R (shear parameters (t, s,
+// wrap parity); RX where rx, uniform over the CTA, else RY), un-applied after
+// the round's diagonal; gy: its Im<lambda|P|psi>. With a pending Z_R the
+// rotation un-applies as the one by +w (t, s negated) and gy changes sign.
+// The wrap parity (u(phi) = -u(w) for odd k) goes to the pending constant sign.
 template <int R, bool RX = false>
-__device__ __forceinline__ void item_bwd(float2 (&p)[16], float2 (&l)[16], float4 zq, float4 yq, uint32_t a,
-                                         uint32_t& D, float& gz, float& gy, bool rx = false) {
-  gz = bwd_shear<R, G_RZ>(p, l, zq.x, zq.y);
+__device__ __forceinline__ void rot_bwd(float2 (&p)[16], float2 (&l)[16], float4 yq, uint32_t a, uint32_t& D,
+                                        float& gy, bool rx = false) {
   const int f = (int)(a << 31);
   const float t = __int_as_float(__float_as_int(yq.x) ^ f);
   const float s = __int_as_float(__float_as_int(yq.y) ^ f);
   const float g = RX && rx ? bwd_shear<R, G_RX>(p, l, t, s) : bwd_shear<R, G_RY>(p, l, t, s);
   gy = __int_as_float(__float_as_int(g) ^ f);
-  D ^= ((uint32_t)(__float_as_int(zq.z) ^ __float_as_int(yq.z)) & 1u) << 4;
+  D ^= ((uint32_t)__float_as_int(yq.z) & 1u) << 4;
 }
 
 // Reduce 8 per-thread values over `lanes` lanes (8, 16 or 32; whole-warp
@@ -424,11 +443,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Parameters of one round step, staged from the round-ordered tables: per
-// round 8 float4 (forward: the 4 items' fused 2x2s; backward: the shear
-// parameters of tz[0..3], ty[0..3]) and the round record.
+// round kRoundPar float4 (the items' rotation shears, then the round's
+// diagonal) and the round record.
 constexpr int kMaxRoundWords = kFwdRoundWords > kBwdRoundWords ? kFwdRoundWords : kBwdRoundWords;
 struct StepPar {
-  float4 v[kMaxStepRounds][8];
+  float4 v[kMaxStepRounds][kRoundPar];
   uint4 rec[kMaxStepRounds * (kMaxRoundWords / 4)];
 };
 
@@ -715,9 +734,9 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
   // (warp 0) asynchronous copy of rounds rb .. rb+nr-1 into sh.par[pb]
   auto stage = [&](int pb, uint32_t rb, int nr) {
     constexpr int RW4 = (BWD ? kBwdRoundWords : kFwdRoundWords) / 4;
-    const int nv = nr * 8, n_all = nv + nr * RW4;
+    const int nv = nr * kRoundPar, n_all = nv + nr * RW4;
     for (int e = lane; e < n_all; e += 32) {
-      if (e < nv) cp_async16(&sh.par[pb].v[0][0] + e, a.rpar + (size_t)rb * 8 + e);
+      if (e < nv) cp_async16(&sh.par[pb].v[0][0] + e, a.rpar + (size_t)rb * kRoundPar + e);
       else cp_async16(&sh.par[pb].rec[e - nv], a.rounds + (size_t)rb * RW4 + (e - nv));
     }
     cp_async_commit();
@@ -869,19 +888,21 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       for (int k = 0; k < nr; ++k) {
         if (!BWD) {
           const uint4 lk = P.rec[k * (kFwdRoundWords / 4) + 1];  // links, bbits, rx mask
-          item_fwd_x<0, RX>(r, P.v[k][0], P.v[k][1], D & 1u, D, lk.z & 1u);
-          item_fwd_x<1, RX>(r, P.v[k][2], P.v[k][3], (D >> 1) & 1u, D, (lk.z >> 1) & 1u);
-          item_fwd_x<2, RX>(r, P.v[k][4], P.v[k][5], (D >> 2) & 1u, D, (lk.z >> 2) & 1u);
-          item_fwd_x<3, RX>(r, P.v[k][6], P.v[k][7], (D >> 3) & 1u, D, (lk.z >> 3) & 1u);
+          rot_fwd<0, RX>(r, P.v[k][0], D & 1u, D, lk.z & 1u);
+          rot_fwd<1, RX>(r, P.v[k][1], (D >> 1) & 1u, D, (lk.z >> 1) & 1u);
+          rot_fwd<2, RX>(r, P.v[k][2], (D >> 2) & 1u, D, (lk.z >> 2) & 1u);
+          rot_fwd<3, RX>(r, P.v[k][3], (D >> 3) & 1u, D, (lk.z >> 3) & 1u);
+          apply_diag(r, &P.v[k][4]);
           chain_pending<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
         } else {
           const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];  // links, bbits, rx mask
           chain_pending<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
           float v[8];
-          item_bwd<0, RX>(r, l, P.v[k][0], P.v[k][4], D & 1u, D, v[0], v[4], lk.z & 1u);
-          item_bwd<1, RX>(r, l, P.v[k][1], P.v[k][5], (D >> 1) & 1u, D, v[1], v[5], (lk.z >> 1) & 1u);
-          item_bwd<2, RX>(r, l, P.v[k][2], P.v[k][6], (D >> 2) & 1u, D, v[2], v[6], (lk.z >> 2) & 1u);
-          item_bwd<3, RX>(r, l, P.v[k][3], P.v[k][7], (D >> 3) & 1u, D, v[3], v[7], (lk.z >> 3) & 1u);
+          diag_bwd(r, l, &P.v[k][4], v);
+          rot_bwd<0, RX>(r, l, P.v[k][0], D & 1u, D, v[4], lk.z & 1u);
+          rot_bwd<1, RX>(r, l, P.v[k][1], (D >> 1) & 1u, D, v[5], (lk.z >> 1) & 1u);
+          rot_bwd<2, RX>(r, l, P.v[k][2], (D >> 2) & 1u, D, v[6], (lk.z >> 2) & 1u);
+          rot_bwd<3, RX>(r, l, P.v[k][3], (D >> 3) & 1u, D, v[7], (lk.z >> 3) & 1u);
           int idx;
           const float sum = butterfly8(v, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
@@ -1266,6 +1287,26 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
   return make_float4((float)tq, (float)sh, __int_as_float(parity), 0.f);
 }
 
+// The diagonal of a round: its RZ runs (terms tz[r], angle phi_r; -1 = none)
+// act on register index j as e^{-i a_j} with a_j = sum_r sigma_r(j) phi_r / 2,
+// sigma_r(j) = +1 where bit r of j is clear, else -1 (RZ(phi) =
+// diag(e^{-i phi/2}, e^{i phi/2})). Returns (cos, sin) of the applied phase
+// (forward: -a_j) or of the un-applied one (backward: +a_j) for j0, j0 + 1,
+// each from one float64 sincos of the summed angle.
+__device__ float4 diag_phases(const PrepArgs& a, const int32_t* tz, int j0, bool apply) {
+  double phi[4];
+  for (int r = 0; r < 4; ++r) phi[r] = tz[r] >= 0 ? term_angle(a, tz[r]) : 0.0;
+  double cs[4];
+  for (int h = 0; h < 2; ++h) {
+    const int j = j0 + h;
+    double al = 0.0;
+    for (int r = 0; r < 4; ++r) al += ((j >> r) & 1) ? -phi[r] : phi[r];
+    al *= apply ? -0.5 : 0.5;
+    sincos(al, &cs[2 * h + 1], &cs[2 * h]);
+  }
+  return make_float4((float)cs[0], (float)cs[1], (float)cs[2], (float)cs[3]);
+}
+
 // The same in float64 (complex128 round programs).
 __device__ Shear64 term_shear64(const PrepArgs& a, int32_t t) {
   Shear64 r{0.0, 0.0, 0, 0};
@@ -1320,25 +1361,38 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     return;
   }
   i -= (int64_t)a.B * a.n_eff;
-  if (i < 8ll * a.n_rpf) {
-    // forward round r, item k: shear parameters of its RY term (j = 0) or of
-    // its RZ-run term (j = 1), at 2k + j
-    const int64_t r = i >> 3;
-    const int k = (int)((i >> 1) & 3), j = (int)(i & 1);
-    const int32_t* rec = reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords;
-    const int32_t t = rec[j ? 8 + k : 12 + k];
-    if (a.rpf64) a.rpf64[r * 8 + 2 * k + j] = term_shear64(a, t);
-    else a.rpf[r * 8 + 2 * k + j] = term_shear_of(a, t);
+  if (a.rpf64 || a.rpb64) {
+    // complex128: per round and item the shears of its rotation and RZ-run terms
+    if (i < (int64_t)kRoundPar64 * a.n_rpf) {
+      const int64_t r = i >> 3;
+      const int k = (int)((i >> 1) & 3), j = (int)(i & 1);
+      const int32_t* rec = reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords;
+      a.rpf64[r * 8 + 2 * k + j] = term_shear64(a, rec[j ? 8 + k : 12 + k]);
+      return;
+    }
+    i -= (int64_t)kRoundPar64 * a.n_rpf;
+    if (i < (int64_t)kRoundPar64 * a.n_rpb) {
+      const int64_t r = i >> 3;
+      const int k = (int)(i & 7);
+      a.rpb64[i] = term_shear64(a, reinterpret_cast<const int32_t*>(a.rpb_src)[r * kBwdRoundWords + k]);
+    }
     return;
   }
-  i -= 8ll * a.n_rpf;
-  if (i < 8ll * a.n_rpb) {
-    // backward round r, slot k: tz[0..3] then ty[0..3]
-    const int64_t r = i >> 3;
-    const int k = (int)(i & 7);
-    const int32_t t = reinterpret_cast<const int32_t*>(a.rpb_src)[r * kBwdRoundWords + k];
-    if (a.rpb64) a.rpb64[i] = term_shear64(a, t);
-    else a.rpb[i] = term_shear_of(a, t);
+  // complex64: per round the 4 rotation shears, then the merged diagonal
+  bool fwd = i < (int64_t)kRoundPar * a.n_rpf;
+  if (!fwd) i -= (int64_t)kRoundPar * a.n_rpf;
+  if (!fwd && i >= (int64_t)kRoundPar * a.n_rpb) return;
+  const int64_t r = i / kRoundPar;
+  const int e = (int)(i - r * kRoundPar);
+  const int32_t* rec = fwd ? reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords
+                           : reinterpret_cast<const int32_t*>(a.rpb_src) + r * kBwdRoundWords;
+  const int32_t* tz = fwd ? rec + 8 : rec;
+  const int32_t* ty = fwd ? rec + 12 : rec + 4;
+  float4* out = (fwd ? a.rpf : a.rpb) + r * kRoundPar;
+  if (e < 4) {
+    out[e] = term_shear_of(a, ty[e]);
+  } else {
+    out[e] = diag_phases(a, tz, 2 * (e - 4), fwd);
   }
 }
 
@@ -1630,7 +1684,7 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + 8ll * a.n_rpf + 8ll * a.n_rpb;
+  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + round_par_elems(a);
   if (total == 0) return cudaSuccess;
   // float64 work per element: small blocks spread it over more SMs
   const int blk = 64;

@@ -16,7 +16,7 @@ struct PassArgs {
   int64_t B;              // samples in this call
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs)
-  const float4* rpar;     // per-round item parameters, 8 float4 per round (round programs)
+  const float4* rpar;     // per-round parameters, kRoundPar float4 per round (round programs)
   const float* tcb;       // tensor-core path: per-round 32x32 real blocks, TF32 hi then lo, K-major
   const float4* mats;     // fused 2x2 matrices, 2 float4 each
   const float2* cs;       // (cos, sin) of theta/2 per gradient term (generic programs)
@@ -73,13 +73,19 @@ struct PrepArgs {
   // round programs: the parameters of every round gathered in round order
   int32_t n_rpf;               // forward rounds
   const uint4* rpf_src;        // forward round records (fused index per item)
-  float4* rpf;                 // [n_rpf][8]: item k's RY-term shear at 2k, its RZ-run-term shear at 2k+1
+  float4* rpf;                 // [n_rpf][kRoundPar]: rotation shears, then the applied diagonal
   int32_t n_rpb;               // backward rounds
   const uint4* rpb_src;        // backward round records (tz[4], ty[4] terms)
-  float4* rpb;                 // [n_rpb][8]: shear parameters of tz[0..3], ty[0..3]
-  Shear64* rpf64;              // if non-null instead of rpf / rpb: the same in float64
-  Shear64* rpb64;              //   (complex128 round programs)
+  float4* rpb;                 // [n_rpb][kRoundPar]: rotation shears, then the un-applied diagonal
+  Shear64* rpf64;              // if non-null instead of rpf / rpb: [n][kRoundPar64] Shear64, item k's
+  Shear64* rpb64;              //   rotation and RZ-run shears (fwd: 2k, 2k+1; bwd: 4 + k, k)
 };
+
+// Table elements of the round parameters (prep work items per round).
+__host__ __device__ inline int64_t round_par_elems(const PrepArgs& a) {
+  const int64_t per = (a.rpf64 || a.rpb64) ? kRoundPar64 : kRoundPar;
+  return per * ((int64_t)a.n_rpf + a.n_rpb);
+}
 
 struct GradReduceArgs {
   const double* g_part;
@@ -149,7 +155,7 @@ struct PassArgs64 {
   int64_t B;
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs), else null
-  const Shear64* rpar;    // per-round item parameters, 8 per round (round programs)
+  const Shear64* rpar;    // per-round item parameters, kRoundPar64 per round (round programs)
   int32_t rx_items;       // round programs with RX items
   const double2* mats;    // fused 2x2 matrices, 4 double2 each: u00, u01, u10, u11 (generic)
   const double2* cs;      // (cos, sin) of phi/2 per gradient term
