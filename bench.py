@@ -608,12 +608,15 @@ def main():
 
     def step(s, inp=None):
         th_, x_, y_ = inp if inp is not None else (theta, x, y)
-        loss, E, g = s.train_step(th_, x_, y_, loss=w.loss)
+        if not hasattr(s, "bench_out"):
+            s.bench_out = s.device_outputs()  # the same buffers every step
+        loss, E, g = s.train_step(th_, x_, y_, loss=w.loss, out=s.bench_out)
         if world > 1:
             dp.allreduce_sum(g)  # data-parallel gradient sum over ranks (NCCL)
         return g
 
     def timed(s, K, inp=None):
+        """K steps, each bracketed by CUDA events after an L2 flush."""
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         launches = 0
@@ -626,21 +629,33 @@ def main():
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in zip(starts, ends)), launches
 
+    def profiled(s, K, inp=None):
+        """Pass-kernel timings: K more steps with CUDA events recorded around
+        every pass launch (the library launches such steps one kernel at a
+        time instead of replaying its recorded graph)."""
+        qfuse.qf_profile(s.handle, True)
+        ms, _ = timed(s, K, inp)
+        p = qfuse.qf_profile_read(s.handle)
+        qfuse.qf_profile(s.handle, False)
+        p["ms_per_step"] = ms / K
+        return p
+
+    # the warm-up records the step's CUDA graph; the timed steps replay it
     for _ in range(args.warmup):
         step(sim)
     torch.cuda.synchronize()
-    qfuse.qf_profile(sim.handle, True)
-    qfuse.qf_profile_read(sim.handle)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    g0 = qfuse.qf_graph_stats(sim.handle)
     with ClockSampler(local) as clk:
         total_ms, launches = timed(sim, args.steps)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    prof = qfuse.qf_profile_read(sim.handle)
-    qfuse.qf_profile(sim.handle, False)
+    g1 = qfuse.qf_graph_stats(sim.handle)
+    step_graph = {"replayed_in_timed_steps": g1["replayed"] - g0["replayed"], "recorded": g1["recorded"]}
+    prof = profiled(sim, args.steps)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -669,7 +684,10 @@ def main():
                                 f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz"),
                 "fwd_kernel": {"achieved": (fwd_fl / info["n_passes"]) / (fwd_launch_ms / 1e3) / 1e12,
                                "ms": fwd_launch_ms},
-                "bwd_kernel_ms": bwd_launch_ms}
+                "bwd_kernel_ms": bwd_launch_ms,
+                "timing": (f"CUDA events on the launching stream around every pass launch of {args.steps} "
+                           f"steps run right after the timed ones (launched kernel by kernel: "
+                           f"{prof['ms_per_step']:.4f} ms per step)")}
     state_bytes = w.B * (1 << w.n) * (16 if c128 else 8)
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     hbm = {"algorithmic_bytes_per_step": 4 * state_bytes,
@@ -699,11 +717,9 @@ def main():
             for _ in range(args.warmup):
                 step(vs, inp)
             torch.cuda.synchronize()
-            qfuse.qf_profile(vs.handle, True)
-            qfuse.qf_profile_read(vs.handle)
             K = min(args.steps, 50 if v128 else 200)
             v_ms, _ = timed(vs, K, inp)
-            vp = qfuse.qf_profile_read(vs.handle)
+            vp = profiled(vs, K, inp)
             variants[name] = {"value": w.B * K / (v_ms / 1e3), "unit": "samples/s", "ms_per_step": v_ms / K,
                               "fwd_ms_per_step": vp["fwd_ms"] / K, "bwd_ms_per_step": vp["bwd_ms"] / K,
                               "device_status": qfuse.qf_device_status(stream)}
@@ -804,6 +820,7 @@ def main():
             "hbm": hbm,
             "e2e": e2e,
             "gpu_launches": launches,
+            "step_graph": step_graph,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "peaks": {"source": peak_src, "hbm_gbs": hbm_gbs},

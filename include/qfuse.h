@@ -275,14 +275,21 @@ qf_status qf_loss(int32_t kind, const double* E_d, const float* y_d, int64_t bat
                   double* loss_d, double* dLdE_d, void* stream);
 
 /* One training step on device buffers: qf_forward, qf_loss, qf_backward.
- * grad_d: float64 [n_params] = dL/dtheta of the whole batch. */
+ * grad_d: float64 [n_params] = dL/dtheta of the whole batch.
+ * Fused plans: from the second consecutive call with the same pointers,
+ * sizes, loss and observable, the step's kernels are replayed from a CUDA
+ * graph the handle recorded on a stream of its own (the buffers' contents may
+ * change between calls; the pointers may not). A call issued while `stream`
+ * is being captured by the caller runs its kernels one by one into that
+ * capture. With pass timing on (qf_profile), a step replays its graph, timing
+ * events included, only when the previous step's timings were read. */
 qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d,
                         const float* y_d, int64_t batch, int32_t loss_kind, qf_pauli obs,
                         double* loss_d, double* E_d, double* grad_d, void* ws_d,
                         size_t ws_bytes, void* stream);
 
 /* The same step from HOST buffers: copies theta_h, x_h (and y_h) into the
- * workspace's staging area, runs qf_train_step, copies loss, E (may be NULL)
+ * workspace's staging area, runs the device step, copies loss, E (may be NULL)
  * and grad back, and synchronises `stream` before returning. Pinned host
  * memory gives asynchronous copies; pageable memory works but is slower.
  * Small steps cross the bus as one packed copy each way through a pinned
@@ -359,6 +366,12 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
 /* Kernels launched by the most recent qf_forward + qf_backward (+ qf_loss
  * inside qf_train_step) on this handle; for launch accounting. */
 qf_status qf_launch_count(const qf_circuit* c, int64_t* launches);
+
+/* How many train steps (qf_train_step, qf_train_step64 and the host-buffer
+ * steps) this handle recorded as CUDA graphs and how many it replayed from
+ * one since it was created; for checking that a training loop hits the
+ * replay path (the same buffers, batch, loss and observable every step). */
+qf_status qf_graph_stats(const qf_circuit* c, int64_t* recorded, int64_t* replayed);
 
 /* ---- batched launch over many circuits ----------------------------------
  * Many circuits of different widths, depths and batch sizes, trained in one

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -63,6 +64,22 @@ struct BlobOffsets {
 
 }  // namespace
 
+// A train step recorded as a CUDA graph for one argument key (pointers,
+// sizes, loss and observable).
+struct StepGraph {
+  std::array<uint64_t, 12> key{};
+  bool profile = false;  // recorded with pass-timing events (qf_profile)
+  cudaGraphExec_t exec = nullptr;
+  bool seen = false;    // the key ran eagerly once
+  bool failed = false;  // recording failed for the key: it stays eager
+  int64_t launches = 0;
+  // timing-event pairs 0 .. ev_pairs-1 recorded by every replay, with their
+  // direction and launch counts
+  size_t ev_pairs = 0;
+  std::vector<int> ev_dir;
+  std::vector<int64_t> ev_launches;
+};
+
 struct qf_circuit {
   qf::Circuit circ;
   bool planned = false;
@@ -88,16 +105,14 @@ struct qf_circuit {
   int64_t launches = 0;
   void* h_stage = nullptr;  // pinned host staging of the host-buffer step (packed copies)
   size_t h_stage_bytes = 0;
-  // the host-buffer step's device part (packed copy in, train step, packed
-  // copy out) recorded once as a CUDA graph for a (workspace, batch, loss,
-  // observable) key seen before, and replayed on the caller's stream
-  cudaStream_t hg_stream = nullptr;
-  cudaGraphExec_t hg_exec = nullptr;
-  bool hg_seen = false;
-  void* hg_ws = nullptr;
-  int64_t hg_batch = -1, hg_launches = 0;
-  int32_t hg_loss = -1;
-  uint64_t hg_x = 0, hg_z = 0;
+  // CUDA graphs of the train steps: the host-buffer step's device part
+  // (packed copy in, step, packed copy out) and the device-buffer step, each
+  // recorded on g_stream for an argument key seen before and replayed on the
+  // caller's stream
+  cudaStream_t g_stream = nullptr;
+  StepGraph hg, dg;
+  bool recording = false;  // a step is being recorded on g_stream
+  int64_t g_recorded = 0, g_replayed = 0;
   int64_t call_launches = 0;
   // pass-kernel timing (qf_profile)
   bool profile = false;
@@ -119,31 +134,36 @@ void destroy_events(qf_circuit* c) {
   c->ev_used = 0;
 }
 
+// A timing event; while a step is being recorded it becomes an event-record
+// node of the graph (every replay records it).
+void record_event(const qf_circuit* c, cudaEvent_t e, cudaStream_t st) {
+  if (c->recording) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
+}
+
 // Record the start of a timed range; returns the pair index or -1.
 int prof_begin(qf_circuit* c, cudaStream_t st) {
   if (!c->profile || c->ev_used >= kMaxProfilePairs) return -1;
   const size_t k = c->ev_used++;
-  cudaEventRecord(c->ev[2 * k], st);
+  record_event(c, c->ev[2 * k], st);
   return (int)k;
 }
 
 void prof_end(qf_circuit* c, int k, int dir, int64_t launches, cudaStream_t st) {
   if (k < 0) return;
-  cudaEventRecord(c->ev[2 * k + 1], st);
+  record_event(c, c->ev[2 * k + 1], st);
   c->ev_dir[k] = dir;
   c->ev_launches[k] = launches;
 }
 
-void drop_host_graph(qf_circuit* c) {
-  if (c->hg_exec) cudaGraphExecDestroy(c->hg_exec);
-  c->hg_exec = nullptr;
-  c->hg_seen = false;
-  c->hg_ws = nullptr;
-  c->hg_batch = -1;
+void drop_graph(StepGraph& G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G = StepGraph();
 }
 
 void free_tables(qf_circuit* c) {
-  drop_host_graph(c);
+  drop_graph(c->hg);
+  drop_graph(c->dg);
   if (c->d_tables) cudaFree(c->d_tables);
   c->d_tables = nullptr;
   c->dt = DevTables();
@@ -351,6 +371,70 @@ T* at(void* ws, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
+// Run a train step through graph G: the first call with a key runs run(st)
+// eagerly; the second records run on the handle's own stream and replays the
+// graph on st; later calls with the key replay. A new key drops the graph. A
+// step issued while st is being captured (by the caller) runs eagerly. With
+// pass timing on (qf_profile), the graph holds the timing events of its
+// passes in slots 0 .. ev_pairs-1: it is recorded and replayed only when no
+// earlier timings are unread (qf_profile_read between steps), otherwise the
+// step runs eagerly and appends its timings.
+template <class F>
+qf_status graph_step(qf_circuit* c, StepGraph& G, const std::array<uint64_t, 12>& key, cudaStream_t st, F&& run) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone ||
+      (c->profile && c->ev_used != 0)) {
+    cudaGetLastError();
+    return run(st);
+  }
+  if (G.key != key || G.profile != c->profile) {
+    drop_graph(G);
+    G.key = key;
+    G.profile = c->profile;
+  }
+  if (!G.exec && G.seen && !G.failed) {
+    if (!c->g_stream && cudaStreamCreateWithFlags(&c->g_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->g_stream = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    G.failed = true;
+    if (c->g_stream && cudaStreamBeginCapture(c->g_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      c->recording = true;
+      const qf_status sc = run(c->g_stream);
+      c->recording = false;
+      const cudaError_t ec = cudaStreamEndCapture(c->g_stream, &g);
+      if (sc == QF_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&G.exec, g, 0) == cudaSuccess) {
+        G.launches = c->launches;
+        G.failed = false;
+        c->g_recorded++;
+        G.ev_pairs = c->profile ? c->ev_used : 0;
+        G.ev_dir.assign(c->ev_dir.begin(), c->ev_dir.begin() + G.ev_pairs);
+        G.ev_launches.assign(c->ev_launches.begin(), c->ev_launches.begin() + G.ev_pairs);
+      } else {
+        G.exec = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    c->ev_used = 0;  // the recording ran nothing
+  }
+  if (G.exec) {
+    QF_CU(cudaGraphLaunch(G.exec, st));
+    c->g_replayed++;
+    c->launches = G.launches;
+    if (c->profile) {
+      std::copy(G.ev_dir.begin(), G.ev_dir.end(), c->ev_dir.begin());
+      std::copy(G.ev_launches.begin(), G.ev_launches.end(), c->ev_launches.begin());
+      c->ev_used = G.ev_pairs;
+    }
+    return QF_OK;
+  }
+  const qf_status s = run(st);
+  if (s == QF_OK) G.seen = true;
+  return s;
+}
+
 // x-mask in the tile coordinates of a pass; false when a bit is outside it.
 bool local_xmask(const qf::PassDesc& pd, uint32_t xm, uint32_t* out) {
   uint32_t r = 0;
@@ -397,7 +481,9 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa{};
   pa.theta = theta;
-  pa.n_fused = (int32_t)P.fuse_off.size() - 1;
+  // round programs take their rotations and diagonals from the round tables;
+  // the fused 2x2s are needed by generic steps and the tensor-core tables
+  pa.n_fused = P.rounds && !c->tc ? 0 : (int32_t)P.fuse_off.size() - 1;
   pa.fuse_off = T.fuse_off;
   pa.fuse_gates = T.fuse_gates;
   pa.mats = at<float4>(ws, L.mats);
@@ -934,7 +1020,7 @@ qf_status qf_circuit_destroy(qf_circuit* c) {
   if (!c) return QF_OK;
   destroy_events(c);
   free_tables(c);
-  if (c->hg_stream) cudaStreamDestroy(c->hg_stream);
+  if (c->g_stream) cudaStreamDestroy(c->g_stream);
   delete c;
   return QF_OK;
 }
@@ -1137,6 +1223,74 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
 
 namespace {
 
+// The argument key of a device-buffer train step.
+std::array<uint64_t, 12> step_key(const void* theta, const void* x, const void* y, int64_t batch, int32_t loss_kind,
+                                  qf_pauli obs, const void* loss, const void* E, const void* grad, const void* ws,
+                                  size_t ws_bytes) {
+  auto u = [](const void* p) { return (uint64_t)(uintptr_t)p; };
+  return {u(theta), u(x), u(y), (uint64_t)batch, (uint64_t)loss_kind, obs.x_mask, obs.z_mask, u(loss), u(E), u(grad),
+          u(ws), (uint64_t)ws_bytes};
+}
+
+qf_status train_step_eager(qf_circuit* c, const float* theta_d, const float* x_d, const float* y_d, int64_t batch,
+                           int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d, double* grad_d, void* ws_d,
+                           size_t ws_bytes, void* stream) {
+  if (c && c->planned && c->path == QF_PATH_FUSED) {
+    // fused: one prep launch fills the forward's and the backward's tables
+    qf_status s = check_call(c, batch, ws_d, ws_bytes);
+    if (s != QF_OK) return s;
+    if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
+        (!grad_d && c->circ.n_params > 0))
+      return fail(QF_ERR_INVALID_ARG, "null data pointer");
+    Obs o;
+    if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->call_launches = 0;
+    s = fused_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
+    if (s != QF_OK) return s;
+    double* dLdE = at<double>(ws_d, c->L.dLdE);
+    s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+    if (s != QF_OK) return s;
+    c->call_launches++;
+    s = fused_backward(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
+    c->launches = c->call_launches;
+    return s;
+  }
+  qf_status s = qf_forward(c, theta_d, x_d, batch, obs, E_d, ws_d, ws_bytes, stream);
+  if (s != QF_OK) return s;
+  double* dLdE = at<double>(ws_d, c->L.dLdE);
+  s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+  if (s != QF_OK) return s;
+  const int64_t fwd_launches = c->launches;
+  s = qf_backward(c, theta_d, x_d, batch, obs, dLdE, grad_d, 0, ws_d, ws_bytes, stream);
+  c->launches = fwd_launches + 1 + c->call_launches;
+  return s;
+}
+
+qf_status train_step_eager64(qf_circuit* c, const double* theta_d, const double* x_d, const double* y_d,
+                             int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d,
+                             double* grad_d, void* ws_d, size_t ws_bytes, void* stream) {
+  qf_status s = check_call(c, batch, ws_d, ws_bytes, true);
+  if (s != QF_OK) return s;
+  if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
+      (!grad_d && c->circ.n_params > 0))
+    return fail(QF_ERR_INVALID_ARG, "null data pointer");
+  Obs o;
+  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  c->call_launches = 0;
+  // one prep launch fills the forward's and the backward's tables
+  s = fused_forward64(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
+  if (s != QF_OK) return s;
+  double* dLdE = at<double>(ws_d, c->L.dLdE);
+  s = qf_loss64(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+  if (s != QF_OK) return s;
+  c->call_launches++;
+  s = fused_backward64(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
+  c->launches = c->call_launches;
+  return s;
+}
+
 // The host-buffer step for real inputs of type R (float: complex64 plans,
 // double: complex128 plans).
 template <class R>
@@ -1146,11 +1300,11 @@ qf_status train_step_host(qf_circuit* c, const R* theta_h, const R* x_h, const R
   constexpr bool F64 = sizeof(R) == 8;
   auto step_on = [&](const R* th, const R* xd, const R* yd, void* strm) -> qf_status {
     if constexpr (F64)
-      return qf_train_step64(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
-                             at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, strm);
+      return train_step_eager64(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
+                                at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, strm);
     else
-      return qf_train_step(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
-                           at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, strm);
+      return train_step_eager(c, th, xd, yd, batch, loss_kind, obs, at<double>(ws_d, c->L.loss),
+                              at<double>(ws_d, c->L.E), at<double>(ws_d, c->L.grad), ws_d, ws_bytes, strm);
   };
   auto step = [&](const R* th, const R* xd, const R* yd) -> qf_status { return step_on(th, xd, yd, stream); };
   qf_status s = check_call(c, batch, ws_d, ws_bytes, F64);
@@ -1184,53 +1338,18 @@ qf_status train_step_host(qf_circuit* c, const R* theta_h, const R* x_h, const R
     if (P) memcpy(h, theta_h, (size_t)P * sizeof(R));
     if (batch) memcpy(h + (L.x - L.theta), x_h, x_bytes(c, batch));
     if (mse) memcpy(h + (L.y - L.theta), y_h, (size_t)batch * sizeof(R));
-    const bool same = c->hg_ws == ws_d && c->hg_batch == batch && c->hg_loss == loss_kind &&
-                      c->hg_x == obs.x_mask && c->hg_z == obs.z_mask;
-    if (!same) {
-      drop_host_graph(c);
-      c->hg_ws = ws_d;
-      c->hg_batch = batch;
-      c->hg_loss = loss_kind;
-      c->hg_x = obs.x_mask;
-      c->hg_z = obs.z_mask;
-    }
-    if (same && c->hg_seen && !c->hg_exec && !c->profile && batch > 0) {
-      // second call with this key: record the device part once (a failed
-      // capture leaves the eager path in use)
-      if (!c->hg_stream && cudaStreamCreateWithFlags(&c->hg_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        c->hg_stream = nullptr;
-      }
-      cudaGraph_t g = nullptr;
-      if (c->hg_stream && cudaStreamBeginCapture(c->hg_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        qf_status sc = QF_ERR_CUDA;
-        if (cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, c->hg_stream) == cudaSuccess) {
-          sc = step_on(th, xd, yd, c->hg_stream);
-          if (sc == QF_OK &&
-              cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, c->hg_stream) != cudaSuccess)
-            sc = QF_ERR_CUDA;
-        }
-        const cudaError_t ec = cudaStreamEndCapture(c->hg_stream, &g);
-        if (sc == QF_OK && ec == cudaSuccess && g &&
-            cudaGraphInstantiate(&c->hg_exec, g, 0) == cudaSuccess) {
-          c->hg_launches = c->launches;
-        } else {
-          c->hg_exec = nullptr;
-        }
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-      }
-    }
-    if (same && c->hg_exec && !c->profile) {
-      QF_CU(cudaGraphLaunch(c->hg_exec, st));
-      c->launches = c->hg_launches;
-    } else {
-      QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, st));
-      s = step(th, xd, yd);
-      if (s != QF_OK) return s;
-      QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, st));
-      c->hg_seen = true;
-    }
+    const std::array<uint64_t, 12> key = {(uint64_t)(uintptr_t)ws_d, (uint64_t)ws_bytes, (uint64_t)batch,
+                                           (uint64_t)loss_kind, obs.x_mask, obs.z_mask, (uint64_t)(uintptr_t)h,
+                                           0, 0, 0, 0, 0};
+    auto run = [&](cudaStream_t strm) -> qf_status {
+      QF_CU(cudaMemcpyAsync(th, h, in_span, cudaMemcpyHostToDevice, strm));
+      const qf_status r = step_on(th, xd, yd, strm);
+      if (r != QF_OK) return r;
+      QF_CU(cudaMemcpyAsync(h, at<double>(ws_d, L.E), out_span, cudaMemcpyDeviceToHost, strm));
+      return QF_OK;
+    };
+    s = batch > 0 ? graph_step(c, c->hg, key, st, run) : run(st);
+    if (s != QF_OK) return s;
     QF_CU(cudaStreamSynchronize(st));
     memcpy(loss_h, h + (L.loss - L.E), 8);
     if (E_h && batch) memcpy(E_h, h, (size_t)batch * 8);
@@ -1379,36 +1498,12 @@ qf_status qf_loss(int32_t kind, const double* E_d, const float* y_d, int64_t bat
 qf_status qf_train_step(qf_circuit* c, const float* theta_d, const float* x_d, const float* y_d, int64_t batch,
                         int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d, double* grad_d, void* ws_d,
                         size_t ws_bytes, void* stream) {
-  if (c && c->planned && c->path == QF_PATH_FUSED) {
-    // fused: one prep launch fills the forward's and the backward's tables
-    qf_status s = check_call(c, batch, ws_d, ws_bytes);
-    if (s != QF_OK) return s;
-    if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
-        (!grad_d && c->circ.n_params > 0))
-      return fail(QF_ERR_INVALID_ARG, "null data pointer");
-    Obs o;
-    if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    c->call_launches = 0;
-    s = fused_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
-    if (s != QF_OK) return s;
-    double* dLdE = at<double>(ws_d, c->L.dLdE);
-    s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
-    if (s != QF_OK) return s;
-    c->call_launches++;
-    s = fused_backward(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
-    c->launches = c->call_launches;
-    return s;
-  }
-  qf_status s = qf_forward(c, theta_d, x_d, batch, obs, E_d, ws_d, ws_bytes, stream);
-  if (s != QF_OK) return s;
-  double* dLdE = at<double>(ws_d, c->L.dLdE);
-  s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
-  if (s != QF_OK) return s;
-  const int64_t fwd_launches = c->launches;
-  s = qf_backward(c, theta_d, x_d, batch, obs, dLdE, grad_d, 0, ws_d, ws_bytes, stream);
-  c->launches = fwd_launches + 1 + c->call_launches;
-  return s;
+  auto run = [&](cudaStream_t st) {
+    return train_step_eager(c, theta_d, x_d, y_d, batch, loss_kind, obs, loss_d, E_d, grad_d, ws_d, ws_bytes, st);
+  };
+  if (!c || !c->planned || c->path != QF_PATH_FUSED || batch <= 0) return run(static_cast<cudaStream_t>(stream));
+  return graph_step(c, c->dg, step_key(theta_d, x_d, y_d, batch, loss_kind, obs, loss_d, E_d, grad_d, ws_d, ws_bytes),
+                    static_cast<cudaStream_t>(stream), run);
 }
 
 qf_status qf_train_step_host(qf_circuit* c, const float* theta_h, const float* x_h, const float* y_h,
@@ -1507,25 +1602,12 @@ qf_status qf_loss64(int32_t kind, const double* E_d, const double* y_d, int64_t 
 qf_status qf_train_step64(qf_circuit* c, const double* theta_d, const double* x_d, const double* y_d,
                           int64_t batch, int32_t loss_kind, qf_pauli obs, double* loss_d, double* E_d,
                           double* grad_d, void* ws_d, size_t ws_bytes, void* stream) {
-  qf_status s = check_call(c, batch, ws_d, ws_bytes, true);
-  if (s != QF_OK) return s;
-  if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
-      (!grad_d && c->circ.n_params > 0))
-    return fail(QF_ERR_INVALID_ARG, "null data pointer");
-  Obs o;
-  if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  c->call_launches = 0;
-  // one prep launch fills the forward's and the backward's tables
-  s = fused_forward64(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
-  if (s != QF_OK) return s;
-  double* dLdE = at<double>(ws_d, c->L.dLdE);
-  s = qf_loss64(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
-  if (s != QF_OK) return s;
-  c->call_launches++;
-  s = fused_backward64(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
-  c->launches = c->call_launches;
-  return s;
+  auto run = [&](cudaStream_t st) {
+    return train_step_eager64(c, theta_d, x_d, y_d, batch, loss_kind, obs, loss_d, E_d, grad_d, ws_d, ws_bytes, st);
+  };
+  if (!c || !c->planned || batch <= 0) return run(static_cast<cudaStream_t>(stream));
+  return graph_step(c, c->dg, step_key(theta_d, x_d, y_d, batch, loss_kind, obs, loss_d, E_d, grad_d, ws_d, ws_bytes),
+                    static_cast<cudaStream_t>(stream), run);
 }
 
 qf_status qf_train_step_host64(qf_circuit* c, const double* theta_h, const double* x_h, const double* y_h,
@@ -1737,7 +1819,7 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       r.grad_off = b->grad_off[i];
       qf::PrepArgs& p = r.prep;
       p = qf::PrepArgs{};
-      p.n_fused = (int32_t)P.fuse_off.size() - 1;
+      p.n_fused = P.rounds ? 0 : (int32_t)P.fuse_off.size() - 1;  // round tables only
       p.fuse_off = T.fuse_off;
       p.fuse_gates = T.fuse_gates;
       p.mats = rel<float4>(w0 + L.mats);
@@ -1932,6 +2014,13 @@ qf_status qf_profile_read(qf_circuit* c, double* fwd_ms, int64_t* fwd_launches, 
 qf_status qf_launch_count(const qf_circuit* c, int64_t* launches) {
   if (!c || !launches) return fail(QF_ERR_INVALID_ARG, "null argument");
   *launches = c->launches;
+  return QF_OK;
+}
+
+qf_status qf_graph_stats(const qf_circuit* c, int64_t* recorded, int64_t* replayed) {
+  if (!c || !recorded || !replayed) return fail(QF_ERR_INVALID_ARG, "null argument");
+  *recorded = c->g_recorded;
+  *replayed = c->g_replayed;
   return QF_OK;
 }
 

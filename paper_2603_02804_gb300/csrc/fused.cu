@@ -1534,16 +1534,12 @@ __device__ void run_item_pass(bool bwd, const PassArgs& a, int32_t b0) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ PassShared sh;
   const int tpc = kThreads >> (a.pd.K - kRegBits);
-  if (a.tps_log2 == 0) {
-    // a tile is a sample: the item's samples b0 .. b0 + tpc - 1 in one call
-    if (bwd) pass_cta<true, true, 2>(a, b0, smem, sh);
-    else pass_cta<false, true, 2>(a, b0, smem, sh);
-  } else {
-    const int64_t tps = 1ll << a.tps_log2;
-    for (int64_t t = 0; t < tps; t += tpc) {
-      if (bwd) pass_cta<true, true, 2>(a, (int64_t)b0 * tps + t, smem, sh);
-      else pass_cta<false, true, 2>(a, (int64_t)b0 * tps + t, smem, sh);
-    }
+  // tpc tiles per call: with one tile per sample (tps = 1) the item's samples
+  // b0 .. b0 + tpc - 1 in one call, else the tiles of sample b0 in turn
+  const int64_t tps = 1ll << a.tps_log2;
+  for (int64_t t = 0; t < tps; t += tpc) {
+    if (bwd) pass_cta<true, true, 2>(a, (int64_t)b0 * tps + t, smem, sh);
+    else pass_cta<false, true, 2>(a, (int64_t)b0 * tps + t, smem, sh);
   }
 }
 

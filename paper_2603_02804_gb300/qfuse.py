@@ -94,6 +94,7 @@ SIGNATURES = {
     "qf_batch_info": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i32),
     "qf_batch_destroy": ([_vp], _i32),
     "qf_launch_count": ([_vp, ctypes.POINTER(_i64)], _i32),
+    "qf_graph_stats": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _i32),
     "qf_profile": ([_vp, _i32], _i32),
     "qf_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)], _i32),
@@ -332,6 +333,13 @@ def qf_launch_count(handle) -> int:
     n = _i64()
     _check(load().qf_launch_count(handle, ctypes.byref(n)))
     return n.value
+
+
+def qf_graph_stats(handle) -> dict:
+    """Train steps recorded as CUDA graphs and replayed from one by this handle."""
+    rec, rep = _i64(), _i64()
+    _check(load().qf_graph_stats(handle, ctypes.byref(rec), ctypes.byref(rep)))
+    return {"recorded": rec.value, "replayed": rep.value}
 
 
 def qf_profile(handle, on: bool) -> None:

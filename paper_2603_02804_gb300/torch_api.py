@@ -125,19 +125,29 @@ class Simulator:
         fn(self.handle, theta, x, B, self.obs, dLdE, g, per_sample, self.ws, self.ws_bytes, self._stream())
         return g
 
-    def train_step(self, theta, x, y=None, loss: str = "sum"):
-        """Forward, loss and backward in one call: (loss [1], E [B], grad [P]) on the device."""
+    def train_step(self, theta, x, y=None, loss: str = "sum", out=None):
+        """Forward, loss and backward in one call: (loss [1], E [B], grad [P]) on the device.
+        ``out``: float64 device tensors (loss [1], E [>= B], grad [P]) to write (e.g. from
+        ``device_outputs()``). The library replays a step from a CUDA graph it recorded
+        when the same buffers come back, so reusing inputs and outputs saves launches."""
         self._check(theta, x)
         B = x.shape[0]
-        out_loss = torch.empty(1, dtype=torch.float64, device=self.device)
-        E = torch.empty(B, dtype=torch.float64, device=self.device)
-        g = torch.empty(self.n_params, dtype=torch.float64, device=self.device)
+        out_loss, E, g = out if out is not None else self.device_outputs(B)
+        if (E.numel() < B or g.numel() != self.n_params or E.dtype != torch.float64 or not E.is_cuda
+                or not g.is_cuda or not out_loss.is_cuda):
+            raise ValueError("out buffers must be float64 CUDA tensors (loss [1], E [>= B], grad [P])")
         if y is not None and (y.dtype != self.real or not y.is_cuda):
             raise TypeError(f"y must be a {self.real} CUDA tensor")
         fn = qfuse.qf_train_step64 if self.f64 else qfuse.qf_train_step
         fn(self.handle, theta, x, y, B, _LOSS[loss], self.obs, out_loss, E, g, self.ws, self.ws_bytes, self._stream())
         self._fwd_id = next(_ids)
         return out_loss, E, g
+
+    def device_outputs(self, batch: int | None = None):
+        """Device buffers (loss [1], E [B], grad [P]) for ``train_step(out=...)``."""
+        B = self.batch if batch is None else batch
+        z = lambda k: torch.empty(k, dtype=torch.float64, device=self.device)
+        return z(1), z(B), z(self.n_params)
 
     def host_outputs(self, batch: int | None = None):
         """Pinned host buffers (loss [1], E [B], grad [P]) for ``train_step_host(out=...)``."""

@@ -352,6 +352,50 @@ def test_train_step_cuda_graph_replay():
     assert torch.equal(out[0], loss_e) and torch.equal(out[1], E_e) and torch.equal(out[2], g_e)
 
 
+def test_device_step_graph_replay_tracks_inputs():
+    """qf_train_step records its launches as a CUDA graph on the second call
+    with the same buffers, batch, loss and observable, and replays it after:
+    with the buffers' contents changed in place, every call must equal an
+    eager step (fresh buffers each call, so no key repeats) bit for bit. With
+    pass timing on, replays carry their timing events."""
+    w = workloads.WORKLOADS["hea12"]
+    theta, x, y = workloads.make_inputs(w, B=32)
+    sim = Simulator(w.n, w.d, 32)
+    ref = Simulator(w.n, w.d, 32)
+    out = sim.device_outputs(32)
+    th_d, x_d, y_d = dev(theta), dev(x), dev(y)
+    rng = np.random.default_rng(8)
+    keep = []
+    for call in range(5):
+        th = (theta + np.float32(0.1 * call)).astype(np.float32)
+        xs = rng.uniform(0, np.pi, x.shape).astype(np.float32)
+        th_d.copy_(torch.from_numpy(th))
+        x_d.copy_(torch.from_numpy(xs))
+        ld, Ed, gd = (t.clone() for t in sim.train_step(th_d, x_d, y_d, loss="mse", out=out))
+        args = (dev(th), dev(xs), dev(y))
+        res = ref.train_step(*args, loss="mse")
+        keep.append((args, res))
+        torch.cuda.synchronize()
+        assert ld.item() == res[0].item(), call
+        assert torch.equal(Ed, res[1]) and torch.equal(gd, res[2]), call
+        assert sim.launches() == ref.launches()
+    # call 0 ran eagerly, call 1 recorded the graph; calls 1-4 replayed it
+    assert qfuse.qf_graph_stats(sim.handle) == {"recorded": 1, "replayed": 4}
+    assert qfuse.qf_graph_stats(ref.handle) == {"recorded": 0, "replayed": 0}
+    qfuse.qf_profile(sim.handle, True)
+    seen = []
+    for call in range(4):
+        sim.train_step(th_d, x_d, y_d, loss="mse", out=out)
+        p = qfuse.qf_profile_read(sim.handle)
+        assert p["fwd_ms"] > 0 and p["bwd_ms"] > 0, (call, p)
+        seen.append((p["fwd_launches"], p["bwd_launches"]))
+    qfuse.qf_profile(sim.handle, False)
+    assert len(set(seen)) == 1, seen
+    assert qfuse.qf_graph_stats(sim.handle) == {"recorded": 2, "replayed": 7}
+    torch.cuda.synchronize()
+    assert torch.equal(out[2], gd)  # the same inputs as the last call above
+
+
 def test_host_step_graph_replay_tracks_inputs():
     """qf_train_step_host records its device part (copies in, step, copies
     out) as a CUDA graph on the second call with the same workspace, batch,
@@ -372,3 +416,4 @@ def test_host_step_graph_replay_tracks_inputs():
         torch.cuda.synchronize()
         assert lh.item() == ld.item(), call
         assert torch.equal(Eh, Ed.cpu()) and torch.equal(gh, gd.cpu()), call
+    assert qfuse.qf_graph_stats(sim.handle)["replayed"] >= 3  # host-buffer calls 1-3
