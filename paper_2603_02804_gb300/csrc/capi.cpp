@@ -206,7 +206,7 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
   L.dLdE = take((size_t)B * 8);
   L.grad = take((size_t)P * 8);
   L.loss = take(8);
-  L.cs = take((size_t)S * 16);  // (cos, sin), float32 or float64, or shear parameters per term
+  L.cs = take((size_t)S * 16);  // (cos, sin) per term, float32 or float64 (generic programs)
   L.enc = take((size_t)B * n_eff * aw);
   L.work = take((size_t)L.state_elems * aw);
   L.lam = take((size_t)L.state_elems * aw);
@@ -457,19 +457,19 @@ void set_input(const qf_circuit* c, const float* x, qf::PassArgs& a) {
   a.n_in = c->circ.n;
 }
 
-// The backward's per-term table: (cos, sin) for generic programs, three-shear
-// parameters for round programs.
+// The backward's parameter tables: (cos, sin) per gradient term for generic
+// programs, the backward round parameters for round programs.
 void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, qf::PrepArgs& pa) {
-  pa.n_terms = n_slots_of(c);
   pa.term_off = T.term_off;
   pa.term_params = T.term_params;
   pa.term_const = T.term_const;
   if (c->path == QF_PATH_FUSED && c->fp.rounds) {
-    pa.shear = at<float4>(ws, L.cs);
+    pa.n_terms = 0;
     pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
     pa.rpb_src = T.bwd_rounds;
     pa.rpb = at<float4>(ws, L.rpb);
   } else {
+    pa.n_terms = n_slots_of(c);
     pa.cs = at<float2>(ws, L.cs);
   }
 }
@@ -592,7 +592,6 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
   a.rx_items = P.has_rx ? 1 : 0;
   a.rpar = P.rounds ? at<float4>(ws, L.rpb) : nullptr;
   a.cs = pa.cs;
-  a.shear = pa.shear;
   a.work = at<float2>(ws, L.work);
   a.lam = at<float2>(ws, L.lam);
   a.slots = at<float2>(ws, L.slots);
@@ -1795,7 +1794,6 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       a.dLdE = rel<const double>(w0 + L.dLdE);
       a.e_part = rel<double>(w0 + L.epart);
       a.g_part = rel<double>(w0 + L.gpart);
-      a.shear = rel<const float4>(w0 + L.cs);
       a.n_slots = P.n_terms;
       r.fa = a;
       r.fa.ops = T.fwd_ops;
@@ -1823,11 +1821,10 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       p.fuse_off = T.fuse_off;
       p.fuse_gates = T.fuse_gates;
       p.mats = rel<float4>(w0 + L.mats);
-      p.n_terms = P.n_terms;
+      p.n_terms = 0;  // round programs: the round tables hold every angle
       p.term_off = T.term_off;
       p.term_params = T.term_params;
       p.term_const = T.term_const;
-      p.shear = rel<float4>(w0 + L.cs);
       p.B = b->B[i];
       p.n = c->circ.n;
       p.n_eff = P.n_eff;

@@ -1263,6 +1263,38 @@ __device__ double term_angle(const PrepArgs& a, int64_t t) {
   return phi;
 }
 
+// term_angle of the terms t[0..3] (-1: none, angle 0) with the loads of the
+// four terms issued together: the index ranges and constants, then the first
+// two parameters of each, then their values (the same summation order as
+// term_angle; a term of more than two parameters finishes in a loop).
+__device__ void term_angles4(const PrepArgs& a, const int32_t* t, double (&phi)[4]) {
+  int b0[4], b1[4], p0[4], p1[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const bool on = t[r] >= 0;
+    b0[r] = on ? a.term_off[t[r]] : 0;
+    b1[r] = on ? a.term_off[t[r] + 1] : 0;
+    phi[r] = on && a.term_const ? a.term_const[t[r]] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    p0[r] = b1[r] > b0[r] ? a.term_params[b0[r]] : -1;
+    p1[r] = b1[r] > b0[r] + 1 ? a.term_params[b0[r] + 1] : -1;
+  }
+  double v0[4], v1[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    v0[r] = p0[r] >= 0 ? theta_at(a, p0[r]) : 0.0;
+    v1[r] = p1[r] >= 0 ? theta_at(a, p1[r]) : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (p0[r] >= 0) phi[r] += v0[r];
+    if (p1[r] >= 0) phi[r] += v1[r];
+    for (int j = b0[r] + 2; j < b1[r]; ++j) phi[r] += theta_at(a, a.term_params[j]);
+  }
+}
+
 // u(phi) = (-1)^k u(w) with w = phi - 2 pi k in (-pi, pi]: the rotation by w/2
 // as three shears needs tan(w/4) (|.| <= 1) and sin(w/2); a missing term (-1)
 // is the identity (all zero). tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the
@@ -1295,7 +1327,7 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
 // each from one float64 sincos of the summed angle.
 __device__ float4 diag_phases(const PrepArgs& a, const int32_t* tz, int j0, bool apply) {
   double phi[4];
-  for (int r = 0; r < 4; ++r) phi[r] = tz[r] >= 0 ? term_angle(a, tz[r]) : 0.0;
+  term_angles4(a, tz, phi);
   double cs[4];
   for (int h = 0; h < 2; ++h) {
     const int j = j0 + h;
@@ -1333,9 +1365,7 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   }
   i -= a.n_fused;
   if (i < a.n_terms) {
-    if (a.shear) {
-      a.shear[i] = term_shear_of(a, (int32_t)i);
-    } else if (a.cs64) {
+    if (a.cs64) {
       double s, c;
       sincos(0.5 * term_angle(a, i), &s, &c);
       a.cs64[i] = make_double2(c, s);
@@ -1518,7 +1548,6 @@ __device__ void load_args(PassArgs& dst, const PassArgs& src, const PassDesc& pd
     dst.pd = pd;
     dst.mats = rebase(dst.mats, ws);
     dst.rpar = rebase(dst.rpar, ws);
-    dst.shear = rebase(dst.shear, ws);
     dst.enc = rebase(dst.enc, ws);
     dst.work = rebase(dst.work, ws);
     dst.lam = rebase(dst.lam, ws);
@@ -1555,7 +1584,6 @@ __global__ void batch_prep_kernel(const BatchArgs a, int64_t total) {
   p.mats = rebase(p.mats, a.ws);
   p.rpf = rebase(p.rpf, a.ws);
   p.rpb = rebase(p.rpb, a.ws);
-  p.shear = rebase(p.shear, a.ws);
   p.enc = rebase(p.enc, a.ws);
   prep_one(p, i - a.prep_off[c]);
 }

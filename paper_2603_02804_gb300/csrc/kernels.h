@@ -20,7 +20,6 @@ struct PassArgs {
   const float* tcb;       // tensor-core path: per-round 32x32 real blocks, TF32 hi then lo, K-major
   const float4* mats;     // fused 2x2 matrices, 2 float4 each
   const float2* cs;       // (cos, sin) of theta/2 per gradient term (generic programs)
-  const float4* shear;    // three-shear parameters per gradient term (round programs)
   const float2* enc;      // (cos, sin) of x/2, [B][n_eff]
   const float2* psi_in;   // given initial states [B][2^n_in] (QF_ENC_STATE_IN), else null
   int32_t n_in;           // qubits of the given states (<= n_eff; padding qubits |0>)
@@ -59,9 +58,7 @@ struct PrepArgs {
   const int32_t* term_off;     // CSR term -> parameters (angles summed)
   const int32_t* term_params;
   const double* term_const;    // constant part of each term's angle (may be null)
-  float2* cs;                  // (cos, sin) of phi/2 per term, or
-  float4* shear;               // if non-null instead: (tan(w/4), sin(w/2), wrap parity, 0),
-                               // w = phi wrapped into (-pi, pi], phi = w + 2 pi k
+  float2* cs;                  // (cos, sin) of phi/2 per term (generic programs), or
   double2* cs64;               // if non-null instead: (cos, sin) of phi/2 in float64
   const float* x;
   const double* x64;           // if non-null: float64 encoding angles, x unused
