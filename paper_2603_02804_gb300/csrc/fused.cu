@@ -165,7 +165,7 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, uint32_t k) {
 // register index j (bit 4 of D: c0, bits 0..3: A). D commutes with every
 // diagonal gate; a gate on register bit r only sees the factor Z_r^(A_r),
 // which is folded into that gate. CZs between two register bits (quadratic in
-// j) are applied to the registers directly.
+// j, the same for every thread) are signs of the round's diagonal table.
 //
 // Links L of one round, thread base index gb (register bits zero), register
 // bit positions p[r]: x = gb ^ y(j) with disjoint supports, so each link q
@@ -180,28 +180,12 @@ __device__ __forceinline__ void link_terms(uint32_t L, uint32_t gb, int n, uint3
   u = (((t1 << 1) | (t1 >> (n - 1))) & nmask) ^ t2;
 }
 
-template <bool BWD>
-__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4], int n,
-                                              uint32_t& D, float2 (&r)[16], float2 (&l)[16]) {
+__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t gb, const uint32_t (&p)[4], int n, uint32_t& D) {
   uint32_t t2, u;
   link_terms(L, gb, n, t2, u);
   const uint32_t A = ((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) |
                      (((u >> p[3]) & 1u) << 3);
   D ^= A | ((__popc(t2 & gb) & 1u) << 4);
-#pragma unroll
-  for (int rb = 0; rb < 3; ++rb) {
-    const int f = (int)(((bbits >> rb) & 1u) << 31);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (((j >> rb) & 3) != 3) continue;
-      r[j].x = __int_as_float(__float_as_int(r[j].x) ^ f);
-      r[j].y = __int_as_float(__float_as_int(r[j].y) ^ f);
-      if (BWD) {
-        l[j].x = __int_as_float(__float_as_int(l[j].x) ^ f);
-        l[j].y = __int_as_float(__float_as_int(l[j].y) ^ f);
-      }
-    }
-  }
 }
 
 // Multiply the registers by D (end of a step).
@@ -893,10 +877,10 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
           rot_fwd<2, RX>(r, P.v[k][2], (D >> 2) & 1u, D, (lk.z >> 2) & 1u);
           rot_fwd<3, RX>(r, P.v[k][3], (D >> 3) & 1u, D, (lk.z >> 3) & 1u);
           apply_diag(r, &P.v[k][4]);
-          chain_pending<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
+          chain_pending(lk.x, gb, pos, a.n_eff, D);
         } else {
           const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];  // links, bbits, rx mask
-          chain_pending<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
+          chain_pending(lk.x, gb, pos, a.n_eff, D);
           float v[8];
           diag_bwd(r, l, &P.v[k][4], v);
           rot_bwd<0, RX>(r, l, P.v[k][0], D & 1u, D, v[4], lk.z & 1u);
@@ -939,7 +923,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         const int nk = nr * 8;
         const int64_t b2 = first_tile >> a.tps_log2;
         const bool first = (first_tile & ((1ll << a.tps_log2) - 1)) == 0;
-        for (int kk = tid; kk < nk; kk += kThreads) {
+        for (int kk = kThreads - 1 - tid; kk < nk; kk += kThreads) {  // the last warp (warp 0 stages)
           const int32_t term = s_slot[buf][kk];
           if (term < 0) continue;
           double sum = 0.0;
@@ -952,7 +936,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         buf ^= 1;
       } else if (BWD && Tt >= 32) {
         const int nk = nr * 8;
-        for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
+        for (int e = kThreads - 1 - tid; e < tiles_per_cta * nk; e += kThreads) {  // from the last warp
           const int tc = e / nk, kk = e - tc * nk;
           const int64_t t2 = first_tile + tc;
           const int32_t term = s_slot[buf][kk];
@@ -1322,10 +1306,12 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
 // The diagonal of a round: its RZ runs (terms tz[r], angle phi_r; -1 = none)
 // act on register index j as e^{-i a_j} with a_j = sum_r sigma_r(j) phi_r / 2,
 // sigma_r(j) = +1 where bit r of j is clear, else -1 (RZ(phi) =
-// diag(e^{-i phi/2}, e^{i phi/2})). Returns (cos, sin) of the applied phase
-// (forward: -a_j) or of the un-applied one (backward: +a_j) for j0, j0 + 1,
-// each from one float64 sincos of the summed angle.
-__device__ float4 diag_phases(const PrepArgs& a, const int32_t* tz, int j0, bool apply) {
+// diag(e^{-i phi/2}, e^{i phi/2})), and its CZ links between register bits r
+// and r + 1 (bit r of bbits) as -1 where both bits of j are set. Returns
+// (cos, sin) of the applied phase (forward: -a_j) or of the un-applied one
+// (backward: +a_j), with those signs, for j0 and j0 + 1, each from one
+// float64 sincos of the summed angle.
+__device__ float4 diag_phases(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int j0, bool apply) {
   double phi[4];
   term_angles4(a, tz, phi);
   double cs[4];
@@ -1335,6 +1321,11 @@ __device__ float4 diag_phases(const PrepArgs& a, const int32_t* tz, int j0, bool
     for (int r = 0; r < 4; ++r) al += ((j >> r) & 1) ? -phi[r] : phi[r];
     al *= apply ? -0.5 : 0.5;
     sincos(al, &cs[2 * h + 1], &cs[2 * h]);
+    const int cz = __popc(bbits & (uint32_t)j & (uint32_t)(j >> 1)) & 1;
+    if (cz) {
+      cs[2 * h] = -cs[2 * h];
+      cs[2 * h + 1] = -cs[2 * h + 1];
+    }
   }
   return make_float4((float)cs[0], (float)cs[1], (float)cs[2], (float)cs[3]);
 }
@@ -1418,11 +1409,12 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
                            : reinterpret_cast<const int32_t*>(a.rpb_src) + r * kBwdRoundWords;
   const int32_t* tz = fwd ? rec + 8 : rec;
   const int32_t* ty = fwd ? rec + 12 : rec + 4;
+  const uint32_t bbits = (uint32_t)(fwd ? rec[5] : rec[9]);
   float4* out = (fwd ? a.rpf : a.rpb) + r * kRoundPar;
   if (e < 4) {
     out[e] = term_shear_of(a, ty[e]);
   } else {
-    out[e] = diag_phases(a, tz, 2 * (e - 4), fwd);
+    out[e] = diag_phases(a, tz, bbits, 2 * (e - 4), fwd);
   }
 }
 
