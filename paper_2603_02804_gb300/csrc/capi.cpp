@@ -476,8 +476,27 @@ void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, vo
 
 // with_terms: also fill the backward's term table in the same prep launch
 // (used by the train step, where the backward follows with the same theta).
+// The loss of a train step, computed with the forward's E reduction when the
+// batch allows one single-block launch for both (done is then set).
+struct StepLoss {
+  int32_t kind;
+  const void* y;  // float32 labels (complex64 plans) or float64 (complex128 plans)
+  double* loss;
+  double* dLdE;
+  bool done = false;
+};
+
+qf_status check_loss(int32_t kind, const double* E_d, const void* y_d, int64_t batch, const double* loss_d,
+                     const double* dLdE_d) {
+  if (kind != QF_LOSS_SUM && kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
+  if (batch < 0 || (batch > 0 && (!E_d || !dLdE_d)) || !loss_d || (kind == QF_LOSS_MSE && batch > 0 && !y_d))
+    return fail(QF_ERR_INVALID_ARG, "bad loss arguments");
+  return QF_OK;
+}
+
 qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, const float* theta, const float* x,
-                        int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false) {
+                        int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false,
+                        StepLoss* sl = nullptr) {
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa{};
   pa.theta = theta;
@@ -553,7 +572,13 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
                                  o.y, a.e_part, st));
     c->call_launches++;
   }
-  QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+  if (sl && qf::e_loss_fusable(B, (int)L.rows)) {
+    QF_CU(qf::launch_e_loss(a.e_part, (int)L.rows, sl->kind, E, static_cast<const float*>(sl->y), B, sl->loss,
+                            sl->dLdE, st));
+    sl->done = true;
+  } else {
+    QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+  }
   c->call_launches++;
   return QF_OK;
 }
@@ -712,7 +737,8 @@ void set_rounds64(const qf_circuit* c, const DevTables& T, const Layout& L, void
 }
 
 qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, const double* theta, const double* x,
-                          int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false) {
+                          int64_t B, const Obs& o, double* E, void* ws, cudaStream_t st, bool with_terms = false,
+                          StepLoss* sl = nullptr) {
   const qf::FusedPlan& P = c->fp;
   qf::PrepArgs pa = prep_args64(c, T, L, ws, theta);
   if (P.rounds) {
@@ -755,7 +781,13 @@ qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, co
                                    o.y, a.e_part, st));
     c->call_launches++;
   }
-  QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+  if (sl && qf::e_loss_fusable(B, (int)L.rows)) {
+    QF_CU(qf::launch_e_loss64(a.e_part, (int)L.rows, sl->kind, E, static_cast<const double*>(sl->y), B, sl->loss,
+                              sl->dLdE, st));
+    sl->done = true;
+  } else {
+    QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+  }
   c->call_launches++;
   return QF_OK;
 }
@@ -1244,13 +1276,17 @@ qf_status train_step_eager(qf_circuit* c, const float* theta_d, const float* x_d
     Obs o;
     if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    c->call_launches = 0;
-    s = fused_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
-    if (s != QF_OK) return s;
     double* dLdE = at<double>(ws_d, c->L.dLdE);
-    s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+    if ((s = check_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE)) != QF_OK) return s;
+    c->call_launches = 0;
+    StepLoss sl{loss_kind, y_d, loss_d, dLdE};
+    s = fused_forward(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true, &sl);
     if (s != QF_OK) return s;
-    c->call_launches++;
+    if (!sl.done) {
+      s = qf_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+      if (s != QF_OK) return s;
+      c->call_launches++;
+    }
     s = fused_backward(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
     c->launches = c->call_launches;
     return s;
@@ -1277,14 +1313,19 @@ qf_status train_step_eager64(qf_circuit* c, const double* theta_d, const double*
   Obs o;
   if ((s = check_obs(c, obs, &o)) != QF_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  c->call_launches = 0;
-  // one prep launch fills the forward's and the backward's tables
-  s = fused_forward64(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true);
-  if (s != QF_OK) return s;
   double* dLdE = at<double>(ws_d, c->L.dLdE);
-  s = qf_loss64(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+  if ((s = check_loss(loss_kind, E_d, y_d, batch, loss_d, dLdE)) != QF_OK) return s;
+  c->call_launches = 0;
+  // one prep launch fills the forward's and the backward's tables; the loss
+  // rides on the forward's E reduction where the batch allows
+  StepLoss sl{loss_kind, y_d, loss_d, dLdE};
+  s = fused_forward64(c, c->dt, c->L, theta_d, x_d, batch, o, E_d, ws_d, st, true, &sl);
   if (s != QF_OK) return s;
-  c->call_launches++;
+  if (!sl.done) {
+    s = qf_loss64(loss_kind, E_d, y_d, batch, loss_d, dLdE, stream);
+    if (s != QF_OK) return s;
+    c->call_launches++;
+  }
   s = fused_backward64(c, c->dt, c->L, theta_d, x_d, batch, o, dLdE, grad_d, 0, ws_d, st, false);
   c->launches = c->call_launches;
   return s;
@@ -1487,9 +1528,8 @@ qf_status qf_backward(qf_circuit* c, const float* theta_d, const float* x_d, int
 
 qf_status qf_loss(int32_t kind, const double* E_d, const float* y_d, int64_t batch, double* loss_d,
                   double* dLdE_d, void* stream) {
-  if (kind != QF_LOSS_SUM && kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
-  if (batch < 0 || (batch > 0 && (!E_d || !dLdE_d)) || !loss_d || (kind == QF_LOSS_MSE && batch > 0 && !y_d))
-    return fail(QF_ERR_INVALID_ARG, "bad loss arguments");
+  const qf_status s = check_loss(kind, E_d, y_d, batch, loss_d, dLdE_d);
+  if (s != QF_OK) return s;
   QF_CU(qf::launch_loss(kind, E_d, y_d, batch, loss_d, dLdE_d, static_cast<cudaStream_t>(stream)));
   return QF_OK;
 }
@@ -1591,9 +1631,8 @@ qf_status qf_backward64(qf_circuit* c, const double* theta_d, const double* x_d,
 
 qf_status qf_loss64(int32_t kind, const double* E_d, const double* y_d, int64_t batch, double* loss_d,
                     double* dLdE_d, void* stream) {
-  if (kind != QF_LOSS_SUM && kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
-  if (batch < 0 || (batch > 0 && (!E_d || !dLdE_d)) || !loss_d || (kind == QF_LOSS_MSE && batch > 0 && !y_d))
-    return fail(QF_ERR_INVALID_ARG, "bad loss arguments");
+  const qf_status s = check_loss(kind, E_d, y_d, batch, loss_d, dLdE_d);
+  if (s != QF_OK) return s;
   QF_CU(qf::launch_loss64(kind, E_d, y_d, batch, loss_d, dLdE_d, static_cast<cudaStream_t>(stream)));
   return QF_OK;
 }

@@ -1279,19 +1279,34 @@ __device__ void term_angles4(const PrepArgs& a, const int32_t* t, double (&phi)[
   }
 }
 
-// u(phi) = (-1)^k u(w) with w = phi - 2 pi k in (-pi, pi]: the rotation by w/2
-// as three shears needs tan(w/4) (|.| <= 1) and sin(w/2); a missing term (-1)
-// is the identity (all zero). tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the
-// half-angle identity; the denominator lies in [1, 2] for |w/2| <= pi/2), so
-// one float64 sincos gives both.
-__device__ void shear_params(const PrepArgs& a, int32_t t, double& tq, double& sh, int& parity) {
+// 1/d for d in [1, 2], accurate far below float32 rounding: the hardware's
+// approximate reciprocal refined by three Newton-Raphson steps
+// r <- r + r (1 - d r), each squaring the relative error (from any start
+// within 2^-8 of 1/d down to the float64 rounding level).
+__device__ __forceinline__ double recip_1_2(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
+// u(phi) = (-1)^k u(w) with w = phi - 2 pi k in [-pi, pi] (k the nearest
+// integer to phi / 2 pi): the rotation by w/2 as three shears needs tan(w/4)
+// (|.| <= 1) and sin(w/2); a missing term (-1) is the identity (all zero).
+// tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the half-angle identity; the
+// denominator lies in [1, 2] for |w/2| <= pi/2), so one float64 sincos gives
+// both. f32: the result is rounded to float32, so the quotient may use
+// recip_1_2 instead of an IEEE division.
+__device__ void shear_params(const PrepArgs& a, int32_t t, double& tq, double& sh, int& parity, bool f32) {
   const double phi = term_angle(a, t);
   const double two_pi = 6.283185307179586476925286766559;
-  const double k = rint(phi / two_pi);
+  const double k = rint(phi * (1.0 / two_pi));
   const double w = phi - two_pi * k;
   double c;
   sincos(0.5 * w, &sh, &c);
-  tq = sh / (1.0 + c);
+  tq = f32 ? sh * recip_1_2(1.0 + c) : sh / (1.0 + c);
   parity = ((long long)k) & 1;
 }
 
@@ -1299,7 +1314,7 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
   if (t < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
   double tq, sh;
   int parity;
-  shear_params(a, t, tq, sh, parity);
+  shear_params(a, t, tq, sh, parity, true);
   return make_float4((float)tq, (float)sh, __int_as_float(parity), 0.f);
 }
 
@@ -1307,27 +1322,25 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
 // act on register index j as e^{-i a_j} with a_j = sum_r sigma_r(j) phi_r / 2,
 // sigma_r(j) = +1 where bit r of j is clear, else -1 (RZ(phi) =
 // diag(e^{-i phi/2}, e^{i phi/2})), and its CZ links between register bits r
-// and r + 1 (bit r of bbits) as -1 where both bits of j are set. Returns
+// and r + 1 (bit r of bbits) as -1 where both bits of j are set. Writes
 // (cos, sin) of the applied phase (forward: -a_j) or of the un-applied one
-// (backward: +a_j), with those signs, for j0 and j0 + 1, each from one
-// float64 sincos of the summed angle.
-__device__ float4 diag_phases(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int j0, bool apply) {
+// (backward: +a_j), with those signs, for j = m and its complement 15 - m:
+// a_{15-m} = -a_m, so one float64 sincos of the summed angle gives both.
+__device__ void diag_phases(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
+                            float2* ph) {
   double phi[4];
   term_angles4(a, tz, phi);
-  double cs[4];
-  for (int h = 0; h < 2; ++h) {
-    const int j = j0 + h;
-    double al = 0.0;
-    for (int r = 0; r < 4; ++r) al += ((j >> r) & 1) ? -phi[r] : phi[r];
-    al *= apply ? -0.5 : 0.5;
-    sincos(al, &cs[2 * h + 1], &cs[2 * h]);
-    const int cz = __popc(bbits & (uint32_t)j & (uint32_t)(j >> 1)) & 1;
-    if (cz) {
-      cs[2 * h] = -cs[2 * h];
-      cs[2 * h + 1] = -cs[2 * h + 1];
-    }
-  }
-  return make_float4((float)cs[0], (float)cs[1], (float)cs[2], (float)cs[3]);
+  double al = 0.0;
+  for (int r = 0; r < 4; ++r) al += ((m >> r) & 1) ? -phi[r] : phi[r];
+  al *= apply ? -0.5 : 0.5;
+  double sn, cs;
+  sincos(al, &sn, &cs);
+  const int mc = 15 - m;
+  const bool f0 = __popc(bbits & (uint32_t)m & (uint32_t)(m >> 1)) & 1;
+  const bool f1 = __popc(bbits & (uint32_t)mc & (uint32_t)(mc >> 1)) & 1;
+  const float c = (float)cs, s = (float)sn;
+  ph[m] = f0 ? make_float2(-c, -s) : make_float2(c, s);
+  ph[mc] = f1 ? make_float2(-c, s) : make_float2(c, -s);
 }
 
 // The same in float64 (complex128 round programs).
@@ -1335,7 +1348,7 @@ __device__ Shear64 term_shear64(const PrepArgs& a, int32_t t) {
   Shear64 r{0.0, 0.0, 0, 0};
   if (t < 0) return r;
   int parity;
-  shear_params(a, t, r.t, r.s, parity);
+  shear_params(a, t, r.t, r.s, parity, false);
   r.wrap = parity;
   return r;
 }
@@ -1414,7 +1427,7 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (e < 4) {
     out[e] = term_shear_of(a, ty[e]);
   } else {
-    out[e] = diag_phases(a, tz, bbits, 2 * (e - 4), fwd);
+    diag_phases(a, tz, bbits, e - 4, fwd, reinterpret_cast<float2*>(out + 4));
   }
 }
 
@@ -1483,18 +1496,28 @@ __global__ void g_reduce_kernel(const GradReduceArgs a) {
 }
 
 // Loss and dL/dE in one block, fixed-order tree reduction (labels float32,
-// or float64 for complex128 plans).
+// or float64 for complex128 plans). With e_part: E_i is first summed from its
+// tps partials in tile order (as e_reduce_kernel does) and stored.
 template <class Y>
-__global__ void loss_kernel(int kind, const double* E, const Y* y, int64_t B, double* loss, double* dLdE) {
+__global__ void loss_kernel(int kind, double* E, const Y* y, int64_t B, double* loss, double* dLdE,
+                            const double* e_part, int tps) {
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+    double Ei;
+    if (e_part) {
+      Ei = 0.0;
+      for (int t = 0; t < tps; ++t) Ei += e_part[i * tps + t];
+      E[i] = Ei;
+    } else {
+      Ei = E[i];
+    }
     if (kind == 1) {
-      const double d = E[i] - (double)y[i];
+      const double d = Ei - (double)y[i];
       s += d * d;
       dLdE[i] = 2.0 * d / (double)B;
     } else {
-      s += E[i];
+      s += Ei;
       dLdE[i] = 1.0;
     }
   }
@@ -1888,14 +1911,33 @@ cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st) {
 
 cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
                         cudaStream_t st) {
-  loss_kernel<float><<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE);
+  loss_kernel<float><<<1, 256, 0, st>>>(kind, const_cast<double*>(E), y, B, loss, dLdE, nullptr, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_loss64(int kind, const double* E, const double* y, int64_t B, double* loss, double* dLdE,
                           cudaStream_t st) {
-  loss_kernel<double><<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE);
+  loss_kernel<double><<<1, 256, 0, st>>>(kind, const_cast<double*>(E), y, B, loss, dLdE, nullptr, 0);
   return cudaGetLastError();
+}
+
+bool e_loss_fusable(int64_t B, int tps) { return tps < 256 && B * tps <= 65536; }
+
+template <class Y>
+static cudaError_t launch_e_loss_t(const double* e_part, int tps, int kind, double* E, const Y* y, int64_t B,
+                                   double* loss, double* dLdE, cudaStream_t st) {
+  loss_kernel<Y><<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE, e_part, tps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_e_loss(const double* e_part, int tps, int kind, double* E, const float* y, int64_t B,
+                          double* loss, double* dLdE, cudaStream_t st) {
+  return launch_e_loss_t<float>(e_part, tps, kind, E, y, B, loss, dLdE, st);
+}
+
+cudaError_t launch_e_loss64(const double* e_part, int tps, int kind, double* E, const double* y, int64_t B,
+                            double* loss, double* dLdE, cudaStream_t st) {
+  return launch_e_loss_t<double>(e_part, tps, kind, E, y, B, loss, dLdE, st);
 }
 
 }  // namespace qf

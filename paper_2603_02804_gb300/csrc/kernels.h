@@ -132,6 +132,14 @@ cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, do
 // The same with float64 labels (complex128 plans).
 cudaError_t launch_loss64(int kind, const double* E, const double* y, int64_t B, double* loss, double* dLdE,
                           cudaStream_t st);
+// E from its per-tile partials and the loss in one single-block launch (the
+// same E, loss and dL/dE as launch_e_reduce then launch_loss), for batches
+// where e_loss_fusable(B, tps).
+bool e_loss_fusable(int64_t B, int tps);
+cudaError_t launch_e_loss(const double* e_part, int tps, int kind, double* E, const float* y, int64_t B,
+                          double* loss, double* dLdE, cudaStream_t st);
+cudaError_t launch_e_loss64(const double* e_part, int tps, int kind, double* E, const double* y, int64_t B,
+                            double* loss, double* dLdE, cudaStream_t st);
 
 // Opt a kernel in to `smem` bytes of dynamic shared memory on the current
 // device, once per device (idempotent; two threads racing on a first launch
