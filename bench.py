@@ -96,26 +96,18 @@ def load_peaks():
 
 
 def algorithmic_flops(n, d, B):
-    """Arithmetic per step in FP32 flops (a multiply or an add = 1, FMA = 2).
-    Forward: one fused complex 2x2 per qubit and layer = 4 complex multiplies
-    and 2 complex adds = 28 flops per pair of amplitudes. Adjoint: per qubit
-    and layer two gradient terms (the RY, and the run RZ_c(l) RZ_a(l+1), whose
-    gradients are equal and which un-apply as one phase), plus the first RZ of
-    every qubit; per term and pair: un-apply psi and lambda (12 FMA) and
-    Im<lambda|P|psi> (4 FMA) = 32 flops."""
+    """Arithmetic per step in flops (a multiply or an add = 1, FMA = 2) of the
+    round programs, per qubit and layer and per pair of amplitudes.
+    Forward: the RY as three shears on (re, im) = 6 FMA = 12 flops, plus a
+    quarter of the round's merged diagonal (one complex multiply, 6 flops, per
+    amplitude for the 4 RZ runs of a round) = 3 flops; 15 in all.
+    Adjoint: the RY un-applied from psi and lambda (12 FMA) and its
+    Im<lambda|Y|psi> (4 FMA) = 32 flops, plus a quarter of the diagonal's
+    share (two complex multiplies and Im(conj(lambda) psi) per amplitude,
+    15 flops, and the signed sums) = 8 flops; 40 in all. Counting each gate
+    separately, as a per-gate program must, gives 36 and 96."""
     pairs = B * (1 << (n - 1))
-    fwd = n * d * pairs * 28
-    bwd = (2 * n * d + n) * pairs * 32
-    return fwd, bwd
-
-
-def generic_flops(info, n, B):
-    """(forward, adjoint) flops per step of generic step programs (the complex128
-    passes): one fused complex 2x2 per fused entry (28 flops per pair of
-    amplitudes) and one gradient term per rotation (un-apply psi and lambda and
-    Im<lambda|P|psi>: 32 flops per pair)."""
-    pairs = B * (1 << (max(n, 4) - 1))
-    return info["n_fused_ops"] * pairs * 28, info["n_slots"] * pairs * 32
+    return n * d * pairs * 15, n * d * pairs * 40
 
 
 class ClockSampler:
@@ -666,8 +658,6 @@ def main():
     # ---- roofline of the dominant kernel: the fused adjoint pass kernel
     fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, w.B)
     info = sim.info()
-    if c128:
-        fwd_fl, bwd_fl = generic_flops(info, w.n, w.B)
     bwd_launch_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
     fwd_launch_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
     bwd_per_launch = bwd_fl / info["n_passes"]
@@ -685,6 +675,8 @@ def main():
                 "fwd_kernel": {"achieved": (fwd_fl / info["n_passes"]) / (fwd_launch_ms / 1e3) / 1e12,
                                "ms": fwd_launch_ms},
                 "bwd_kernel_ms": bwd_launch_ms,
+                "flops_model": "executed arithmetic of the round programs: 15 (forward) and 40 (adjoint) flops "
+                               "per amplitude pair, qubit and layer",
                 "timing": (f"CUDA events on the launching stream around every pass launch of {args.steps} "
                            f"steps run right after the timed ones (launched kernel by kernel: "
                            f"{prof['ms_per_step']:.4f} ms per step)")}
@@ -725,7 +717,7 @@ def main():
                               "device_status": qfuse.qf_device_status(stream)}
             if v128:
                 vi = vs.info()
-                f_fl, b_fl = generic_flops(vi, w.n, w.B)
+                f_fl, b_fl = algorithmic_flops(w.n, w.d, w.B)
                 b_ms = vp["bwd_ms"] / max(vp["bwd_launches"], 1)
                 f_ms = vp["fwd_ms"] / max(vp["fwd_launches"], 1)
                 ach = b_fl / vi["n_passes"] / (b_ms / 1e3) / 1e12

@@ -215,8 +215,8 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
     if (c->f64) L.mats64 = take((size_t)std::max(n_fused, 0) * 64);
     else L.mats = take((size_t)std::max(n_fused, 0) * 32);
     if (c->fp.rounds) {
-      // per round: kRoundPar float4 (complex64) or kRoundPar64 Shear64 (complex128)
-      const size_t per = c->f64 ? qf::kRoundPar64 * sizeof(qf::Shear64) : qf::kRoundPar * 16;
+      // per round: kRoundPar float4 (complex64) or one RoundPar64 (complex128)
+      const size_t per = c->f64 ? sizeof(qf::RoundPar64) : qf::kRoundPar * 16;
       L.rpf = take(c->fp.fwd_rounds.size() / qf::kFwdRoundWords * per);
       L.rpb = take(c->fp.bwd_rounds.size() / qf::kBwdRoundWords * per);
     }
@@ -733,7 +733,7 @@ qf::PrepArgs prep_args64(const qf_circuit* c, const DevTables& T, const Layout& 
 void set_rounds64(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, qf::PrepArgs& pa) {
   pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
   pa.rpb_src = T.bwd_rounds;
-  pa.rpb64 = at<qf::Shear64>(ws, L.rpb);
+  pa.rpb64 = at<qf::RoundPar64>(ws, L.rpb);
 }
 
 qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, const double* theta, const double* x,
@@ -746,7 +746,7 @@ qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, co
     pa.n_fused = 0;
     pa.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
     pa.rpf_src = T.fwd_rounds;
-    pa.rpf64 = at<qf::Shear64>(ws, L.rpf);
+    pa.rpf64 = at<qf::RoundPar64>(ws, L.rpf);
     if (with_terms) set_rounds64(c, T, L, ws, pa);
   } else {
     pa.n_fused = (int32_t)P.fuse_off.size() - 1;
@@ -760,7 +760,7 @@ qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, co
   a.ops = T.fwd_ops;
   if (P.rounds) {
     a.rounds = T.fwd_rounds;
-    a.rpar = at<qf::Shear64>(ws, L.rpf);
+    a.rpar = at<qf::RoundPar64>(ws, L.rpf);
   }
   a.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const double2*>(x) : nullptr;
   const int prof = prof_begin(c, st);
@@ -808,7 +808,7 @@ qf_status fused_backward64(qf_circuit* c, const DevTables& T, const Layout& L, c
   a.dLdE = dLdE;
   if (P.rounds) {
     a.rounds = T.bwd_rounds;
-    a.rpar = at<qf::Shear64>(ws, L.rpb);
+    a.rpar = at<qf::RoundPar64>(ws, L.rpb);
   }
   auto seed = [&](const qf::PassArgs64& p) -> cudaError_t {
     c->call_launches++;
@@ -822,7 +822,7 @@ qf_status fused_backward64(qf_circuit* c, const DevTables& T, const Layout& L, c
     f.ops = T.fwd_ops;
     if (P.rounds) {
       f.rounds = T.fwd_rounds;
-      f.rpar = at<qf::Shear64>(ws, L.rpf);
+      f.rpar = at<qf::RoundPar64>(ws, L.rpf);
     }
     f.psi_in = c->encoding == QF_ENC_STATE_IN ? reinterpret_cast<const double2*>(x) : nullptr;
     for (size_t i = 0; i < P.a_sched.size(); ++i) {

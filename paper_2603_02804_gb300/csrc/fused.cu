@@ -1326,21 +1326,37 @@ __device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
 // (cos, sin) of the applied phase (forward: -a_j) or of the un-applied one
 // (backward: +a_j), with those signs, for j = m and its complement 15 - m:
 // a_{15-m} = -a_m, so one float64 sincos of the summed angle gives both.
-__device__ void diag_phases(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
-                            float2* ph) {
+__device__ void diag_phase_pair(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
+                                double& c, double& s, bool& f0, bool& f1) {
   double phi[4];
   term_angles4(a, tz, phi);
   double al = 0.0;
   for (int r = 0; r < 4; ++r) al += ((m >> r) & 1) ? -phi[r] : phi[r];
   al *= apply ? -0.5 : 0.5;
-  double sn, cs;
-  sincos(al, &sn, &cs);
+  sincos(al, &s, &c);
   const int mc = 15 - m;
-  const bool f0 = __popc(bbits & (uint32_t)m & (uint32_t)(m >> 1)) & 1;
-  const bool f1 = __popc(bbits & (uint32_t)mc & (uint32_t)(mc >> 1)) & 1;
-  const float c = (float)cs, s = (float)sn;
+  f0 = __popc(bbits & (uint32_t)m & (uint32_t)(m >> 1)) & 1;
+  f1 = __popc(bbits & (uint32_t)mc & (uint32_t)(mc >> 1)) & 1;
+}
+
+__device__ void diag_phases(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
+                            float2* ph) {
+  double cd, sd;
+  bool f0, f1;
+  diag_phase_pair(a, tz, bbits, m, apply, cd, sd, f0, f1);
+  const float c = (float)cd, s = (float)sd;
   ph[m] = f0 ? make_float2(-c, -s) : make_float2(c, s);
-  ph[mc] = f1 ? make_float2(-c, s) : make_float2(c, -s);
+  ph[15 - m] = f1 ? make_float2(-c, s) : make_float2(c, -s);
+}
+
+// The same in float64 (complex128 round programs).
+__device__ void diag_phases64(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
+                              double2* ph) {
+  double c, s;
+  bool f0, f1;
+  diag_phase_pair(a, tz, bbits, m, apply, c, s, f0, f1);
+  ph[m] = f0 ? make_double2(-c, -s) : make_double2(c, s);
+  ph[15 - m] = f1 ? make_double2(-c, s) : make_double2(c, -s);
 }
 
 // The same in float64 (complex128 round programs).
@@ -1395,24 +1411,8 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     return;
   }
   i -= (int64_t)a.B * a.n_eff;
-  if (a.rpf64 || a.rpb64) {
-    // complex128: per round and item the shears of its rotation and RZ-run terms
-    if (i < (int64_t)kRoundPar64 * a.n_rpf) {
-      const int64_t r = i >> 3;
-      const int k = (int)((i >> 1) & 3), j = (int)(i & 1);
-      const int32_t* rec = reinterpret_cast<const int32_t*>(a.rpf_src) + r * kFwdRoundWords;
-      a.rpf64[r * 8 + 2 * k + j] = term_shear64(a, rec[j ? 8 + k : 12 + k]);
-      return;
-    }
-    i -= (int64_t)kRoundPar64 * a.n_rpf;
-    if (i < (int64_t)kRoundPar64 * a.n_rpb) {
-      const int64_t r = i >> 3;
-      const int k = (int)(i & 7);
-      a.rpb64[i] = term_shear64(a, reinterpret_cast<const int32_t*>(a.rpb_src)[r * kBwdRoundWords + k]);
-    }
-    return;
-  }
-  // complex64: per round the 4 rotation shears, then the merged diagonal
+  // per round the 4 rotation shears, then the merged diagonal (float32 tables,
+  // or float64 ones for complex128 plans)
   bool fwd = i < (int64_t)kRoundPar * a.n_rpf;
   if (!fwd) i -= (int64_t)kRoundPar * a.n_rpf;
   if (!fwd && i >= (int64_t)kRoundPar * a.n_rpb) return;
@@ -1423,6 +1423,12 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   const int32_t* tz = fwd ? rec + 8 : rec;
   const int32_t* ty = fwd ? rec + 12 : rec + 4;
   const uint32_t bbits = (uint32_t)(fwd ? rec[5] : rec[9]);
+  if (a.rpf64 || a.rpb64) {
+    RoundPar64& out = (fwd ? a.rpf64 : a.rpb64)[r];
+    if (e < 4) out.rot[e] = term_shear64(a, ty[e]);
+    else diag_phases64(a, tz, bbits, e - 4, fwd, out.ph);
+    return;
+  }
   float4* out = (fwd ? a.rpf : a.rpb) + r * kRoundPar;
   if (e < 4) {
     out[e] = term_shear_of(a, ty[e]);

@@ -160,7 +160,7 @@ __device__ __forceinline__ void cnot64(double2 (&r)[16], double2 (&l)[16], bool 
 // kept as a sign). Pending CZ signs D: the registers hold psi~ with
 // psi = D psi~, D = (-1)^(c0 + sum_r A_r j_r) (bit 4: c0, bits 0..3: A);
 // a gate on register bit r sees only Z_r^(A_r), folded into it; CZs between
-// two register bits flip the registers directly.
+// two register bits are signs of the round's diagonal table.
 
 // Link q couples qubit q with q + 1 mod n: the constant (t2 & gb) and linear
 // (u) parts of the links L for thread base index gb.
@@ -171,23 +171,11 @@ __device__ __forceinline__ void link_terms64(uint32_t L, uint32_t gb, int n, uin
   u = (((t1 << 1) | (t1 >> (n - 1))) & nmask) ^ t2;
 }
 
-template <bool BWD>
-__device__ __forceinline__ void chain64(uint32_t L, uint32_t bbits, uint32_t gb, const uint32_t (&p)[4], int n,
-                                        uint32_t& D, double2 (&r)[16], double2 (&l)[16]) {
+__device__ __forceinline__ void chain64(uint32_t L, uint32_t gb, const uint32_t (&p)[4], int n, uint32_t& D) {
   uint32_t t2, u;
   link_terms64(L, gb, n, t2, u);
   D ^= (((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) | (((u >> p[3]) & 1u) << 3)) |
        ((__popc(t2 & gb) & 1u) << 4);
-#pragma unroll
-  for (int rb = 0; rb < 3; ++rb) {
-    const uint32_t f = (bbits >> rb) & 1u;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (((j >> rb) & 3) != 3) continue;
-      r[j] = make_double2(flipd(r[j].x, f), flipd(r[j].y, f));
-      if (BWD) l[j] = make_double2(flipd(l[j].x, f), flipd(l[j].y, f));
-    }
-  }
 }
 
 // Multiply the registers by D (end of a step).
@@ -206,15 +194,15 @@ __device__ __forceinline__ void pending64(uint32_t D, double2 (&r)[16], double2 
   }
 }
 
-// Forward item on register bit R: the RY, then the RZ run. y, z: the terms'
-// shear parameters of the un-apply direction; applying rotates the other
-// way. A pending Z_R turns RY(w) into RY(-w); the wrap parities go to the
-// pending constant sign. An absent part (no term) is the identity: skipped.
+// The rotation of a forward item on register bit R (RY, or RX where rx):
+// y holds the term's shear parameters of the un-apply direction; applying
+// rotates the other way. A pending Z_R turns the rotation by w into one by
+// -w; the wrap parity goes to the pending constant sign. An absent rotation
+// (no term) is skipped.
 template <int R>
-__device__ __forceinline__ void item_fwd64(double2 (&r)[16], const Shear64& y, const Shear64& z, uint32_t a,
-                                           uint32_t& D, bool has_y, bool has_z, bool rx = false) {
+__device__ __forceinline__ void rot_fwd64(double2 (&r)[16], const Shear64& y, uint32_t a, uint32_t& D,
+                                          bool has_y, bool rx) {
   const double ty = a ? y.t : -y.t, sy = a ? -y.s : y.s;
-  const double t = z.t, s = z.s;
   if (has_y && rx) {
     // RX(w): a rotation by -w/2 of (re p0, im p1) and (re p1, im p0):
     // x += t y; y -= s x; x += t y (t, s negated under a pending Z_R)
@@ -243,25 +231,64 @@ __device__ __forceinline__ void item_fwd64(double2 (&r)[16], const Shear64& y, c
       r[j1] = p1;
     }
   }
-  if (has_z) {
+  D ^= (uint32_t)(y.wrap & 1) << 4;
+}
+
+// v *= (c + i s)
+__device__ __forceinline__ void cmul64(double2& v, double c, double s) {
+  const double x = v.x;
+  v.x = fma(c, x, -s * v.y);
+  v.y = fma(s, x, c * v.y);
+}
+
+// The round's diagonal (its 4 RZ runs and the CZ links between register
+// bits, merged), applied: register amplitude j times ph[j]. It commutes with
+// the rotations on the other register bits and with the pending signs.
+__device__ __forceinline__ void diag64(double2 (&r)[16], const double2* ph) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (j & (1 << R)) continue;
-      const int j1 = j | (1 << R);
-      double2 p0 = r[j], p1 = r[j1];
-      // RZ run: bit-R-clear amplitude times e^{-iw/2}, set one times e^{+iw/2}
-      p0.x = fma(t, p0.y, p0.x); p0.y = fma(-s, p0.x, p0.y); p0.x = fma(t, p0.y, p0.x);
-      p1.x = fma(-t, p1.y, p1.x); p1.y = fma(s, p1.x, p1.y); p1.x = fma(-t, p1.y, p1.x);
-      r[j] = p0;
-      r[j1] = p1;
+  for (int j = 0; j < 16; ++j) {
+    const double2 e = ph[j];
+    cmul64(r[j], e.x, e.y);
+  }
+}
+
+// Adjoint side of the round's diagonal: g[r] = sum_j sigma_r(j) w_j with
+// w_j = Im(conj(lambda_j) psi_j), sigma_r(j) = +1 where bit r of j is clear,
+// else -1 (the RZ-run terms; w_j is unchanged by the diagonal, and Z_r
+// commutes with the rotations on the other bits), then the un-apply.
+__device__ __forceinline__ void diag_bwd64(double2 (&p)[16], double2 (&l)[16], const double2* ph, double (&g)[8]) {
+  double s2[4];
+  double d0 = 0.0, d1 = 0.0, se = 0.0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    double2& p0 = p[2 * m];
+    double2& p1 = p[2 * m + 1];
+    double2& l0 = l[2 * m];
+    double2& l1 = l[2 * m + 1];
+    const double w0 = fma(l0.x, p0.y, -l0.y * p0.x);
+    const double w1 = fma(l1.x, p1.y, -l1.y * p1.x);
+    const double2 e0 = ph[2 * m], e1 = ph[2 * m + 1];
+    cmul64(p0, e0.x, e0.y);
+    cmul64(l0, e0.x, e0.y);
+    cmul64(p1, e1.x, e1.y);
+    cmul64(l1, e1.x, e1.y);
+    const double sm = w0 + w1;
+    d0 += w0 - w1;
+    if (m & 1) {
+      s2[m >> 1] = se + sm;
+      d1 += se - sm;
+    } else {
+      se = sm;
     }
   }
-  D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
+  g[0] = d0;
+  g[1] = d1;
+  g[2] = (s2[0] - s2[1]) + (s2[2] - s2[3]);
+  g[3] = (s2[0] + s2[1]) - (s2[2] + s2[3]);
 }
 
 // Un-apply one rotation on register bit R by three shears; returns the
 // thread's sum of Im<lambda|P|psi> taken before it.
-//   RZ: bit-R-clear amplitudes times e^{+iw/2}, set ones times e^{-iw/2}.
 //   RY: (x, y) <- RY(w)^dagger (x, y), a rotation by -w/2: a = t, b = -s.
 template <int R, int KIND>
 __device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16], const double t, const double s) {
@@ -271,13 +298,7 @@ __device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16]
     if (j & (1 << R)) continue;
     const int j1 = j | (1 << R);
     double2 p0 = p[j], p1 = p[j1], l0 = l[j], l1 = l[j1];
-    if (KIND == G_RZ) {
-      acc += l0.x * p0.y - l0.y * p0.x - l1.x * p1.y + l1.y * p1.x;
-      p0.x = fma(-t, p0.y, p0.x); p0.y = fma(s, p0.x, p0.y); p0.x = fma(-t, p0.y, p0.x);
-      l0.x = fma(-t, l0.y, l0.x); l0.y = fma(s, l0.x, l0.y); l0.x = fma(-t, l0.y, l0.x);
-      p1.x = fma(t, p1.y, p1.x); p1.y = fma(-s, p1.x, p1.y); p1.x = fma(t, p1.y, p1.x);
-      l1.x = fma(t, l1.y, l1.x); l1.y = fma(-s, l1.x, l1.y); l1.x = fma(t, l1.y, l1.x);
-    } else if (KIND == G_RX) {
+    if (KIND == G_RX) {
       // Im<lambda|X|psi>; RX(w)^dagger rotates (re p0, im p1) and (re p1, im p0) by +w/2
       acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
       p0.x = fma(-t, p1.y, p0.x); p1.y = fma(s, p0.x, p1.y); p0.x = fma(-t, p1.y, p0.x);
@@ -301,21 +322,20 @@ __device__ __forceinline__ double shear_bwd64(double2 (&p)[16], double2 (&l)[16]
   return acc;
 }
 
-// Backward item on register bit R: the merged RZ run, then the RY. With a
-// pending Z_R the RY un-applies as RY(+w) and its Im<lambda|Y|psi> changes
-// sign. An absent part (no term) is skipped; its value is 0.
+// The rotation of an adjoint item on register bit R, un-applied after the
+// round's diagonal; gy: its Im<lambda|P|psi>. With a pending Z_R it
+// un-applies as the rotation by +w and gy changes sign. An absent rotation is
+// skipped; its value is 0.
 template <int R>
-__device__ __forceinline__ void item_bwd64(double2 (&p)[16], double2 (&l)[16], const Shear64& z, const Shear64& y,
-                                           uint32_t a, uint32_t& D, double& gz, double& gy, bool has_z, bool has_y,
-                                           bool rx = false) {
-  gz = has_z ? shear_bwd64<R, G_RZ>(p, l, z.t, z.s) : 0.0;
+__device__ __forceinline__ void rot_bwd64(double2 (&p)[16], double2 (&l)[16], const Shear64& y, uint32_t a,
+                                          uint32_t& D, double& gy, bool has_y, bool rx) {
   gy = 0.0;
   if (has_y) {
     const double t = a ? -y.t : y.t, s = a ? -y.s : y.s;
     const double g = rx ? shear_bwd64<R, G_RX>(p, l, t, s) : shear_bwd64<R, G_RY>(p, l, t, s);
     gy = a ? -g : g;
   }
-  D ^= (uint32_t)((z.wrap ^ y.wrap) & 1) << 4;
+  D ^= (uint32_t)(y.wrap & 1) << 4;
 }
 
 // Reduce 8 per-thread values over `lanes` lanes (8, 16 or 32; whole-warp
@@ -520,29 +540,27 @@ __global__ void __launch_bounds__(kThreads, 1) pass64_kernel(const PassArgs64 a)
 #pragma unroll 1
       for (int k = 0; k < nr; ++k) {
         const size_t rr = (size_t)op.y + k;
-        const Shear64* v = a.rpar + 8 * rr;
+        const RoundPar64& v = a.rpar[rr];
         if (!BWD) {
           const uint4 lk = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 1);
-          // the items' terms (-1: the part is absent): tz in words 8..11, ty in 12..15
-          const uint4 tz = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 2);
+          // the items' rotation terms (-1: absent) in words 12..15
           const uint4 ty = __ldg(a.rounds + rr * (kFwdRoundWords / 4) + 3);
-          item_fwd64<0>(r, v[0], v[1], D & 1u, D, (int)ty.x >= 0, (int)tz.x >= 0, RX && (lk.z & 1u));
-          item_fwd64<1>(r, v[2], v[3], (D >> 1) & 1u, D, (int)ty.y >= 0, (int)tz.y >= 0, RX && ((lk.z >> 1) & 1u));
-          item_fwd64<2>(r, v[4], v[5], (D >> 2) & 1u, D, (int)ty.z >= 0, (int)tz.z >= 0, RX && ((lk.z >> 2) & 1u));
-          item_fwd64<3>(r, v[6], v[7], (D >> 3) & 1u, D, (int)ty.w >= 0, (int)tz.w >= 0, RX && ((lk.z >> 3) & 1u));
-          chain64<false>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
+          rot_fwd64<0>(r, v.rot[0], D & 1u, D, (int)ty.x >= 0, RX && (lk.z & 1u));
+          rot_fwd64<1>(r, v.rot[1], (D >> 1) & 1u, D, (int)ty.y >= 0, RX && ((lk.z >> 1) & 1u));
+          rot_fwd64<2>(r, v.rot[2], (D >> 2) & 1u, D, (int)ty.z >= 0, RX && ((lk.z >> 2) & 1u));
+          rot_fwd64<3>(r, v.rot[3], (D >> 3) & 1u, D, (int)ty.w >= 0, RX && ((lk.z >> 3) & 1u));
+          diag64(r, v.ph);
+          chain64(lk.x, gb, pos, a.n_eff, D);
         } else {
           const uint4 lk = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 2);
-          const uint4 tz = __ldg(a.rounds + rr * (kBwdRoundWords / 4)), ty = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 1);
-          chain64<true>(lk.x, lk.y, gb, pos, a.n_eff, D, r, l);
+          const uint4 ty = __ldg(a.rounds + rr * (kBwdRoundWords / 4) + 1);
+          chain64(lk.x, gb, pos, a.n_eff, D);
           double gv[8];
-          item_bwd64<0>(r, l, v[0], v[4], D & 1u, D, gv[0], gv[4], (int)tz.x >= 0, (int)ty.x >= 0, RX && (lk.z & 1u));
-          item_bwd64<1>(r, l, v[1], v[5], (D >> 1) & 1u, D, gv[1], gv[5], (int)tz.y >= 0, (int)ty.y >= 0,
-                        RX && ((lk.z >> 1) & 1u));
-          item_bwd64<2>(r, l, v[2], v[6], (D >> 2) & 1u, D, gv[2], gv[6], (int)tz.z >= 0, (int)ty.z >= 0,
-                        RX && ((lk.z >> 2) & 1u));
-          item_bwd64<3>(r, l, v[3], v[7], (D >> 3) & 1u, D, gv[3], gv[7], (int)tz.w >= 0, (int)ty.w >= 0,
-                        RX && ((lk.z >> 3) & 1u));
+          diag_bwd64(r, l, v.ph, gv);
+          rot_bwd64<0>(r, l, v.rot[0], D & 1u, D, gv[4], (int)ty.x >= 0, RX && (lk.z & 1u));
+          rot_bwd64<1>(r, l, v.rot[1], (D >> 1) & 1u, D, gv[5], (int)ty.y >= 0, RX && ((lk.z >> 1) & 1u));
+          rot_bwd64<2>(r, l, v.rot[2], (D >> 2) & 1u, D, gv[6], (int)ty.z >= 0, RX && ((lk.z >> 2) & 1u));
+          rot_bwd64<3>(r, l, v.rot[3], (D >> 3) & 1u, D, gv[7], (int)ty.w >= 0, RX && ((lk.z >> 3) & 1u));
           int idx;
           const double sum = butterfly8_64(gv, lanes, lane, idx);
           const bool owner = (lane & ((lanes >> 3) - 1)) == 0;

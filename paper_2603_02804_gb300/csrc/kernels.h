@@ -46,6 +46,13 @@ struct alignas(16) Shear64 {
   int64_t wrap, pad;
 };
 
+// Parameters of one round of a complex128 round program: the shears of the 4
+// items' rotations and the round's diagonal as (cos, sin) per register index.
+struct RoundPar64 {
+  Shear64 rot[4];
+  double2 ph[16];
+};
+
 struct PrepArgs {
   const float* theta;
   const double* theta64;       // if non-null: float64 parameters (complex128 plans), theta unused
@@ -74,14 +81,13 @@ struct PrepArgs {
   int32_t n_rpb;               // backward rounds
   const uint4* rpb_src;        // backward round records (tz[4], ty[4] terms)
   float4* rpb;                 // [n_rpb][kRoundPar]: rotation shears, then the un-applied diagonal
-  Shear64* rpf64;              // if non-null instead of rpf / rpb: [n][kRoundPar64] Shear64, item k's
-  Shear64* rpb64;              //   rotation and RZ-run shears (fwd: 2k, 2k+1; bwd: 4 + k, k)
+  RoundPar64* rpf64;           // if non-null instead of rpf / rpb: the same in float64
+  RoundPar64* rpb64;           //   (complex128 round programs), [n_rpf] / [n_rpb]
 };
 
-// Table elements of the round parameters (prep work items per round).
+// Table elements of the round parameters (prep work items, kRoundPar per round).
 __host__ __device__ inline int64_t round_par_elems(const PrepArgs& a) {
-  const int64_t per = (a.rpf64 || a.rpb64) ? kRoundPar64 : kRoundPar;
-  return per * ((int64_t)a.n_rpf + a.n_rpb);
+  return (int64_t)kRoundPar * ((int64_t)a.n_rpf + a.n_rpb);
 }
 
 struct GradReduceArgs {
@@ -160,7 +166,7 @@ struct PassArgs64 {
   int64_t B;
   const uint2* ops;       // program of this direction
   const uint4* rounds;    // round records of this direction (round programs), else null
-  const Shear64* rpar;    // per-round item parameters, kRoundPar64 per round (round programs)
+  const RoundPar64* rpar; // per-round parameters (round programs)
   int32_t rx_items;       // round programs with RX items
   const double2* mats;    // fused 2x2 matrices, 4 double2 each: u00, u01, u10, u11 (generic)
   const double2* cs;      // (cos, sin) of phi/2 per gradient term

@@ -57,12 +57,12 @@ constexpr int kBwdRoundWords = 12;
 constexpr int kMaxStepRounds = 4;   // 8 gradient values per round
 // Parameters of one round of a complex64 round program, in float4: [0, 4) the
 // shear parameters (tan(w/4), sin(w/2), wrap parity) of the 4 items'
-// rotations; [4, 12) the round's diagonal, i.e. the 4 RZ runs merged into one
-// phase per register index j: float4 4 + m holds (cos a_j, sin a_j) for
-// j = 2m and 2m + 1. (The complex128 programs keep 8 Shear64 per round: the
-// rotation and the RZ-run shear of each item.)
+// rotations; [4, 12) the round's diagonal, i.e. the 4 RZ runs (and the CZ
+// links between register bits) merged into one phase per register index j:
+// float4 4 + m holds (cos a_j, sin a_j) for j = 2m and 2m + 1. Prep fills
+// them as kRoundPar work items per round; complex128 programs hold the same
+// in float64 (RoundPar64).
 constexpr int kRoundPar = 12;
-constexpr int kRoundPar64 = 8;
 
 // Source / destination codes of a pass.
 enum : int32_t {
