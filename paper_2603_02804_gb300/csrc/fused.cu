@@ -919,7 +919,9 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       sb ^= 1;
       if (BWD && Tt >= 32 && a.g_accum) {
         // every tile of this call belongs to one sample: one thread per term sums
-        // the tiles in order and adds to the sample's row (stored by its tile 0)
+        // the tiles in order and adds to the sample's row (stored by its tile 0);
+        // within a tile the warp sums add in float32, as the warp shuffles do,
+        // then float64 across tiles
         const int nk = nr * 8;
         const int64_t b2 = first_tile >> a.tps_log2;
         const bool first = (first_tile & ((1ll << a.tps_log2) - 1)) == 0;
@@ -928,22 +930,26 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
           if (term < 0) continue;
           double sum = 0.0;
           for (int tc = 0; tc < tiles_per_cta; ++tc)
-            if (first_tile + tc < total_tiles)
-              for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
+            if (first_tile + tc < total_tiles) {
+              float sf = 0.f;
+              for (int w = 0; w < wpt; ++w) sf += s_red[buf][tc * wpt + w][kk];
+              sum += (double)sf;
+            }
           double* dst = a.g_part + b2 * a.n_slots + term;
           *dst = first ? 0.5 * sum : *dst + 0.5 * sum;
         }
         buf ^= 1;
       } else if (BWD && Tt >= 32) {
+        // the tile's warp sums in float32 (one float64 value per tile and term)
         const int nk = nr * 8;
         for (int e = kThreads - 1 - tid; e < tiles_per_cta * nk; e += kThreads) {  // from the last warp
           const int tc = e / nk, kk = e - tc * nk;
           const int64_t t2 = first_tile + tc;
           const int32_t term = s_slot[buf][kk];
           if (t2 < total_tiles && term >= 0) {
-            double sum = 0.0;
-            for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
-            a.g_part[t2 * a.n_slots + term] = 0.5 * sum;
+            float sf = 0.f;
+            for (int w = 0; w < wpt; ++w) sf += s_red[buf][tc * wpt + w][kk];
+            a.g_part[t2 * a.n_slots + term] = (double)(0.5f * sf);
           }
         }
         buf ^= 1;
@@ -1026,13 +1032,13 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       }
       __syncthreads();
       if (BWD && Tt >= 32) {
-        for (int e = tid; e < tiles_per_cta * nk; e += kThreads) {
+        for (int e = kThreads - 1 - tid; e < tiles_per_cta * nk; e += kThreads) {  // from the last warp
           const int tc = e / nk, kk = e - tc * nk;
           const int64_t t2 = first_tile + tc;
           if (t2 < total_tiles) {
-            double sum = 0.0;
-            for (int w = 0; w < wpt; ++w) sum += (double)s_red[buf][tc * wpt + w][kk];
-            a.g_part[t2 * a.n_slots + s_slot[buf][kk]] = 0.5 * sum;
+            float sf = 0.f;
+            for (int w = 0; w < wpt; ++w) sf += s_red[buf][tc * wpt + w][kk];
+            a.g_part[t2 * a.n_slots + s_slot[buf][kk]] = (double)(0.5f * sf);
           }
         }
         buf ^= 1;
