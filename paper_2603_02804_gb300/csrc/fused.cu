@@ -632,6 +632,7 @@ __device__ __forceinline__ void tc_rounds(const TcCtx& tc, const StepPar& P, int
 struct PassShared {
   StepPar par[2];
   uint32_t lg[256];
+  uint32_t base[4][kThreads];  // per register group: the thread's tile index with the group's bits zero
   float red[2][kThreads / 32][kMaxStepSlots];
   int32_t slot[2][kMaxStepSlots];
   double dred[kThreads / 32];
@@ -685,6 +686,12 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
     for (int j = 0; j < tl2; ++j)
       if ((h >> j) & 1) g |= 1u << s_gmap[kRegBits + j];
     s_lg[h] = g;
+  }
+  // each thread's base index per register group, once per pass (read back by
+  // the same thread at every step of that group)
+  for (int g = 0; g < 4; ++g) {
+    const uint32_t gm = (1u << s_grp[g][0]) | (1u << s_grp[g][1]) | (1u << s_grp[g][2]) | (1u << s_grp[g][3]);
+    sh.base[g][tid] = pdep32(tau, ((1u << K) - 1u) & ~gm);
   }
   __syncthreads();
 
@@ -851,8 +858,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       }
       const StepPar& P = sh.par[sb];
       const uint32_t lb0 = s_grp[g][0], lb1 = s_grp[g][1], lb2 = s_grp[g][2], lb3 = s_grp[g][3];
-      const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
-      const uint32_t base = pdep32(tau, ((1u << K) - 1u) & ~gm);
+      const uint32_t base = sh.base[g][tid];
       const uint32_t pb = swz(base);
       const uint32_t so[4] = {swz(1u << lb0), swz(1u << lb1), swz(1u << lb2), swz(1u << lb3)};
       const uint32_t gb = gidx(base);
@@ -959,8 +965,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       const int nops = (op.x >> 8) & 0xffff;
       const int nk = (int)op.y;
       const uint32_t lb0 = s_grp[g][0], lb1 = s_grp[g][1], lb2 = s_grp[g][2], lb3 = s_grp[g][3];
-      const uint32_t gm = (1u << lb0) | (1u << lb1) | (1u << lb2) | (1u << lb3);
-      const uint32_t base = pdep32(tau, ((1u << K) - 1u) & ~gm);
+      const uint32_t base = sh.base[g][tid];
       const uint32_t pb = swz(base);
       const uint32_t so[4] = {swz(1u << lb0), swz(1u << lb1), swz(1u << lb2), swz(1u << lb3)};
       const uint32_t gb = gidx(base);
