@@ -1119,9 +1119,11 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
 }
 
 // RX: round programs holding RX items (their own instance, so that programs
-// of RZ / RY items keep the plain code).
-template <bool BWD, bool ROUNDS, bool RX = false>
-__global__ void __launch_bounds__(kThreads, 2) pass_kernel(const PassArgs a) {
+// of RZ / RY items keep the plain code). MINB: CTAs per SM the registers are
+// budgeted for; a forward pass (one 32 KiB state per CTA) of more tiles than
+// two CTAs per SM hold runs with three per SM.
+template <bool BWD, bool ROUNDS, bool RX = false, int MINB = 2>
+__global__ void __launch_bounds__(kThreads, MINB) pass_kernel(const PassArgs a) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ PassShared sh;
   pass_cta<BWD, ROUNDS, 8, false, RX>(a, (int64_t)blockIdx.x * (kThreads >> (a.pd.K - kRegBits)), smem, sh);
@@ -1766,7 +1768,21 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
     else if (rounds) pass_kernel<true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else pass_kernel<true, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   } else {
-    if (rx) pass_kernel<false, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    // more tiles than two CTAs per SM hold: the three-CTA round instances
+    // (fewer registers, more warps to hide latency across the waves)
+    static int n_sm = 0;
+    if (n_sm == 0) {
+      int dev = 0, v = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                   cudaSuccess)
+        n_sm = v;
+      else
+        return cudaGetLastError();
+    }
+    const bool three = rounds && grid > 2ll * n_sm;
+    if (rx && three) pass_kernel<false, true, true, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    else if (rx) pass_kernel<false, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
+    else if (three) pass_kernel<false, true, false, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else if (rounds) pass_kernel<false, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else pass_kernel<false, false><<<(unsigned)grid, kThreads, smem, st>>>(a);
   }
