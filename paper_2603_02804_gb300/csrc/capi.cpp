@@ -37,6 +37,7 @@ struct Layout {
   size_t mats64 = 0, tcb = 0;  // tensor-core path: float64 fused 2x2s, per-round B blocks
   size_t work = 0, lam = 0, slots = 0, hslots = 0;
   size_t epart = 0, gpart = 0, gred = 0;  // gred: stage-1 scratch of a two-stage gradient reduction
+  size_t done = 0;                         // CTA counter of a forward pass that finishes the loss
   size_t total = 0;
   int64_t state_elems = 0;  // batch * 2^n_eff
   int64_t rows = 0;         // partial rows per sample (tiles or chunks)
@@ -206,6 +207,7 @@ Layout make_layout(const qf_circuit* c, int64_t B) {
   L.dLdE = take((size_t)B * 8);
   L.grad = take((size_t)P * 8);
   L.loss = take(8);
+  L.done = take(4);
   L.cs = take((size_t)S * 16);  // (cos, sin) per term, float32 or float64 (generic programs)
   L.enc = take((size_t)B * n_eff * aw);
   L.work = take((size_t)L.state_elems * aw);
@@ -523,6 +525,10 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   pa.n_eff = P.n_eff;
   pa.qshift = P.qshift;
   pa.enc = at<float2>(ws, L.enc);
+  // a train step's loss rides on the pass that computes the expectation (its
+  // last CTA), or on the E-reduction launch
+  const bool loss_in_pass = sl && B > 0 && qf::e_loss_fusable(B, (int)L.rows);
+  if (loss_in_pass) pa.zero_word = at<uint32_t>(ws, L.done);
   QF_CU(qf::launch_prep(pa, st));
   c->call_launches++;
   if (c->tc) {
@@ -555,12 +561,24 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   a.n_slots = P.n_terms;
   const int prof = prof_begin(c, st);
   int32_t full_expect = -1;  // slot of psi_M when the observable reaches outside the last tile
+  bool loss_done = false;
   for (size_t pi = 0; pi < P.fwd.size(); ++pi) {
     a.pd = P.fwd[pi];
     a.pd.xm_local = 0;
     if ((a.pd.flags & qf::PF_EXPECT) && !local_xmask(a.pd, o.x, &a.pd.xm_local)) {
       a.pd.flags &= ~qf::PF_EXPECT;
       full_expect = a.pd.psi_dst;
+    }
+    a.done = nullptr;
+    if (loss_in_pass && (a.pd.flags & qf::PF_EXPECT)) {
+      a.done = at<uint32_t>(ws, L.done);
+      a.E = E;
+      a.y = static_cast<const float*>(sl->y);
+      a.loss = sl->loss;
+      a.dLdE_out = sl->dLdE;
+      a.loss_kind = sl->kind;
+      a.loss_scale = 2.0 / (double)B;
+      loss_done = true;
     }
     if (c->tc) QF_CU(qf::launch_pass_tc(a, st));
     else QF_CU(qf::launch_pass(false, a, st));
@@ -572,14 +590,17 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
                                  o.y, a.e_part, st));
     c->call_launches++;
   }
-  if (sl && qf::e_loss_fusable(B, (int)L.rows)) {
+  if (loss_done) {
+    sl->done = true;
+  } else if (sl && qf::e_loss_fusable(B, (int)L.rows)) {
     QF_CU(qf::launch_e_loss(a.e_part, (int)L.rows, sl->kind, E, static_cast<const float*>(sl->y), B, sl->loss,
                             sl->dLdE, st));
     sl->done = true;
+    c->call_launches++;
   } else {
     QF_CU(qf::launch_e_reduce(a.e_part, B, (int)L.rows, E, st));
+    c->call_launches++;
   }
-  c->call_launches++;
   return QF_OK;
 }
 

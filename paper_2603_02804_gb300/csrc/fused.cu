@@ -629,8 +629,13 @@ __device__ __forceinline__ void tc_rounds(const TcCtx& tc, const StepPar& P, int
 
 // ---------------------------------------------------------------------------
 // Static shared memory of a pass (the tiles themselves are dynamic).
+template <class Y>
+__device__ void loss_block(int kind, double* E, const Y* y, int64_t B, double scale, double* loss, double* dLdE,
+                           const double* e_part, int tps, int tid);
+
 struct PassShared {
   StepPar par[2];
+  uint32_t ticket;             // the CTA's finishing order (loss on the last CTA)
   uint32_t lg[256];
   uint32_t base[4][kThreads];  // per register group: the thread's tile index with the group's bits zero
   float red[2][kThreads / 32][kMaxStepSlots];
@@ -1116,6 +1121,21 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
     }
   }
   __syncthreads();
+  static_assert(kThreads == 256, "loss_block reduces over 256 threads");
+  if (!BWD && a.done && (pd.flags & PF_EXPECT)) {
+    // the last CTA to finish sums E over every CTA's partials and finishes
+    // the loss (the partials are fenced before the count)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh.ticket = atomicAdd(a.done, 1u);
+    __syncthreads();
+    if (sh.ticket == gridDim.x - 1) {
+      __threadfence();
+      loss_block<float>(a.loss_kind, a.E, a.y, a.B, a.loss_scale, a.loss, a.dLdE_out, a.e_part, 1 << a.tps_log2,
+                        tid);
+    }
+    __syncthreads();
+  }
 }
 
 // RX: round programs holding RX items (their own instance, so that programs
@@ -1201,6 +1221,7 @@ __device__ void prep_one(const PrepArgs& a, int64_t i);
 
 __global__ void prep_kernel(const PrepArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && a.zero_word) *a.zero_word = 0u;
   prep_one(a, i);
 }
 
@@ -1508,25 +1529,29 @@ __global__ void g_reduce_kernel(const GradReduceArgs a) {
   double s = 0.0;
   for (int k = a.param_off[p]; k < a.param_off[p + 1]; ++k) {
     const int64_t col = (int64_t)a.param_slots[k] * a.slot_step;
+#pragma unroll 8
     for (int64_t t = lane; t < rows; t += 32) s += a.g_part[(row0 + t) * a.slot_stride + col];
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) a.grad[out] = s;
 }
 
-// Loss and dL/dE in one block, fixed-order tree reduction (labels float32,
-// or float64 for complex128 plans). With e_part: E_i is first summed from its
-// tps partials in tile order (as e_reduce_kernel does) and stored.
+// Loss and dL/dE in one block of 256 threads with a fixed-order reduction
+// (warp shuffles, then the 8 warp sums in warp 0); labels float32, or float64
+// for complex128 plans. scale = 2 / B (MSE: dL/dE_i = scale (E_i - y_i)).
+// With e_part: E_i is first summed from its tps partials in tile order (as
+// e_reduce_kernel does) and stored; they are read from L2, as they may come
+// from other CTAs of the same launch.
 template <class Y>
-__global__ void loss_kernel(int kind, double* E, const Y* y, int64_t B, double* loss, double* dLdE,
-                            const double* e_part, int tps) {
-  __shared__ double red[256];
+__device__ void loss_block(int kind, double* E, const Y* y, int64_t B, double scale, double* loss, double* dLdE,
+                           const double* e_part, int tps, int tid) {
+  __shared__ double red[8];
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+  for (int64_t i = tid; i < B; i += 256) {
     double Ei;
     if (e_part) {
       Ei = 0.0;
-      for (int t = 0; t < tps; ++t) Ei += e_part[i * tps + t];
+      for (int t = 0; t < tps; ++t) Ei += __ldcg(e_part + i * tps + t);
       E[i] = Ei;
     } else {
       Ei = E[i];
@@ -1534,19 +1559,26 @@ __global__ void loss_kernel(int kind, double* E, const Y* y, int64_t B, double* 
     if (kind == 1) {
       const double d = Ei - (double)y[i];
       s += d * d;
-      dLdE[i] = 2.0 * d / (double)B;
+      dLdE[i] = scale * d;
     } else {
       s += Ei;
       dLdE[i] = 1.0;
     }
   }
-  red[threadIdx.x] = s;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (tid < 32) {
+    s = tid < 8 ? red[tid] : 0.0;
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) loss[0] = kind == 1 ? s * (0.5 * scale) : s;
   }
-  if (threadIdx.x == 0) loss[0] = kind == 1 ? red[0] / (double)B : red[0];
+}
+
+template <class Y>
+__global__ void __launch_bounds__(256) loss_kernel(int kind, double* E, const Y* y, int64_t B, double scale,
+                                                   double* loss, double* dLdE, const double* e_part, int tps) {
+  loss_block<Y>(kind, E, y, B, scale, loss, dLdE, e_part, tps, threadIdx.x);
 }
 
 // ---- batched persistent launch -------------------------------------------------
@@ -1742,8 +1774,9 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64
 
 // ---- launchers ----------------------------------------------------------------
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + round_par_elems(a);
-  if (total == 0) return cudaSuccess;
+  int64_t total = (int64_t)a.n_fused + a.n_terms + (int64_t)a.B * a.n_eff + round_par_elems(a);
+  if (total == 0 && !a.zero_word) return cudaSuccess;
+  if (total == 0) total = 1;  // element 0 only clears the counter
   // float64 work per element: small blocks spread it over more SMs
   const int blk = 64;
   prep_kernel<<<(unsigned)((total + blk - 1) / blk), blk, 0, st>>>(a);
@@ -1944,13 +1977,15 @@ cudaError_t launch_g_reduce(const GradReduceArgs& a, cudaStream_t st) {
 
 cudaError_t launch_loss(int kind, const double* E, const float* y, int64_t B, double* loss, double* dLdE,
                         cudaStream_t st) {
-  loss_kernel<float><<<1, 256, 0, st>>>(kind, const_cast<double*>(E), y, B, loss, dLdE, nullptr, 0);
+  loss_kernel<float><<<1, 256, 0, st>>>(kind, const_cast<double*>(E), y, B, B > 0 ? 2.0 / (double)B : 0.0, loss,
+                                         dLdE, nullptr, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_loss64(int kind, const double* E, const double* y, int64_t B, double* loss, double* dLdE,
                           cudaStream_t st) {
-  loss_kernel<double><<<1, 256, 0, st>>>(kind, const_cast<double*>(E), y, B, loss, dLdE, nullptr, 0);
+  loss_kernel<double><<<1, 256, 0, st>>>(kind, const_cast<double*>(E), y, B, B > 0 ? 2.0 / (double)B : 0.0, loss,
+                                          dLdE, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -1959,7 +1994,7 @@ bool e_loss_fusable(int64_t B, int tps) { return tps < 256 && B * tps <= 65536; 
 template <class Y>
 static cudaError_t launch_e_loss_t(const double* e_part, int tps, int kind, double* E, const Y* y, int64_t B,
                                    double* loss, double* dLdE, cudaStream_t st) {
-  loss_kernel<Y><<<1, 256, 0, st>>>(kind, E, y, B, loss, dLdE, e_part, tps);
+  loss_kernel<Y><<<1, 256, 0, st>>>(kind, E, y, B, B > 0 ? 2.0 / (double)B : 0.0, loss, dLdE, e_part, tps);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,16 @@ struct PassArgs {
   int32_t n_slots;
   int32_t g_accum;        // round programs: add the partials of a sample's tiles into one row
   int32_t rx_items;       // round programs with RX items (the RX-capable kernels run them)
+  // The pass that computes the expectation may also finish the loss: with
+  // done != null, the last CTA to finish sums E from e_part and writes E, the
+  // loss and dL/dE as loss_kernel does (done: a CTA counter prep zeroes).
+  uint32_t* done;
+  double* E;              // [B]
+  const float* y;         // labels (MSE)
+  double* loss;           // [1]
+  double* dLdE_out;       // [B]
+  int32_t loss_kind;
+  double loss_scale;      // 2 / B
 };
 
 // Float64 three-shear parameters of a gradient term (complex128 round
@@ -83,6 +93,7 @@ struct PrepArgs {
   float4* rpb;                 // [n_rpb][kRoundPar]: rotation shears, then the un-applied diagonal
   RoundPar64* rpf64;           // if non-null instead of rpf / rpb: the same in float64
   RoundPar64* rpb64;           //   (complex128 round programs), [n_rpf] / [n_rpb]
+  uint32_t* zero_word;         // if non-null: set to 0 (the forward's CTA counter)
 };
 
 // Table elements of the round parameters (prep work items, kRoundPar per round).

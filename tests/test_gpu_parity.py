@@ -80,9 +80,38 @@ def test_hea12_train_step_mse():
     assert abs(loss.item() - orc.mse_loss(Er, y)) < TOL
     assert np.max(np.abs(g.cpu().numpy() - gr)) < TOL
     n_launch = sim.launches()
-    # forward + backward with one shared parameter-table launch; the loss
-    # shares the forward's E-reduction launch (one tile per sample)
-    assert n_launch == sim.info()["launches_fwd"] + sim.info()["launches_bwd"] - 1
+    # forward + backward with one shared parameter-table launch; E and the
+    # loss are finished by the last CTA of the expectation pass, so the
+    # forward's E-reduction launch is not needed either
+    assert n_launch == sim.info()["launches_fwd"] + sim.info()["launches_bwd"] - 2
+
+
+@pytest.mark.parametrize("n,d,B,kw", [(14, 3, 5, {}), (13, 4, 300, {}), (12, 3, 7, {"tc_path": True}),
+                                       (10, 4, 9, {"tile_bits": 7})])
+def test_train_step_loss_finished_in_pass(n, d, B, kw):
+    """The train step's E, loss and dL/dE come from the last CTA of the
+    expectation pass: several tiles per sample (n = 13, 14), more CTAs than
+    SM slots (B = 300), the tensor-core forward, several samples per CTA
+    (7-qubit tiles); against the oracle's MSE loss and its gradient."""
+    rng = np.random.default_rng(40 + n + d + B)
+    theta = rng.uniform(0, 2 * np.pi, 3 * n * d).astype(np.float32)
+    x = rng.uniform(0, np.pi, (B, n)).astype(np.float32)
+    y = rng.choice([-1.0, 1.0], B).astype(np.float32)
+    sim = Simulator(n, d, B, **kw)
+    loss, E, g = sim.train_step(dev(theta), dev(x), dev(y), loss="mse")
+    torch.cuda.synchronize()
+    c = orc.hea(n, d)
+    Er = orc.expectation(c, f64(theta), f64(x), "Z")
+    gr, _ = orc.gradient(c, f64(theta), f64(x), "Z", dLdE=orc.mse_dLdE(Er, f64(y)))
+    assert np.max(np.abs(E.cpu().numpy() - Er)) < TOL
+    assert abs(loss.item() - orc.mse_loss(Er, f64(y))) < TOL
+    assert np.max(np.abs(g.cpu().numpy() - gr)) < TOL
+    # a second step on the same buffers (replayed graph) gives the same numbers
+    out = sim.device_outputs(B)
+    r1 = [t.clone() for t in sim.train_step(dev(theta), dev(x), dev(y), loss="mse", out=out)]
+    r2 = [t.clone() for t in sim.train_step(dev(theta), dev(x), dev(y), loss="mse", out=out)]
+    assert all(torch.equal(a, b) for a, b in zip(r1, r2))
+    assert torch.equal(r1[1], E) and torch.equal(r1[2], g)
 
 
 def test_train_step_host_buffers():
