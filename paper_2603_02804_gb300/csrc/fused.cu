@@ -1227,6 +1227,11 @@ __global__ void prep_kernel(const PrepArgs a) {
 
 namespace {
 
+// One out-of-line float64 sincos shared by every table of prep, so that the
+// kernel's element kinds run one copy of its code (prep runs after an L2
+// flush in timed steps, and each inlined copy is fetched separately).
+__device__ __noinline__ void sincos_prep(double x, double* s, double* c) { sincos(x, s, c); }
+
 // Parameter p as float64 (float32 parameters are promoted exactly).
 __device__ __forceinline__ double theta_at(const PrepArgs& a, int p) {
   return a.theta64 ? a.theta64[p] : (double)a.theta[p];
@@ -1238,7 +1243,7 @@ __device__ void fused_u(const PrepArgs& a, int64_t m, float4& m0, float4& m1, do
   for (int j = a.fuse_off[m]; j < a.fuse_off[m + 1]; ++j) {
     const FuseGate fg = a.fuse_gates[j];
     double s, c;
-    sincos(0.5 * (fg.param >= 0 ? theta_at(a, fg.param) : fg.angle), &s, &c);
+    sincos_prep(0.5 * (fg.param >= 0 ? theta_at(a, fg.param) : fg.angle), &s, &c);
     // g = c I - i s P
     double g[2][2][2];
     if (fg.kind == G_RX) {
@@ -1339,7 +1344,7 @@ __device__ void shear_params(const PrepArgs& a, int32_t t, double& tq, double& s
   const double k = rint(phi * (1.0 / two_pi));
   const double w = phi - two_pi * k;
   double c;
-  sincos(0.5 * w, &sh, &c);
+  sincos_prep(0.5 * w, &sh, &c);
   tq = f32 ? sh * recip_1_2(1.0 + c) : sh / (1.0 + c);
   parity = ((long long)k) & 1;
 }
@@ -1367,7 +1372,7 @@ __device__ void diag_phase_pair(const PrepArgs& a, const int32_t* tz, uint32_t b
   double al = 0.0;
   for (int r = 0; r < 4; ++r) al += ((m >> r) & 1) ? -phi[r] : phi[r];
   al *= apply ? -0.5 : 0.5;
-  sincos(al, &s, &c);
+  sincos_prep(al, &s, &c);
   const int mc = 15 - m;
   f0 = __popc(bbits & (uint32_t)m & (uint32_t)(m >> 1)) & 1;
   f1 = __popc(bbits & (uint32_t)mc & (uint32_t)(mc >> 1)) & 1;
@@ -1421,11 +1426,11 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   if (i < a.n_terms) {
     if (a.cs64) {
       double s, c;
-      sincos(0.5 * term_angle(a, i), &s, &c);
+      sincos_prep(0.5 * term_angle(a, i), &s, &c);
       a.cs64[i] = make_double2(c, s);
     } else {
       double s, c;
-      sincos(0.5 * term_angle(a, i), &s, &c);
+      sincos_prep(0.5 * term_angle(a, i), &s, &c);
       a.cs[i] = make_float2((float)c, (float)s);
     }
     return;
@@ -1438,7 +1443,7 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
     if (q < a.n) {
       // simulated bit q holds circuit qubit (q - qshift) mod n
       const int qc = a.qshift ? (q + a.n - a.qshift) % a.n : q;
-      sincos(0.5 * (a.x64 ? a.x64[bb * a.n + qc] : (double)a.x[bb * a.n + qc]), &s, &c);
+      sincos_prep(0.5 * (a.x64 ? a.x64[bb * a.n + qc] : (double)a.x[bb * a.n + qc]), &s, &c);
     }
     if (a.enc64) a.enc64[i] = make_double2(c, s);
     else a.enc[i] = make_float2((float)c, (float)s);
