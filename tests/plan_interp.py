@@ -143,9 +143,56 @@ def term_angle(prog, t, theta):
     return float(sum(float(theta[p]) for p in prog.terms[t][1])) + prog.term_const[t]
 
 
-def fwd_ops(prog, pd, psi, n_eff, theta, slots):
+def round_diagonal(n_eff, regs, phi, bbits, sign):
+    """A round's RZ runs (angles phi[r] on qubits regs[r]) and its CZ links
+    between register bits (bit r of bbits: regs[r], regs[r + 1]) as one
+    diagonal over the whole vector, the way the round kernels apply it: the
+    phase of register index j is exp(sign * i * a_j), a_j = sum_r sigma_r(j)
+    phi_r / 2 with sigma_r(j) = +1 where bit r of j is clear (sign -1: the RZ
+    runs applied, +1: un-applied), times -1 where a register-register link
+    joins two set bits."""
+    x = np.arange(2 ** n_eff, dtype=np.int64)
+    j = np.zeros_like(x)
+    for r in range(4):
+        j |= ((x >> regs[r]) & 1) << r
+    a = np.zeros(2 ** n_eff)
+    for r in range(4):
+        a += np.where((j >> r) & 1, -phi[r], phi[r]) / 2
+    cz = np.zeros_like(x)
+    for r in range(3):
+        if (bbits >> r) & 1:
+            cz ^= ((j >> r) & 1) & ((j >> (r + 1)) & 1)
+    return np.exp(sign * 1j * a) * (1 - 2 * cz)
+
+
+def _round_parts(prog, rec_tz, rec_ty, rx, regs, theta):
+    phi = [term_angle(prog, t, theta) if t >= 0 else 0.0 for t in rec_tz]
+    rots = []
+    for r in range(4):
+        t = rec_ty[r]
+        if t >= 0:
+            kind = RX if (rx >> r) & 1 else RY
+            assert prog.terms[t][0] == kind
+            rots.append((r, kind, term_angle(prog, t, theta)))
+    return phi, rots
+
+
+def _links_rest(links, bbits, regs):
+    """The round's links other than those between register bits (those are in
+    the diagonal table)."""
+    for r in range(3):
+        if (bbits >> r) & 1:
+            assert regs[r + 1] == regs[r] + 1 and (links >> regs[r]) & 1
+            links &= ~(1 << regs[r])
+    return links
+
+
+def fwd_ops(prog, pd, psi, n_eff, theta, slots, kernel_order=False):
     """Apply the forward op range of pass pd to psi (whole vector); OP_CKPT
-    writes slots."""
+    writes slots. kernel_order: round programs run as the round kernels do:
+    the four rotations from the rotation terms, then the round's diagonal
+    (its RZ-run terms and register-register CZ signs), then the other links;
+    otherwise each item's fused 2x2 and then all the links."""
     k = pd["op_begin"]
     group = None
     while k < pd["op_end"]:
@@ -156,6 +203,14 @@ def fwd_ops(prog, pd, psi, n_eff, theta, slots):
             nr = (w0 >> 8) & 0xFFFF
             for j in range(nr):
                 rec = prog.round_words[(w1 + j) * FWD_ROUND_WORDS:(w1 + j + 1) * FWD_ROUND_WORDS]
+                if kernel_order:
+                    regs = [pd["gmap"][group[r]] for r in range(4)]
+                    phi, rots = _round_parts(prog, rec[8:12], rec[12:16], rec[6], regs, theta)
+                    for r, kind, angle in rots:
+                        psi = apply1(psi, n_eff, regs[r], rot(kind, angle))
+                    psi = psi * round_diagonal(n_eff, regs, phi, rec[5], -1)
+                    psi = psi * chain_sign(n_eff, _links_rest(rec[4] & 0xFFFFFFFF, rec[5], regs))
+                    continue
                 for r in range(4):
                     psi = apply1(psi, n_eff, pd["gmap"][group[r]], fused_matrix(prog, rec[r], theta))
                 psi = psi * chain_sign(n_eff, rec[4] & 0xFFFFFFFF)
@@ -191,7 +246,7 @@ def layout_x(prog, xrow, n):
     return np.asarray([xrow[(p - s) % n] for p in range(n)]) if s else xrow
 
 
-def run_forward(prog, n, n_eff, theta, xrow, xm, zm):
+def run_forward(prog, n, n_eff, theta, xrow, xm, zm, kernel_order=False):
     xrow, xm, zm = layout_x(prog, xrow, n), layout_mask(prog, xm, n), layout_mask(prog, zm, n)
     slots = {}
     work = None
@@ -199,7 +254,7 @@ def run_forward(prog, n, n_eff, theta, xrow, xm, zm):
     for pd in prog.passes:
         src = pd["psi_src"]
         psi = encode(xrow, n, n_eff) if src == SRC_GENERATE else (slots[src] if src >= 0 else work).copy()
-        psi = fwd_ops(prog, pd, psi, n_eff, theta, slots)
+        psi = fwd_ops(prog, pd, psi, n_eff, theta, slots, kernel_order)
         dst = pd["psi_dst"]
         if dst >= 0:
             slots[dst] = psi.copy()
@@ -216,8 +271,12 @@ def _grad_unapply(psi, lam, n_eff, q, kind, angle):
     return g, apply1(psi, n_eff, q, ud), apply1(lam, n_eff, q, ud)
 
 
-def bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen):
-    """Run the adjoint op range of pass pd on (psi, lam); returns both."""
+def bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen, kernel_order=False):
+    """Run the adjoint op range of pass pd on (psi, lam); returns both.
+    kernel_order: round programs run as the round kernels do: the other links,
+    then the round's four RZ-run terms at once from Im(conj(lambda) psi) with
+    the register signs, the diagonal un-applied from both states, then each
+    rotation's term and un-apply."""
     k = pd["op_begin"]
     group = None
     while k < pd["op_end"]:
@@ -228,6 +287,25 @@ def bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen):
             nr = (w0 >> 8) & 0xFFFF
             for j in range(nr):
                 rec = prog.round_words[(w1 + j) * BWD_ROUND_WORDS:(w1 + j + 1) * BWD_ROUND_WORDS]
+                if kernel_order:
+                    regs = [pd["gmap"][group[r]] for r in range(4)]
+                    s = chain_sign(n_eff, _links_rest(rec[8] & 0xFFFFFFFF, rec[9], regs))
+                    psi, lam = psi * s, lam * s
+                    phi, rots = _round_parts(prog, rec[0:4], rec[4:8], rec[10], regs, theta)
+                    w = np.imag(np.conj(lam) * psi)
+                    x = np.arange(2 ** n_eff, dtype=np.int64)
+                    for r in range(4):
+                        t = rec[r]
+                        if t >= 0:
+                            grad_term[t] += 0.5 * np.sum(np.where((x >> regs[r]) & 1, -w, w))
+                            seen[t] += 1
+                    dg = round_diagonal(n_eff, regs, phi, rec[9], +1)
+                    psi, lam = psi * dg, lam * dg
+                    for r, kind, angle in rots:
+                        g, psi, lam = _grad_unapply(psi, lam, n_eff, regs[r], kind, angle)
+                        grad_term[rec[4 + r]] += g
+                        seen[rec[4 + r]] += 1
+                    continue
                 s = chain_sign(n_eff, rec[8] & 0xFFFFFFFF)
                 psi, lam = psi * s, lam * s
                 for r in range(4):
@@ -272,7 +350,7 @@ def _term_grad(prog, grad_term, seen, n_params):
     return grad
 
 
-def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params):
+def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params, kernel_order=False):
     """Per-parameter gradient; every gradient term must be visited once."""
     xm, zm = layout_mask(prog, xm, n_eff), layout_mask(prog, zm, n_eff)  # a shift implies n = n_eff
     grad_term = np.zeros(len(prog.terms))
@@ -282,7 +360,7 @@ def run_backward(prog, n_eff, theta, slots, xm, zm, dLdE, n_params):
         src = pd["psi_src"]
         psi = (slots[src] if src >= 0 else work).copy()
         lam = 2 * dLdE * observable(psi, n_eff, xm, zm) if pd["lam_src"] == LAM_SEED else lam_buf.copy()
-        psi, lam = bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen)
+        psi, lam = bwd_ops(prog, pd, psi, lam, n_eff, theta, slots, grad_term, seen, kernel_order)
         if pd["psi_dst"] == BUF_WORK:
             work = psi
         if pd["lam_dst"] == LAM_BUF:

@@ -86,7 +86,7 @@ def test_host_only_plan_refuses_device_calls():
         qfuse.qf_circuit_destroy(h)
 
 
-def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, oracle_circ=None):
+def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, oracle_circ=None, kernel_order=False):
     info = qfuse.qf_plan_info(handle)
     n_eff = info["n_eff"]
     fwd = pi.parse(qfuse.qf_plan_export(handle, 0))
@@ -100,9 +100,9 @@ def interp_check(handle, n, theta, x, obs, slot_param, slot_kind, tol=1e-10, ora
     pq = qfuse.pauli(obs, n)
     gp, Ep = orc.gradient(oracle_circ, theta, x, obs, per_sample=True)
     for b in range(len(x)):
-        E, slots = pi.run_forward(fwd, n, n_eff, theta, x[b], pq.x_mask, pq.z_mask)
+        E, slots = pi.run_forward(fwd, n, n_eff, theta, x[b], pq.x_mask, pq.z_mask, kernel_order)
         assert abs(E - Ep[b]) < tol
-        g = pi.run_backward(bwd, n_eff, theta, slots, pq.x_mask, pq.z_mask, 1.0, len(theta))
+        g = pi.run_backward(bwd, n_eff, theta, slots, pq.x_mask, pq.z_mask, 1.0, len(theta), kernel_order)
         assert np.max(np.abs(g - gp[b])) < tol
     return info, fwd.rounds_mode
 
@@ -350,9 +350,9 @@ def test_xyz_ring_ansatz_rows():
 @pytest.mark.parametrize("n,d,K,ck", [(5, 2, 0, 0), (7, 3, 0, 1), (9, 2, 0, 0), (13, 2, 0, 1), (14, 2, 8, 1),
                                       (17, 2, 0, 0)])
 def test_xyz_ring_ansatz_plans_match_oracle(n, d, K, ck, program):
-    """The paper's Rx, Ry, Rz + CZ-ring ansatz: round programs (RX rewritten as
-    RZ RY RZ with constant angles, the ring's CZ(n-1, 0) as link n-1) and
-    generic programs both give the oracle's expectations and gradients."""
+    """The paper's Rx, Ry, Rz + CZ-ring ansatz: round programs (RX items, the
+    ring's CZ(n-1, 0) as link n-1) and generic programs both give the
+    oracle's expectations and gradients."""
     from paper_2603_02804_gb300 import workloads
     rng = np.random.default_rng(900 + 7 * n + d)
     rows = workloads.xyz_ring_gates(n, d)
@@ -367,6 +367,51 @@ def test_xyz_ring_ansatz_plans_match_oracle(n, d, K, ck, program):
         slot_kind = [r[0] for r in rows if r[0] != orc.CZ]
         info, rounds = interp_check(h, n, theta, x, "ZXY"[: min(3, n)], slot_param, slot_kind, oracle_circ=c)
         assert rounds == (program == 0 and info["tile_bits"] >= 7)
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+@pytest.mark.parametrize("kind,n,d,K,ck", [
+    ("hea", 7, 3, 0, 1), ("hea", 9, 4, 0, 2), ("hea", 12, 3, 0, 1), ("hea", 13, 3, 0, 1), ("hea", 15, 3, 7, 1),
+    ("hea", 17, 2, 0, 0), ("ring", 9, 2, 0, 0), ("ring", 14, 2, 8, 1),
+])
+def test_round_programs_in_kernel_order_match_oracle(kind, n, d, K, ck):
+    """Round programs executed the way the round kernels execute them (the
+    interpreter's kernel order): per round the rotations from the rotation
+    terms, then one diagonal built from the RZ-run terms' summed angles per
+    register index with the register-register CZ signs, then the other links;
+    the adjoint takes the four RZ-run terms at the diagonal from
+    Im(conj(lambda) psi) before any rotation of the round. Expectations and
+    gradients must equal the oracle's, which pins the merged diagonal's
+    algebra (signs, direction, the links it absorbs) without a GPU."""
+    from paper_2603_02804_gb300 import workloads
+    rng = np.random.default_rng(1300 + 11 * n + d)
+    if kind == "hea":
+        rows = None
+        h = qfuse.qf_hea_create(n, d)
+        P = 3 * n * d
+        c = orc.hea(n, d)
+        slot_param = list(range(P))
+        slot_kind = [orc.RY if (p % 3) == 1 else orc.RZ for p in range(P)]
+    else:
+        rows = workloads.xyz_ring_gates(n, d)
+        P = 3 * n * d
+        h = qfuse.qf_circuit_create(n, rows, P)
+        c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=P)
+        slot_param = [r[3] for r in rows if r[0] != orc.CZ]
+        slot_kind = [r[0] for r in rows if r[0] != orc.CZ]
+    try:
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, program=0)
+        theta = rng.uniform(0, 2 * np.pi, P).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
+        info, rounds = interp_check(h, n, theta, x, "ZXY"[: min(3, n)], slot_param, slot_kind, oracle_circ=c,
+                                    kernel_order=True)
+        assert rounds
+        if kind == "hea":
+            # some round of the plan carries register-register CZ signs in its diagonal
+            fwd = pi.parse(qfuse.qf_plan_export(h, 0))
+            W = pi.FWD_ROUND_WORDS
+            assert any(fwd.round_words[W * k + 5] for k in range(len(fwd.round_words) // W))
     finally:
         qfuse.qf_circuit_destroy(h)
 
