@@ -1070,8 +1070,8 @@ qf_status qf_circuit_create(int32_t n_qubits, const qf_gate* gates, int32_t n_ga
 
 qf_status qf_circuit_destroy(qf_circuit* c) {
   if (!c) return QF_OK;
+  free_tables(c);     // drops the step graphs, which may hold the timing events
   destroy_events(c);
-  free_tables(c);
   if (c->g_stream) cudaStreamDestroy(c->g_stream);
   delete c;
   return QF_OK;
