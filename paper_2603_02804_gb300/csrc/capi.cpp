@@ -56,11 +56,14 @@ struct DevTables {
   const double* term_const = nullptr;     // constant part of each term's angle (fused plans)
   const int32_t* param_off = nullptr;     // CSR parameter -> terms
   const int32_t* param_terms = nullptr;
+  const qf::RoundTerm* fwd_rterms = nullptr;  // round programs: each round's terms, resolved
+  const qf::RoundTerm* bwd_rterms = nullptr;
 };
 
 // Byte offsets of each table inside the blob.
 struct BlobOffsets {
   size_t fwd = 0, bwd = 0, foff = 0, fg = 0, frd = 0, brd = 0, to = 0, tp = 0, tcst = 0, po = 0, ps = 0;
+  size_t frt = 0, brt = 0;
 };
 
 }  // namespace
@@ -253,6 +256,37 @@ size_t push_table(std::vector<char>& blob, const std::vector<T>& v) {
   return at;
 }
 
+// The terms of every round record (rotation terms, then RZ-run terms), each
+// with its parameters and constant resolved, so that prep reads a round's
+// angles without walking the term maps.
+template <class W>
+std::vector<qf::RoundTerm> round_terms(const qf::FusedPlan& P, const std::vector<W>& rounds, int words,
+                                       int tz_at, int ty_at) {
+  std::vector<qf::RoundTerm> out;
+  const size_t n_rounds = rounds.size() / (size_t)words;
+  out.reserve(n_rounds * 8);
+  auto ref = [&](int32_t t) {
+    qf::RoundTerm e{-1, -1, 0.0};
+    if (t < 0) return e;
+    const int b0 = P.term_off[t], b1 = P.term_off[t + 1];
+    e.c = P.term_const.empty() ? 0.0 : P.term_const[t];
+    if (b1 - b0 > 2) {
+      e.p0 = -2 - t;
+      e.c = 0.0;
+      return e;
+    }
+    if (b1 > b0) e.p0 = P.term_params[b0];
+    if (b1 > b0 + 1) e.p1 = P.term_params[b0 + 1];
+    return e;
+  };
+  for (size_t r = 0; r < n_rounds; ++r) {
+    const int32_t* rec = reinterpret_cast<const int32_t*>(rounds.data()) + r * words;
+    for (int k = 0; k < 4; ++k) out.push_back(ref(rec[ty_at + k]));
+    for (int k = 0; k < 4; ++k) out.push_back(ref(rec[tz_at + k]));
+  }
+  return out;
+}
+
 // Serialise the plan's device tables into c->blob (host memory).
 void build_blob(qf_circuit* c) {
   std::vector<char>& blob = c->blob;
@@ -271,6 +305,10 @@ void build_blob(qf_circuit* c) {
     o.tcst = push_table(blob, c->fp.term_const);
     o.po = push_table(blob, c->fp.param_off);
     o.ps = push_table(blob, c->fp.param_terms);
+    if (c->fp.rounds) {
+      o.frt = push_table(blob, round_terms(c->fp, c->fp.fwd_rounds, qf::kFwdRoundWords, 8, 12));
+      o.brt = push_table(blob, round_terms(c->fp, c->fp.bwd_rounds, qf::kBwdRoundWords, 0, 4));
+    }
   } else {
     std::vector<int32_t> toff(c->gp.n_slots + 1);
     for (int t = 0; t <= c->gp.n_slots; ++t) toff[t] = t;
@@ -294,6 +332,10 @@ DevTables tables_at(const qf_circuit* c, void* base) {
     t.fwd_rounds = reinterpret_cast<const uint4*>(b + c->bo.frd);
     t.bwd_rounds = reinterpret_cast<const uint4*>(b + c->bo.brd);
     t.term_const = reinterpret_cast<const double*>(b + c->bo.tcst);
+    if (c->fp.rounds) {
+      t.fwd_rterms = reinterpret_cast<const qf::RoundTerm*>(b + c->bo.frt);
+      t.bwd_rterms = reinterpret_cast<const qf::RoundTerm*>(b + c->bo.brt);
+    }
   }
   t.term_off = reinterpret_cast<const int32_t*>(b + c->bo.to);
   t.term_params = reinterpret_cast<const int32_t*>(b + c->bo.tp);
@@ -469,6 +511,7 @@ void set_term_table(const qf_circuit* c, const DevTables& T, const Layout& L, vo
     pa.n_terms = 0;
     pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
     pa.rpb_src = T.bwd_rounds;
+    pa.rpb_terms = T.bwd_rterms;
     pa.rpb = at<float4>(ws, L.rpb);
   } else {
     pa.n_terms = n_slots_of(c);
@@ -516,6 +559,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
   if (P.rounds) {
     pa.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
     pa.rpf_src = T.fwd_rounds;
+    pa.rpf_terms = T.fwd_rterms;
     pa.rpf = at<float4>(ws, L.rpf);
   }
   if (c->tc) pa.mats64 = at<double>(ws, L.mats64);
@@ -754,6 +798,7 @@ qf::PrepArgs prep_args64(const qf_circuit* c, const DevTables& T, const Layout& 
 void set_rounds64(const qf_circuit* c, const DevTables& T, const Layout& L, void* ws, qf::PrepArgs& pa) {
   pa.n_rpb = (int32_t)(c->fp.bwd_rounds.size() / qf::kBwdRoundWords);
   pa.rpb_src = T.bwd_rounds;
+    pa.rpb_terms = T.bwd_rterms;
   pa.rpb64 = at<qf::RoundPar64>(ws, L.rpb);
 }
 
@@ -767,6 +812,7 @@ qf_status fused_forward64(qf_circuit* c, const DevTables& T, const Layout& L, co
     pa.n_fused = 0;
     pa.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
     pa.rpf_src = T.fwd_rounds;
+    pa.rpf_terms = T.fwd_rterms;
     pa.rpf64 = at<qf::RoundPar64>(ws, L.rpf);
     if (with_terms) set_rounds64(c, T, L, ws, pa);
   } else {
@@ -1892,9 +1938,11 @@ qf_status qf_batch_create(int32_t n_circuits, qf_circuit* const* circuits, const
       p.enc = rel<float2>(w0 + L.enc);
       p.n_rpf = (int32_t)(P.fwd_rounds.size() / qf::kFwdRoundWords);
       p.rpf_src = T.fwd_rounds;
+      p.rpf_terms = T.fwd_rterms;
       p.rpf = rel<float4>(w0 + L.rpf);
       p.n_rpb = (int32_t)(P.bwd_rounds.size() / qf::kBwdRoundWords);
       p.rpb_src = T.bwd_rounds;
+      p.rpb_terms = T.bwd_rterms;
       p.rpb = rel<float4>(w0 + L.rpb);
       r.n_params = c->circ.n_params;
       r.param_off = T.param_off;

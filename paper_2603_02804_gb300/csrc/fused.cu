@@ -1318,6 +1318,16 @@ __device__ void term_angles4(const PrepArgs& a, const int32_t* t, double (&phi)[
   }
 }
 
+// The angle of a resolved round term (the same summation order as
+// term_angle: the constant, then the parameters).
+__device__ __forceinline__ double round_term_angle(const PrepArgs& a, const RoundTerm& e) {
+  if (e.p0 <= -2) return term_angle(a, -2 - e.p0);
+  double phi = e.c;
+  if (e.p0 >= 0) phi += theta_at(a, e.p0);
+  if (e.p1 >= 0) phi += theta_at(a, e.p1);
+  return phi;
+}
+
 // 1/d for d in [1, 2], accurate far below float32 rounding: the hardware's
 // approximate reciprocal refined by three Newton-Raphson steps
 // r <- r + r (1 - d r), each squaring the relative error (from any start
@@ -1333,13 +1343,12 @@ __device__ __forceinline__ double recip_1_2(double d) {
 
 // u(phi) = (-1)^k u(w) with w = phi - 2 pi k in [-pi, pi] (k the nearest
 // integer to phi / 2 pi): the rotation by w/2 as three shears needs tan(w/4)
-// (|.| <= 1) and sin(w/2); a missing term (-1) is the identity (all zero).
+// (|.| <= 1) and sin(w/2); angle 0 (also a missing term) gives all zero.
 // tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the half-angle identity; the
 // denominator lies in [1, 2] for |w/2| <= pi/2), so one float64 sincos gives
 // both. f32: the result is rounded to float32, so the quotient may use
 // recip_1_2 instead of an IEEE division.
-__device__ void shear_params(const PrepArgs& a, int32_t t, double& tq, double& sh, int& parity, bool f32) {
-  const double phi = term_angle(a, t);
+__device__ void shear_params(double phi, double& tq, double& sh, int& parity, bool f32) {
   const double two_pi = 6.283185307179586476925286766559;
   const double k = rint(phi * (1.0 / two_pi));
   const double w = phi - two_pi * k;
@@ -1349,26 +1358,32 @@ __device__ void shear_params(const PrepArgs& a, int32_t t, double& tq, double& s
   parity = ((long long)k) & 1;
 }
 
-__device__ float4 term_shear_of(const PrepArgs& a, int32_t t) {
-  if (t < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ float4 shear_of(double phi) {
   double tq, sh;
   int parity;
-  shear_params(a, t, tq, sh, parity, true);
+  shear_params(phi, tq, sh, parity, true);
   return make_float4((float)tq, (float)sh, __int_as_float(parity), 0.f);
 }
 
-// The diagonal of a round: its RZ runs (terms tz[r], angle phi_r; -1 = none)
+// The same in float64 (complex128 round programs).
+__device__ Shear64 shear64_of(double phi) {
+  Shear64 r{0.0, 0.0, 0, 0};
+  int parity;
+  shear_params(phi, r.t, r.s, parity, false);
+  r.wrap = parity;
+  return r;
+}
+
+// The diagonal of a round: its RZ runs (angles phi_r; 0 for a missing term)
 // act on register index j as e^{-i a_j} with a_j = sum_r sigma_r(j) phi_r / 2,
 // sigma_r(j) = +1 where bit r of j is clear, else -1 (RZ(phi) =
 // diag(e^{-i phi/2}, e^{i phi/2})), and its CZ links between register bits r
-// and r + 1 (bit r of bbits) as -1 where both bits of j are set. Writes
+// and r + 1 (bit r of bbits) as -1 where both bits of j are set. Gives
 // (cos, sin) of the applied phase (forward: -a_j) or of the un-applied one
-// (backward: +a_j), with those signs, for j = m and its complement 15 - m:
-// a_{15-m} = -a_m, so one float64 sincos of the summed angle gives both.
-__device__ void diag_phase_pair(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
-                                double& c, double& s, bool& f0, bool& f1) {
-  double phi[4];
-  term_angles4(a, tz, phi);
+// (backward: +a_j) for j = m, and the CZ signs of m and its complement
+// 15 - m: a_{15-m} = -a_m, so one float64 sincos of the summed angle serves both.
+__device__ void diag_phase_pair(const double (&phi)[4], uint32_t bbits, int m, bool apply, double& c, double& s,
+                                bool& f0, bool& f1) {
   double al = 0.0;
   for (int r = 0; r < 4; ++r) al += ((m >> r) & 1) ? -phi[r] : phi[r];
   al *= apply ? -0.5 : 0.5;
@@ -1378,34 +1393,22 @@ __device__ void diag_phase_pair(const PrepArgs& a, const int32_t* tz, uint32_t b
   f1 = __popc(bbits & (uint32_t)mc & (uint32_t)(mc >> 1)) & 1;
 }
 
-__device__ void diag_phases(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
-                            float2* ph) {
+__device__ void diag_phases(const double (&phi)[4], uint32_t bbits, int m, bool apply, float2* ph) {
   double cd, sd;
   bool f0, f1;
-  diag_phase_pair(a, tz, bbits, m, apply, cd, sd, f0, f1);
+  diag_phase_pair(phi, bbits, m, apply, cd, sd, f0, f1);
   const float c = (float)cd, s = (float)sd;
   ph[m] = f0 ? make_float2(-c, -s) : make_float2(c, s);
   ph[15 - m] = f1 ? make_float2(-c, s) : make_float2(c, -s);
 }
 
 // The same in float64 (complex128 round programs).
-__device__ void diag_phases64(const PrepArgs& a, const int32_t* tz, uint32_t bbits, int m, bool apply,
-                              double2* ph) {
+__device__ void diag_phases64(const double (&phi)[4], uint32_t bbits, int m, bool apply, double2* ph) {
   double c, s;
   bool f0, f1;
-  diag_phase_pair(a, tz, bbits, m, apply, c, s, f0, f1);
+  diag_phase_pair(phi, bbits, m, apply, c, s, f0, f1);
   ph[m] = f0 ? make_double2(-c, -s) : make_double2(c, s);
   ph[15 - m] = f1 ? make_double2(-c, s) : make_double2(c, -s);
-}
-
-// The same in float64 (complex128 round programs).
-__device__ Shear64 term_shear64(const PrepArgs& a, int32_t t) {
-  Shear64 r{0.0, 0.0, 0, 0};
-  if (t < 0) return r;
-  int parity;
-  shear_params(a, t, r.t, r.s, parity, false);
-  r.wrap = parity;
-  return r;
 }
 
 }  // namespace
@@ -1461,19 +1464,27 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
                            : reinterpret_cast<const int32_t*>(a.rpb_src) + r * kBwdRoundWords;
   const int32_t* tz = fwd ? rec + 8 : rec;
   const int32_t* ty = fwd ? rec + 12 : rec + 4;
-  const uint32_t bbits = (uint32_t)(fwd ? rec[5] : rec[9]);
-  if (a.rpf64 || a.rpb64) {
-    RoundPar64& out = (fwd ? a.rpf64 : a.rpb64)[r];
-    if (e < 4) out.rot[e] = term_shear64(a, ty[e]);
-    else diag_phases64(a, tz, bbits, e - 4, fwd, out.ph);
+  // the round's terms resolved at plan time (their loads issue together), or
+  // through the term maps
+  const RoundTerm* rt = fwd ? a.rpf_terms : a.rpb_terms;
+  if (rt) rt += r * 8;
+  const bool f64 = a.rpf64 || a.rpb64;
+  if (e < 4) {
+    const double phi = rt ? round_term_angle(a, rt[e]) : (ty[e] >= 0 ? term_angle(a, ty[e]) : 0.0);
+    if (f64) (fwd ? a.rpf64 : a.rpb64)[r].rot[e] = shear64_of(phi);
+    else (fwd ? a.rpf : a.rpb)[r * kRoundPar + e] = shear_of(phi);
     return;
   }
-  float4* out = (fwd ? a.rpf : a.rpb) + r * kRoundPar;
-  if (e < 4) {
-    out[e] = term_shear_of(a, ty[e]);
+  const uint32_t bbits = (uint32_t)(fwd ? rec[5] : rec[9]);
+  double phi[4];
+  if (rt) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) phi[q] = round_term_angle(a, rt[4 + q]);
   } else {
-    diag_phases(a, tz, bbits, e - 4, fwd, reinterpret_cast<float2*>(out + 4));
+    term_angles4(a, tz, phi);
   }
+  if (f64) diag_phases64(phi, bbits, e - 4, fwd, (fwd ? a.rpf64 : a.rpb64)[r].ph);
+  else diag_phases(phi, bbits, e - 4, fwd, reinterpret_cast<float2*>((fwd ? a.rpf : a.rpb) + r * kRoundPar + 4));
 }
 
 // E_b = sum over the tiles of sample b, in tile order (deterministic).

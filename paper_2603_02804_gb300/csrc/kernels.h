@@ -63,6 +63,14 @@ struct RoundPar64 {
   double2 ph[16];
 };
 
+// A gradient term of a round record, resolved when the plan is made: its
+// angle is c + theta[p0] + theta[p1] (-1: no such parameter); p0 <= -2 marks a
+// term of more than two parameters, t = -2 - p0, summed through the CSR maps.
+struct RoundTerm {
+  int32_t p0, p1;
+  double c;
+};
+
 struct PrepArgs {
   const float* theta;
   const double* theta64;       // if non-null: float64 parameters (complex128 plans), theta unused
@@ -94,6 +102,8 @@ struct PrepArgs {
   RoundPar64* rpf64;           // if non-null instead of rpf / rpb: the same in float64
   RoundPar64* rpb64;           //   (complex128 round programs), [n_rpf] / [n_rpb]
   uint32_t* zero_word;         // if non-null: set to 0 (the forward's CTA counter)
+  const RoundTerm* rpf_terms;  // per forward / backward round: its 4 rotation terms, then its
+  const RoundTerm* rpb_terms;  //   4 RZ-run terms (-1 terms: no parameter, angle 0)
 };
 
 // Table elements of the round parameters (prep work items, kRoundPar per round).
