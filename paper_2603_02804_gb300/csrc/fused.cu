@@ -1214,9 +1214,12 @@ __global__ void tc_table_kernel(const uint4* fwd_rounds, int32_t n_rounds, const
 }
 
 // ---------------------------------------------------------------------------
-// Gate tables from theta in float64, rounded once to float32:
-//   fused 2x2 products (forward), (cos, sin) of theta/2 per slot (backward),
-//   (cos, sin) of x/2 per sample and qubit (encoding).
+// Gate tables from theta in float64, rounded once to float32 (or kept in
+// float64 for complex128 plans): generic programs' fused 2x2 products
+// (forward) and (cos, sin) of theta/2 per term (backward); round programs'
+// per-round rotation shears and diagonal phases (both directions); (cos, sin)
+// of x/2 per sample and qubit (encoding). Element 0 also clears the forward
+// pass's CTA counter when a train step finishes its loss in that pass.
 __device__ void prep_one(const PrepArgs& a, int64_t i);
 
 __global__ void prep_kernel(const PrepArgs a) {
