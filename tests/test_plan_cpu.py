@@ -373,7 +373,8 @@ def test_xyz_ring_ansatz_plans_match_oracle(n, d, K, ck, program):
 
 @pytest.mark.parametrize("kind,n,d,K,ck", [
     ("hea", 7, 3, 0, 1), ("hea", 9, 4, 0, 2), ("hea", 12, 3, 0, 1), ("hea", 13, 3, 0, 1), ("hea", 15, 3, 7, 1),
-    ("hea", 17, 2, 0, 0), ("ring", 9, 2, 0, 0), ("ring", 14, 2, 8, 1),
+    ("hea", 17, 2, 0, 0), ("ring", 9, 2, 0, 0), ("ring", 14, 2, 8, 1), ("sweep", 9, 5, 0, 0),
+    ("sweep", 13, 4, 0, 1),
 ])
 def test_round_programs_in_kernel_order_match_oracle(kind, n, d, K, ck):
     """Round programs executed the way the round kernels execute them (the
@@ -394,8 +395,10 @@ def test_round_programs_in_kernel_order_match_oracle(kind, n, d, K, ck):
         slot_param = list(range(P))
         slot_kind = [orc.RY if (p % 3) == 1 else orc.RZ for p in range(P)]
     else:
-        rows = workloads.xyz_ring_gates(n, d)
-        P = 3 * n * d
+        # the Rx,Ry,Rz + CZ ring ansatz, or the fusion-depth circuit (d consecutive
+        # Rx,Ry,Rz gates per qubit, no entangler)
+        rows = workloads.xyz_ring_gates(n, d) if kind == "ring" else workloads.consecutive_gates(n, d)
+        P = 3 * n * d if kind == "ring" else n * d
         h = qfuse.qf_circuit_create(n, rows, P)
         c = orc.Circuit(n=n, gates=np.array(rows, np.int32), n_params=P)
         slot_param = [r[3] for r in rows if r[0] != orc.CZ]
