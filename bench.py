@@ -639,13 +639,13 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    g0 = qfuse.qf_graph_stats(sim.handle)
+    g0 = sim.graph_stats()
     with ClockSampler(local) as clk:
         total_ms, launches = timed(sim, args.steps)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    g1 = qfuse.qf_graph_stats(sim.handle)
+    g1 = sim.graph_stats()
     step_graph = {"replayed_in_timed_steps": g1["replayed"] - g0["replayed"], "recorded": g1["recorded"]}
     prof = profiled(sim, args.steps)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)

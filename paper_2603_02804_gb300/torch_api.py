@@ -87,6 +87,12 @@ class Simulator:
     def launches(self) -> int:
         return qfuse.qf_launch_count(self.handle)
 
+    def graph_stats(self) -> dict:
+        """Train steps this simulator recorded as CUDA graphs and replayed from one
+        ({"recorded": r, "replayed": n}); a loop on fixed buffers replays every
+        step from the second on."""
+        return qfuse.qf_graph_stats(self.handle)
+
     def _stream(self):
         return torch.cuda.current_stream(self.device)
 
