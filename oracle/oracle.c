@@ -29,7 +29,10 @@
  * block forward from its stored input, keeping every intermediate state of
  * that block (gradient checkpointing, Sec. 3.4). block >= M keeps all states.
  *
- * Parallelism: OpenMP over samples only.
+ * Parallelism: OpenMP over samples when there are at least as many samples
+ * as threads; otherwise the samples run one after another and every loop over
+ * the 2^n amplitudes is split across the threads instead (the arithmetic per
+ * amplitude is unchanged; only the order of the final sums in <a|b> differs).
  */
 #include <complex.h>
 #include <math.h>
@@ -41,6 +44,16 @@
 #endif
 
 typedef double complex cplx;
+
+/* 1 while the amplitude loops run in parallel (fewer samples than threads). */
+static int amp_par = 0;
+
+/* Amplitude loops shorter than this stay on one thread (below 2^17 complex128
+ * amplitudes, 2 MiB, the fork and join per gate cost more than the loop). */
+#define OR_PAR_MIN_DIM ((uint64_t)1 << 17)
+
+/* The parallel clause of an amplitude loop over `dim` entries. */
+#define OR_AMP_PAR(dim) if (amp_par && (dim) >= OR_PAR_MIN_DIM) schedule(static)
 
 /* Gate kinds understood by the oracle. */
 enum { OR_RX = 0, OR_RY = 1, OR_RZ = 2, OR_CZ = 3, OR_CNOT = 4 };
@@ -104,6 +117,9 @@ static void dagger(cplx u[2][2], cplx ud[2][2]) {
  * (a0', a1') = u (a0, a1). */
 static void apply_1q(cplx *psi, int n, int t, cplx u[2][2]) {
     const uint64_t dim = (uint64_t)1 << n, bit = (uint64_t)1 << t;
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
     for (uint64_t x = 0; x < dim; ++x) {
         if (x & bit) continue;
         cplx a0 = psi[x], a1 = psi[x | bit];
@@ -116,6 +132,9 @@ static void apply_1q(cplx *psi, int n, int t, cplx u[2][2]) {
 static void apply_cz(cplx *psi, int n, int c, int t) {
     const uint64_t dim = (uint64_t)1 << n;
     const uint64_t bc = (uint64_t)1 << c, bt = (uint64_t)1 << t;
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
     for (uint64_t x = 0; x < dim; ++x)
         if ((x & bc) && (x & bt)) psi[x] = -psi[x];
 }
@@ -124,6 +143,9 @@ static void apply_cz(cplx *psi, int n, int c, int t) {
 static void apply_cnot(cplx *psi, int n, int c, int t) {
     const uint64_t dim = (uint64_t)1 << n;
     const uint64_t bc = (uint64_t)1 << c, bt = (uint64_t)1 << t;
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
     for (uint64_t x = 0; x < dim; ++x) {
         if (!(x & bc) || (x & bt)) continue;
         cplx tmp = psi[x];
@@ -143,10 +165,18 @@ static void apply_gate(cplx *psi, int n, const or_gate *g, const double *theta,
     else apply_1q(psi, n, g->q0, u);
 }
 
+/* dst = src over 2^n amplitudes. */
+static void copy_state(cplx *dst, const cplx *src, int n) {
+    const uint64_t dim = (uint64_t)1 << n;
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
+    for (uint64_t x = 0; x < dim; ++x) dst[x] = src[x];
+}
+
 /* O psi for a Pauli string, applied one qubit at a time. */
 static void apply_pauli(cplx *out, const cplx *psi, int n, const int32_t *letters) {
-    const uint64_t dim = (uint64_t)1 << n;
-    memcpy(out, psi, dim * sizeof(cplx));
+    copy_state(out, psi, n);
     for (int q = 0; q < n; ++q) {
         if (letters[q] == OR_I) continue;
         cplx p[2][2];
@@ -158,9 +188,16 @@ static void apply_pauli(cplx *out, const cplx *psi, int n, const int32_t *letter
 /* <a|b> = sum_x conj(a_x) b_x */
 static cplx inner(const cplx *a, const cplx *b, int n) {
     const uint64_t dim = (uint64_t)1 << n;
-    cplx s = 0;
-    for (uint64_t x = 0; x < dim; ++x) s += conj(a[x]) * b[x];
-    return s;
+    double sr = 0, si = 0;
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim) reduction(+ : sr, si)
+#endif
+    for (uint64_t x = 0; x < dim; ++x) {
+        const cplx t = conj(a[x]) * b[x];
+        sr += creal(t);
+        si += cimag(t);
+    }
+    return sr + I * si;
 }
 
 /* Initial state. When init_state is non-null it is copied (interleaved
@@ -169,11 +206,17 @@ static cplx inner(const cplx *a, const cplx *b, int n) {
 static void prepare(cplx *psi, int n, const double *xrow, const double *init_state) {
     const uint64_t dim = (uint64_t)1 << n;
     if (init_state) {
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
         for (uint64_t x = 0; x < dim; ++x)
             psi[x] = init_state[2 * x] + I * init_state[2 * x + 1];
         return;
     }
-    memset(psi, 0, dim * sizeof(cplx));
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
+    for (uint64_t x = 0; x < dim; ++x) psi[x] = 0;
     psi[0] = 1;
     for (int q = 0; q < n; ++q) {
         cplx u[2][2];
@@ -184,6 +227,20 @@ static void prepare(cplx *psi, int n, const double *xrow, const double *init_sta
 
 /* ---- public entry points ------------------------------------------------ */
 
+/* Thread count for this call (n_threads > 0 sets it) and where the threads
+ * go: over samples when there are at least as many samples as threads,
+ * else over the amplitudes of one sample at a time. */
+static void set_parallelism(int B, int n_threads) {
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+    amp_par = B < omp_get_max_threads();
+#else
+    (void)B;
+    (void)n_threads;
+    amp_par = 0;
+#endif
+}
+
 /* Final state of one sample: psi_out gets 2*2^n doubles (re, im interleaved).
  * x: [n] encoding angles (ignored when init_state is given). */
 int oracle_final_state(int n, const or_gate *gates, int n_gates, const double *theta,
@@ -191,6 +248,7 @@ int oracle_final_state(int n, const or_gate *gates, int n_gates, const double *t
     const uint64_t dim = (uint64_t)1 << n;
     cplx *psi = malloc(dim * sizeof(cplx));
     if (!psi) return -1;
+    set_parallelism(1, 0);
     prepare(psi, n, x, init_state);
     for (int j = 0; j < n_gates; ++j) apply_gate(psi, n, &gates[j], theta, 0);
     for (uint64_t k = 0; k < dim; ++k) {
@@ -208,9 +266,9 @@ int oracle_expectation(int n, const or_gate *gates, int n_gates, const double *t
                        const int32_t *letters, double *E_out, int n_threads) {
     const uint64_t dim = (uint64_t)1 << n;
     int fail = 0;
+    set_parallelism(B, n_threads);
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : fail)
+#pragma omp parallel for if (!amp_par) schedule(dynamic, 1) reduction(| : fail)
 #endif
     for (int b = 0; b < B; ++b) {
         cplx *psi = malloc(dim * sizeof(cplx));
@@ -245,9 +303,9 @@ int oracle_gradient(int n, const or_gate *gates, int n_gates, const double *thet
     double *per = calloc((size_t)B * (n_params > 0 ? n_params : 1), sizeof(double));
     if (!per) return -1;
     int fail = 0;
+    set_parallelism(B, n_threads);
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : fail)
+#pragma omp parallel for if (!amp_par) schedule(dynamic, 1) reduction(| : fail)
 #endif
     for (int b = 0; b < B; ++b) {
         /* block inputs: state before gate k*block, k = 0..n_blocks-1 */
@@ -268,22 +326,26 @@ int oracle_gradient(int n, const or_gate *gates, int n_gates, const double *thet
         prepare(psi, n, x ? x + (size_t)b * n : 0,
                 init_states ? init_states + (size_t)b * 2 * dim : 0);
         for (int j = 0; j < n_gates; ++j) {
-            if (j % block == 0) memcpy(ckpt + (size_t)(j / block) * dim, psi, dim * sizeof(cplx));
+            if (j % block == 0) copy_state(ckpt + (size_t)(j / block) * dim, psi, n);
             apply_gate(psi, n, &gates[j], theta, 0);
         }
         /* E (Eq. 1) and seed lambda_M = 2 (dL/dE) O psi_M (Eq. 4) */
         apply_pauli(tmp, psi, n, letters);
         if (E_out) E_out[b] = creal(inner(psi, tmp, n));
-        for (uint64_t k = 0; k < dim; ++k) lam[k] = 2.0 * dLdE[b] * tmp[k];
+        const double seed = 2.0 * dLdE[b];
+#ifdef _OPENMP
+#pragma omp parallel for OR_AMP_PAR(dim)
+#endif
+        for (uint64_t k = 0; k < dim; ++k) lam[k] = seed * tmp[k];
 
         /* backward pass, block by block in reverse */
         for (int k = n_blocks - 1; k >= 0; --k) {
             const int j0 = k * block;
             const int j1 = (j0 + block < n_gates) ? j0 + block : n_gates;
             /* recompute psi_{j-1} for every gate of the block from its input */
-            memcpy(psi, ckpt + (size_t)k * dim, dim * sizeof(cplx));
+            copy_state(psi, ckpt + (size_t)k * dim, n);
             for (int j = j0; j < j1; ++j) {
-                memcpy(inside + (size_t)(j - j0) * dim, psi, dim * sizeof(cplx));
+                copy_state(inside + (size_t)(j - j0) * dim, psi, n);
                 apply_gate(psi, n, &gates[j], theta, 0);
             }
             for (int j = j1 - 1; j >= j0; --j) {
@@ -293,7 +355,7 @@ int oracle_gradient(int n, const or_gate *gates, int n_gates, const double *thet
                     /* Eq. 3: Re <lambda_j| dU_j |psi_{j-1}> */
                     cplx du[2][2];
                     rotation_derivative(gt->kind, theta[gt->param], du);
-                    memcpy(tmp, psi_prev, dim * sizeof(cplx));
+                    copy_state(tmp, psi_prev, n);
                     apply_1q(tmp, n, gt->q0, du);
                     g[gt->param] += creal(inner(lam, tmp, n));
                 }

@@ -346,3 +346,29 @@ def test_threads_do_not_change_result():
     g1, e1 = orc.gradient(c, theta, x, "Z", threads=1)
     g4, e4 = orc.gradient(c, theta, x, "Z", threads=4)
     assert np.array_equal(g1, g4) and np.array_equal(e1, e4)
+
+
+def test_amplitude_parallel_mode_matches_serial():
+    """With fewer samples than threads the oracle splits its amplitude loops
+    over the threads (n >= 17). Pinned against closed forms there, and against
+    the one-thread run, which differs only in the order of the final sums."""
+    n = 17
+    c = orc.hea(n, 1)
+    rng = np.random.default_rng(17)
+    theta = rng.uniform(0, 2 * np.pi, c.n_params)
+    x = rng.uniform(0, np.pi, (2, n))
+    g_par, e_par = orc.gradient(c, theta, x, "Z", per_sample=True, threads=4)
+    a0, b0 = theta[0], theta[1]
+    for s in range(2):
+        x0 = x[s, 0]
+        assert abs(e_par[s] - (np.cos(x0) * np.cos(b0) - np.sin(x0) * np.cos(a0) * np.sin(b0))) < 1e-13
+        expect = np.zeros(c.n_params)
+        expect[0] = np.sin(x0) * np.sin(a0) * np.sin(b0)
+        expect[1] = -np.cos(x0) * np.sin(b0) - np.sin(x0) * np.cos(a0) * np.cos(b0)
+        assert np.max(np.abs(g_par[s] - expect)) < 1e-13
+    c2 = orc.hea(n, 2)
+    theta2 = rng.uniform(0, 2 * np.pi, c2.n_params)
+    g1, e1 = orc.gradient(c2, theta2, x[:1], "ZIX", per_sample=True, threads=1)
+    g4, e4 = orc.gradient(c2, theta2, x[:1], "ZIX", per_sample=True, threads=4)
+    assert np.max(np.abs(g1 - g4)) < 1e-12 and np.max(np.abs(e1 - e4)) < 1e-12
+    assert np.max(np.abs(g1)) > 1e-3  # a non-trivial gradient
