@@ -352,9 +352,15 @@ qf_status qf_train_step_host64(qf_circuit* c, const double* theta_h, const doubl
  *  - plan tables plus the step's buffers for `batch` samples must fit in
  *    QF_NOALLOC_MAX_BYTES; otherwise QF_ERR_WORKSPACE is returned and
  *    qf_last_error() states the bytes needed.
- *  - the first call on a device looks up the block's device address (once per
- *    device, with that device current); make that first call before any
- *    stream capture.
+ *  - batch must not exceed the batch the circuit was planned for
+ *    (QF_ERR_INVALID_ARG otherwise).
+ *  - the first call on a device sets it up: it looks up the block's device
+ *    address with that device current. Make that first call before any
+ *    stream capture. Later calls outside a capture look the address up again
+ *    (so a cudaDeviceReset between calls is handled); calls during a capture
+ *    reuse the address of the last uncaptured call on that device.
+ *  - every call copies the plan's tables from the handle's host memory into
+ *    the block, then runs the step there.
  *  - every call shares the one block and it keeps the last call's contents;
  *    each kernel writes every scratch element it later reads, so nothing needs
  *    clearing. Calls that overlap on the GPU (other streams, other threads)

@@ -1624,7 +1624,15 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
   if (!c) return fail(QF_ERR_INVALID_ARG, "null circuit");
   if (!c->planned) return fail(QF_ERR_WORKSPACE, "circuit has no plan (call qf_plan, host_only is enough)");
   if (check_precision(c, false) != QF_OK) return QF_ERR_INVALID_ARG;
-  if (batch < 0) return fail(QF_ERR_INVALID_ARG, "negative batch");
+  if (batch < 0 || batch > c->batch) return fail(QF_ERR_INVALID_ARG, "batch exceeds the planned batch");
+  // one sample's state alone must fit in the block (this also keeps the
+  // layout's byte counts far from overflow for any planned batch)
+  const size_t state_bytes = (size_t)8 << n_eff_of(c);
+  if (batch > 0 && (size_t)batch > (size_t)QF_NOALLOC_MAX_BYTES / state_bytes)
+    return fail(QF_ERR_WORKSPACE, "qf_train_step_noalloc: " + std::to_string(batch) + " samples of " +
+                                      std::to_string(state_bytes) + " bytes each exceed the fixed " +
+                                      std::to_string((size_t)QF_NOALLOC_MAX_BYTES) +
+                                      " bytes (QF_NOALLOC_MAX_BYTES); use a smaller batch or qf_train_step");
   if (loss_kind != QF_LOSS_SUM && loss_kind != QF_LOSS_MSE) return fail(QF_ERR_INVALID_ARG, "unknown loss");
   if ((!theta_d && c->circ.n_params > 0) || (batch > 0 && (!x_d || !E_d)) || !loss_d ||
       (!grad_d && c->circ.n_params > 0) || (loss_kind == QF_LOSS_MSE && batch > 0 && !y_d))
@@ -1645,8 +1653,8 @@ qf_status qf_train_step_noalloc(qf_circuit* c, const float* theta_d, const float
   if (e != cudaSuccess) return fail(QF_ERR_CUDA, std::string("pending CUDA error: ") + cudaGetErrorString(e));
   void* scratch = nullptr;
   size_t cap = 0;
-  QF_CU(qf::noalloc_scratch(&scratch, &cap));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  QF_CU(qf::noalloc_scratch(st, &scratch, &cap));
   QF_CU(cudaMemcpyAsync(scratch, c->blob.data(), tbytes, cudaMemcpyHostToDevice, st));
   const DevTables T = tables_at(c, scratch);
   void* ws = static_cast<char*>(scratch) + tbytes;

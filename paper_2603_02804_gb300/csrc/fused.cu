@@ -1331,40 +1331,26 @@ __device__ __forceinline__ double round_term_angle(const PrepArgs& a, const Roun
   return phi;
 }
 
-// 1/d for d in [1, 2], accurate far below float32 rounding: the hardware's
-// approximate reciprocal refined by three Newton-Raphson steps
-// r <- r + r (1 - d r), each squaring the relative error (from any start
-// within 2^-8 of 1/d down to the float64 rounding level).
-__device__ __forceinline__ double recip_1_2(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  r = fma(r, fma(-d, r, 1.0), r);
-  r = fma(r, fma(-d, r, 1.0), r);
-  r = fma(r, fma(-d, r, 1.0), r);
-  return r;
-}
-
 // u(phi) = (-1)^k u(w) with w = phi - 2 pi k in [-pi, pi] (k the nearest
 // integer to phi / 2 pi): the rotation by w/2 as three shears needs tan(w/4)
 // (|.| <= 1) and sin(w/2); angle 0 (also a missing term) gives all zero.
 // tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the half-angle identity; the
 // denominator lies in [1, 2] for |w/2| <= pi/2), so one float64 sincos gives
-// both. f32: the result is rounded to float32, so the quotient may use
-// recip_1_2 instead of an IEEE division.
-__device__ void shear_params(double phi, double& tq, double& sh, int& parity, bool f32) {
+// both.
+__device__ void shear_params(double phi, double& tq, double& sh, int& parity) {
   const double two_pi = 6.283185307179586476925286766559;
   const double k = rint(phi * (1.0 / two_pi));
   const double w = phi - two_pi * k;
   double c;
   sincos_prep(0.5 * w, &sh, &c);
-  tq = f32 ? sh * recip_1_2(1.0 + c) : sh / (1.0 + c);
+  tq = sh / (1.0 + c);
   parity = ((long long)k) & 1;
 }
 
 __device__ float4 shear_of(double phi) {
   double tq, sh;
   int parity;
-  shear_params(phi, tq, sh, parity, true);
+  shear_params(phi, tq, sh, parity);
   return make_float4((float)tq, (float)sh, __int_as_float(parity), 0.f);
 }
 
@@ -1372,7 +1358,7 @@ __device__ float4 shear_of(double phi) {
 __device__ Shear64 shear64_of(double phi) {
   Shear64 r{0.0, 0.0, 0, 0};
   int parity;
-  shear_params(phi, r.t, r.s, parity, false);
+  shear_params(phi, r.t, r.s, parity);
   r.wrap = parity;
   return r;
 }
@@ -1765,12 +1751,27 @@ cudaError_t opt_in(const void* fn, size_t smem, OptIn& o) {
   return e;
 }
 
-int batch_grid() {
-  int dev = 0, sms = 0;
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return 2 * sms;
+  const bool tab = dev >= 0 && dev < 64;
+  if (tab) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (tab) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
+
+int64_t stream_grid(int64_t want) {
+  const int64_t cap = 16ll * device_sms();
+  return cap > 0 && want > cap ? cap : want;
+}
+
+int batch_grid() { return 2 * device_sms(); }
 
 cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64_t n_grad_out, cudaStream_t st) {
   static OptIn once;
@@ -1822,15 +1823,8 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
   } else {
     // more tiles than two CTAs per SM hold: the three-CTA round instances
     // (fewer registers, more warps to hide latency across the waves)
-    static int n_sm = 0;
-    if (n_sm == 0) {
-      int dev = 0, v = 0;
-      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
-                                                   cudaSuccess)
-        n_sm = v;
-      else
-        return cudaGetLastError();
-    }
+    const int n_sm = device_sms();
+    if (n_sm == 0) return cudaErrorInvalidDevice;
     const bool three = rounds && grid > 2ll * n_sm;
     if (rx && three) pass_kernel<false, true, true, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else if (rx) pass_kernel<false, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
@@ -1898,7 +1892,7 @@ cudaError_t launch_seed_full(const float2* psi, float2* lam, int n_eff, int64_t 
   const int64_t total = B << n_eff;
   if (total == 0) return cudaSuccess;
   const int64_t want = (total + kThreads - 1) / kThreads;
-  const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+  const unsigned grid = (unsigned)stream_grid(want);
   seed_full_kernel<<<grid, kThreads, 0, st>>>(psi, lam, n_eff, B, xm, zm, yc, dLdE);
   return cudaGetLastError();
 }

@@ -836,7 +836,7 @@ cudaError_t launch_seed_full64(const double2* psi, double2* lam, int n_eff, int6
   const int64_t total = B << n_eff;
   if (total == 0) return cudaSuccess;
   const int64_t want = (total + kThreads - 1) / kThreads;
-  const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+  const unsigned grid = (unsigned)stream_grid(want);
   seed_full64_kernel<<<grid, kThreads, 0, st>>>(psi, lam, n_eff, B, xm, zm, yc, dLdE);
   return cudaGetLastError();
 }

@@ -258,7 +258,12 @@ struct BatchArgs {
 // prep, work-queue reset, persistent forward+adjoint, gradient and loss
 // reductions: 4 kernels and one memset on `st`.
 cudaError_t launch_batch(const BatchArgs& a, int grid, int64_t prep_total, int64_t n_grad_out, cudaStream_t st);
+// Persistent batch kernel grid: two CTAs per SM of the current device.
 int batch_grid();
+// SMs of the current device (queried once per device; 0 if the query fails).
+int device_sms();
+// Grid of a grid-strided kernel that wants `want` CTAs: at most 16 per SM.
+int64_t stream_grid(int64_t want);
 
 // ---- per-gate comparator ------------------------------------------------------
 struct PerGateArgs {
@@ -283,7 +288,9 @@ cudaError_t pg_copy(const float2* src, float2* dst, int64_t n, cudaStream_t st);
 int32_t pg_chunks(int32_t n_eff);
 
 // Device address of the fixed scratch block on the current device
-// (QF_NOALLOC_MAX_BYTES bytes); looked up once per device.
-cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
+// (QF_NOALLOC_MAX_BYTES bytes). Looked up with the device current on every
+// call whose stream is not being captured, and cached per device for calls
+// made during a capture (which then need an earlier uncaptured call).
+cudaError_t noalloc_scratch(cudaStream_t st, void** ptr, size_t* bytes);
 
 }  // namespace qf

@@ -26,19 +26,28 @@ void* g_addr[kMaxDevices] = {};
 namespace qf {
 
 // Device address of the scratch on the current device. In host code the
-// array's name only stands for the device symbol, so the address has to be
-// looked up once per device, with that device current.
-cudaError_t noalloc_scratch(void** ptr, size_t* bytes) {
+// array's name only stands for the device symbol, so the address is looked up
+// with cudaGetSymbolAddress while that device is current. The lookup runs on
+// every call made outside a stream capture: after a cudaDeviceReset the
+// module is loaded again and the old address is no longer valid. A call made
+// during a capture may not trigger a module load, so it uses the address that
+// the last uncaptured call on this device cached, and fails without one.
+cudaError_t noalloc_scratch(cudaStream_t st, void** ptr, size_t* bytes) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_addr[dev] = p;
+  } else if (!g_addr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *ptr = g_addr[dev];
   *bytes = QF_NOALLOC_MAX_BYTES;

@@ -257,9 +257,8 @@ __global__ void pg_copy_kernel(const float4* src, float4* dst, int64_t n4) {
 }
 
 unsigned grid_for(int64_t n) {
-  int64_t g = (n + kPgThreads - 1) / kPgThreads;
-  const int64_t cap = 152 * 16;
-  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+  const int64_t g = stream_grid((n + kPgThreads - 1) / kPgThreads);
+  return (unsigned)(g < 1 ? 1 : g);
 }
 
 }  // namespace

@@ -38,6 +38,24 @@ def _outputs(w, B):
     return z(1), z(B), z(w.n_params)
 
 
+def _tiny_noalloc_call(stream):
+    """A different circuit and batch through the shared block (4 qubits, B=8,
+    L = sum E), so that the next hea12 call meets a block holding another
+    call's contents."""
+    w = workloads.WORKLOADS["tiny"]
+    theta, x, _ = workloads.make_inputs(w)
+    h = qfuse.qf_hea_create(w.n, w.d)
+    qfuse.qf_plan(h, w.B, host_only=True)
+    try:
+        loss, E, g = _outputs(w, w.B)
+        qfuse.qf_train_step_noalloc(h, torch.from_numpy(theta).cuda(), torch.from_numpy(x).cuda(), None, w.B,
+                                    qfuse.QF_LOSS_SUM, qfuse.pauli("Z", w.n), loss, E, g, stream)
+        torch.cuda.synchronize()
+        assert abs(loss.item() - E.sum().item()) < TOL
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
 def test_noalloc_step_matches_workspace_step_twice():
     B = 64
     w, theta, x, y = _inputs(B)
@@ -51,7 +69,8 @@ def test_noalloc_step_matches_workspace_step_twice():
     loss_r, E_r, g_r = _outputs(w, B)
     qfuse.qf_train_step(ref_h, theta, x, y, B, qfuse.QF_LOSS_MSE, obs, loss_r, E_r, g_r, ws, ws_bytes, stream)
 
-    # no-allocation entry point on a host-only plan (no device tables either)
+    # no-allocation entry point on a host-only plan (no device tables either);
+    # between the two compared calls another circuit and batch use the block
     h = qfuse.qf_hea_create(w.n, w.d)
     qfuse.qf_plan(h, B, host_only=True)
     try:
@@ -62,9 +81,26 @@ def test_noalloc_step_matches_workspace_step_twice():
             assert abs(loss.item() - loss_r.item()) < TOL, call
             assert torch.max(torch.abs(E - E_r)).item() < TOL, call
             assert torch.max(torch.abs(g - g_r)).item() < TOL, call
+            if call == 0:
+                _tiny_noalloc_call(stream)
     finally:
         qfuse.qf_circuit_destroy(h)
         qfuse.qf_circuit_destroy(ref_h)
+
+
+def test_noalloc_step_refuses_a_batch_beyond_the_plan():
+    B = 8
+    w, theta, x, y = _inputs(B)
+    h = qfuse.qf_hea_create(w.n, w.d)
+    qfuse.qf_plan(h, B, host_only=True)
+    try:
+        loss, E, g = _outputs(w, B)
+        with pytest.raises(qfuse.QFError) as e:
+            qfuse.qf_train_step_noalloc(h, theta, x, y, 1 << 40, qfuse.QF_LOSS_MSE, qfuse.pauli("Z", w.n),
+                                        loss, E, g)
+        assert e.value.status == qfuse.QF_ERR_INVALID_ARG
+    finally:
+        qfuse.qf_circuit_destroy(h)
 
 
 def test_noalloc_step_refuses_batches_beyond_the_fixed_block():
