@@ -146,7 +146,22 @@ typedef struct {
                           re, im; the paper's memory-saving mode halves the
                           precision of stored states). Checkpoints, psi_M and
                           all arithmetic stay float64                           */
-  int32_t reserved[6];
+  int32_t catch_up;    /* fused round programs over several tiles (n > tile_bits):
+                          how a pass fills rounds when the qubits of a register
+                          group have done different numbers of rotations (the CZ
+                          chain lets a qubit run at most one layer ahead of its
+                          neighbours). 0 = the planner's choice (both rules and
+                          every qubit layout priced on a prefix of the circuit),
+                          1 = strict (catch-up rounds take only the tile's least
+                          advanced qubits), 2 = rising (the level cap rises until
+                          some group can take a round). Tuning knob of Sec. 3.2's
+                          fusion grouping; results do not depend on it          */
+  int32_t fwd_ctas;    /* fused forward round passes: CTAs per SM the pass kernel
+                          is budgeted for (registers per thread): 0 = automatic
+                          (3 when a pass has more tiles than two CTAs per SM
+                          hold, else 2), 2 or 3. Tuning knob; results do not
+                          depend on it                                          */
+  int32_t reserved[4];
 } qf_plan_opts;
 
 /* Summary of a plan (host-side numbers). */
@@ -177,6 +192,9 @@ typedef struct {
                               planner's layout; 0 for QF_ENC_STATE_IN circuits).
                               Inputs, observables and results use circuit
                               qubits; only exported programs show the layout  */
+  int32_t catch_up;        /* catch-up rule of the plan: 1 strict, 2 rising
+                              (0: single-tile or generic programs)             */
+  int32_t fwd_ctas;        /* as planned (opts->fwd_ctas)                      */
 } qf_plan_info_t;
 
 /* Create the hardware-efficient ansatz of the paper's benchmarks with the

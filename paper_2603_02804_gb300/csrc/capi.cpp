@@ -97,7 +97,8 @@ struct qf_circuit {
   // layout chosen by the planner for (tile_bits option, program option); kept
   // so that re-planning (e.g. qf_plan_fit's search) does not search again
   bool lay_valid = false;
-  int lay_tile_bits = 0, lay_generic = 0, lay_shift = 0, lay_strict = 0;
+  int lay_tile_bits = 0, lay_generic = 0, lay_catch_up = 0, lay_shift = 0, lay_strict = 0;
+  int fwd_ctas = 0;         // forward round passes: CTAs per SM of the kernel instance (0: automatic)
   int64_t batch = 0;
   qf::FusedPlan fp;
   qf::PerGatePlan gp;
@@ -625,7 +626,7 @@ qf_status fused_forward(qf_circuit* c, const DevTables& T, const Layout& L, cons
       loss_done = true;
     }
     if (c->tc) QF_CU(qf::launch_pass_tc(a, st));
-    else QF_CU(qf::launch_pass(false, a, st));
+    else QF_CU(qf::launch_pass(false, a, st, c->fwd_ctas));
     c->call_launches++;
   }
   prof_end(c, prof, 0, (int64_t)P.fwd.size(), st);
@@ -715,7 +716,7 @@ qf_status fused_backward(qf_circuit* c, const DevTables& T, const Layout& L, con
         x.pd.lam_src = qf::LAM_BUF;
       }
       if (c->tc && !bwd) QF_CU(qf::launch_pass_tc(x, st));
-      else QF_CU(qf::launch_pass(bwd, x, st));
+      else QF_CU(qf::launch_pass(bwd, x, st, c->fwd_ctas));
       c->call_launches++;
     }
     prof_end(c, prof, 1, (int64_t)P.a_sched.size(), st);
@@ -1146,6 +1147,9 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     return fail(QF_ERR_UNSUPPORTED, "complex128 runs on the fused path");
   if (o.precision == QF_PREC_C128 && o.tc_path)
     return fail(QF_ERR_UNSUPPORTED, "the tensor-core path is complex64 (3xTF32)");
+  if (o.catch_up < 0 || o.catch_up > 2) return fail(QF_ERR_INVALID_ARG, "catch_up must be 0, 1 or 2");
+  if (o.fwd_ctas != 0 && o.fwd_ctas != 2 && o.fwd_ctas != 3)
+    return fail(QF_ERR_INVALID_ARG, "fwd_ctas must be 0, 2 or 3");
   try {
     free_tables(c);
     c->planned = false;
@@ -1163,7 +1167,10 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
     req.mem_save = o.mem_save != 0;
     // given states arrive in circuit order: their plans keep the identity layout
     req.relabel = c->encoding == QF_ENC_RY_X;
-    if (c->lay_valid && c->lay_tile_bits == o.tile_bits && c->lay_generic == (int)req.generic) {
+    req.catch_up = o.catch_up == 1 ? 1 : o.catch_up == 2 ? 0 : -1;
+    c->fwd_ctas = o.fwd_ctas;
+    if (c->lay_valid && c->lay_tile_bits == o.tile_bits && c->lay_generic == (int)req.generic &&
+        c->lay_catch_up == o.catch_up) {
       req.qshift = c->lay_shift;
       req.strict = c->lay_strict;
     }
@@ -1173,6 +1180,7 @@ qf_status qf_plan(qf_circuit* c, const qf_plan_opts* opts, int64_t batch, size_t
       c->lay_valid = true;
       c->lay_tile_bits = o.tile_bits;
       c->lay_generic = (int)req.generic;
+      c->lay_catch_up = o.catch_up;
       c->lay_shift = c->fp.qshift;
       c->lay_strict = c->fp.strict;
       c->gp = qf::PerGatePlan();
@@ -1303,6 +1311,8 @@ qf_status qf_plan_info(const qf_circuit* c, qf_plan_info_t* info) {
     info->n_pass_slots = c->fp.n_aslots;
     info->tc_path = c->tc ? 1 : 0;
     info->qubit_shift = c->fp.qshift;
+    info->catch_up = c->fp.rounds && c->fp.n_eff > c->fp.K ? (c->fp.strict ? 1 : 2) : 0;
+    info->fwd_ctas = c->fwd_ctas;
     if (c->tc) info->launches_fwd += 1;  // the B-block table
     if (c->fp.ckpt_mode == 1) info->launches_bwd = (int32_t)c->fp.a_sched.size() + 1 + qf::g_reduce_stages(c->L.rows, 1);
   } else {

@@ -1803,7 +1803,7 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
+cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st, int fwd_ctas) {
   const int tiles_per_cta = kThreads >> (a.pd.K - kRegBits);
   const int64_t total_tiles = (int64_t)a.B << a.tps_log2;
   const int64_t grid = (total_tiles + tiles_per_cta - 1) / tiles_per_cta;
@@ -1825,7 +1825,7 @@ cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st) {
     // (fewer registers, more warps to hide latency across the waves)
     const int n_sm = device_sms();
     if (n_sm == 0) return cudaErrorInvalidDevice;
-    const bool three = rounds && grid > 2ll * n_sm;
+    const bool three = rounds && (fwd_ctas == 3 || (fwd_ctas == 0 && grid > 2ll * n_sm));
     if (rx && three) pass_kernel<false, true, true, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else if (rx) pass_kernel<false, true, true><<<(unsigned)grid, kThreads, smem, st>>>(a);
     else if (three) pass_kernel<false, true, false, 3><<<(unsigned)grid, kThreads, smem, st>>>(a);

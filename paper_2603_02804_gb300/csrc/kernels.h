@@ -136,7 +136,9 @@ inline int64_t g_reduce_scratch(int64_t B, int64_t tps, int64_t n_slots) {
 }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
-cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st);
+// fwd_ctas: CTAs per SM of the forward round-pass instance (0: 3 when the
+// grid exceeds two CTAs per SM, else 2); the adjoint always runs two.
+cudaError_t launch_pass(bool bwd, const PassArgs& a, cudaStream_t st, int fwd_ctas = 0);
 // Forward pass on the tensor cores (round programs, 12-qubit tiles).
 cudaError_t launch_pass_tc(const PassArgs& a, cudaStream_t st);
 // Per-round B blocks of the tensor-core path from the float64 fused 2x2s.

@@ -8,6 +8,8 @@
 // its rotations so every parameter gets its own gradient term (Sec. 3.3).
 #include "planner.h"
 
+#include <limits>
+
 #include <algorithm>
 #include <cstdlib>
 #include <functional>
@@ -723,12 +725,12 @@ Circuit shifted(const Circuit& c, int s) {
 // 128-byte runs of the state), so a chain whose end sits there is cut into two
 // segments by most tiles, and each pass's light cone is shallower. For
 // multi-tile round programs the planner therefore tries every cyclic shift
-// of the qubits and both catch-up rules on a prefix of the circuit (about
-// 16 layers of the ansatz; the plan's structure repeats) and keeps the
-// cheapest.
+// of the qubits and both catch-up rules (or the one req.catch_up names) on a
+// prefix of the circuit (about 16 layers of the ansatz; the plan's structure
+// repeats) and keeps the cheapest.
 void choose_layout(const Circuit& c, const PlanRequest& req, int* qshift, int* strict) {
   *qshift = 0;
-  *strict = 0;
+  *strict = req.catch_up > 0 ? 1 : 0;
   Circuit pre = c;
   pre.layers = -1;
   pre.gates.resize(std::min<size_t>(c.gates.size(), (size_t)64 * std::max(c.n, 1)));
@@ -738,12 +740,13 @@ void choose_layout(const Circuit& c, const PlanRequest& req, int* qshift, int* s
   rq.mem_save = false;
   const FusedPlan probe = plan_fused_with(pre, rq, false);
   if (!probe.rounds || probe.n_eff <= probe.K) return;
-  double best = plan_cost(probe);
+  double best = req.catch_up > 0 ? std::numeric_limits<double>::infinity() : plan_cost(probe);
   const int shifts = req.relabel && c.n >= 5 ? c.n : 1;
   for (int s = 0; s < shifts; ++s) {
     const Circuit cs = shifted(pre, s);
     for (int st = 0; st < 2; ++st) {
       if (s == 0 && st == 0) continue;  // the probe
+      if (req.catch_up >= 0 && st != req.catch_up) continue;
       const double cost = plan_cost(plan_fused_with(cs, rq, st != 0));
       if (cost < best) {
         best = cost;

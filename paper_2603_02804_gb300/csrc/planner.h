@@ -83,6 +83,7 @@ struct PlanRequest {
   bool relabel = true;   // the planner may simulate the qubits in a cyclically shifted order
   int qshift = -1;       // layout to use (-1: choose), as FusedPlan::qshift
   int strict = -1;       // catch-up rule to use (-1: choose), as FusedPlan::strict
+  int catch_up = -1;     // rule the layout search may choose (-1: either, 0: rising, 1: strict)
 };
 
 // Throws std::runtime_error with a message on invalid input.

@@ -45,7 +45,8 @@ class qf_plan_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("ckpt_layers", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("program", ctypes.c_int32), ("ckpt_mode", ctypes.c_int32),
                 ("mem_save", ctypes.c_int32), ("tc_path", ctypes.c_int32), ("no_host_staging", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("precision", ctypes.c_int32), ("catch_up", ctypes.c_int32), ("fwd_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class qf_plan_info_t(ctypes.Structure):
@@ -54,7 +55,7 @@ class qf_plan_info_t(ctypes.Structure):
         "n_fused_ops", "n_ckpt", "ckpt_layers", "launches_fwd", "launches_bwd")] + [
         ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64)] + [
         (name, ctypes.c_int32) for name in ("ckpt_mode", "mem_save", "n_pass_slots", "tc_path", "precision",
-                                            "qubit_shift")]
+                                            "qubit_shift", "catch_up", "fwd_ctas")]
 
 
 _vp = ctypes.c_void_p
@@ -185,9 +186,10 @@ def qf_circuit_destroy(handle: int) -> None:
 
 def qf_plan(handle: int, batch: int, path: int = QF_PATH_FUSED, tile_bits: int = 0, ckpt_layers: int = 0,
             host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False,
-            tc_path: bool = False, host_staging: bool = True, precision: int = QF_PREC_C64) -> int:
+            tc_path: bool = False, host_staging: bool = True, precision: int = QF_PREC_C64, catch_up: int = 0,
+            fwd_ctas: int = 0) -> int:
     o = qf_plan_opts(path, tile_bits, ckpt_layers, int(host_only), int(program), int(ckpt_mode), int(mem_save),
-                     int(tc_path), int(not host_staging), int(precision))
+                     int(tc_path), int(not host_staging), int(precision), int(catch_up), int(fwd_ctas))
     ws = _sz()
     _check(load().qf_plan(handle, ctypes.byref(o), batch, ctypes.byref(ws)))
     return ws.value
@@ -202,11 +204,12 @@ def qf_mem_model(k: float, d: float, b: float):
 
 def qf_plan_fit(handle: int, batch: int, mem_bytes: int, path: int = QF_PATH_FUSED, tile_bits: int = 0,
                 host_only: bool = False, program: int = 0, ckpt_mode: int = 0, mem_save: bool = False,
-                tc_path: bool = False, host_staging: bool = True, precision: int = QF_PREC_C64):
+                tc_path: bool = False, host_staging: bool = True, precision: int = QF_PREC_C64, catch_up: int = 0,
+                fwd_ctas: int = 0):
     """Plan with a checkpoint interval that fits mem_bytes (mode 0: the smallest;
     mode 1: the one with the smallest workspace): (c, workspace bytes)."""
     o = qf_plan_opts(path, tile_bits, 0, int(host_only), int(program), int(ckpt_mode), int(mem_save),
-                     int(tc_path), int(not host_staging), int(precision))
+                     int(tc_path), int(not host_staging), int(precision), int(catch_up), int(fwd_ctas))
     c = _i32()
     ws = _sz()
     _check(load().qf_plan_fit(handle, ctypes.byref(o), batch, mem_bytes, ctypes.byref(c), ctypes.byref(ws)))

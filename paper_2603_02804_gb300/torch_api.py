@@ -42,13 +42,16 @@ class Simulator:
     simulates complex128 states in float64 arithmetic; theta, x (and y) are
     then float64 (states: complex128) and the *64 entry points run.
     ``program=1`` forces generic steps where round programs would be used.
+    ``catch_up`` (0 planner's choice, 1 strict, 2 rising) and ``fwd_ctas``
+    (0 automatic, 2, 3) are tuning knobs that leave the results unchanged
+    (``autotune.Autotuner`` picks them).
     """
 
     def __init__(self, n: int, d: int = 0, batch: int = 1, *, entangler: str = "chain", path: str = "fused",
                  tile_bits: int = 0, ckpt_layers: int = 0, gates=None, n_params: int = 0, obs="Z",
                  device=None, ckpt_mode: int = 0, mem_save: bool = False, tc_path: bool = False,
                  encoding: str = "angles", host_staging: bool = True, precision: str = "complex64",
-                 program: int = 0):
+                 program: int = 0, catch_up: int = 0, fwd_ctas: int = 0):
         _cuda_check()
         self.device = torch.device(device or "cuda")
         self.encoding = encoding
@@ -67,7 +70,8 @@ class Simulator:
         with torch.cuda.device(self.device):
             self.ws_bytes = qfuse.qf_plan(self.handle, batch, _PATHS[path], tile_bits, ckpt_layers,
                                           ckpt_mode=ckpt_mode, mem_save=mem_save, tc_path=tc_path,
-                                          host_staging=host_staging, precision=_PREC[precision], program=program)
+                                          host_staging=host_staging, precision=_PREC[precision], program=program,
+                                          catch_up=catch_up, fwd_ctas=fwd_ctas)
             self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
         self.batch = batch
         self._fwd_id = 0
@@ -220,9 +224,10 @@ class Batch:
     """Many hardware-efficient-ansatz circuits trained in one persistent launch.
 
     specs: list of (n_qubits, n_layers, batch). tile_bits: None (12, the
-    whole state for n <= 12), an int, or a callable (n, d, B) -> K, e.g. an
-    autotuner's choice. Inputs and outputs are concatenated over circuits in
-    spec order (offsets from `layout()`).
+    whole state for n <= 12), an int, or a callable (n, d, B) returning K or
+    a dict of plan options (tile_bits, catch_up), e.g. an autotuner's choice.
+    Inputs and outputs are concatenated over circuits in spec order (offsets
+    from `layout()`).
     """
 
     def __init__(self, specs, loss: str = "sum", obs="Z", ckpt_layers: int = 0, tile_bits=None, device=None):
@@ -231,12 +236,16 @@ class Batch:
         self.specs = [(int(n), int(d), int(B)) for n, d, B in specs]
         self.loss = loss
         self.handles = []
+        self.plan_opts = []
         pauli_list = []
         for n, d, B in self.specs:
             h = qfuse.qf_hea_create(n, d, qfuse.QF_ENT_CHAIN)
             self.handles.append(h)
-            K = tile_bits(n, d, B) if callable(tile_bits) else (tile_bits or 0)
-            qfuse.qf_plan(h, B, qfuse.QF_PATH_FUSED, K, ckpt_layers, host_only=True)
+            cfg = tile_bits(n, d, B) if callable(tile_bits) else (tile_bits or 0)
+            cfg = cfg if isinstance(cfg, dict) else {"tile_bits": int(cfg)}
+            self.plan_opts.append({"tile_bits": int(cfg.get("tile_bits", 0)), "catch_up": int(cfg.get("catch_up", 0))})
+            qfuse.qf_plan(h, B, qfuse.QF_PATH_FUSED, self.plan_opts[-1]["tile_bits"], ckpt_layers, host_only=True,
+                          catch_up=self.plan_opts[-1]["catch_up"])
             pauli_list.append(qfuse.pauli(obs, n) if not isinstance(obs, qfuse.qf_pauli) else obs)
         with torch.cuda.device(self.device):
             self.handle, self.ws_bytes = qfuse.qf_batch_create(self.handles, [B for _, _, B in self.specs],

@@ -454,3 +454,49 @@ def test_cnot_gate_lists_match_oracle(seed):
         assert not rounds
     finally:
         qfuse.qf_circuit_destroy(h)
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+@pytest.mark.parametrize("n,d,K,ck", [(13, 3, 0, 1), (15, 3, 7, 1), (17, 2, 10, 0), (14, 4, 9, 2)])
+def test_forced_catch_up_rules_match_oracle(rule, n, d, K, ck):
+    """Both catch-up rules (strict, rising) that the autotuner may force give
+    programs whose expectations and gradients equal the oracle's."""
+    rng = np.random.default_rng(1500 + 7 * n + d + rule)
+    h = qfuse.qf_hea_create(n, d)
+    try:
+        qfuse.qf_plan(h, 2, tile_bits=K, ckpt_layers=ck, host_only=True, catch_up=rule)
+        info = qfuse.qf_plan_info(h)
+        assert info["catch_up"] == rule
+        P = 3 * n * d
+        theta = rng.uniform(0, 2 * np.pi, P).astype(np.float32).astype(np.float64)
+        x = rng.uniform(0, np.pi, (2, n)).astype(np.float32).astype(np.float64)
+        slot_kind = [orc.RY if (p % 3) == 1 else orc.RZ for p in range(P)]
+        interp_check(h, n, theta, x, "ZXY", list(range(P)), slot_kind, oracle_circ=orc.hea(n, d),
+                     kernel_order=True)
+    finally:
+        qfuse.qf_circuit_destroy(h)
+
+
+def test_tuning_options_are_validated_and_reported():
+    h = qfuse.qf_hea_create(14, 3)
+    try:
+        for kw in (dict(catch_up=3), dict(catch_up=-1), dict(fwd_ctas=1), dict(fwd_ctas=4)):
+            with pytest.raises(qfuse.QFError) as e:
+                qfuse.qf_plan(h, 4, host_only=True, **kw)
+            assert e.value.status == qfuse.QF_ERR_INVALID_ARG
+        qfuse.qf_plan(h, 4, host_only=True, fwd_ctas=3)
+        info = qfuse.qf_plan_info(h)
+        assert info["fwd_ctas"] == 3 and info["catch_up"] in (1, 2)
+        # the planner's choice is one of the two rules; forcing it reports it
+        for rule in (1, 2):
+            qfuse.qf_plan(h, 4, host_only=True, catch_up=rule)
+            assert qfuse.qf_plan_info(h)["catch_up"] == rule
+        # a single-tile circuit has no catch-up rounds
+        h2 = qfuse.qf_hea_create(10, 3)
+        try:
+            qfuse.qf_plan(h2, 4, host_only=True, catch_up=1)
+            assert qfuse.qf_plan_info(h2)["catch_up"] == 0
+        finally:
+            qfuse.qf_circuit_destroy(h2)
+    finally:
+        qfuse.qf_circuit_destroy(h)
