@@ -1,15 +1,21 @@
 """Benchmark: forward + gradient samples/s of the fused path on one GB300.
 
-Workload (default): hardware-efficient ansatz, 12 qubits, 20 layers of
-[RZ, RY, RZ on every qubit + CZ chain], RY(x) encoding, batch 256, MSE loss
-of <Z_0> against labels in {-1, +1}; one step = forward expectations + loss +
-adjoint gradients reduced per parameter (qf_train_step), inputs resident in
-HBM. Synthetic seeded inputs (theta ~ U[0, 2pi), x ~ U[0, pi]^12).
+Workload (default, ``hea20``): the large configuration of the paper's
+checkpointing experiment (Sec. 4.3, Table 1) with this build's ansatz:
+hardware-efficient ansatz, 20 qubits, 1,000 layers of [RZ, RY, RZ on every
+qubit + CZ chain] (60,000 parameters), RY(x) encoding, L = sum_b <Z_0>_b,
+1,000 samples trained in micro-batches, the checkpoint interval chosen from
+free device memory. One step = forward expectations + loss + adjoint gradients
+reduced per parameter (qf_train_step) over ONE micro-batch; the timed steps
+walk through the micro-batches of the epoch, inputs resident in HBM. Synthetic
+seeded inputs (theta ~ U[0, 2pi), x ~ U[0, pi]^20). ``--workload hea12`` (and
+the others) time the smaller configurations.
 
 Printed JSON line (rank 0): value = samples/s of the whole job, plus the
 unfused one-kernel-per-gate comparator on the same GPU, the roofline of the
 dominant kernel (fused adjoint pass), an end-to-end number through the
-host-buffer C-ABI call, the oracle's CPU throughput, and sampled SM clocks.
+host-buffer C-ABI call, the oracle's CPU throughput, the max-abs error of
+every timed path against the float64 oracle, and sampled SM clocks.
 
 ``--impl reference`` times the float64 CPU oracle instead (the reference
 arm): each step is the oracle's training step on a bounded sample of the
@@ -19,6 +25,8 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -31,22 +39,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2603_02804_gb300 import workloads  # noqa: E402
+from paper_2603_02804_gb300.record_traffic import TABLE as TRAFFIC_FILE, sources_sha  # noqa: E402
 
-WORKLOAD = "hea12"
+WORKLOAD = "hea20"
 FP32_LANES_PER_SM = 128
-N_SM = 152
 # GB300's dense FP64 rate (the complex128 path's denominator), TFLOP/s nominal
 FP64_TFLOPS_NOMINAL = 1.25
-# DRAM bytes (read + write) of one adjoint pass launch from an ncu capture of the current kernel build
-# (profiles/pass_kernels_hea12.md); None where no capture of the current build exists.
-ADJOINT_TRAFFIC_BYTES = {"hea12": 16_860_160}
+PARITY_TOL = 1e-5
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS) + ["mixed512", "paper_hea", "fusion_sweep"])
     ap.add_argument("--qubits", type=int, default=29, help="paper_hea: number of qubits")
@@ -54,8 +60,12 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="mixed512: 12-qubit tiles for every circuit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
+    ap.add_argument("--no-error-check", action="store_true", help="skip the oracle error of the timed paths")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
+    ap.add_argument("--micro-batch", type=int, default=0, help="hea20: samples per step (default 100)")
+    ap.add_argument("--ckpt", type=int, default=0, help="hea20: checkpoint interval (default: from memory)")
+    ap.add_argument("--pergate-samples", type=int, default=32, help="hea20: samples of the per-gate comparator step")
     ap.add_argument("--tc", action="store_true", help="forward rounds on the tensor cores (3xTF32)")
     ap.add_argument("--ckpt-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--mem-save", action="store_true", help="checkpoint mode 1 with bfloat16 pass outputs")
@@ -95,6 +105,15 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def fp32_peak_tflops(peaks):
+    """FP32 FMA peak of this GPU: SMs (queried) x 128 lanes x 2 flops x the
+    maximum SM clock (from the measured peaks file)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz"
+
+
 def algorithmic_flops(n, d, B):
     """Arithmetic per step in flops (a multiply or an add = 1, FMA = 2) of the
     round programs, per qubit and layer and per pair of amplitudes.
@@ -108,6 +127,30 @@ def algorithmic_flops(n, d, B):
     separately, as a per-gate program must, gives 36 and 96."""
     pairs = B * (1 << (n - 1))
     return n * d * pairs * 15, n * d * pairs * 40
+
+
+def per_gate_model_flops(n, d, B):
+    """The per-gate work model: 6 flops per amplitude per rotation forward,
+    16 per amplitude per rotation in the adjoint (un-apply psi 6, un-apply
+    lambda 6, Im<lambda|P|psi> about 4), 3 rotations per qubit and layer."""
+    amps = B * (1 << n)
+    return 3 * n * d * amps * 6, 3 * n * d * amps * 16
+
+
+def measured_traffic(key, amps):
+    """DRAM bytes (read + write) per launch of the dominant kernel, scaled to
+    `amps` amplitudes per launch from an ncu capture of the current sources;
+    (None, reason) when no capture of these sources exists."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, "no ncu capture recorded"
+    with open(TRAFFIC_FILE) as f:
+        tab = json.load(f)
+    e = tab.get(key)
+    if e is None:
+        return None, f"no ncu capture recorded for {key}"
+    if e.get("sources_sha") != sources_sha():
+        return None, "kernel sources changed since the ncu capture"
+    return e["bytes_per_amp"] * amps, e["case"]
 
 
 class ClockSampler:
@@ -157,37 +200,114 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(w, max_seconds=20.0):
-    """The float64 oracle's training step (forward, MSE/sum loss, adjoint
-    gradient) on the host cores, over a bounded sample of the workload."""
-    from oracle import oracle as orc
-    orc.build()
-    theta, x, y = workloads.make_inputs(w)
-    c = orc.hea(w.n, w.d)
-    threads = orc.max_threads()
-    # size the sample: time one sample first
-    t0 = time.perf_counter()
-    _oracle_step(orc, c, w, theta, x[:1], None if y is None else y[:1], threads)
-    one = time.perf_counter() - t0
-    per_thread = max(1, int(max_seconds / max(one, 1e-6)))
-    B = int(min(w.B, max(threads, per_thread * threads // 4)))
-    t0 = time.perf_counter()
-    _oracle_step(orc, c, w, theta, x[:B], None if y is None else y[:B], threads)
-    dt = time.perf_counter() - t0
-    return {"value": B / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
-            "sample": f"{B} of the {w.B} samples of one {w.name} training step (n={w.n}, d={w.d}), "
-                      f"float64, OpenMP over samples"}
-
-
-def _oracle_step(orc, c, w, theta, x, y, threads):
+# ---------------------------------------------------------------- the oracle (CPU)
+def _oracle_step(orc, c, w, theta, x, y, threads, B_total):
+    """The oracle's training step on samples x (of a batch of B_total)."""
     th = theta.astype(np.float64)
     xx = x.astype(np.float64)
     if w.loss == "mse":
         E = orc.expectation(c, th, xx, w.obs, threads=threads)
-        dLdE = orc.mse_dLdE(E, y) * len(E) / w.B
+        dLdE = orc.mse_dLdE(E, y) * len(E) / B_total
     else:
         dLdE = np.ones(len(xx))
     return orc.gradient(c, th, xx, w.obs, dLdE=dLdE, threads=threads)
+
+
+def _oracle_sample(w, theta, x, threads, target_s):
+    """Size a bounded sample of the workload for the oracle: whole samples when
+    one takes well under target_s, else one sample over the first d' of the d
+    layers (the oracle's cost is linear in the gate count, so one such step
+    counts as d'/d of a sample). Returns (circuit, d', samples per step)."""
+    from oracle import oracle as orc
+    d_cal = min(w.d, 2)
+    t0 = time.perf_counter()
+    _oracle_step(orc, orc.hea(w.n, d_cal), w, theta[:3 * w.n * d_cal], x[:1], None if w.loss != "mse" else
+                 np.ones(1, np.float32), threads, w.B)
+    per_layer = (time.perf_counter() - t0) / d_cal
+    if per_layer * w.d <= target_s:
+        d_s = w.d
+        par = max(1, threads) if w.B >= threads else 1
+        B_s = int(max(1, min(w.B, par * max(1, int(target_s / max(per_layer * w.d, 1e-6))))))
+    else:
+        d_s = int(max(1, min(w.d, target_s / max(per_layer, 1e-9))))
+        B_s = 1
+    return orc.hea(w.n, d_s), d_s, B_s
+
+
+def cpu_baseline(w, target_s=20.0):
+    """The float64 oracle's training step (forward, loss, adjoint gradient) on
+    the host cores, over a bounded sample of the workload (about target_s)."""
+    from oracle import oracle as orc
+    orc.build()
+    theta, x, y = workloads.make_inputs(w)
+    threads = orc.max_threads()
+    c, d_s, B_s = _oracle_sample(w, theta, x, threads, target_s)
+    t0 = time.perf_counter()
+    _oracle_step(orc, c, w, theta[:3 * w.n * d_s], x[:B_s], None if y is None else y[:B_s], threads, w.B)
+    dt = time.perf_counter() - t0
+    units = B_s * d_s / w.d
+    what = (f"{B_s} of the {w.B} samples" if d_s == w.d else
+            f"1 sample over the first {d_s} of the {w.d} layers (counted as {d_s}/{w.d} of a sample; the oracle's "
+            f"time is linear in the gate count)")
+    return {"value": units / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
+            "sample": f"{what} of the {w.name} workload (n={w.n}, d={w.d}), float64, OpenMP over "
+                      f"{'samples' if B_s >= threads else 'amplitudes'}", "seconds": dt}
+
+
+def _oracle_error_worker(n, d, theta, x0, obs, threads, q):
+    """(spawned process) E and dE/dtheta of one sample, full depth."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    t0 = time.perf_counter()
+    g, E = orc.gradient(orc.hea(n, d), theta.astype(np.float64), x0.astype(np.float64)[None, :], obs,
+                        per_sample=True, threads=threads)
+    q.put((float(E[0]), g[0], time.perf_counter() - t0))
+
+
+class OracleJob:
+    """The oracle's E and per-sample gradient of one sample at the benchmark's
+    full size, computed in a spawned process on the host cores while the GPU
+    legs run (the GPU work is launched asynchronously from one thread)."""
+
+    def __init__(self, w, theta, x0, threads):
+        from oracle import oracle as orc
+        orc.build()
+        ctx = mp.get_context("spawn")
+        self.q = ctx.Queue()
+        self.p = ctx.Process(target=_oracle_error_worker, args=(w.n, w.d, theta, x0, w.obs, threads, self.q),
+                             daemon=True)
+        self.p.start()
+        self.res = None
+        self.threads = threads
+
+    def result(self, timeout):
+        if self.res is None:
+            try:
+                self.res = self.q.get(timeout=timeout)
+            except Exception:
+                self.res = False
+            self.p.join(timeout=5)
+            if self.p.is_alive():
+                self.p.terminate()
+        return self.res or None
+
+
+def gpu_sample_grad(sim, theta, x0):
+    """E and dE/dtheta of one sample through the path's forward and backward."""
+    import torch
+    E = sim.forward(theta, x0)
+    g = sim.backward(theta, x0, torch.ones(1, dtype=torch.float64), per_sample=True)
+    torch.cuda.synchronize()
+    return float(E.cpu()[0]), g.cpu().numpy()[0]
+
+
+def error_entry(ref, got, what):
+    if ref is None or got is None:
+        return None
+    e_err = abs(got[0] - ref[0])
+    g_err = float(np.max(np.abs(got[1] - ref[1])))
+    return {"E": e_err, "grad": g_err, "within_1e-5": bool(e_err <= PARITY_TOL and g_err <= PARITY_TOL),
+            "sample": what}
 
 
 def run_reference(args, w):
@@ -197,33 +317,298 @@ def run_reference(args, w):
     from oracle import oracle as orc
     orc.build()
     theta, x, y = workloads.make_inputs(w)
-    c = orc.hea(w.n, w.d)
     threads = orc.max_threads()
-    t0 = time.perf_counter()
-    _oracle_step(orc, c, w, theta, x[:1], None if y is None else y[:1], threads)
-    one = time.perf_counter() - t0
     # each step: a bounded sample sized so that the whole run stays within minutes
-    budget = 120.0 / max(args.steps + args.warmup, 1)
-    Bs = int(max(1, min(w.B, threads * max(1, int(budget / max(one, 1e-6))))))
+    target = min(10.0, 150.0 / max(args.steps + args.warmup, 1))
+    c, d_s, B_s = _oracle_sample(w, theta, x, threads, target)
+    th = theta[:3 * w.n * d_s]
     for _ in range(args.warmup):
-        _oracle_step(orc, c, w, theta, x[:Bs], None if y is None else y[:Bs], threads)
+        _oracle_step(orc, c, w, th, x[:B_s], None if y is None else y[:B_s], threads, w.B)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _oracle_step(orc, c, w, theta, x[:Bs], None if y is None else y[:Bs], threads)
+        _oracle_step(orc, c, w, th, x[:B_s], None if y is None else y[:B_s], threads, w.B)
     dt = time.perf_counter() - t0
-    value = Bs * args.steps / dt
+    units = B_s * d_s / w.d
+    value = units * args.steps / dt
+    what = (f"{B_s} samples of the {w.name} batch per step" if d_s == w.d else
+            f"1 sample over the first {d_s} of the {w.d} layers per step, counted as {d_s}/{w.d} of a sample "
+            f"(the oracle's time is linear in the gate count)")
     line = {
         "impl": "reference", "metric": "fwd+grad samples/s", "value": value, "unit": "samples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
-        "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} batch={w.B} loss={w.loss} obs=Z0",
-                   "sample_per_step": Bs},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{Bs} samples of the {w.name} batch per step"},
+        "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} [RZ,RY,RZ + CZ chain], RY(x) encoding, "
+                               f"loss={w.loss}, obs=Z0", "sample_per_step": what},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle", "sample": what},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- large workload
+def run_large(args, w):
+    """n=20, d=1000, 1000 samples: one step = one micro-batch of mb samples
+    (qf_train_step), the checkpoint interval chosen from free memory."""
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2603_02804_gb300 import build as qbuild
+    if rank == 0:
+        qbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2603_02804_gb300 import dp, qfuse
+    from paper_2603_02804_gb300.torch_api import Simulator
+
+    if args.warmup < 3:
+        args.warmup = 3
+    peaks, peak_src = load_peaks()
+    theta_np, x_np, _ = workloads.make_inputs(w)
+    if rank > 0:  # weak scaling: every rank trains its own samples
+        x_np = workloads.draw_x(w.B, w.n, w.seeds[1] + 1000 * rank)
+    N = w.B
+    mb = min(args.micro_batch or int(w.extra.get("micro_batch", 100)), N)
+    n_mb = (N + mb - 1) // mb
+    solo = rank == 0 and world == 1
+    ncores = os.cpu_count() or 1
+    job = None
+    if solo and not args.no_error_check:
+        job = OracleJob(w, theta_np, x_np[0], max(1, ncores - 4))
+
+    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
+    free, _ = torch.cuda.mem_get_info()
+    h = qfuse.qf_hea_create(w.n, w.d)
+    if args.ckpt:
+        c = args.ckpt
+    else:
+        c, _ = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True, **opts)
+    qfuse.qf_circuit_destroy(h)
+    sim = Simulator(w.n, w.d, mb, ckpt_layers=c, obs=w.obs, **opts)
+    dev = torch.device("cuda", local)
+    theta = torch.from_numpy(theta_np).to(dev)
+    xs = [torch.from_numpy(np.ascontiguousarray(x_np[i:i + mb])).to(dev) for i in range(0, N, mb)]
+    out = sim.device_outputs()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s, k, o):
+        _, _, g = s.train_step(theta, xs[k % len(xs)], loss=w.loss, out=o)
+        if world > 1:
+            dp.allreduce_sum(g)  # data-parallel gradient sum over ranks (NCCL)
+
+    for k in range(args.warmup):
+        step(sim, k, out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            step(sim, k, out)
+            launches += sim.launches()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t = torch.tensor([t0.elapsed_time(t1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms = total_ms / args.steps
+    timed_samples = sum(xs[k % len(xs)].shape[0] for k in range(args.steps))
+    value = timed_samples * world / (total_ms / 1e3)
+
+    # ---- pass-kernel timings (CUDA events around every pass launch) of 2 more steps
+    K_p = 2
+    qfuse.qf_profile(sim.handle, True)
+    qfuse.qf_profile_read(sim.handle)
+    for k in range(K_p):
+        step(sim, k, out)
+    prof = qfuse.qf_profile_read(sim.handle)
+    qfuse.qf_profile(sim.handle, False)
+    info = sim.info()
+    passes = info["n_passes"]
+    bwd_launch_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
+    fwd_launch_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
+    fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, mb)
+    pg_fwd, pg_bwd = per_gate_model_flops(w.n, w.d, mb)
+    fp32_peak, peak_what = fp32_peak_tflops(peaks)
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    amps = mb * (1 << w.n)
+    # algorithmic bytes of one adjoint launch: psi and lambda read and written
+    # (32 B/amp), plus the re-anchor reads of the stored checkpoints (8 B/amp
+    # each; n_ckpt - 1 of them over the whole adjoint), averaged per launch
+    bwd_bytes = amps * (32 * passes + 8 * max(info["n_ckpt"] - 1, 0)) / passes
+    achieved = bwd_fl / passes / (bwd_launch_ms / 1e3) / 1e12
+    traffic, traffic_note = measured_traffic(w.name, amps) if not (args.tc or args.ckpt_mode) else (None, "variant")
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+        "traffic": traffic, "traffic_note": traffic_note,
+        "kernel": "pass_kernel<true> (fused adjoint pass)", "peak_source": f"{peak_what} (derived: FP32 FMA peak)",
+        "bwd_kernel_ms": bwd_launch_ms, "fwd_kernel_ms": fwd_launch_ms,
+        "flops_model": "executed arithmetic of the round programs: 15 (forward) and 40 (adjoint) flops per "
+                       "amplitude pair, qubit and layer",
+        "per_gate_flops_model": {"achieved": pg_bwd / passes / (bwd_launch_ms / 1e3) / 1e12,
+                                 "frac": pg_bwd / passes / (bwd_launch_ms / 1e3) / 1e12 / fp32_peak,
+                                 "note": "16 flops per amplitude per rotation (6 + 6 un-apply, 4 gradient), "
+                                         "as a per-gate program counts them"},
+        "hbm": {"achieved_gbs": bwd_bytes / (bwd_launch_ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
+                "frac": bwd_bytes / (bwd_launch_ms / 1e3) / 1e9 / hbm_gbs, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": bwd_bytes},
+        "fwd_kernel": {"achieved": fwd_fl / passes / (fwd_launch_ms / 1e3) / 1e12,
+                       "hbm_gbs": amps * 16 / (fwd_launch_ms / 1e3) / 1e9},
+        "timing": f"CUDA events on the launching stream around every pass launch of {K_p} steps run after the "
+                  f"timed ones ({prof['bwd_launches']} adjoint and {prof['fwd_launches']} forward launches)",
+    }
+
+    # ---- end to end through the host-buffer call (pinned host memory)
+    K_e = max(1, min(args.steps, 3))
+    th_h = torch.from_numpy(theta_np).pin_memory()
+    xs_h = [torch.from_numpy(np.ascontiguousarray(x_np[i:i + mb])).pin_memory() for i in range(0, N, mb)]
+    outs_h = sim.host_outputs()
+    sim.train_step_host(th_h, xs_h[0], loss=w.loss, out=outs_h)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for k in range(K_e):
+        sim.train_step_host(th_h, xs_h[k % len(xs_h)], loss=w.loss, out=outs_h)
+    e_dt = time.perf_counter() - e0
+    e2e = {"value": mb * world * K_e / e_dt, "unit": "samples/s", "steps": K_e,
+           "h2d_bytes_per_step": theta_np.nbytes + xs_h[0].numel() * 4,
+           "d2h_bytes_per_step": 8 + 8 * mb + 8 * w.n_params}
+
+    # ---- error of each timed path against the oracle (sample 0, full depth)
+    x0 = xs[0][:1].contiguous()
+    got = {"fused": gpu_sample_grad(sim, theta, x0)} if job else {}
+    ws_gb = sim.ws_bytes / 1e9
+    del sim, out
+    torch.cuda.empty_cache()
+
+    # ---- unfused per-gate comparator on a subset of samples
+    per_gate = None
+    if not args.no_per_gate and solo:
+        B_pg = min(args.pergate_samples, mb)
+        warm = Simulator(w.n, 2, B_pg, path="per_gate", obs=w.obs)
+        warm.train_step(theta[:3 * w.n * 2], xs[0][:B_pg], loss=w.loss)
+        del warm
+        pg = Simulator(w.n, w.d, B_pg, path="per_gate", obs=w.obs)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pg.train_step(theta, xs[0][:B_pg], loss=w.loss)
+        p1.record(stream)
+        pg_launches = pg.launches()
+        torch.cuda.synchronize()
+        pg_ms = p0.elapsed_time(p1)
+        per_gate = {"value": B_pg / (pg_ms / 1e3), "unit": "samples/s", "ms_per_step": pg_ms,
+                    "gpu_launches_per_step": pg_launches,
+                    "sample": f"1 step of {B_pg} samples (state {B_pg * 8 * (1 << w.n) / 1e6:.0f} MB, larger than L2), "
+                              f"full depth"}
+        if job:
+            got["per_gate"] = gpu_sample_grad(pg, theta, x0)
+        del pg
+        torch.cuda.empty_cache()
+
+    # ---- variants: tensor-core forward, checkpoint mode 1, bfloat16 storage
+    variants = None
+    if not args.no_variants and solo:
+        variants = {}
+        for name, kw in (("tc_path", dict(tc_path=True)), ("ckpt_mode_1", dict(ckpt_mode=1)),
+                         ("ckpt_mode_1_mem_save", dict(ckpt_mode=1, mem_save=True))):
+            if kw == {k: v for k, v in opts.items() if v}:
+                continue
+            free, _ = torch.cuda.mem_get_info()
+            h = qfuse.qf_hea_create(w.n, w.d)
+            cv, _ = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True, **kw)
+            qfuse.qf_circuit_destroy(h)
+            vs = Simulator(w.n, w.d, mb, ckpt_layers=cv, obs=w.obs, **kw)
+            vo = vs.device_outputs()
+            step(vs, 0, vo)
+            torch.cuda.synchronize()
+            K_v = 2
+            qfuse.qf_profile(vs.handle, True)
+            qfuse.qf_profile_read(vs.handle)
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for k in range(K_v):
+                step(vs, k + 1, vo)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vp = qfuse.qf_profile_read(vs.handle)
+            v_ms = v0.elapsed_time(v1) / K_v
+            variants[name] = {"value": mb / (v_ms / 1e3), "unit": "samples/s", "ms_per_step": v_ms,
+                              "ckpt_layers": cv, "workspace_gb": vs.ws_bytes / 1e9,
+                              "fwd_ms_per_step": vp["fwd_ms"] / K_v, "bwd_ms_per_step": vp["bwd_ms"] / K_v,
+                              "device_status": qfuse.qf_device_status(stream)}
+            if job:
+                got[name] = gpu_sample_grad(vs, theta, x0)
+            del vs, vo
+            torch.cuda.empty_cache()
+
+    cpu = None
+    ref = None
+    if job:
+        r = job.result(timeout=600)
+        if r:
+            ref = (r[0], r[1])
+    errors = None
+    if job:
+        what = f"sample 0 of micro-batch 0, E and dE/dtheta (all {w.n_params}) vs the float64 oracle, full depth"
+        errors = {k: error_entry(ref, v, what) for k, v in got.items()}
+        if ref is None:
+            errors["note"] = "oracle did not finish in time"
+        else:
+            errors["oracle_seconds"] = r[2]
+            errors["oracle_threads"] = job.threads
+        if variants:
+            for k in variants:
+                variants[k]["error"] = errors.get(k)
+        if per_gate:
+            per_gate["error"] = errors.get("per_gate")
+    if solo and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": "fwd+grad samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded): theta~U[0,2pi), x~U[0,pi]^n",
+            "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d} [RZ,RY,RZ + CZ chain] ({w.n_params} params), "
+                                   f"RY(x) encoding, L=sum E, obs=Z0, complex64; {N} samples/GPU per epoch in "
+                                   f"micro-batches of {mb}, one step = one micro-batch; checkpoint mode "
+                                   f"{'A (re-run)' if args.ckpt_mode else 'B (reverse + re-anchor)'}, "
+                                   f"interval c={c} layers from memory",
+                       "micro_batch": mb, "micro_batches_per_epoch": n_mb, "ckpt_layers": c,
+                       "ckpt_mode": args.ckpt_mode, "mem_save": bool(args.mem_save), "tc_path": bool(args.tc),
+                       "passes_per_direction": passes, "tile_bits": info["tile_bits"], "workspace_gb": ws_gb,
+                       "parallelism": f"dp{world}",
+                       "l2": f"inputs larger than L2 (state of a micro-batch {amps * 8 / 1e6:.0f} MB)",
+                       "fwd_ms_per_step": prof["fwd_ms"] / K_p, "bwd_ms_per_step": prof["bwd_ms"] / K_p},
+            "error_vs_oracle": errors,
+            "per_gate": per_gate,
+            "speedup_vs_per_gate": (value / per_gate["value"]) if per_gate else None,
+            "variants": variants,
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "peaks": {"source": peak_src, "hbm_gbs": hbm_gbs},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -243,7 +628,7 @@ def run_mixed(args):
     if args.circuits:
         circs = circs[:args.circuits]  # a subset of the same draw (profiling cases)
     specs = [(c.n, c.d, c.B) for c in circs]
-    tuner = Autotuner(path=os.environ.get("QF_AUTOTUNE_CACHE"))  # JSON cache file, or in memory only
+    tuner = Autotuner(path=os.environ.get("QF_AUTOTUNE_CACHE"), kind="batch")  # JSON cache file, or in memory
     t0 = time.perf_counter()
     bt = Batch(specs, loss="sum", tile_bits=None if args.no_autotune else tuner)
     tune_s = time.perf_counter() - t0
@@ -289,7 +674,7 @@ def run_mixed(args):
     e_dt = (time.perf_counter() - e0) / max(1, args.steps // 4)
     fl = sum(sum(algorithmic_flops(n, d, B)) for n, d, B in specs)
     ms = total_ms / args.steps
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    fp32_peak, peak_what = fp32_peak_tflops(peaks)
     achieved = fl / (ms / 1e3) / 1e12
     line = {
         "metric": "fwd+grad samples/s", "value": bt.n_samples * world / (ms / 1e3), "unit": "samples/s",
@@ -302,7 +687,7 @@ def run_mixed(args):
         "graph": {"value": bt.n_samples * world * args.steps / (graph_ms / 1e3), "unit": "samples/s",
                   "ms_per_step": graph_ms / args.steps},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": None, "peak_source": peak_what,
                      "kernel": "batch_kernel (whole step: prep + persistent + reductions)"},
         "e2e": {"value": bt.n_samples * world / e_dt, "unit": "samples/s",
                 "h2d_bytes_per_step": theta.numel() * 4 + x.numel() * 4,
@@ -310,85 +695,6 @@ def run_mixed(args):
         "gpu_launches": 4 * args.steps,
         "per_gate": None, "cpu_baseline": None, "clocks": clk.summary(),
         "autotune": tuner.cache,
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_epoch(args, w):
-    """Large workload (n=20, d=1000, 1000 samples): micro-batches of `mb`
-    samples with the checkpoint interval chosen from free HBM; one step = one
-    epoch over all samples (gradients summed over micro-batches)."""
-    import torch
-    from paper_2603_02804_gb300 import build as qbuild
-    from paper_2603_02804_gb300 import qfuse
-    from paper_2603_02804_gb300.torch_api import Simulator
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    qbuild.build()
-    peaks, peak_src = load_peaks()
-    theta_np, x_np, _ = workloads.make_inputs(w)
-    N = w.B
-    mb = int(w.extra.get("micro_batch", 100))
-    free, _ = torch.cuda.mem_get_info()
-    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
-    h = qfuse.qf_hea_create(w.n, w.d)
-    c, ws_need = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True, **opts)
-    qfuse.qf_circuit_destroy(h)
-    sim = Simulator(w.n, w.d, mb, ckpt_layers=c, obs=w.obs, **opts)
-    theta = torch.from_numpy(theta_np).cuda()
-    xs = [torch.from_numpy(x_np[i:i + mb]).cuda() for i in range(0, N, mb)]
-    grad = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def epoch():
-        grad.zero_()
-        for xb in xs:
-            _, _, g = sim.train_step(theta, xb, loss=w.loss)
-            grad.add_(g)
-
-    sim.train_step(theta, xs[0], loss=w.loss)
-    epoch()  # warm every kernel of the timed epoch (library and torch)
-    torch.cuda.synchronize()
-    qfuse.qf_profile(sim.handle, True)
-    qfuse.qf_profile_read(sim.handle)
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        t0.record(stream)
-        for _ in range(args.steps):
-            epoch()
-        t1.record(stream)
-        torch.cuda.synchronize()
-    prof = qfuse.qf_profile_read(sim.handle)
-    ms = t0.elapsed_time(t1) / args.steps
-    info = sim.info()
-    fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, mb)
-    bwd_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    # the adjoint phase's flops over its time (checkpoint mode 1: it also re-runs the forward)
-    phase_fl = (bwd_fl + (fwd_fl if args.ckpt_mode == 1 else 0)) * len(xs) * args.steps
-    ach = phase_fl / (prof["bwd_ms"] / 1e3) / 1e12
-    bytes_bwd = 32 * mb * (1 << w.n)  # read + write psi and lambda per adjoint pass
-    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
-    line = {
-        "metric": "fwd+grad samples/s", "value": N * world / (ms / 1e3), "unit": "samples/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": f"{w.name}: HEA n={w.n} d={w.d}, {N} samples per step (epoch) in micro-batches "
-                               f"of {mb}, L=sum E, obs=Z0", "ckpt_layers_from_memory": c,
-                   "ckpt_mode": args.ckpt_mode, "mem_save": bool(args.mem_save), "tc_path": bool(args.tc),
-                   "fwd_ms_per_step": prof["fwd_ms"] / args.steps, "bwd_ms_per_step": prof["bwd_ms"] / args.steps,
-                   "workspace_gb": sim.ws_bytes / 1e9, "passes": info["n_passes"],
-                   "l2": "inputs larger than L2"},
-        "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                     "traffic": None, "kernel": ("pass_kernel<true,true> (fused adjoint)" if args.ckpt_mode == 0 else
-                                                 "adjoint phase: pass_kernel<true,true> and forward re-runs"),
-                     "bwd_pass_ms": bwd_ms,
-                     "hbm": {"achieved_gbs": bytes_bwd / (bwd_ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
-                             "frac": bytes_bwd / (bwd_ms / 1e3) / 1e9 / hbm_gbs, "peak_source": peak_src}},
-        "gpu_launches": None, "per_gate": None, "cpu_baseline": None, "e2e": None, "clocks": clk.summary(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -492,7 +798,6 @@ def run_fusion_sweep(args):
     20-qubit state, batch 100, random initial states, forward alone and forward + adjoint, as m grows."""
     import torch
     from paper_2603_02804_gb300 import build as qbuild
-    from paper_2603_02804_gb300 import qfuse
     from paper_2603_02804_gb300.torch_api import Simulator
 
     rank, world, local = dist_env()
@@ -542,19 +847,10 @@ def run_fusion_sweep(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.workload == "paper_hea":
-        return run_paper(args)
-    if args.workload == "fusion_sweep":
-        return run_fusion_sweep(args)
-    if args.workload == "mixed512":
-        return run_mixed(args)
-    if args.workload == "hea20":
-        return run_epoch(args, override(workloads.WORKLOADS["hea20"], args))
-    w = override(workloads.WORKLOADS[args.workload], args)
-    if args.impl == "reference":
-        return run_reference(args, w)
+# ---------------------------------------------------------------- small workloads
+def run_small(args, w):
+    """Workloads whose batch is one step (hea12, hea16, tiny): qf_train_step
+    on the whole batch, L2 flushed between the timed steps."""
     if args.warmup < 3:
         args.warmup = 3
 
@@ -597,6 +893,31 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     from paper_2603_02804_gb300 import dp
+
+    # the oracle's per-sample E and dE/dtheta of every sample (float64)
+    ref = None
+    solo = rank == 0 and world == 1
+    if solo and not args.no_error_check:
+        from oracle import oracle as orc
+        orc.build()
+        t32, x32, _ = workloads.make_inputs(w)
+        g_r, E_r = orc.gradient(orc.hea(w.n, w.d), t32.astype(np.float64), x32.astype(np.float64), w.obs,
+                                per_sample=True)
+        ref = (E_r, g_r)
+
+    def path_error(s, inp=None):
+        """Max-abs error of E and of every per-sample gradient dE_b/dtheta
+        against the oracle, over the whole batch."""
+        if ref is None:
+            return None
+        th_, x_ = (inp[0], inp[1]) if inp is not None else (theta, x)
+        E = s.forward(th_, x_)
+        g = s.backward(th_, x_, torch.ones(x_.shape[0], dtype=torch.float64), per_sample=True)
+        torch.cuda.synchronize()
+        e_err = float(np.max(np.abs(E.cpu().numpy() - ref[0])))
+        g_err = float(np.max(np.abs(g.cpu().numpy() - ref[1])))
+        return {"E": e_err, "grad": g_err, "within_1e-5": bool(e_err <= PARITY_TOL and g_err <= PARITY_TOL),
+                "sample": f"all {x_.shape[0]} samples, E and per-sample dE/dtheta vs the float64 oracle"}
 
     def step(s, inp=None):
         th_, x_, y_ = inp if inp is not None else (theta, x, y)
@@ -654,6 +975,7 @@ def main():
     total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = w.B * world * args.steps / (total_ms / 1e3)
+    main_error = path_error(sim) if not c128 else None
 
     # ---- roofline of the dominant kernel: the fused adjoint pass kernel
     fwd_fl, bwd_fl = algorithmic_flops(w.n, w.d, w.B)
@@ -661,17 +983,17 @@ def main():
     bwd_launch_ms = prof["bwd_ms"] / max(prof["bwd_launches"], 1)
     fwd_launch_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
     bwd_per_launch = bwd_fl / info["n_passes"]
-    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    fp32_peak, peak_what = fp32_peak_tflops(peaks)
     alu_peak = FP64_TFLOPS_NOMINAL if c128 else fp32_peak
     achieved = bwd_per_launch / (bwd_launch_ms / 1e3) / 1e12
+    amps_launch = w.B * (1 << w.n)
+    traffic, traffic_note = (measured_traffic(w.name, amps_launch) if not (args.tc or args.ckpt_mode or c128)
+                             else (None, "variant"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak,
-                "traffic": ADJOINT_TRAFFIC_BYTES.get(w.name) if not (args.tc or args.ckpt_mode or c128) else None,
+                "frac": achieved / alu_peak, "traffic": traffic, "traffic_note": traffic_note,
                 "kernel": ("pass64_kernel<true> (fused adjoint, complex128)" if c128
                            else "pass_kernel<true> (fused adjoint)"),
-                "peak_source": ("GB300 dense FP64, nominal" if c128 else
-                                f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz"),
+                "peak_source": ("GB300 dense FP64, nominal" if c128 else f"{peak_what} (derived: FP32 FMA peak)"),
                 "fwd_kernel": {"achieved": (fwd_fl / info["n_passes"]) / (fwd_launch_ms / 1e3) / 1e12,
                                "ms": fwd_launch_ms},
                 "bwd_kernel_ms": bwd_launch_ms,
@@ -714,7 +1036,8 @@ def main():
             vp = profiled(vs, K, inp)
             variants[name] = {"value": w.B * K / (v_ms / 1e3), "unit": "samples/s", "ms_per_step": v_ms / K,
                               "fwd_ms_per_step": vp["fwd_ms"] / K, "bwd_ms_per_step": vp["bwd_ms"] / K,
-                              "device_status": qfuse.qf_device_status(stream)}
+                              "device_status": qfuse.qf_device_status(stream),
+                              "error": path_error(vs, inp)}
             if v128:
                 vi = vs.info()
                 f_fl, b_fl = algorithmic_flops(w.n, w.d, w.B)
@@ -768,7 +1091,8 @@ def main():
         torch.cuda.synchronize()
         pg_ms, pg_launches = timed(pg, args.steps)
         per_gate = {"value": w.B * world * args.steps / (pg_ms / 1e3), "unit": "samples/s",
-                    "ms_per_step": pg_ms / args.steps, "gpu_launches_per_step": pg_launches // args.steps}
+                    "ms_per_step": pg_ms / args.steps, "gpu_launches_per_step": pg_launches // args.steps,
+                    "error": path_error(pg)}
         del pg
 
     # ---- end to end through the host-buffer call (pinned host memory)
@@ -789,7 +1113,7 @@ def main():
            "d2h_bytes_per_step": d2h}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if solo and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
 
     if rank == 0:
@@ -805,6 +1129,7 @@ def main():
                        "precision": args.precision,
                        "ckpt_layers": info["ckpt_layers"], "parallelism": f"dp{world}",
                        "l2": "flushed between timed steps (256 MiB write)"},
+            "error_vs_oracle": main_error,
             "per_gate": per_gate,
             "speedup_vs_per_gate": (value / per_gate["value"]) if per_gate else None,
             "variants": variants,
@@ -822,6 +1147,22 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    args = parse()
+    if args.workload == "paper_hea":
+        return run_paper(args)
+    if args.workload == "fusion_sweep":
+        return run_fusion_sweep(args)
+    if args.workload == "mixed512":
+        return run_mixed(args)
+    w = override(workloads.WORKLOADS[args.workload], args)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if args.workload == "hea20":
+        return run_large(args, w)
+    return run_small(args, w)
 
 
 if __name__ == "__main__":

@@ -96,3 +96,28 @@ def test_mixed512_full_launch_sampled():
         t0, t1 = bt.theta_off[i], bt.theta_off[i + 1]
         assert np.max(np.abs(E[s0:s1] - Er)) < TOL, (i, c.n, c.d, c.B)
         assert np.max(np.abs(g[t0:t1] - gr)) < TOL, (i, c.n, c.d, c.B)
+
+
+def test_mixed512_heaviest_circuits_against_oracle():
+    """The most expensive circuits of the 512-circuit workload (n = 18, the
+    largest depths; most of its flops are n >= 17 circuits), launched
+    together as one persistent batch with the same plans and tile widths as
+    the full launch, one sample each (their first), every expectation and
+    gradient compared with the oracle."""
+    circs = workloads.mixed_circuits(512)
+    heavy = sorted(circs, key=lambda c: -(1 << c.n) * c.d * c.n)[:4]
+    assert all(c.n == 18 for c in heavy) and min(c.d for c in heavy) >= 150
+    specs = [(c.n, c.d, 1) for c in heavy]
+    bt = Batch(specs, loss="sum")
+    lv, E, g = bt.train_step(cat([c.theta for c in heavy]), cat([c.x[:1] for c in heavy]))
+    torch.cuda.synchronize()
+    E, g = E.cpu().numpy(), g.cpu().numpy()
+    total = 0.0
+    for i, c in enumerate(heavy):
+        gr, Er = orc.gradient(orc.hea(c.n, c.d), f64(c.theta), f64(c.x[:1]), "Z")
+        s0, s1 = bt.sample_off[i], bt.sample_off[i + 1]
+        t0, t1 = bt.theta_off[i], bt.theta_off[i + 1]
+        assert np.max(np.abs(E[s0:s1] - Er)) < TOL, (c.cid, c.n, c.d)
+        assert np.max(np.abs(g[t0:t1] - gr)) < TOL, (c.cid, c.n, c.d)
+        total += Er.sum()
+    assert abs(lv.item() - total) < TOL * len(heavy)
