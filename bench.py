@@ -234,13 +234,13 @@ def _oracle_sample(w, theta, x, threads, target_s):
     return orc.hea(w.n, d_s), d_s, B_s
 
 
-def cpu_baseline(w, target_s=20.0):
+def cpu_baseline(w, target_s=20.0, threads=0):
     """The float64 oracle's training step (forward, loss, adjoint gradient) on
     the host cores, over a bounded sample of the workload (about target_s)."""
     from oracle import oracle as orc
     orc.build()
     theta, x, y = workloads.make_inputs(w)
-    threads = orc.max_threads()
+    threads = threads or orc.max_threads()
     c, d_s, B_s = _oracle_sample(w, theta, x, threads, target_s)
     t0 = time.perf_counter()
     _oracle_step(orc, c, w, theta[:3 * w.n * d_s], x[:B_s], None if y is None else y[:B_s], threads, w.B)
@@ -252,6 +252,15 @@ def cpu_baseline(w, target_s=20.0):
     return {"value": units / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
             "sample": f"{what} of the {w.name} workload (n={w.n}, d={w.d}), float64, OpenMP over "
                       f"{'samples' if B_s >= threads else 'amplitudes'}", "seconds": dt}
+
+
+def cpu_baseline_spawned(w, threads):
+    """cpu_baseline in a spawned process: a process holding a CUDA context and
+    torch's threads slows the oracle's OpenMP threads down, so the oracle is
+    timed in a clean process, on `threads` of the host cores."""
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        return pool.apply(cpu_baseline, (w, 20.0, threads))
 
 
 def _oracle_error_worker(n, d, theta, x0, obs, threads, q):
@@ -575,7 +584,7 @@ def run_large(args, w):
         if per_gate:
             per_gate["error"] = errors.get("per_gate")
     if solo and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        cpu = cpu_baseline_spawned(w, max(1, ncores - 2))
 
     if rank == 0:
         line = {
@@ -1114,7 +1123,7 @@ def run_small(args, w):
 
     cpu = None
     if solo and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        cpu = cpu_baseline_spawned(w, max(1, (os.cpu_count() or 1) - 2))
 
     if rank == 0:
         line = {

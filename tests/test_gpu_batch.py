@@ -7,6 +7,7 @@ from oracle import oracle as orc
 from paper_2603_02804_gb300 import build as qbuild
 from paper_2603_02804_gb300 import workloads
 from paper_2603_02804_gb300.torch_api import Batch
+from tests import oracle_proc
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -114,7 +115,7 @@ def test_mixed512_heaviest_circuits_against_oracle():
     E, g = E.cpu().numpy(), g.cpu().numpy()
     total = 0.0
     for i, c in enumerate(heavy):
-        gr, Er = orc.gradient(orc.hea(c.n, c.d), f64(c.theta), f64(c.x[:1]), "Z")
+        gr, Er = oracle_proc.call("gradient", orc.hea(c.n, c.d), f64(c.theta), f64(c.x[:1]), "Z")
         s0, s1 = bt.sample_off[i], bt.sample_off[i + 1]
         t0, t1 = bt.theta_off[i], bt.theta_off[i + 1]
         assert np.max(np.abs(E[s0:s1] - Er)) < TOL, (c.cid, c.n, c.d)

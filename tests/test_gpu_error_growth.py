@@ -1,6 +1,7 @@
 """Error of the float32 fused path against the float64 oracle as depth grows
 beyond 100 layers: n = 12 with checkpoints every 10 layers, and n = 20 through
-the plan of the large workload's epoch. Reported, with a loose bound: the
+the plan of the large workload's epoch (the n = 20 oracle runs in a spawned
+worker process). Reported, with a loose bound: the
 parity bar of 1e-5 applies up to 100 layers."""
 import numpy as np
 import pytest
@@ -10,6 +11,7 @@ from oracle import oracle as orc
 from paper_2603_02804_gb300 import build as qbuild
 from paper_2603_02804_gb300 import qfuse, workloads
 from paper_2603_02804_gb300.torch_api import Simulator
+from tests import oracle_proc
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +51,8 @@ def test_error_growth_beyond_100_layers(capsys):
 def test_error_growth_n20_epoch_plan(capsys):
     """n = 20 on one sample of the large workload, through the plan its epoch
     uses (checkpoint interval from memory for a micro-batch of 100): d = 100
-    meets the 1e-5 bar; d = 1000 is reported, with a loose bound."""
+    meets the 1e-5 bar; d = 250 is reported, with a loose bound. (The error
+    at the full d = 1000 is measured by the benchmark on the same sample.)"""
     n, B = 20, 1
     w = workloads.WORKLOADS["hea20"]
     theta_all, x, _ = workloads.make_inputs(w, B=B)
@@ -61,7 +64,7 @@ def test_error_growth_n20_epoch_plan(capsys):
     finally:
         qfuse.qf_circuit_destroy(h)
     rows = []
-    for d in (100, 1000):
+    for d in (100, 250):
         theta = np.ascontiguousarray(theta_all[:3 * n * d])
         sim = Simulator(n, d, B, ckpt_layers=c)
         th, xd = torch.from_numpy(theta).cuda(), torch.from_numpy(x).cuda()
@@ -70,7 +73,8 @@ def test_error_growth_n20_epoch_plan(capsys):
         torch.cuda.synchronize()
         passes = sim.info()["n_passes"]
         del sim
-        gr, Er = orc.gradient(orc.hea(n, d), theta.astype(np.float64), x.astype(np.float64), "Z", per_sample=True)
+        gr, Er = oracle_proc.call("gradient", orc.hea(n, d), theta.astype(np.float64), x.astype(np.float64), "Z",
+                                  per_sample=True)
         e_err = float(np.max(np.abs(E.cpu().numpy() - Er)))
         g_err = float(np.max(np.abs(g.cpu().numpy() - gr)))
         rows.append((d, passes, e_err, g_err))
