@@ -1,8 +1,9 @@
 """Autotuner for the fused path's plan options.
 
-What it tunes, per (GPU, SM count, n, depth bucket, batch bucket, launch
-kind), by timing qf_train_step (or the persistent batch step) on synthetic
-inputs of the circuit's shape:
+What it tunes, per (GPU, SM count, launch kind, n, depth bucket, batch
+bucket), by timing qf_train_step (or the persistent batch step) on synthetic
+inputs of that shape (depth and batch rounded up to powers of two, capped at
+64; persistent batches are timed at 16 samples):
 
 - tile width K (qubits held in shared memory per pass; fusion width of the
   pass, Sec. 3.2): 7..12 for circuits wider than one tile. A register group
@@ -48,7 +49,13 @@ def device_info() -> tuple[str, int]:
 
 def key(n: int, d: int, B: int, kind: str = "single", dev: tuple[str, int] | None = None) -> str:
     name, sms = dev if dev is not None else device_info()
-    return f"{name}|sms={sms}|{kind}|n={n}|d~{bucket(d)}|B~{bucket(B)}"
+    return f"{name}|sms={sms}|{kind}|n={n}|d~{d}|B~{B}"
+
+
+# Persistent batches run many circuits' samples side by side, so the batch of
+# one circuit does not change how its passes fill the GPU: batch-kind shapes
+# are timed at this batch.
+BATCH_KIND_SAMPLES = 16
 
 
 def _synthetic(n, d, B, seed=0):
@@ -125,10 +132,16 @@ class Autotuner:
                 log[tag] = float("inf")
         return log[tag]
 
+    def shape(self, n: int, d: int, B: int) -> tuple[int, int, int]:
+        """The shape timed for a circuit: depth and batch rounded up to powers
+        of two and capped (a batch-kind tuner times every batch at 16)."""
+        bb = BATCH_KIND_SAMPLES if self.kind == "batch" else min(bucket(B), self.max_batch)
+        return n, min(bucket(d), self.max_depth), bb
+
     def search(self, n: int, d: int, B: int) -> tuple[dict, dict]:
-        """Coordinate descent over width, rule and instance on the bucketed
-        shape (depth and batch capped to keep tuning short)."""
-        dd, bb = min(bucket(d), self.max_depth), min(bucket(B), self.max_batch)
+        """Coordinate descent over width, rule and instance on the timed
+        shape."""
+        _, dd, bb = self.shape(n, d, B)
         log: dict[str, float] = {}
         best = dict(DEFAULT)
         best_t = self._time(n, dd, bb, best, log)
@@ -156,7 +169,7 @@ class Autotuner:
         """Plan options for a circuit (the defaults when n <= 12)."""
         if n <= 12:
             return dict(DEFAULT)
-        k = key(n, d, B, self.kind, self.dev)
+        k = key(*self.shape(n, d, B), self.kind, self.dev)
         if k not in self.cache:
             best, log = self.search(n, d, B)
             self.timings[k] = log

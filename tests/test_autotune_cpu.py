@@ -24,11 +24,15 @@ def model(best_K, best_rule, best_ctas):
     return timer, calls
 
 
-def test_bucket_and_key():
+def test_bucket_shape_and_key():
     assert [at.bucket(v) for v in (1, 2, 3, 4, 5, 64, 65, 200)] == [1, 2, 4, 4, 8, 64, 128, 256]
-    k = at.key(17, 150, 40, "batch", DEV)
-    assert k == "NVIDIA GB300|sms=152|batch|n=17|d~256|B~64"
-    assert at.key(17, 150, 40, "batch", ("NVIDIA GB300", 148)) != k
+    single = at.Autotuner(path=None, dev=DEV)
+    batch = at.Autotuner(path=None, kind="batch", dev=DEV)
+    assert single.shape(17, 150, 40) == (17, 64, 64) and single.shape(17, 20, 5) == (17, 32, 8)
+    assert batch.shape(17, 150, 40) == (17, 64, 16) and batch.shape(17, 20, 5) == (17, 32, 16)
+    k = at.key(*batch.shape(17, 150, 40), "batch", DEV)
+    assert k == "NVIDIA GB300|sms=152|batch|n=17|d~64|B~16"
+    assert at.key(*batch.shape(17, 150, 40), "batch", ("NVIDIA GB300", 148)) != k
 
 
 def test_small_circuits_keep_defaults_without_timing():
@@ -57,7 +61,9 @@ def test_batch_kind_does_not_tune_the_forward_instance():
     timer, calls = model(10, 1, 3)
     t = at.Autotuner(path=None, kind="batch", timer=timer, dev=DEV)
     cfg = t.choose(14, 30, 5)
-    assert cfg["fwd_ctas"] == 0 and all(c[4] == "batch" for c in calls)
+    assert cfg["fwd_ctas"] == 0 and all(c[4] == "batch" and c[2] == 16 for c in calls)
+    assert len(calls) == 8
+    t.choose(14, 17, 60)  # the same timed shape: from the cache
     assert len(calls) == 8
 
 
