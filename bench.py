@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--micro-batch", type=int, default=0, help="hea20: samples per step (default 100)")
     ap.add_argument("--ckpt", type=int, default=0, help="hea20: checkpoint interval (default: from memory)")
     ap.add_argument("--pergate-samples", type=int, default=32, help="hea20: samples of the per-gate comparator step")
+    ap.add_argument("--tile-bits", type=int, default=0, help="plan option tile_bits (0: library default)")
+    ap.add_argument("--catch-up", type=int, default=0, choices=[0, 1, 2], help="plan option catch_up")
+    ap.add_argument("--fwd-ctas", type=int, default=0, choices=[0, 2, 3], help="plan option fwd_ctas")
+    ap.add_argument("--autotune", action="store_true",
+                    help="hea20: choose tile width, catch-up rule and forward instance with the autotuner first")
     ap.add_argument("--tc", action="store_true", help="forward rounds on the tensor cores (3xTF32)")
     ap.add_argument("--ckpt-mode", type=int, default=0, choices=[0, 1])
     ap.add_argument("--mem-save", action="store_true", help="checkpoint mode 1 with bfloat16 pass outputs")
@@ -392,7 +397,19 @@ def run_large(args, w):
     if solo and not args.no_error_check:
         job = OracleJob(w, theta_np, x_np[0], max(1, ncores - 4))
 
-    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
+    tuned = None
+    tune_s = 0.0
+    knobs = dict(tile_bits=args.tile_bits, catch_up=args.catch_up, fwd_ctas=args.fwd_ctas)
+    if args.autotune:
+        from paper_2603_02804_gb300.autotune import Autotuner
+        t_start = time.perf_counter()
+        tuner = Autotuner(path=os.environ.get("QF_AUTOTUNE_CACHE"))
+        knobs = tuner.choose(w.n, w.d, mb)
+        tune_s = time.perf_counter() - t_start
+        tuned = {"choice": knobs, "timed_shape": list(tuner.shape(w.n, w.d, mb)), "seconds": tune_s,
+                 "timings_ms": next(iter(tuner.timings.values()), None)}
+        torch.cuda.empty_cache()
+    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc, **knobs)
     free, _ = torch.cuda.mem_get_info()
     h = qfuse.qf_hea_create(w.n, w.d)
     if args.ckpt:
@@ -533,13 +550,13 @@ def run_large(args, w):
         variants = {}
         for name, kw in (("tc_path", dict(tc_path=True)), ("ckpt_mode_1", dict(ckpt_mode=1)),
                          ("ckpt_mode_1_mem_save", dict(ckpt_mode=1, mem_save=True))):
-            if kw == {k: v for k, v in opts.items() if v}:
+            if all(opts.get(k) == v for k, v in kw.items()):
                 continue
             free, _ = torch.cuda.mem_get_info()
             h = qfuse.qf_hea_create(w.n, w.d)
-            cv, _ = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True, **kw)
+            cv, _ = qfuse.qf_plan_fit(h, mb, int(0.8 * free), host_only=True, **kw, **knobs)
             qfuse.qf_circuit_destroy(h)
-            vs = Simulator(w.n, w.d, mb, ckpt_layers=cv, obs=w.obs, **kw)
+            vs = Simulator(w.n, w.d, mb, ckpt_layers=cv, obs=w.obs, **kw, **knobs)
             vo = vs.device_outputs()
             step(vs, 0, vo)
             torch.cuda.synchronize()
@@ -600,6 +617,7 @@ def run_large(args, w):
                        "micro_batch": mb, "micro_batches_per_epoch": n_mb, "ckpt_layers": c,
                        "ckpt_mode": args.ckpt_mode, "mem_save": bool(args.mem_save), "tc_path": bool(args.tc),
                        "passes_per_direction": passes, "tile_bits": info["tile_bits"], "workspace_gb": ws_gb,
+                       "catch_up": info["catch_up"], "fwd_ctas": info["fwd_ctas"], "autotune": tuned,
                        "parallelism": f"dp{world}",
                        "l2": f"inputs larger than L2 (state of a micro-batch {amps * 8 / 1e6:.0f} MB)",
                        "fwd_ms_per_step": prof["fwd_ms"] / K_p, "bwd_ms_per_step": prof["bwd_ms"] / K_p},
@@ -894,7 +912,8 @@ def run_small(args, w):
     x = torch.from_numpy(x_np).to(dev)
     y = torch.from_numpy(y_np).to(dev) if y_np is not None else None
     ckpt = w.ckpt_layers or 0
-    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc)
+    opts = dict(ckpt_mode=args.ckpt_mode, mem_save=args.mem_save, tc_path=args.tc, tile_bits=args.tile_bits,
+                catch_up=args.catch_up, fwd_ctas=args.fwd_ctas)
     if c128:
         opts["precision"] = "complex128"
     sim = Simulator(w.n, w.d, w.B, ckpt_layers=ckpt, obs=w.obs, **opts)
@@ -1028,7 +1047,7 @@ def run_small(args, w):
         for name, kw in (("tc_path", dict(tc_path=True)), ("ckpt_mode_1", dict(ckpt_mode=1)),
                          ("ckpt_mode_1_mem_save", dict(ckpt_mode=1, mem_save=True)),
                          ("complex128", dict(precision="complex128"))):
-            if kw == opts:
+            if all(opts.get(k) == v for k, v in kw.items()):
                 continue
             v128 = kw.get("precision") == "complex128"
             inp = inp64 if v128 else None
