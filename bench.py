@@ -142,6 +142,34 @@ def per_gate_model_flops(n, d, B):
     return 3 * n * d * amps * 6, 3 * n * d * amps * 16
 
 
+def adjoint_bytes_per_amp(handle):
+    """Algorithmic HBM bytes per amplitude of the plan's adjoint passes, from
+    the exported program: psi and lambda read where a pass loads them (a seed
+    pass makes lambda from psi), psi and lambda written where a later pass
+    needs them, and 8 bytes per re-anchor from a stored state in the middle of
+    a pass. Returns (mean per launch, launches)."""
+    from paper_2603_02804_gb300 import qfuse
+    w = [int(v) for v in qfuse.qf_plan_export(handle, 1)]
+    n_pass = w[2]
+    i = 3
+    heads = []
+    for _ in range(n_pass):
+        heads.append(w[i:i + 11])
+        i += 11 + 32
+    n_ops = w[i]
+    codes = [w[i + 1 + 2 * k] & 15 for k in range(n_ops)]
+    BUF_NONE, LAM_SEED = -3, -1
+    total = 0
+    for op_begin, op_end, psi_src, psi_dst, lam_src, lam_dst, *_ in heads:
+        b = 8                                   # psi in
+        b += 8 if lam_src != LAM_SEED else 0    # lambda in
+        b += 8 if psi_dst != BUF_NONE else 0    # psi out
+        b += 8 if lam_dst != BUF_NONE else 0    # lambda out
+        b += 8 * sum(1 for c in codes[op_begin:op_end] if c == 7)  # re-anchors
+        total += b
+    return total / max(n_pass, 1), n_pass
+
+
 def measured_traffic(key, amps):
     """DRAM bytes (read + write) per launch of the dominant kernel, scaled to
     `amps` amplitudes per launch from an ncu capture of the current sources;
@@ -472,10 +500,9 @@ def run_large(args, w):
     fp32_peak, peak_what = fp32_peak_tflops(peaks)
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     amps = mb * (1 << w.n)
-    # algorithmic bytes of one adjoint launch: psi and lambda read and written
-    # (32 B/amp), plus the re-anchor reads of the stored checkpoints (8 B/amp
-    # each; n_ckpt - 1 of them over the whole adjoint), averaged per launch
-    bwd_bytes = amps * (32 * passes + 8 * max(info["n_ckpt"] - 1, 0)) / passes
+    # algorithmic bytes of one adjoint launch, averaged over the plan's passes
+    bpa, _ = adjoint_bytes_per_amp(sim.handle)
+    bwd_bytes = amps * bpa
     achieved = bwd_fl / passes / (bwd_launch_ms / 1e3) / 1e12
     traffic, traffic_note = measured_traffic(w.name, amps) if not (args.tc or args.ckpt_mode) else (None, "variant")
     roofline = {
@@ -491,7 +518,7 @@ def run_large(args, w):
                                          "as a per-gate program counts them"},
         "hbm": {"achieved_gbs": bwd_bytes / (bwd_launch_ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
                 "frac": bwd_bytes / (bwd_launch_ms / 1e3) / 1e9 / hbm_gbs, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": bwd_bytes},
+                "algorithmic_bytes_per_launch": bwd_bytes, "algorithmic_bytes_per_amp": bpa},
         "fwd_kernel": {"achieved": fwd_fl / passes / (fwd_launch_ms / 1e3) / 1e12,
                        "hbm_gbs": amps * 16 / (fwd_launch_ms / 1e3) / 1e9},
         "timing": f"CUDA events on the launching stream around every pass launch of {K_p} steps run after the "

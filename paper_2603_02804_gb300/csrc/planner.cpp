@@ -881,6 +881,24 @@ FusedPlan plan_fused_with(const Circuit& c_in, const PlanRequest& req, bool stri
     passes.push_back(std::move(pr));
     if (M == 0) break;
   }
+  // A checkpoint whose boundary falls inside a pass of a multi-pass plan moves
+  // to that pass's output: the forward then writes no extra copy, and the
+  // adjoint pass that undoes the next forward pass starts from the stored
+  // state (re-anchored for free) instead of reloading it in the middle of a
+  // pass. The last pass's output is psi_M, and a single-pass plan has no
+  // later boundary: there the checkpoints stay after their steps.
+  if (P.n_eff > K)
+    for (size_t pi = 0; pi + 1 < passes.size(); ++pi) {
+      std::vector<int>& ck = passes[pi].ckpt_after_step;
+      const int ns = (int)ck.size();
+      if (ns == 0 || ck[ns - 1] >= 0) continue;
+      for (int si = ns - 2; si >= 0; --si)
+        if (ck[si] >= 0) {
+          ck[ns - 1] = ck[si];
+          ck[si] = -1;
+          break;
+        }
+    }
   const int final_slot = n_ckpt_slots;
   P.n_ckpt = n_ckpt_slots + 1;
 

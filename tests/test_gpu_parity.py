@@ -13,6 +13,7 @@ from oracle import oracle as orc
 from paper_2603_02804_gb300 import build as qbuild
 from paper_2603_02804_gb300 import qfuse, workloads
 from paper_2603_02804_gb300.torch_api import HEA, QFuseFn, Simulator
+from tests import oracle_proc
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -125,18 +126,23 @@ def test_train_step_host_buffers():
     assert np.max(np.abs(g.numpy() - gr)) < TOL
 
 
-def test_hea16_full_batch_sampled_rows():
+def test_hea16_full_batch():
     """n=16, d=100, B=128, checkpoint every 10 layers (multi-pass tiles):
-    per-sample gradients of 4 sampled rows against the oracle."""
+    E and the per-sample gradients of all 128 samples against the oracle,
+    and the MSE train step's whole-batch gradient against the oracle's."""
     w = workloads.WORKLOADS["hea16"]
-    theta, x, _ = workloads.make_inputs(w)
+    theta, x, y = workloads.make_inputs(w)
     E, g, sim = gpu_run(w.n, w.d, theta, x, ckpt=w.ckpt_layers)
     assert sim.info()["n_passes"] > 1
-    rows = [0, 37, 91, 127]
-    gr, Er = orc.gradient(orc.hea(w.n, w.d), f64(theta), f64(x[rows]), "Z", per_sample=True)
-    assert np.max(np.abs(E[rows] - Er)) < TOL
-    assert np.max(np.abs(g[rows] - gr)) < TOL
-    assert np.all(np.abs(E) <= 1 + 1e-6)
+    gr, Er = oracle_proc.call("gradient", orc.hea(w.n, w.d), f64(theta), f64(x), "Z", per_sample=True)
+    assert np.max(np.abs(E - Er)) < TOL
+    assert np.max(np.abs(g - gr)) < TOL
+    # the MSE loss's gradient is the dL/dE-weighted sum of the rows
+    loss, E2, g2 = sim.train_step(dev(theta), dev(x), dev(y), loss="mse")
+    torch.cuda.synchronize()
+    dLdE = orc.mse_dLdE(Er, y)
+    assert abs(loss.item() - orc.mse_loss(Er, y)) < TOL
+    assert np.max(np.abs(g2.cpu().numpy() - dLdE @ gr)) < TOL
 
 
 def _oracle_loss(args):
