@@ -229,8 +229,9 @@ __device__ __forceinline__ void rx_fwd(float2 (&r)[16], float4 yq, uint32_t a) {
 
 // The rotation of a forward item on register bit R (RY, or RX where rx; rx is
 // uniform over the CTA): applying is the un-apply rotation the other way,
-// (t, s) -> (-t, -s). A pending Z_R turns the rotation by w into one by -w;
-// the wrap parity goes to the pending constant sign.
+// (t, s) -> (-t, -s). A pending Z_R turns the rotation by w into one by -w.
+// The rotation by w is u(phi) up to the sign (-1)^k of its wrap; prep folds
+// the round's signs into the round's diagonal (a global sign of the state).
 template <int R, bool RX>
 __device__ __forceinline__ void rot_fwd(float2 (&r)[16], float4 yq, uint32_t a, uint32_t& D, bool rx) {
   if (RX && rx) {
@@ -251,7 +252,6 @@ __device__ __forceinline__ void rot_fwd(float2 (&r)[16], float4 yq, uint32_t a, 
       r[j] = p0; r[j1] = p1;
     }
   }
-  D ^= ((uint32_t)__float_as_int(yq.z) & 1u) << 4;
 }
 
 // v *= (c + i s)
@@ -357,11 +357,12 @@ __device__ __forceinline__ float bwd_shear(float2 (&p)[16], float2 (&l)[16], con
   return acc;
 }
 
-// The rotation of an adjoint item on register bit R (shear parameters (t, s,
-// wrap parity); RX where rx, uniform over the CTA, else RY), un-applied after
-// the round's diagonal; gy: its Im<lambda|P|psi>. With a pending Z_R the
-// rotation un-applies as the one by +w (t, s negated) and gy changes sign.
-// The wrap parity (u(phi) = -u(w) for odd k) goes to the pending constant sign.
+// The rotation of an adjoint item on register bit R (shear parameters (t, s);
+// RX where rx, uniform over the CTA, else RY), un-applied after the round's
+// diagonal; gy: its Im<lambda|P|psi>. With a pending Z_R the rotation
+// un-applies as the one by +w (t, s negated) and gy changes sign. The wrap
+// sign (u(phi) = -u(w) for odd k) is folded into the round's diagonal, which
+// multiplies psi and lambda alike (their gradient terms do not change).
 template <int R, bool RX = false>
 __device__ __forceinline__ void rot_bwd(float2 (&p)[16], float2 (&l)[16], float4 yq, uint32_t a, uint32_t& D,
                                         float& gy, bool rx = false) {
@@ -370,7 +371,6 @@ __device__ __forceinline__ void rot_bwd(float2 (&p)[16], float2 (&l)[16], float4
   const float s = __int_as_float(__float_as_int(yq.y) ^ f);
   const float g = RX && rx ? bwd_shear<R, G_RX>(p, l, t, s) : bwd_shear<R, G_RY>(p, l, t, s);
   gy = __int_as_float(__float_as_int(g) ^ f);
-  D ^= ((uint32_t)__float_as_int(yq.z) & 1u) << 4;
 }
 
 // Reduce 8 per-thread values over `lanes` lanes (8, 16 or 32; whole-warp
@@ -1337,9 +1337,13 @@ __device__ __forceinline__ double round_term_angle(const PrepArgs& a, const Roun
 // tan(w/4) = sin(w/2) / (1 + cos(w/2)) (the half-angle identity; the
 // denominator lies in [1, 2] for |w/2| <= pi/2), so one float64 sincos gives
 // both.
+__device__ __forceinline__ double wrap_count(double phi) {
+  return rint(phi * (1.0 / 6.283185307179586476925286766559));
+}
+
 __device__ void shear_params(double phi, double& tq, double& sh, int& parity) {
   const double two_pi = 6.283185307179586476925286766559;
-  const double k = rint(phi * (1.0 / two_pi));
+  const double k = wrap_count(phi);
   const double w = phi - two_pi * k;
   double c;
   sincos_prep(0.5 * w, &sh, &c);
@@ -1382,11 +1386,12 @@ __device__ void diag_phase_pair(const double (&phi)[4], uint32_t bbits, int m, b
   f1 = __popc(bbits & (uint32_t)mc & (uint32_t)(mc >> 1)) & 1;
 }
 
-__device__ void diag_phases(const double (&phi)[4], uint32_t bbits, int m, bool apply, float2* ph) {
+// neg: the round's items' wrap signs multiply to -1; the phases carry it.
+__device__ void diag_phases(const double (&phi)[4], uint32_t bbits, int m, bool apply, bool neg, float2* ph) {
   double cd, sd;
   bool f0, f1;
   diag_phase_pair(phi, bbits, m, apply, cd, sd, f0, f1);
-  const float c = (float)cd, s = (float)sd;
+  const float c = neg ? -(float)cd : (float)cd, s = neg ? -(float)sd : (float)sd;
   ph[m] = f0 ? make_float2(-c, -s) : make_float2(c, s);
   ph[15 - m] = f1 ? make_float2(-c, s) : make_float2(c, -s);
 }
@@ -1472,8 +1477,18 @@ __device__ void prep_one(const PrepArgs& a, int64_t i) {
   } else {
     term_angles4(a, tz, phi);
   }
-  if (f64) diag_phases64(phi, bbits, e - 4, fwd, (fwd ? a.rpf64 : a.rpb64)[r].ph);
-  else diag_phases(phi, bbits, e - 4, fwd, reinterpret_cast<float2*>((fwd ? a.rpf : a.rpb) + r * kRoundPar + 4));
+  if (f64) {
+    diag_phases64(phi, bbits, e - 4, fwd, (fwd ? a.rpf64 : a.rpb64)[r].ph);
+  } else {
+    // the product of the 4 rotations' wrap signs (-1)^k, the same k as their shears
+    long long k = 0;
+    for (int q = 0; q < 4; ++q) {
+      const double phr = rt ? round_term_angle(a, rt[q]) : (ty[q] >= 0 ? term_angle(a, ty[q]) : 0.0);
+      k += (long long)wrap_count(phr);
+    }
+    diag_phases(phi, bbits, e - 4, fwd, (k & 1) != 0,
+                reinterpret_cast<float2*>((fwd ? a.rpf : a.rpb) + r * kRoundPar + 4));
+  }
 }
 
 // E_b = sum over the tiles of sample b, in tile order (deterministic).

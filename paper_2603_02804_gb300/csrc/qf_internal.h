@@ -59,7 +59,9 @@ constexpr int kMaxStepRounds = 4;   // 8 gradient values per round
 // shear parameters (tan(w/4), sin(w/2), wrap parity) of the 4 items'
 // rotations; [4, 12) the round's diagonal, i.e. the 4 RZ runs (and the CZ
 // links between register bits) merged into one phase per register index j:
-// float4 4 + m holds (cos a_j, sin a_j) for j = 2m and 2m + 1. Prep fills
+// float4 4 + m holds (cos a_j, sin a_j) for j = 2m and 2m + 1, times the
+// product of the 4 rotations' wrap signs (the kernels do not read the
+// parities themselves). Prep fills
 // them as kRoundPar work items per round; complex128 programs hold the same
 // in float64 (RoundPar64).
 constexpr int kRoundPar = 12;
