@@ -180,12 +180,19 @@ __device__ __forceinline__ void link_terms(uint32_t L, uint32_t gb, int n, uint3
   u = (((t1 << 1) | (t1 >> (n - 1))) & nmask) ^ t2;
 }
 
-__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t gb, const uint32_t (&p)[4], int n, uint32_t& D) {
-  uint32_t t2, u;
-  link_terms(L, gb, n, t2, u);
-  const uint32_t A = ((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) |
-                     (((u >> p[3]) & 1u) << 3);
-  D ^= A | ((__popc(t2 & gb) & 1u) << 4);
+// The pending-sign update of one round's links, from per-step constants of
+// the thread (rgb = gb rotated right by one qubit, lgb = left, g12 = gb &
+// rgb): as rotation distributes over &, u = rotl(L) & lgb ^ L & rgb (the
+// link_terms u), and the constant part is |L & g12|. When the register bits
+// sit on consecutive qubits (contig), A is one shift of u.
+__device__ __forceinline__ void chain_pending(uint32_t L, uint32_t rgb, uint32_t lgb, uint32_t g12, int n,
+                                                const uint32_t (&p)[4], bool contig, uint32_t& D) {
+  const uint32_t nmask = n >= 32 ? ~0u : ((1u << n) - 1u);
+  const uint32_t u = ((((L << 1) | (L >> (n - 1))) & nmask) & lgb) ^ (L & rgb);
+  const uint32_t A = contig ? (u >> p[0]) & 15u
+                            : ((u >> p[0]) & 1u) | (((u >> p[1]) & 1u) << 1) | (((u >> p[2]) & 1u) << 2) |
+                                  (((u >> p[3]) & 1u) << 3);
+  D ^= A | ((__popc(L & g12) & 1u) << 4);
 }
 
 // Multiply the registers by D (end of a step).
@@ -875,6 +882,12 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         r[j] = tp[pb ^ reg_off(j, so)];
         if (BWD) l[j] = tl[pb ^ reg_off(j, so)];
       }
+      const int nq = a.n_eff;
+      const uint32_t nmask = nq >= 32 ? ~0u : ((1u << nq) - 1u);
+      const uint32_t rgb = ((gb >> 1) | ((gb & 1u) << (nq - 1))) & nmask;
+      const uint32_t lgb = ((gb << 1) | (gb >> (nq - 1))) & nmask;
+      const uint32_t g12 = gb & rgb;
+      const bool contig = pos[1] == pos[0] + 1 && pos[2] == pos[0] + 2 && pos[3] == pos[0] + 3;
       uint32_t D = 0;
       if constexpr (TC) {
         tc_rounds(*tc, P, nr, tc->bsm + (size_t)sb * kMaxStepRounds * kTcBFloats, gb, pos, a.n_eff, r, ph, tid);
@@ -888,10 +901,10 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
           rot_fwd<2, RX>(r, P.v[k][2], (D >> 2) & 1u, D, (lk.z >> 2) & 1u);
           rot_fwd<3, RX>(r, P.v[k][3], (D >> 3) & 1u, D, (lk.z >> 3) & 1u);
           apply_diag(r, &P.v[k][4]);
-          chain_pending(lk.x, gb, pos, a.n_eff, D);
+          chain_pending(lk.x, rgb, lgb, g12, nq, pos, contig, D);
         } else {
           const uint4 lk = P.rec[k * (kBwdRoundWords / 4) + 2];  // links, bbits, rx mask
-          chain_pending(lk.x, gb, pos, a.n_eff, D);
+          chain_pending(lk.x, rgb, lgb, g12, nq, pos, contig, D);
           float v[8];
           diag_bwd(r, l, &P.v[k][4], v);
           rot_bwd<0, RX>(r, l, P.v[k][0], D & 1u, D, v[4], lk.z & 1u);
