@@ -699,13 +699,22 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       if ((h >> j) & 1) g |= 1u << s_gmap[kRegBits + j];
     s_lg[h] = g;
   }
-  // each thread's base index per register group, once per pass (read back by
-  // the same thread at every step of that group)
-  for (int g = 0; g < 4; ++g) {
-    const uint32_t gm = (1u << s_grp[g][0]) | (1u << s_grp[g][1]) | (1u << s_grp[g][2]) | (1u << s_grp[g][3]);
-    sh.base[g][tid] = pdep32(tau, ((1u << K) - 1u) & ~gm);
-  }
   __syncthreads();
+  // each thread's base index per register group, once per pass (read back by
+  // only the same thread, at every step of that group): computed while the
+  // tile loads are in flight where the pass loads its tiles
+  bool bases = false;
+  auto set_bases = [&]() {
+    for (int g = 0; g < 4; ++g) {
+      const uint32_t gm = (1u << s_grp[g][0]) | (1u << s_grp[g][1]) | (1u << s_grp[g][2]) | (1u << s_grp[g][3]);
+      sh.base[g][tid] = pdep32(tau, ((1u << K) - 1u) & ~gm);
+    }
+    bases = true;
+  };
+  // (the persistent batch kernel and the RX instances keep the bases ahead
+  // of the loads: their registers are tighter)
+  constexpr bool kBasesInLoads = LOADS == 8 && !RX && !TC;
+  if (!kBasesInLoads) set_bases();
 
   auto gidx = [&](uint32_t i) -> uint32_t { return outer | (i & 15u) | s_lg[i >> 4]; };
   auto state_ptr = [&](int32_t code) -> float2* {
@@ -797,6 +806,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
         else vp[it] = __ldcg(reinterpret_cast<const float4*>(src + g));
         if (two) vl[it] = __ldcg(reinterpret_cast<const float4*>(lsrc + g));
       }
+      if (kBasesInLoads && i0 == 0) set_bases();
 #pragma unroll
       for (int it = 0; it < LOADS; ++it) {
         const uint32_t i = 2u * ((uint32_t)(i0 + it) * Tt + tau);
@@ -805,6 +815,7 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
       }
     }
   }
+  if (!bases) set_bases();
   if (BWD && pd.lam_src == LAM_BUF && psrc == SRC_GENERATE && active) {
     const float2* src = a.lam + sbase;
 #pragma unroll
