@@ -7,8 +7,9 @@ plugin inside another framework's memory pool). They cannot call cudaMalloc
 or hand the library a workspace sized per call, so this entry point keeps its
 buffers in one fixed 32 MiB block that the library reserves per GPU. The test
 checks, through the C-ABI, that it returns what the regular workspace entry
-point (qf_train_step) returns, on two calls in a row, and that a request too
-large for the fixed block is refused with a clear error.
+point (qf_train_step) returns, on two calls in a row with another circuit's
+call between them, and what the float64 oracle returns, and that requests
+beyond the plan or the fixed block are refused with a clear error.
 """
 import numpy as np
 import pytest
@@ -83,6 +84,14 @@ def test_noalloc_step_matches_workspace_step_twice():
             assert torch.max(torch.abs(g - g_r)).item() < TOL, call
             if call == 0:
                 _tiny_noalloc_call(stream)
+        # and against the float64 oracle directly (MSE loss, its gradient)
+        from oracle import oracle as orc
+        th64, x64, y64 = (t.cpu().numpy().astype(np.float64) for t in (theta, x, y))
+        E_o = orc.expectation(orc.hea(w.n, w.d), th64, x64, "Z")
+        g_o, _ = orc.gradient(orc.hea(w.n, w.d), th64, x64, "Z", dLdE=orc.mse_dLdE(E_o, y64))
+        assert abs(loss.item() - orc.mse_loss(E_o, y64)) < TOL
+        assert np.max(np.abs(E.cpu().numpy() - E_o)) < TOL
+        assert np.max(np.abs(g.cpu().numpy() - g_o)) < TOL
     finally:
         qfuse.qf_circuit_destroy(h)
         qfuse.qf_circuit_destroy(ref_h)
