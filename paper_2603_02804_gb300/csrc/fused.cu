@@ -706,8 +706,19 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
   bool bases = false;
   auto set_bases = [&]() {
     for (int g = 0; g < 4; ++g) {
-      const uint32_t gm = (1u << s_grp[g][0]) | (1u << s_grp[g][1]) | (1u << s_grp[g][2]) | (1u << s_grp[g][3]);
-      sh.base[g][tid] = pdep32(tau, ((1u << K) - 1u) & ~gm);
+      // tau's bits scattered into the tile bits outside the group (pdep32 of
+      // tau into the complement of the group's bits): a zero inserted at each
+      // of the 4 group bits, lowest first, so that 4 steps replace K - 4
+      uint32_t m = (1u << s_grp[g][0]) | (1u << s_grp[g][1]) | (1u << s_grp[g][2]) | (1u << s_grp[g][3]);
+      uint32_t x = tau;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t low = m & (0u - m);
+        const uint32_t hi = x & ~(low - 1u);
+        x = (x ^ hi) | (hi << 1);
+        m ^= low;
+      }
+      sh.base[g][tid] = x;
     }
     bases = true;
   };
@@ -923,8 +934,15 @@ __device__ __forceinline__ void pass_cta(const PassArgs& a, const int64_t first_
           rot_bwd<2, RX>(r, l, P.v[k][2], (D >> 2) & 1u, D, v[6], (lk.z >> 2) & 1u);
           rot_bwd<3, RX>(r, l, P.v[k][3], (D >> 3) & 1u, D, v[7], (lk.z >> 3) & 1u);
           int idx;
-          const float sum = butterfly8(v, lanes, lane, idx);
-          const bool owner = (lane & ((lanes >> 3) - 1)) == 0;
+          float sum;
+          bool owner;
+          if (lanes == 32) {  // tiles of 9 qubits and more: the shuffle pattern as constants
+            sum = butterfly8(v, 32, lane, idx);
+            owner = (lane & 3) == 0;
+          } else {
+            sum = butterfly8(v, lanes, lane, idx);
+            owner = (lane & ((lanes >> 3) - 1)) == 0;
+          }
           const int32_t term =
               reinterpret_cast<const int32_t*>(&P.rec[k * (kBwdRoundWords / 4)])[idx];
           if (Tt >= 32) {
