@@ -267,13 +267,9 @@ def _oracle_sample(w, theta, x, threads, target_s):
     return orc.hea(w.n, d_s), d_s, B_s
 
 
-def cpu_baseline(w, target_s=20.0, threads=0):
-    """The float64 oracle's training step (forward, loss, adjoint gradient) on
-    the host cores, over a bounded sample of the workload (about target_s)."""
-    from oracle import oracle as orc
-    orc.build()
-    theta, x, y = workloads.make_inputs(w)
-    threads = threads or orc.max_threads()
+def _timed_oracle_step(orc, w, theta, x, y, threads, target_s):
+    """(samples/s, description, seconds) of the oracle's step on a bounded
+    sample of the workload sized to about target_s on `threads` threads."""
     c, d_s, B_s = _oracle_sample(w, theta, x, threads, target_s)
     t0 = time.perf_counter()
     _oracle_step(orc, c, w, theta[:3 * w.n * d_s], x[:B_s], None if y is None else y[:B_s], threads, w.B)
@@ -282,9 +278,26 @@ def cpu_baseline(w, target_s=20.0, threads=0):
     what = (f"{B_s} of the {w.B} samples" if d_s == w.d else
             f"1 sample over the first {d_s} of the {w.d} layers (counted as {d_s}/{w.d} of a sample; the oracle's "
             f"time is linear in the gate count)")
-    return {"value": units / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
-            "sample": f"{what} of the {w.name} workload (n={w.n}, d={w.d}), float64, OpenMP over "
-                      f"{'samples' if B_s >= threads else 'amplitudes'}", "seconds": dt}
+    what = (f"{what} of the {w.name} workload (n={w.n}, d={w.d}), float64"
+            + (f", OpenMP over {'samples' if B_s >= threads else 'amplitudes'}" if threads > 1 else ", one thread"))
+    return units / dt, what, dt
+
+
+def cpu_baseline(w, target_s=20.0, threads=0):
+    """The float64 oracle's training step (forward, loss, adjoint gradient) on
+    the host cores, over a bounded sample of the workload (about target_s),
+    and on one core over a smaller sample (about target_s / 4)."""
+    from oracle import oracle as orc
+    orc.build()
+    theta, x, y = workloads.make_inputs(w)
+    threads = threads or orc.max_threads()
+    value, what, dt = _timed_oracle_step(orc, w, theta, x, y, threads, target_s)
+    out = {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle", "sample": what, "seconds": dt}
+    if threads > 1:
+        v1, what1, dt1 = _timed_oracle_step(orc, w, theta, x, y, 1, target_s / 4)
+        out["single_thread"] = {"value": v1, "unit": "samples/s", "sample": what1, "seconds": dt1,
+                                "speedup_on_cores": value / v1}
+    return out
 
 
 def cpu_baseline_spawned(w, threads):

@@ -38,3 +38,17 @@ def test_fused_arm_refuses_without_a_gpu():
     r = run_bench("--steps", "1", "--warmup", "3", timeout=120)
     assert r.returncode != 0
     assert "GPU" in (r.stderr + r.stdout)
+
+
+def test_cpu_baseline_reports_cores_and_single_thread():
+    """The oracle baseline that the fused lines carry: its thread count, a
+    bounded sample, and the one-thread rate beside it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2603_02804_gb300 import workloads
+    r = bench.cpu_baseline(workloads.WORKLOADS["hea12"], 2.0, 2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0 and r["unit"] == "samples/s"
+    assert "of the 256 samples of the hea12 workload" in r["sample"]
+    st = r["single_thread"]
+    assert st["value"] > 0 and st["unit"] == "samples/s" and "one thread" in st["sample"]
+    assert abs(st["speedup_on_cores"] - r["value"] / st["value"]) < 1e-12
